@@ -1,0 +1,254 @@
+/*
+ * mc.h -- C-ABI of the GB300 explicit-state explorer for auto-tuning by
+ * model checking (Garanina, Staroletov, Gorlatch: "Auto-Tuning
+ * High-Performance Programs Using Model Checking in Promela").
+ *
+ * The library explores, on one GPU, the transition system of an OpenCL
+ * kernel launch (Section 4, Step 1, processes `main`, `host`, `device`,
+ * `unit`, `pex`, `clock`, Listings 3-9) with its scheduling semantics kept
+ * and the per-processing-element ticking folded into a cost table:
+ *
+ *   state  (i, j, n_0..n_{P-1}): WG index i and TS index j chosen by the
+ *          nondeterministic `select` of `main` (Listing 3), and n_c, the
+ *          work-groups compute unit c has taken (`host`/`device`,
+ *          Listings 4-5);
+ *   clock  clk_c = n_c * t_c with t_c = cost[i][j] * speed[c] -- the time
+ *          the unit has worked; the model time of a state is max_c clk_c
+ *          (`clock`, Listing 9);
+ *   FIN    a state whose N_ij work-groups are all dispatched (Listing 4).
+ *
+ * Dispatch rules: MC_FREE lets any unit take the next work-group (every
+ * interleaving); MC_GREEDY lets only the units whose clock is minimal take it
+ * (the unit that reported `done` first is re-dispatched, Listing 5), ties in
+ * every order.
+ *
+ * Queries follow the counterexample method (Section 2, Section 4 Steps 2-4):
+ * mc_check decides the over-time property  G(FIN -> time > T)  and returns a
+ * counterexample trace when it fails; mc_min_time finds the minimal T for
+ * which a counterexample exists and the (WG, TS) of that counterexample.
+ *
+ * Conventions
+ *   - Every function returns MC_OK (0) or a negative MC_ERR_* code; nothing
+ *     throws across the ABI.  mc_strerror() names the code.
+ *   - All pointers in mc_model_desc are HOST pointers owned by the caller;
+ *     mc_model_create copies them.  The library owns the model, its device
+ *     buffers and every mc_trace it returns.
+ *   - A model is not thread-safe.  Queries run on the model's CUDA stream
+ *     (default: the legacy default stream; see mc_set_stream) and return
+ *     after that stream has finished the query's work.
+ *   - Device memory comes from the allocator set by mc_set_allocator
+ *     (default: cudaMalloc/cudaFree), allocated on the first query or by
+ *     mc_reserve, and released by mc_model_destroy.
+ *   - There is no CPU fallback: without a usable CUDA device, queries return
+ *     MC_ERR_CUDA.
+ */
+#ifndef MC_H
+#define MC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ error codes */
+#define MC_OK 0
+#define MC_ERR_INVAL (-1)      /* bad argument or model description         */
+#define MC_ERR_NOMEM (-2)      /* device or host allocation failed          */
+#define MC_ERR_TABLE_FULL (-3) /* visited-set probe limit reached           */
+#define MC_ERR_FRONTIER (-4)   /* frontier log capacity exceeded            */
+#define MC_ERR_TIMEOUT (-5)    /* a device-side wait exceeded its limit     */
+#define MC_ERR_CUDA (-6)       /* CUDA runtime error (see mc_last_error)    */
+#define MC_ERR_OVERFLOW (-7)   /* key wider than 128 bits, clock >= 2^40,
+                                  a level wider than 2^32, or a, b > 4095   */
+
+typedef enum { MC_FREE = 0, MC_GREEDY = 1 } mc_rule;
+
+/* How mc_min_time searches for T_min (Section 2, Fig. 1; Section 4 Step 3). */
+typedef enum {
+  MC_SEARCH_SINGLE = 0, /* one exploration, min-reduction over terminal times,
+                           then the certificate checks at T_min-1 and T_min  */
+  MC_SEARCH_LOWER = 1,  /* check(T), then T := counterexample time - 1, until
+                           the property holds                                */
+  MC_SEARCH_BISECT = 2  /* bisection between 0 and T_ini (Fig. 1)            */
+} mc_search;
+
+typedef struct mc_model mc_model;
+typedef struct mc_trace mc_trace;
+
+/* Model description (Section 4, Step 1).  All arrays are host memory owned
+ * by the caller and copied by mc_model_create.  Row-major [i][j] arrays are
+ * indexed by i < n_wg (work-group size index) and j < n_ts (tile size index). */
+typedef struct {
+  uint32_t n_wg;                /* a = |D_WG|, 1..4095                       */
+  uint32_t n_ts;                /* b = |D_TS|, 1..4095                       */
+  uint32_t P;                   /* compute units, 1..16                      */
+  const uint32_t* wg_values;    /* [a] WG values, echoed in results; NULL ok */
+  const uint32_t* ts_values;    /* [b] TS values, echoed in results; NULL ok */
+  const uint32_t* n_workgroups; /* [a*b] N_ij >= 1 work-groups               */
+  const uint32_t* cost;         /* [a*b] time of one work-group, >= 1        */
+  const uint32_t* speed;        /* [P] speed factor per unit, >= 1; NULL = 1 */
+  uint32_t rule;                /* mc_rule                                   */
+  uint32_t key_bits;            /* packed state width: 0 = auto (64 when the
+                                   state fits in 64 bits, else 128), 64, 128 */
+} mc_model_desc;
+
+/* Query options.  Start from mc_options_default(). */
+typedef struct {
+  uint32_t prune;               /* 1: drop successors whose clock exceeds T
+                                   (they cannot reach a violating terminal)  */
+  uint32_t early_exit;          /* 1: mc_check stops after the first BFS level
+                                   that holds a violating terminal           */
+  uint32_t search;              /* mc_search used by mc_min_time             */
+  uint32_t refine;              /* SINGLE: also run check(T_min - 1)         */
+  uint64_t sim_seed;            /* seed of the T_ini simulation              */
+  uint32_t sim_walks;           /* random runs taken for T_ini (>= 1)        */
+  uint32_t load_factor_pct;     /* visited-set load-factor cap, 10..90       */
+  uint32_t table_log2;          /* 0: size the visited set from the bound;
+                                   else 2^table_log2 slots                   */
+  uint32_t threads_per_block;   /* 0: 256; else 64..1024, multiple of 32     */
+  uint32_t blocks_per_sm;       /* 0: occupancy maximum                      */
+  uint32_t max_probes;          /* 0: whole table; else bucket probe limit   */
+  uint64_t log_capacity;        /* 0: closed-form bound; else states kept in
+                                   the frontier log (MC_ERR_FRONTIER beyond) */
+  uint64_t barrier_timeout_ns;  /* 0: 60 s.  Limit of each device-wide wait  */
+  uint32_t debug_barrier_extra; /* test hook: >0 makes every device-wide wait
+                                   expect that many extra arrivals, so it
+                                   times out and the query returns
+                                   MC_ERR_TIMEOUT.  Keep 0.                 */
+  uint32_t reserved[7];
+} mc_options;
+
+/* Result of mc_check (Section 4, Step 2: Phi = G(FIN -> time > T)). */
+typedef struct {
+  uint32_t holds;        /* 1: every kept terminal has time > T            */
+  uint32_t levels;       /* BFS levels explored (last level + 1)           */
+  uint64_t states;       /* unique states kept in those levels             */
+  uint64_t cex_time;     /* counterexample model time (holds == 0)         */
+  uint32_t cex_wg_index; /* i of the counterexample                        */
+  uint32_t cex_ts_index; /* j of the counterexample                        */
+  uint32_t cex_wg;       /* wg_values[i] (or i when wg_values was NULL)    */
+  uint32_t cex_ts;       /* ts_values[j] (or j)                            */
+  uint32_t cex_level;    /* BFS level of the counterexample terminal       */
+  uint32_t key_words;    /* 1 or 2: u64 words per packed state             */
+  uint64_t cex_key[2];   /* packed counterexample state, {lo, hi}          */
+} mc_check_result;
+
+/* Result of mc_min_time (Section 4, Steps 3 and 4). */
+typedef struct {
+  uint64_t t_min;        /* minimal model time of any terminal             */
+  uint64_t t_ini;        /* initial bound from the simulation              */
+  uint32_t wg_index;     /* configuration of the counterexample of check(T_min) */
+  uint32_t ts_index;
+  uint32_t wg;           /* wg_values[wg_index] (or the index)             */
+  uint32_t ts;           /* ts_values[ts_index] (or the index)             */
+  uint64_t states;       /* unique states summed over every exploration    */
+  uint32_t checks;       /* explorations run                               */
+  uint32_t level;        /* BFS level of the witness terminal              */
+  uint64_t witness_key[2];
+} mc_min_result;
+
+/* Packed-state layout, for decoding trace keys.  Bits from the top of the
+ * used width: [i+1 : wg_bits][j+1 : ts_bits][n_0 : n_bits]...[n_{P-1}];
+ * n_c sits at bit offset n_shift[c] = (P-1-c) * n_bits, j+1 at ts_shift,
+ * i+1 at wg_shift.  s0 (nothing selected) is the all-zero key.             */
+typedef struct {
+  uint32_t key_bits;     /* 64 or 128                                      */
+  uint32_t key_words;    /* 1 or 2                                         */
+  uint32_t used_bits;    /* wg_bits + ts_bits + P * n_bits                 */
+  uint32_t P, n_bits, ts_bits, wg_bits, ts_shift, wg_shift;
+  uint32_t max_level;    /* deepest BFS level: max N_ij + 2                */
+  uint32_t n_shift[16];
+  uint64_t table_slots;  /* visited-set slots                              */
+  uint64_t log_capacity; /* frontier-log entries                           */
+  uint64_t max_width;    /* bound on one level's width                     */
+  uint64_t state_bound;  /* bound on all reachable states (saturates)      */
+  uint64_t device_bytes; /* device memory the model needs                  */
+} mc_layout;
+
+typedef void* (*mc_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*mc_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
+/* Fill *opt with the defaults: prune 1, early_exit 1, search SINGLE,
+ * refine 1, sim_seed 2305091300, sim_walks 1, load_factor_pct 50, the rest 0. */
+void mc_options_default(mc_options* opt);
+
+/* Validate and copy the description; compute the key layout and the
+ * closed-form bounds that size the device buffers.  No device memory is
+ * touched.  opt may be NULL (defaults).  Errors: INVAL (NULL or zero sizes,
+ * P > 16, N/cost/speed of 0, unknown rule or key_bits), OVERFLOW. */
+int mc_model_create(const mc_model_desc* desc, const mc_options* opt, mc_model** out);
+
+/* Free the model, its device buffers (through the allocator that made them)
+ * and its pinned host buffers.  NULL is ignored. */
+void mc_model_destroy(mc_model* m);
+
+/* Replace the options of later queries.  Options that size buffers
+ * (load_factor_pct, table_log2, log_capacity) only act before the buffers
+ * exist.  Errors: INVAL. */
+int mc_set_options(mc_model* m, const mc_options* opt);
+
+/* CUDA stream (a cudaStream_t, NULL = legacy default stream) for every later
+ * query.  Errors: INVAL. */
+int mc_set_stream(mc_model* m, void* stream);
+
+/* Device allocator for the model's buffers; call before the first query or
+ * mc_reserve.  alloc returns NULL on failure.  Errors: INVAL (NULL function,
+ * or buffers already allocated). */
+int mc_set_allocator(mc_model* m, mc_alloc_fn alloc, mc_free_fn free_fn, void* ctx);
+
+/* Allocate the device buffers now.  Errors: NOMEM, CUDA, OVERFLOW. */
+int mc_reserve(mc_model* m);
+
+/* Key layout and buffer sizes of the model.  Errors: INVAL. */
+int mc_model_layout(const mc_model* m, mc_layout* out);
+
+/* Decide G(FIN -> time > T) (Section 4, Step 2) by level-synchronous BFS.
+ * With prune, successors whose max clock exceeds T are dropped; with
+ * early_exit, the search ends after the first level holding a terminal of
+ * time <= T.  The counterexample is, in that first level, the violating
+ * terminal with the smallest (time, key); *cex (NULL ok) receives the path
+ * s0 -> counterexample when the property fails, else NULL.  Errors: INVAL,
+ * NOMEM, TABLE_FULL, FRONTIER, TIMEOUT, CUDA. */
+int mc_check(mc_model* m, uint64_t T, mc_check_result* out, mc_trace** cex);
+
+/* Find T_min, the least T for which check(T) fails, and its configuration
+ * (Section 4, Steps 3 and 4) with the options' search mode.  T_ini comes from
+ * sim_walks random runs (Step 3's simulation).  In every mode the reported
+ * configuration and witness are the counterexample of check(T_min), so all
+ * modes agree.  *trace (NULL ok) receives the witness path.  Errors: as
+ * mc_check. */
+int mc_min_time(mc_model* m, mc_min_result* out, mc_trace** trace);
+
+/* Count every reachable state (no pruning, no early exit).  Errors: as mc_check. */
+int mc_count_states(mc_model* m, uint64_t* out);
+
+/* T_ini: the least terminal time over `walks` random runs (Section 4,
+ * Step 3).  Walk w draws splitmix64 outputs number (w << 32) + 0, 1, ...
+ * of the stream seeded with `seed`: the WG index (x % a), the TS index
+ * (x % b), then per work-group the unit among the allowed ones in index
+ * order (x % count).  Errors: INVAL, NOMEM, CUDA. */
+int mc_simulate(mc_model* m, uint64_t seed, uint32_t walks, uint64_t* t_ini);
+
+/* Per-level widths of the model's last exploration; *n receives the level
+ * count and up to cap widths are copied.  Errors: INVAL, CUDA. */
+int mc_last_widths(mc_model* m, uint64_t* out, uint32_t cap, uint32_t* n);
+
+/* Trace accessors: states s0 .. witness, each key_words u64 ({lo, hi}). */
+int mc_trace_length(const mc_trace* t);
+uint32_t mc_trace_key_words(const mc_trace* t);
+const uint64_t* mc_trace_states(const mc_trace* t);
+void mc_trace_free(mc_trace* t);
+
+/* Static name of an error code. */
+const char* mc_strerror(int code);
+
+/* Detail of the model's last MC_ERR_CUDA (a static or model-owned string). */
+const char* mc_last_error(const mc_model* m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MC_H */

@@ -1,0 +1,730 @@
+// Host side of the C-ABI declared in include/mc.h: model validation, key
+// layout, closed-form sizing of the device buffers, and the query drivers of
+// the counterexample method (Section 2; Section 4, Steps 2-4).  Every step of
+// a query runs in the kernels of mc_kernels.cu; this file only enqueues them
+// on the model's stream and reads back a few words of results.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mc.h"
+#include "mc_internal.h"
+
+using mc::Ctrl;
+using mc::ExploreArgs;
+using mc::kNone;
+using mc::Params;
+
+namespace {
+
+constexpr int kSlots = 4;  // pinned per-pass result slots
+
+struct Buf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+uint32_t bits_for(uint64_t x) {  // bits to store values 0..x
+  uint32_t b = 0;
+  while (x) {
+    ++b;
+    x >>= 1;
+  }
+  return b;
+}
+
+// C(n, k) saturating at 2^64 - 1
+uint64_t binom_sat(uint64_t n, uint64_t k) {
+  if (k > n) return 0;
+  if (k > n - k) k = n - k;
+  unsigned __int128 r = 1;
+  for (uint64_t i = 0; i < k; ++i) {
+    r = r * (n - i) / (i + 1);
+    if (r > (unsigned __int128)UINT64_MAX) return UINT64_MAX;
+  }
+  return (uint64_t)r;
+}
+
+uint64_t add_sat(uint64_t a, uint64_t b) { return a > UINT64_MAX - b ? UINT64_MAX : a + b; }
+uint64_t mul_sat(uint64_t a, uint64_t b) {
+  if (a == 0 || b == 0) return 0;
+  return a > UINT64_MAX / b ? UINT64_MAX : a * b;
+}
+
+}  // namespace
+
+struct mc_trace {
+  uint32_t words = 1;
+  std::vector<uint64_t> keys;
+};
+
+struct mc_model {
+  // description
+  uint32_t a = 0, b = 0, P = 0, rule = 0;
+  std::vector<uint32_t> wg, ts, N, cost, speed;
+  mc_options opt{};
+  // layout and bounds
+  uint32_t key_bits = 64, key_words = 1, n_bits = 0, ts_bits = 0, wg_bits = 0;
+  uint32_t ts_shift = 0, wg_shift = 0, used_bits = 0, max_level = 0, tile = 1;
+  uint64_t max_width = 0, state_bound = 0;
+  uint64_t log_cap = 0, table_slots = 0, device_bytes = 0;
+  // device state
+  bool reserved = false;
+  int device = -1;
+  int grid = 0, threads = 0;
+  cudaStream_t stream = nullptr;
+  mc_alloc_fn alloc = nullptr;
+  mc_free_fn dealloc = nullptr;
+  void* actx = nullptr;
+  std::vector<Buf> bufs;
+  uint32_t* d_params = nullptr;
+  void* d_table = nullptr;
+  void* d_log_keys = nullptr;
+  uint32_t* d_log_par = nullptr;
+  uint8_t* d_ctrl_block = nullptr;
+  Ctrl* d_ctrl = nullptr;
+  uint64_t *d_width = nullptr, *d_off = nullptr, *d_best = nullptr, *d_trace = nullptr;
+  uint64_t *d_tini = nullptr, *d_tmin = nullptr;
+  Ctrl* h_ctrl = nullptr;       // pinned [kSlots]
+  uint64_t* h_trace = nullptr;  // pinned [(max_level + 2) * 2]
+  uint64_t* h_scalar = nullptr; // pinned [4]
+  std::string last_err;
+  uint32_t last_levels = 0;
+  Params params{};
+};
+
+namespace {
+
+int cuda_fail(mc_model* m, cudaError_t e, const char* what) {
+  m->last_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return MC_ERR_CUDA;
+}
+
+#define MC_CUDA(m, call)                                  \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail((m), e_, #call); \
+  } while (0)
+
+// Makes the model's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  int target = -1;
+  explicit DeviceGuard(int dev) : target(dev) {
+    if (dev >= 0 && cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (target >= 0 && prev >= 0 && prev != target) cudaSetDevice(prev);
+  }
+};
+
+void* dev_alloc(mc_model* m, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (m->alloc) {
+    p = m->alloc(bytes, (void*)m->stream, m->actx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) m->bufs.push_back({p, bytes});
+  return p;
+}
+
+void release(mc_model* m) {
+  if (!m->bufs.empty()) {
+    DeviceGuard g(m->device);
+    cudaStreamSynchronize(m->stream);
+    for (const Buf& b : m->bufs) {
+      if (m->dealloc) m->dealloc(b.ptr, b.bytes, (void*)m->stream, m->actx);
+      else cudaFree(b.ptr);
+    }
+    m->bufs.clear();
+  }
+  if (m->h_ctrl) cudaFreeHost(m->h_ctrl);
+  if (m->h_trace) cudaFreeHost(m->h_trace);
+  if (m->h_scalar) cudaFreeHost(m->h_scalar);
+  m->h_ctrl = nullptr;
+  m->h_trace = nullptr;
+  m->h_scalar = nullptr;
+  m->reserved = false;
+}
+
+bool valid_options(const mc_options* o) {
+  if (o->load_factor_pct < 10 || o->load_factor_pct > 90) return false;
+  if (o->sim_walks == 0) return false;
+  if (o->search > MC_SEARCH_BISECT) return false;
+  if (o->threads_per_block && (o->threads_per_block < 64 || o->threads_per_block > 512 ||
+                               o->threads_per_block % 32))
+    return false;
+  if (o->table_log2 && (o->table_log2 < 3 || o->table_log2 > 40)) return false;
+  return true;
+}
+
+// sizes of the frontier log and the visited set
+int size_buffers(mc_model* m) {
+  const uint64_t n_init = 1 + (uint64_t)m->a + (uint64_t)m->a * m->b;
+  m->log_cap = m->opt.log_capacity ? std::max(m->opt.log_capacity, n_init) : m->state_bound;
+  if (m->log_cap == UINT64_MAX) return MC_ERR_NOMEM;
+  if (std::min(m->max_width, m->log_cap) >= (1ull << 32)) return MC_ERR_OVERFLOW;
+  const uint64_t per_bucket = m->key_words == 1 ? 4 : 2;
+  uint64_t slots;
+  if (m->opt.table_log2) {
+    slots = 1ull << m->opt.table_log2;
+  } else {
+    const uint64_t want = mul_sat(std::max<uint64_t>(m->max_width, 1), 100) / m->opt.load_factor_pct + 1;
+    slots = 64;
+    while (slots < want && slots < (1ull << 40)) slots <<= 1;
+    if (slots < want) return MC_ERR_NOMEM;
+  }
+  if (slots < per_bucket) slots = per_bucket;
+  m->table_slots = slots;
+  const uint64_t key_bytes = 8ull * m->key_words;
+  const uint64_t ctrl_bytes = sizeof(Ctrl) + 8ull * (m->max_level + 2) * 5 + 64;
+  uint64_t total = mul_sat(slots, key_bytes);
+  total = add_sat(total, mul_sat(m->log_cap, key_bytes + 4));
+  total = add_sat(total, ctrl_bytes + 4ull * (2ull * m->a * m->b + m->P));
+  m->device_bytes = total;
+  return MC_OK;
+}
+
+int reserve(mc_model* m) {
+  if (m->reserved) return MC_OK;
+  int rc = size_buffers(m);
+  if (rc) return rc;
+  int dev = 0;
+  MC_CUDA(m, cudaGetDevice(&dev));
+  m->device = dev;
+  int sms = 0;
+  MC_CUDA(m, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int coop = 0;
+  MC_CUDA(m, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) {
+    m->last_err = "device lacks cooperative launch";
+    return MC_ERR_CUDA;
+  }
+  m->threads = m->opt.threads_per_block ? (int)m->opt.threads_per_block : 256;
+  int bps = 0;
+  if (mc::explore_kernel_occupancy(m->key_words, m->tile, m->rule, m->threads, &bps) || bps < 1) {
+    m->last_err = "occupancy query failed";
+    cudaGetLastError();
+    return MC_ERR_CUDA;
+  }
+  if (m->opt.blocks_per_sm) bps = std::min<int>(bps, (int)m->opt.blocks_per_sm);
+  m->grid = sms * bps;
+
+  const uint64_t key_bytes = 8ull * m->key_words;
+  const size_t np = 2ull * m->a * m->b + m->P;
+  m->d_params = (uint32_t*)dev_alloc(m, np * 4);
+  m->d_table = dev_alloc(m, m->table_slots * key_bytes);
+  m->d_log_keys = dev_alloc(m, m->log_cap * key_bytes);
+  m->d_log_par = (uint32_t*)dev_alloc(m, m->log_cap * 4);
+  const size_t L2 = m->max_level + 2;
+  const size_t ctrl_bytes = 256 + 8 * L2 * 3 + 16 * L2 + 64;
+  m->d_ctrl_block = (uint8_t*)dev_alloc(m, ctrl_bytes);
+  if (!m->d_params || !m->d_table || !m->d_log_keys || !m->d_log_par || !m->d_ctrl_block) {
+    release(m);
+    return MC_ERR_NOMEM;
+  }
+  uint8_t* q = m->d_ctrl_block;
+  m->d_ctrl = (Ctrl*)q;
+  q += 256;
+  m->d_width = (uint64_t*)q;
+  q += 8 * L2;
+  m->d_off = (uint64_t*)q;
+  q += 8 * L2;
+  m->d_best = (uint64_t*)q;
+  q += 8 * L2;
+  m->d_trace = (uint64_t*)q;
+  q += 16 * L2;
+  m->d_tini = (uint64_t*)q;
+  m->d_tmin = (uint64_t*)q + 1;
+
+  if (cudaMallocHost((void**)&m->h_ctrl, sizeof(Ctrl) * kSlots) != cudaSuccess ||
+      cudaMallocHost((void**)&m->h_trace, 16 * L2) != cudaSuccess ||
+      cudaMallocHost((void**)&m->h_scalar, 32) != cudaSuccess) {
+    cudaGetLastError();
+    release(m);
+    return MC_ERR_NOMEM;
+  }
+  std::vector<uint32_t> host(np);
+  std::copy(m->N.begin(), m->N.end(), host.begin());
+  std::copy(m->cost.begin(), m->cost.end(), host.begin() + (size_t)m->a * m->b);
+  std::copy(m->speed.begin(), m->speed.end(), host.begin() + 2ull * m->a * m->b);
+  MC_CUDA(m, cudaMemcpyAsync(m->d_params, host.data(), np * 4, cudaMemcpyHostToDevice, m->stream));
+  MC_CUDA(m, cudaStreamSynchronize(m->stream));
+
+  Params& p = m->params;
+  p.a = m->a;
+  p.b = m->b;
+  p.P = m->P;
+  p.rule = m->rule;
+  p.n_bits = m->n_bits;
+  p.ts_shift = m->ts_shift;
+  p.wg_shift = m->wg_shift;
+  p.ts_mask = (1u << m->ts_bits) - 1;
+  p.wg_mask = (1u << m->wg_bits) - 1;
+  p.max_level = m->max_level;
+  p.n_mask = (1ull << m->n_bits) - 1;
+  const uint32_t nf = m->P * m->n_bits;
+  p.swar_ok = nf <= 64;
+  p.swar_mask = nf >= 64 ? ~0ull : ((1ull << nf) - 1);
+  p.swar_mul = 0;
+  for (uint32_t t = 0; t < m->P && t * m->n_bits < 64; ++t) p.swar_mul |= 1ull << (t * m->n_bits);
+  p.N = m->d_params;
+  p.cost = m->d_params + (size_t)m->a * m->b;
+  p.speed = m->d_params + 2ull * m->a * m->b;
+  m->reserved = true;
+  return MC_OK;
+}
+
+// Enqueue one exploration pass; its Ctrl header lands in h_ctrl[slot].
+int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, bool prune,
+                 bool early_exit, bool witness, uint64_t* tmin_out, int slot) {
+  ExploreArgs A{};
+  A.p = m->params;
+  A.table = m->d_table;
+  const uint64_t per_bucket = m->key_words == 1 ? 4 : 2;
+  A.bucket_mask = m->table_slots / per_bucket - 1;
+  A.table_u64 = m->table_slots * m->key_words;
+  A.max_probes = m->opt.max_probes ? m->opt.max_probes
+                                   : (uint32_t)std::min<uint64_t>(m->table_slots / per_bucket, 0xFFFFFFFFu);
+  A.prune = prune;
+  A.early_exit = early_exit;
+  A.want_witness = witness;
+  A.log_keys = m->d_log_keys;
+  A.log_par = m->d_log_par;
+  A.log_cap = m->log_cap;
+  A.ctrl = m->d_ctrl;
+  A.width = m->d_width;
+  A.off = m->d_off;
+  A.best = m->d_best;
+  A.trace = m->d_trace;
+  A.T = T;
+  A.T_src = T_src;
+  A.T_delta = delta;
+  A.tmin_out = tmin_out;
+  A.barrier_target = (uint32_t)m->grid + m->opt.debug_barrier_extra;
+  A.timeout_ns = m->opt.barrier_timeout_ns ? m->opt.barrier_timeout_ns : 60ull * 1000000000ull;
+  MC_CUDA(m, cudaMemsetAsync(m->d_ctrl, 0, sizeof(Ctrl), m->stream));
+  MC_CUDA(m, mc::launch_explore(m->key_words, m->tile, m->rule, m->grid, m->threads, A, m->stream));
+  MC_CUDA(m, cudaMemcpyAsync(&m->h_ctrl[slot], m->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost,
+                             m->stream));
+  return MC_OK;
+}
+
+int sync(mc_model* m) {
+  MC_CUDA(m, cudaStreamSynchronize(m->stream));
+  return MC_OK;
+}
+
+int pass_error(mc_model* m, int slot) {
+  const Ctrl& c = m->h_ctrl[slot];
+  m->last_levels = c.levels;
+  return c.err ? (int)c.err : MC_OK;  // the kernel stores the negative MC_ERR_* code
+}
+
+uint32_t wg_value(const mc_model* m, uint32_t i) { return m->wg.empty() ? i : m->wg[i]; }
+uint32_t ts_value(const mc_model* m, uint32_t j) { return m->ts.empty() ? j : m->ts[j]; }
+
+int make_trace(mc_model* m, const Ctrl& c, mc_trace** out) {
+  if (!out) return MC_OK;
+  *out = nullptr;
+  if (c.trace_len == 0) return MC_OK;
+  mc_trace* t = new (std::nothrow) mc_trace;
+  if (!t) return MC_ERR_NOMEM;
+  t->words = m->key_words;
+  t->keys.resize((size_t)c.trace_len * m->key_words);
+  for (uint32_t l = 0; l < c.trace_len; ++l) {
+    t->keys[(size_t)l * m->key_words] = m->h_trace[2 * l];
+    if (m->key_words == 2) t->keys[(size_t)l * 2 + 1] = m->h_trace[2 * l + 1];
+  }
+  *out = t;
+  return MC_OK;
+}
+
+void fill_check(const mc_model* m, const Ctrl& c, mc_check_result* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->holds = c.stop_level == 0;
+  out->levels = c.levels;
+  out->states = c.states;
+  out->key_words = m->key_words;
+  if (!out->holds) {
+    out->cex_time = mc::pack_time(c.wpack);
+    out->cex_wg_index = mc::pack_i(c.wpack);
+    out->cex_ts_index = mc::pack_j(c.wpack);
+    out->cex_wg = wg_value(m, out->cex_wg_index);
+    out->cex_ts = ts_value(m, out->cex_ts_index);
+    out->cex_level = c.stop_level;
+    out->cex_key[0] = c.wkey_lo;
+    out->cex_key[1] = m->key_words == 2 ? c.wkey_hi : 0;
+  }
+}
+
+int run_simulation(mc_model* m, uint64_t seed, uint32_t walks, uint64_t* dst) {
+  MC_CUDA(m, cudaMemsetAsync(dst, 0xFF, 8, m->stream));
+  MC_CUDA(m, mc::launch_simulate(m->params, seed, walks, dst, m->stream));
+  return MC_OK;
+}
+
+#define MC_TRY(x)        \
+  do {                   \
+    int rc_ = (x);       \
+    if (rc_) return rc_; \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+void mc_options_default(mc_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->prune = 1;
+  o->early_exit = 1;
+  o->search = MC_SEARCH_SINGLE;
+  o->refine = 1;
+  o->sim_seed = 2305091300ull;
+  o->sim_walks = 1;
+  o->load_factor_pct = 50;
+}
+
+int mc_model_create(const mc_model_desc* d, const mc_options* opt, mc_model** out) {
+  if (!d || !out) return MC_ERR_INVAL;
+  *out = nullptr;
+  if (d->n_wg == 0 || d->n_ts == 0 || d->P == 0 || d->P > mc::kMaxP) return MC_ERR_INVAL;
+  if (!d->n_workgroups || !d->cost) return MC_ERR_INVAL;
+  if (d->rule > MC_GREEDY) return MC_ERR_INVAL;
+  if (d->key_bits != 0 && d->key_bits != 64 && d->key_bits != 128) return MC_ERR_INVAL;
+  if (d->n_wg > 4095 || d->n_ts > 4095) return MC_ERR_OVERFLOW;
+  mc_options o;
+  if (opt) o = *opt;
+  else mc_options_default(&o);
+  if (!valid_options(&o)) return MC_ERR_INVAL;
+
+  mc_model* m = new (std::nothrow) mc_model;
+  if (!m) return MC_ERR_NOMEM;
+  m->a = d->n_wg;
+  m->b = d->n_ts;
+  m->P = d->P;
+  m->rule = d->rule;
+  m->opt = o;
+  const size_t ab = (size_t)m->a * m->b;
+  m->N.assign(d->n_workgroups, d->n_workgroups + ab);
+  m->cost.assign(d->cost, d->cost + ab);
+  if (d->speed) m->speed.assign(d->speed, d->speed + m->P);
+  else m->speed.assign(m->P, 1);
+  if (d->wg_values) m->wg.assign(d->wg_values, d->wg_values + m->a);
+  if (d->ts_values) m->ts.assign(d->ts_values, d->ts_values + m->b);
+  uint32_t n_max = 0, s_max = 0;
+  for (size_t k = 0; k < ab; ++k) {
+    if (m->N[k] == 0 || m->cost[k] == 0) {
+      delete m;
+      return MC_ERR_INVAL;
+    }
+    n_max = std::max(n_max, m->N[k]);
+  }
+  for (uint32_t s : m->speed) {
+    if (s == 0) {
+      delete m;
+      return MC_ERR_INVAL;
+    }
+    s_max = std::max(s_max, s);
+  }
+  // every clock stays below 2^40 (packed (time, i, j) reductions)
+  for (size_t k = 0; k < ab; ++k) {
+    if ((unsigned __int128)m->N[k] * m->cost[k] * s_max >= ((unsigned __int128)1 << 40)) {
+      delete m;
+      return MC_ERR_OVERFLOW;
+    }
+  }
+  // key layout: [i+1][j+1][n_0]...[n_{P-1}] from the top of the used bits
+  m->n_bits = bits_for(n_max);
+  m->ts_bits = bits_for(m->b);
+  m->wg_bits = bits_for(m->a);
+  m->used_bits = m->wg_bits + m->ts_bits + m->P * m->n_bits;
+  m->ts_shift = m->P * m->n_bits;
+  m->wg_shift = m->ts_shift + m->ts_bits;
+  if (d->key_bits == 0) m->key_bits = m->used_bits <= 64 ? 64 : 128;
+  else m->key_bits = d->key_bits;
+  if (m->used_bits > m->key_bits) {
+    delete m;
+    return MC_ERR_OVERFLOW;
+  }
+  m->key_words = m->key_bits / 64;
+  m->max_level = n_max + 2;
+  m->tile = 1;
+  while (m->tile < m->P) m->tile <<= 1;
+
+  // closed-form bounds on the widths of the levels (sizing only):
+  //   FREE:   C(k+P-1, P-1) states of sum(n) = k per configuration;
+  //   GREEDY: at most C(P, floor(P/2)) per configuration and level, since
+  //           after k dispatches only the units tied at the next start time
+  //           can differ.
+  const uint64_t greedy_cap = binom_sat(m->P, m->P / 2);
+  uint64_t total = add_sat(1 + (uint64_t)m->a, ab);
+  uint64_t widest = 0;
+  for (uint32_t k = 1; k <= n_max; ++k) {
+    uint64_t cnt = 0;
+    for (size_t c = 0; c < ab; ++c) cnt += m->N[c] >= k;
+    uint64_t per = binom_sat((uint64_t)k + m->P - 1, m->P - 1);
+    if (m->rule == MC_GREEDY) per = std::min(per, greedy_cap);
+    const uint64_t w = mul_sat(per, cnt);
+    widest = std::max(widest, w);
+    total = add_sat(total, w);
+  }
+  m->max_width = widest;
+  m->state_bound = total;
+  *out = m;
+  return MC_OK;
+}
+
+void mc_model_destroy(mc_model* m) {
+  if (!m) return;
+  release(m);
+  delete m;
+}
+
+int mc_set_options(mc_model* m, const mc_options* o) {
+  if (!m || !o || !valid_options(o)) return MC_ERR_INVAL;
+  mc_options keep = m->opt;
+  m->opt = *o;
+  if (m->reserved) {  // buffer sizes are fixed once allocated
+    m->opt.load_factor_pct = keep.load_factor_pct;
+    m->opt.table_log2 = keep.table_log2;
+    m->opt.log_capacity = keep.log_capacity;
+    m->opt.threads_per_block = keep.threads_per_block;
+    m->opt.blocks_per_sm = keep.blocks_per_sm;
+  }
+  return MC_OK;
+}
+
+int mc_set_stream(mc_model* m, void* stream) {
+  if (!m) return MC_ERR_INVAL;
+  m->stream = (cudaStream_t)stream;
+  return MC_OK;
+}
+
+int mc_set_allocator(mc_model* m, mc_alloc_fn alloc, mc_free_fn free_fn, void* ctx) {
+  if (!m || !alloc || !free_fn || m->reserved) return MC_ERR_INVAL;
+  m->alloc = alloc;
+  m->dealloc = free_fn;
+  m->actx = ctx;
+  return MC_OK;
+}
+
+int mc_reserve(mc_model* m) {
+  if (!m) return MC_ERR_INVAL;
+  return reserve(m);
+}
+
+int mc_model_layout(const mc_model* m, mc_layout* out) {
+  if (!m || !out) return MC_ERR_INVAL;
+  std::memset(out, 0, sizeof(*out));
+  out->key_bits = m->key_bits;
+  out->key_words = m->key_words;
+  out->used_bits = m->used_bits;
+  out->P = m->P;
+  out->n_bits = m->n_bits;
+  out->ts_bits = m->ts_bits;
+  out->wg_bits = m->wg_bits;
+  out->ts_shift = m->ts_shift;
+  out->wg_shift = m->wg_shift;
+  out->max_level = m->max_level;
+  for (uint32_t c = 0; c < m->P; ++c) out->n_shift[c] = (m->P - 1 - c) * m->n_bits;
+  out->max_width = m->max_width;
+  out->state_bound = m->state_bound;
+  mc_model* mm = const_cast<mc_model*>(m);
+  if (!m->reserved) size_buffers(mm);
+  out->table_slots = m->table_slots;
+  out->log_capacity = m->log_cap;
+  out->device_bytes = m->device_bytes;
+  return MC_OK;
+}
+
+int mc_check(mc_model* m, uint64_t T, mc_check_result* out, mc_trace** cex) {
+  if (!m || !out) return MC_ERR_INVAL;
+  if (cex) *cex = nullptr;
+  DeviceGuard g(m->device);
+  MC_TRY(reserve(m));
+  MC_TRY(enqueue_pass(m, T, nullptr, 0, m->opt.prune, m->opt.early_exit, true, nullptr, 0));
+  const size_t L2 = m->max_level + 2;
+  if (cex) MC_CUDA(m, cudaMemcpyAsync(m->h_trace, m->d_trace, 16 * L2, cudaMemcpyDeviceToHost, m->stream));
+  MC_TRY(sync(m));
+  MC_TRY(pass_error(m, 0));
+  fill_check(m, m->h_ctrl[0], out);
+  if (!out->holds) MC_TRY(make_trace(m, m->h_ctrl[0], cex));
+  return MC_OK;
+}
+
+int mc_count_states(mc_model* m, uint64_t* out) {
+  if (!m || !out) return MC_ERR_INVAL;
+  DeviceGuard g(m->device);
+  MC_TRY(reserve(m));
+  MC_TRY(enqueue_pass(m, UINT64_MAX, nullptr, 0, false, false, false, nullptr, 0));
+  MC_TRY(sync(m));
+  MC_TRY(pass_error(m, 0));
+  *out = m->h_ctrl[0].states;
+  return MC_OK;
+}
+
+int mc_simulate(mc_model* m, uint64_t seed, uint32_t walks, uint64_t* t_ini) {
+  if (!m || !t_ini || walks == 0) return MC_ERR_INVAL;
+  DeviceGuard g(m->device);
+  MC_TRY(reserve(m));
+  MC_TRY(run_simulation(m, seed, walks, m->d_tini));
+  MC_CUDA(m, cudaMemcpyAsync(m->h_scalar, m->d_tini, 8, cudaMemcpyDeviceToHost, m->stream));
+  MC_TRY(sync(m));
+  *t_ini = m->h_scalar[0];
+  return MC_OK;
+}
+
+int mc_min_time(mc_model* m, mc_min_result* out, mc_trace** trace) {
+  if (!m || !out) return MC_ERR_INVAL;
+  if (trace) *trace = nullptr;
+  std::memset(out, 0, sizeof(*out));
+  DeviceGuard g(m->device);
+  MC_TRY(reserve(m));
+  const bool prune = m->opt.prune, ee = m->opt.early_exit;
+  const size_t L2 = m->max_level + 2;
+  MC_TRY(run_simulation(m, m->opt.sim_seed, m->opt.sim_walks, m->d_tini));
+  int final_slot = -1;
+
+  if (m->opt.search == MC_SEARCH_SINGLE) {
+    // one pass with a device-side min-reduction over terminal times, then
+    // the certificate checks at T_min - 1 (must hold) and T_min (fails);
+    // thresholds stay on the device, so the host waits once
+    MC_CUDA(m, cudaMemsetAsync(m->d_tmin, 0, 8, m->stream));
+    MC_TRY(enqueue_pass(m, UINT64_MAX, prune ? m->d_tini : nullptr, 0, prune, false, false,
+                        m->d_tmin, 0));
+    int slot = 1;
+    if (m->opt.refine) MC_TRY(enqueue_pass(m, 0, m->d_tmin, -1, prune, ee, false, nullptr, slot++));
+    MC_TRY(enqueue_pass(m, 0, m->d_tmin, 0, prune, ee, true, nullptr, slot));
+    final_slot = slot;
+    MC_CUDA(m, cudaMemcpyAsync(m->h_scalar, m->d_tini, 8, cudaMemcpyDeviceToHost, m->stream));
+    if (trace) MC_CUDA(m, cudaMemcpyAsync(m->h_trace, m->d_trace, 16 * L2, cudaMemcpyDeviceToHost, m->stream));
+    MC_TRY(sync(m));
+    out->t_ini = m->h_scalar[0];
+    for (int s = 0; s <= final_slot; ++s) {
+      MC_TRY(pass_error(m, s));
+      out->states += m->h_ctrl[s].states;
+      out->checks += 1;
+    }
+    if (m->h_ctrl[0].best_pack == kNone) {
+      m->last_err = "no terminal below T_ini";
+      return MC_ERR_CUDA;
+    }
+    if ((m->opt.refine && m->h_ctrl[1].stop_level != 0) || m->h_ctrl[final_slot].stop_level == 0) {
+      m->last_err = "certificate checks disagree with the minimum";
+      return MC_ERR_CUDA;
+    }
+  } else {
+    MC_CUDA(m, cudaMemcpyAsync(m->h_scalar, m->d_tini, 8, cudaMemcpyDeviceToHost, m->stream));
+    MC_TRY(sync(m));
+    out->t_ini = m->h_scalar[0];
+    // run one check, keep its header in `slot`
+    auto check = [&](uint64_t T, int slot) -> int {
+      MC_TRY(enqueue_pass(m, T, nullptr, 0, prune, ee, true, nullptr, slot));
+      MC_TRY(sync(m));
+      MC_TRY(pass_error(m, slot));
+      out->states += m->h_ctrl[slot].states;
+      out->checks += 1;
+      return MC_OK;
+    };
+    int last = -1;  // slot of the last failing check
+    if (m->opt.search == MC_SEARCH_LOWER) {
+      // Step 3: lower T below each counterexample until the property holds
+      uint64_t T = out->t_ini;
+      for (;;) {
+        const int slot = last == 0 ? 1 : 0;
+        MC_TRY(check(T, slot));
+        if (m->h_ctrl[slot].stop_level == 0) break;
+        last = slot;
+        T = mc::pack_time(m->h_ctrl[slot].wpack) - 1;
+      }
+    } else {
+      // bisection (Fig. 1) between 0 (no terminal has time 0) and T_ini;
+      // a counterexample at mid lowers hi to its own time
+      uint64_t lo = 0, hi = out->t_ini;
+      while (hi - lo > 1) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        const int slot = last == 0 ? 1 : 0;
+        MC_TRY(check(mid, slot));
+        if (m->h_ctrl[slot].stop_level == 0) {
+          lo = mid;
+        } else {
+          hi = mc::pack_time(m->h_ctrl[slot].wpack);
+          last = slot;
+        }
+      }
+      if (last < 0 || mc::pack_time(m->h_ctrl[last].wpack) != hi) {
+        const int slot = last == 0 ? 1 : 0;
+        MC_TRY(check(hi, slot));
+        last = slot;
+      }
+    }
+    if (last < 0 || m->h_ctrl[last].stop_level == 0) {
+      m->last_err = "search ended without a counterexample";
+      return MC_ERR_CUDA;
+    }
+    final_slot = last;
+    if (trace) {
+      MC_CUDA(m, cudaMemcpyAsync(m->h_trace, m->d_trace, 16 * L2, cudaMemcpyDeviceToHost, m->stream));
+      MC_TRY(sync(m));
+    }
+  }
+  const Ctrl& c = m->h_ctrl[final_slot];
+  out->t_min = mc::pack_time(c.wpack);
+  out->wg_index = mc::pack_i(c.wpack);
+  out->ts_index = mc::pack_j(c.wpack);
+  out->wg = wg_value(m, out->wg_index);
+  out->ts = ts_value(m, out->ts_index);
+  out->level = c.stop_level;
+  out->witness_key[0] = c.wkey_lo;
+  out->witness_key[1] = m->key_words == 2 ? c.wkey_hi : 0;
+  MC_TRY(make_trace(m, c, trace));
+  return MC_OK;
+}
+
+int mc_last_widths(mc_model* m, uint64_t* out, uint32_t cap, uint32_t* n) {
+  if (!m || !n || (!out && cap)) return MC_ERR_INVAL;
+  *n = m->reserved ? m->last_levels : 0;
+  if (!m->reserved || cap == 0) return MC_OK;
+  DeviceGuard g(m->device);
+  const uint32_t k = std::min(cap, *n);
+  MC_CUDA(m, cudaMemcpyAsync(out, m->d_width, 8ull * k, cudaMemcpyDeviceToHost, m->stream));
+  MC_TRY(sync(m));
+  return MC_OK;
+}
+
+int mc_trace_length(const mc_trace* t) {
+  return t ? (int)(t->keys.size() / t->words) : 0;
+}
+
+uint32_t mc_trace_key_words(const mc_trace* t) { return t ? t->words : 0; }
+
+const uint64_t* mc_trace_states(const mc_trace* t) { return t && !t->keys.empty() ? t->keys.data() : nullptr; }
+
+void mc_trace_free(mc_trace* t) { delete t; }
+
+const char* mc_strerror(int code) {
+  switch (code) {
+    case MC_OK: return "ok";
+    case MC_ERR_INVAL: return "invalid argument";
+    case MC_ERR_NOMEM: return "out of memory";
+    case MC_ERR_TABLE_FULL: return "visited set full (probe limit reached)";
+    case MC_ERR_FRONTIER: return "frontier log capacity exceeded";
+    case MC_ERR_TIMEOUT: return "device-side wait timed out";
+    case MC_ERR_CUDA: return "CUDA error";
+    case MC_ERR_OVERFLOW: return "overflow (key width, clock range or level width)";
+  }
+  return "unknown error";
+}
+
+const char* mc_last_error(const mc_model* m) { return m ? m->last_err.c_str() : ""; }
+
+}  // extern "C"

@@ -1,0 +1,96 @@
+// Internal declarations shared by the host side (mc_api.cu) and the kernels
+// (mc_kernels.cu) of the explorer.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mc {
+
+constexpr uint32_t kMaxP = 16;
+constexpr uint64_t kNone = ~0ull;          // "no value" for packed minima
+constexpr int kPackIdxBits = 12;           // i and j fields of a packed (time, i, j)
+constexpr uint32_t kNoParent = 0xFFFFFFFFu;
+
+// Packed (time, i, j) used for device-side min-reductions: time < 2^40,
+// i, j < 2^12.
+__host__ __device__ inline uint64_t pack_tij(uint64_t t, uint32_t i, uint32_t j) {
+  return (t << (2 * kPackIdxBits)) | ((uint64_t)i << kPackIdxBits) | j;
+}
+__host__ __device__ inline uint64_t pack_time(uint64_t p) { return p >> (2 * kPackIdxBits); }
+__host__ __device__ inline uint32_t pack_i(uint64_t p) { return (uint32_t)(p >> kPackIdxBits) & 0xFFFu; }
+__host__ __device__ inline uint32_t pack_j(uint64_t p) { return (uint32_t)p & 0xFFFu; }
+
+// Model constants every kernel needs (passed by value).
+struct Params {
+  uint32_t a, b, P, rule;
+  uint32_t n_bits;        // bits of one n_c field
+  uint32_t ts_shift;      // bit offset of j+1
+  uint32_t wg_shift;      // bit offset of i+1
+  uint32_t ts_mask;       // (1 << ts_bits) - 1
+  uint32_t wg_mask;       // (1 << wg_bits) - 1
+  uint32_t max_level;     // max N_ij + 2
+  uint64_t n_mask;        // (1 << n_bits) - 1
+  uint64_t swar_mask;     // low P*n_bits bits (when P*n_bits <= 64)
+  uint64_t swar_mul;      // sum_t 2^(t*n_bits): the product's top field sums the n fields
+  uint32_t swar_ok;       // 1 when P*n_bits <= 64
+  uint32_t pad;
+  const uint32_t* N;      // device [a*b]
+  const uint32_t* cost;   // device [a*b]
+  const uint32_t* speed;  // device [P]
+};
+
+// Per-pass control block header (device memory, zeroed before each pass).
+struct Ctrl {
+  uint32_t err;           // first error code of the pass (0 = none)
+  uint32_t bar_count;     // device-wide barrier arrivals
+  uint32_t bar_gen;       // device-wide barrier generation
+  uint32_t bar_abort;     // set when a barrier wait timed out
+  uint32_t levels;        // last explored level + 1
+  uint32_t stop_level;    // first level holding a violating terminal (0 = none)
+  uint32_t witness_level; // level the witness was taken from (0 = none)
+  uint32_t trace_len;     // states in the trace buffer
+  uint64_t states;        // sum of the widths of the explored levels
+  uint64_t best_pack;     // min packed (time, i, j) over all violating terminals
+  uint64_t wkey_lo;       // witness key
+  uint64_t wkey_hi;
+  uint64_t widx;          // witness index inside its level
+  uint64_t wpack;         // packed (time, i, j) of the first violating level
+  uint64_t T;             // threshold the pass used
+};
+
+// Everything one exploration pass needs.
+struct ExploreArgs {
+  Params p;
+  void* table;            // visited set: buckets of 32 bytes
+  uint64_t bucket_mask;   // buckets - 1
+  uint64_t table_u64;     // table size in u64 words (for clearing)
+  uint32_t max_probes;    // bucket probes before MC_ERR_TABLE_FULL
+  uint32_t prune;
+  uint32_t early_exit;
+  uint32_t want_witness;  // find the witness of the first violating level + trace
+  void* log_keys;         // frontier log: keys of every kept state, level by level
+  uint32_t* log_par;      // parent index inside the previous level
+  uint64_t log_cap;
+  Ctrl* ctrl;
+  uint64_t* width;        // [max_level + 2] kept states per level
+  uint64_t* off;          // [max_level + 2] first log entry of each level
+  uint64_t* best;         // [max_level + 2] min packed violating terminal per level
+  uint64_t* trace;        // [(max_level + 1) * 2] trace keys {lo, hi}
+  uint64_t T;             // threshold, unless T_src is set
+  const uint64_t* T_src;  // device threshold source (T = *T_src + T_delta)
+  int64_t T_delta;
+  uint64_t* tmin_out;     // if set: receives pack_time(best_pack) at the end
+  uint32_t barrier_target;// arrivals that complete a device-wide barrier
+  uint32_t pad;
+  uint64_t timeout_ns;
+};
+
+// Launch helpers implemented in mc_kernels.cu.
+int explore_kernel_occupancy(int key_words, int tile, int rule, int threads, int* blocks_per_sm);
+cudaError_t launch_explore(int key_words, int tile, int rule, int grid, int threads,
+                           const ExploreArgs& args, cudaStream_t stream);
+cudaError_t launch_simulate(const Params& p, uint64_t seed, uint32_t walks, uint64_t* t_out,
+                            cudaStream_t stream);
+
+}  // namespace mc

@@ -1,0 +1,614 @@
+// Device side of the explorer: one persistent, cooperatively launched kernel
+// per exploration pass, plus the simulation kernel that gives T_ini.
+//
+// Layout in HBM (one model):
+//   frontier log   keys (u64 or 2 x u64) and u32 parent indices of every kept
+//                  state, level after level; a state's parent index points
+//                  into the previous level, so the log doubles as the BFS tree
+//                  the counterexample trace is read from (Section 4, Step 4).
+//   visited set    open addressing, 32-byte buckets (4 u64 keys or 2 u128
+//                  keys), linear probing over buckets, lock-free atomicCAS
+//                  insert.  The key 0 (s0) marks an empty slot.
+//   control block  per-level widths, log offsets, minima of packed
+//                  (time, i, j) over violating terminals, the trace buffer.
+//
+// Why a per-pass table that is never cleared between levels: every
+// transition raises sum(n) by one (the WG/TS selects sit at levels 1 and 2
+// and are written directly), so a state can only be generated again within
+// its own BFS level.  A slot holding a key of an earlier level is therefore
+// as good as empty: insertion treats it as free and overwrites it with CAS.
+// Keys of one level never leave the table during that level, so two threads
+// inserting the same key walk the same probe sequence and meet at the same
+// slot.  The table only has to hold one level (sized from the widest level),
+// and nothing is cleared between levels.
+#include <cstdint>
+
+#include "mc_internal.h"
+#include "mc.h"
+
+namespace mc {
+namespace {
+
+typedef unsigned __int128 u128;
+
+// ------------------------------------------------------------------ memory
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void set_error(Ctrl* ctrl, int code) {
+  atomicCAS(&ctrl->err, 0u, (uint32_t)code);
+}
+
+// ------------------------------------------------------------------ keys
+template <class K>
+struct KeyOps;
+
+template <>
+struct KeyOps<uint64_t> {
+  static constexpr int kSlots = 4;  // keys per 32-byte bucket
+  __device__ static uint64_t load(const void* base, uint64_t i) {
+    return __ldcg(reinterpret_cast<const unsigned long long*>(base) + i);
+  }
+  __device__ static void store(void* base, uint64_t i, uint64_t k) {
+    reinterpret_cast<unsigned long long*>(base)[i] = k;
+  }
+  __device__ static uint64_t lo(uint64_t k) { return k; }
+  __device__ static uint64_t hi(uint64_t) { return 0; }
+};
+
+template <>
+struct KeyOps<u128> {
+  static constexpr int kSlots = 2;
+  __device__ static u128 load(const void* base, uint64_t i) {
+    ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(base) + i);
+    return ((u128)v.y << 64) | v.x;
+  }
+  __device__ static void store(void* base, uint64_t i, u128 k) {
+    reinterpret_cast<ulonglong2*>(base)[i] = make_ulonglong2((uint64_t)k, (uint64_t)(k >> 64));
+  }
+  __device__ static uint64_t lo(u128 k) { return (uint64_t)k; }
+  __device__ static uint64_t hi(u128 k) { return (uint64_t)(k >> 64); }
+};
+
+// splitmix64 output function (Steele, Lea, Flood 2014)
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t key_hash(uint64_t k) { return mix64(k); }
+__device__ __forceinline__ uint64_t key_hash(u128 k) {
+  return mix64((uint64_t)k ^ mix64((uint64_t)(k >> 64) + 0x9E3779B97F4A7C15ull));
+}
+
+template <class K>
+__device__ __forceinline__ uint32_t field(K key, uint32_t shift, uint64_t mask) {
+  return (uint32_t)((uint64_t)(key >> shift) & mask);
+}
+
+// sum of the n_c fields of a key = its BFS level - 2
+template <class K>
+__device__ __forceinline__ uint32_t sum_n(K key, const Params& p) {
+  if (p.swar_ok) {
+    uint64_t x = (uint64_t)key & p.swar_mask;
+    return (uint32_t)(((x * p.swar_mul) >> ((p.P - 1) * p.n_bits)) & p.n_mask);
+  }
+  uint32_t s = 0;
+  for (uint32_t c = 0; c < p.P; ++c) s += field(key, (p.P - 1 - c) * p.n_bits, p.n_mask);
+  return s;
+}
+
+// model time of a key (max over units of n_c * cost * speed_c)
+template <class K>
+__device__ __forceinline__ uint64_t key_time(K key, const Params& p, uint32_t cfg) {
+  uint64_t c0 = __ldg(p.cost + cfg);
+  uint64_t mx = 0;
+  for (uint32_t c = 0; c < p.P; ++c) {
+    uint64_t t = (uint64_t)field(key, (p.P - 1 - c) * p.n_bits, p.n_mask) * c0 * __ldg(p.speed + c);
+    mx = t > mx ? t : mx;
+  }
+  return mx;
+}
+
+// ------------------------------------------------------------------ visited set
+__device__ __forceinline__ u128 cas128(u128* addr, u128 cmp, u128 val) {
+  uint64_t olo, ohi;
+  asm volatile(
+      "{\n\t.reg .b128 c, v, o;\n\t"
+      "mov.b128 c, {%2, %3};\n\t"
+      "mov.b128 v, {%4, %5};\n\t"
+      "atom.relaxed.gpu.global.cas.b128 o, [%6], c, v;\n\t"
+      "mov.b128 {%0, %1}, o;\n\t}"
+      : "=l"(olo), "=l"(ohi)
+      : "l"((uint64_t)cmp), "l"((uint64_t)(cmp >> 64)), "l"((uint64_t)val),
+        "l"((uint64_t)(val >> 64)), "l"(addr)
+      : "memory");
+  return ((u128)ohi << 64) | olo;
+}
+
+__device__ __forceinline__ uint64_t slot_cas(uint64_t* addr, uint64_t cmp, uint64_t val) {
+  return atomicCAS(reinterpret_cast<unsigned long long*>(addr), cmp, val);
+}
+__device__ __forceinline__ u128 slot_cas(u128* addr, u128 cmp, u128 val) { return cas128(addr, cmp, val); }
+
+template <class K>
+__device__ __forceinline__ void load_bucket(const K* b, K (&v)[KeyOps<K>::kSlots]);
+
+template <>
+__device__ __forceinline__ void load_bucket<uint64_t>(const uint64_t* b, uint64_t (&v)[4]) {
+  ulonglong2 x = __ldcg(reinterpret_cast<const ulonglong2*>(b));
+  ulonglong2 y = __ldcg(reinterpret_cast<const ulonglong2*>(b) + 1);
+  v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+}
+template <>
+__device__ __forceinline__ void load_bucket<u128>(const u128* b, u128 (&v)[2]) {
+  ulonglong2 x = __ldcg(reinterpret_cast<const ulonglong2*>(b));
+  ulonglong2 y = __ldcg(reinterpret_cast<const ulonglong2*>(b) + 1);
+  v[0] = ((u128)x.y << 64) | x.x;
+  v[1] = ((u128)y.y << 64) | y.x;
+}
+
+// Insert `key` (sum of n fields = lvl) into the visited set.
+// Returns 1 if this thread inserted it, 0 if it was already there, -1 when
+// the probe limit was reached.  A slot is free when it holds 0 or a key of an
+// earlier level; the first free slot of the probe sequence is taken.
+template <class K>
+__device__ int visited_insert(K* table, uint64_t bucket_mask, uint32_t max_probes, K key,
+                              uint32_t lvl, const Params& p) {
+  constexpr int S = KeyOps<K>::kSlots;
+  uint64_t bkt = key_hash(key) & bucket_mask;
+  for (uint32_t probe = 0; probe < max_probes; ++probe) {
+    K* slot = table + bkt * S;
+    K v[S];
+    load_bucket<K>(slot, v);
+    bool hit = false;
+#pragma unroll
+    for (int s = 0; s < S; ++s) hit |= (v[s] == key);
+    if (hit) return 0;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      K cur = v[s];
+      // a slot changes at most once per level (free -> a key of this
+      // level), so two CAS attempts settle it; the bound is defensive
+      for (int tries = 0; tries < 3; ++tries) {
+        if (cur == key) return 0;
+        if (cur != (K)0 && sum_n(cur, p) >= lvl) break;  // taken this level
+        K old = slot_cas(slot + s, cur, key);
+        if (old == cur) return 1;
+        cur = old;
+      }
+    }
+    bkt = (bkt + 1) & bucket_mask;
+  }
+  return -1;
+}
+
+// ------------------------------------------------------------------ device-wide barrier
+// All blocks are co-resident (cooperative launch).  Each wait is bounded by
+// timeout_ns of %globaltimer; on expiry the block records MC_ERR_TIMEOUT,
+// raises bar_abort so the other waiters leave too, and returns false.
+__device__ bool grid_sync(const ExploreArgs& A) {
+  __shared__ uint32_t s_ok;
+  Ctrl* ctrl = A.ctrl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t ok = 1;
+    uint32_t gen = ld_acquire_u32(&ctrl->bar_gen);
+    __threadfence();
+    uint32_t arrived = atomicAdd(&ctrl->bar_count, 1u) + 1;
+    if (arrived == A.barrier_target) {
+      atomicExch(&ctrl->bar_count, 0u);
+      st_release_u32(&ctrl->bar_gen, gen + 1);
+    } else {
+      uint64_t t0 = globaltimer();
+      uint32_t spins = 0;
+      while (ld_acquire_u32(&ctrl->bar_gen) == gen) {
+        if (ld_relaxed_u32(&ctrl->bar_abort)) { ok = 0; break; }
+        if ((++spins & 15u) == 0 && globaltimer() - t0 > A.timeout_ns) {
+          set_error(ctrl, MC_ERR_TIMEOUT);
+          atomicExch(&ctrl->bar_abort, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ------------------------------------------------------------------ tile reductions
+template <int TILE>
+__device__ __forceinline__ uint64_t tile_max(uint64_t v) {
+#pragma unroll
+  for (int o = TILE / 2; o > 0; o >>= 1) {
+    uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+template <int TILE>
+__device__ __forceinline__ uint64_t tile_min(uint64_t v) {
+#pragma unroll
+  for (int o = TILE / 2; o > 0; o >>= 1) {
+    uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+
+// ------------------------------------------------------------------ expansion of one level
+// A tile of TILE >= P lanes handles one state; lane c proposes the successor
+// in which unit c takes the next work-group (Listings 4-5): FREE allows every
+// unit, GREEDY only the units with the smallest clock.  Successors are
+// inserted into the visited set; winners are appended to the next level of
+// the frontier log (warp-aggregated), and a winner that is terminal (FIN,
+// Listing 4) with time <= T updates the level's minimum packed
+// (time, i, j) -- the property G(FIN -> time > T) of Step 2.
+template <class K, int TILE, int RULE>
+__device__ __forceinline__ void expand_level(const ExploreArgs& A, uint64_t T, uint32_t L,
+                                             uint64_t offL, uint64_t W, uint64_t offN) {
+  const Params& p = A.p;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t c = lane & (TILE - 1);
+  constexpr uint32_t kTilesPerWarp = 32 / TILE;
+  const uint64_t warp_gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const uint32_t k_cur = L - 2;  // sum of n at level L
+  const uint32_t c_shift = (p.P - 1 - (c < p.P ? c : 0)) * p.n_bits;
+  const uint64_t speed_c = c < p.P ? __ldg(p.speed + c) : 0;
+  K* table = reinterpret_cast<K*>(A.table);
+
+  for (uint64_t base = warp_gid * kTilesPerWarp; base < W; base += n_warps * kTilesPerWarp) {
+    const uint64_t s = base + lane / TILE;
+    const bool valid = s < W;
+    K key = valid ? KeyOps<K>::load(A.log_keys, offL + s) : (K)0;
+    uint32_t i = 0, j = 0, r = 0;
+    uint64_t t_c = 0, clk = 0;
+    if (valid) {
+      i = field(key, p.wg_shift, p.wg_mask) - 1;
+      j = field(key, p.ts_shift, p.ts_mask) - 1;
+      const uint32_t cfg = i * p.b + j;
+      r = __ldg(p.N + cfg) - k_cur;
+      if (c < p.P) {
+        t_c = (uint64_t)__ldg(p.cost + cfg) * speed_c;
+        clk = (uint64_t)field(key, c_shift, p.n_mask) * t_c;
+      }
+    }
+    const uint64_t mx = tile_max<TILE>(clk);
+    bool allowed = valid && c < p.P && r > 0;
+    if (RULE == MC_GREEDY) {
+      const uint64_t mn = tile_min<TILE>((valid && c < p.P) ? clk : kNone);
+      allowed = allowed && clk == mn;
+    }
+    const uint64_t nclk = clk + t_c;
+    const uint64_t succ_time = nclk > mx ? nclk : mx;
+    if (A.prune && succ_time > T) allowed = false;
+    const K succ = key + ((K)1 << c_shift);
+    int won = 0;
+    if (allowed) {
+      const int rc = visited_insert<K>(table, A.bucket_mask, A.max_probes, succ, k_cur + 1, p);
+      if (rc < 0) set_error(A.ctrl, MC_ERR_TABLE_FULL);
+      won = rc > 0;
+    }
+    const uint32_t m = __ballot_sync(0xffffffffu, won);
+    if (m) {
+      const uint32_t leader = __ffs(m) - 1;
+      unsigned long long pos0 = 0;
+      if (lane == leader) pos0 = atomicAdd(reinterpret_cast<unsigned long long*>(&A.width[L + 1]),
+                                           (unsigned long long)__popc(m));
+      pos0 = __shfl_sync(0xffffffffu, pos0, leader);
+      if (won) {
+        const uint64_t at = offN + pos0 + __popc(m & ((1u << lane) - 1u));
+        if (at < A.log_cap) {
+          KeyOps<K>::store(A.log_keys, at, succ);
+          A.log_par[at] = (uint32_t)s;
+        } else {
+          set_error(A.ctrl, MC_ERR_FRONTIER);
+        }
+      }
+      // Step 2: a terminal winner with time <= T violates G(FIN -> time > T)
+      uint64_t pk = (won && r == 1 && succ_time <= T) ? pack_tij(succ_time, i, j) : kNone;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t w = __shfl_xor_sync(0xffffffffu, pk, o);
+        pk = w < pk ? w : pk;
+      }
+      if (lane == 0 && pk != kNone && pk < ld_relaxed_u64(&A.best[L + 1]))
+        atomicMin(reinterpret_cast<unsigned long long*>(&A.best[L + 1]), (unsigned long long)pk);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ the exploration pass
+template <class K, int TILE, int RULE>
+__global__ void __launch_bounds__(512) explore_kernel(const ExploreArgs A) {
+  const Params& p = A.p;
+  Ctrl* ctrl = A.ctrl;
+  const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+
+  uint64_t T = A.T;
+  if (A.T_src) T = ld_relaxed_u64(A.T_src) + (uint64_t)A.T_delta;
+
+  // prologue: empty visited set, level arrays, levels 0..2 (the selects of
+  // WG and TS, Listing 3) written directly: they are distinct by construction
+  {
+    ulonglong2* tb = reinterpret_cast<ulonglong2*>(A.table);
+    const uint64_t n16 = A.table_u64 / 2;
+    for (uint64_t x = gtid; x < n16; x += nthreads) tb[x] = make_ulonglong2(0, 0);
+    for (uint64_t l = gtid; l < (uint64_t)p.max_level + 2; l += nthreads) {
+      A.width[l] = l == 0 ? 1 : l == 1 ? p.a : l == 2 ? (uint64_t)p.a * p.b : 0;
+      A.off[l] = l == 0 ? 0 : l == 1 ? 1 : l == 2 ? 1 + (uint64_t)p.a : 0;
+      A.best[l] = kNone;
+    }
+    const uint64_t n_init = 1 + (uint64_t)p.a + (uint64_t)p.a * p.b;
+    for (uint64_t x = gtid; x < n_init; x += nthreads) {
+      K key = 0;
+      uint32_t par = kNoParent;
+      if (x >= 1 && x <= p.a) {
+        key = (K)x << p.wg_shift;
+        par = 0;
+      } else if (x > p.a) {
+        const uint64_t y = x - 1 - p.a;
+        const uint32_t i = (uint32_t)(y / p.b), j = (uint32_t)(y % p.b);
+        key = ((K)(i + 1) << p.wg_shift) | ((K)(j + 1) << p.ts_shift);
+        par = i;
+      }
+      KeyOps<K>::store(A.log_keys, x, key);
+      A.log_par[x] = par;
+    }
+    if (gtid == 0) {
+      ctrl->T = T;
+      ctrl->best_pack = kNone;
+      ctrl->wkey_lo = kNone;
+      ctrl->wkey_hi = kNone;
+      ctrl->widx = kNone;
+    }
+  }
+  if (!grid_sync(A)) return;
+
+  // level loop (one device-wide barrier per level)
+  uint32_t last = 2;
+  uint64_t off_last = 1 + (uint64_t)p.a;
+  for (;;) {
+    const uint32_t L = last;
+    const uint64_t W = ld_relaxed_u64(&A.width[L]);
+    if (L >= p.max_level) break;  // the deepest level holds only terminals
+    const uint64_t offN = off_last + W;
+    if (gtid == 0) A.off[L + 1] = offN;
+    expand_level<K, TILE, RULE>(A, T, L, off_last, W, offN);
+    if (!grid_sync(A)) return;
+    if (ld_relaxed_u32(&ctrl->err)) break;
+    const uint64_t Wn = ld_relaxed_u64(&A.width[L + 1]);
+    if (Wn == 0) break;
+    last = L + 1;
+    off_last = offN;
+    if (A.early_exit && ld_relaxed_u64(&A.best[last]) != kNone) break;
+  }
+  if (ld_relaxed_u32(&ctrl->err)) return;
+
+  // first level holding a violating terminal, and the minimum over all
+  // levels.  With early exit only the last level can hold one; otherwise
+  // every block scans the per-level minima (a few thousand words at most).
+  uint32_t wl = 0;
+  uint64_t best_all = kNone;
+  if (A.early_exit) {
+    best_all = ld_relaxed_u64(&A.best[last]);
+    wl = best_all != kNone ? last : 0;
+  } else {
+    __shared__ unsigned long long s_best;
+    __shared__ unsigned int s_wl;
+    if (threadIdx.x == 0) {
+      s_best = kNone;
+      s_wl = 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    for (uint32_t l = 3 + threadIdx.x; l <= last; l += blockDim.x) {
+      const uint64_t b = ld_relaxed_u64(&A.best[l]);
+      if (b != kNone) {
+        atomicMin(&s_best, (unsigned long long)b);
+        atomicMin(&s_wl, l);
+      }
+    }
+    __syncthreads();
+    best_all = s_best;
+    wl = s_wl == 0xFFFFFFFFu ? 0 : s_wl;
+  }
+  if (gtid == 0) {
+    ctrl->levels = last + 1;
+    ctrl->states = off_last + ld_relaxed_u64(&A.width[last]);
+    ctrl->stop_level = wl;
+    ctrl->best_pack = best_all;
+    ctrl->wpack = wl ? ld_relaxed_u64(&A.best[wl]) : kNone;
+    if (A.tmin_out && best_all != kNone) *A.tmin_out = pack_time(best_all);
+  }
+  if (!A.want_witness || wl == 0) return;
+
+  // witness: the violating terminal of level wl with the smallest key among
+  // those with the level's minimum (time, i, j)
+  const uint64_t target = ld_relaxed_u64(&A.best[wl]);
+  const uint64_t offW = ld_relaxed_u64(&A.off[wl]);
+  const uint64_t Ww = ld_relaxed_u64(&A.width[wl]);
+  const uint32_t ti = pack_i(target), tj = pack_j(target);
+  const uint64_t tt = pack_time(target);
+  const uint32_t cfg_t = ti * p.b + tj;
+  const uint32_t n_t = __ldg(p.N + cfg_t);
+  for (uint64_t x = gtid; x < Ww; x += nthreads) {
+    const K key = KeyOps<K>::load(A.log_keys, offW + x);
+    if (field(key, p.wg_shift, p.wg_mask) - 1 != ti || field(key, p.ts_shift, p.ts_mask) - 1 != tj)
+      continue;
+    if (sum_n(key, p) != n_t || key_time(key, p, cfg_t) != tt) continue;
+    if (sizeof(K) == 8)
+      atomicMin(reinterpret_cast<unsigned long long*>(&ctrl->wkey_lo),
+                (unsigned long long)KeyOps<K>::lo(key));
+    else
+      atomicMin(reinterpret_cast<unsigned long long*>(&ctrl->wkey_hi),
+                (unsigned long long)KeyOps<K>::hi(key));
+  }
+  if (!grid_sync(A)) return;
+  if (sizeof(K) == 16) {
+    const uint64_t whi = ld_relaxed_u64(&ctrl->wkey_hi);
+    for (uint64_t x = gtid; x < Ww; x += nthreads) {
+      const K key = KeyOps<K>::load(A.log_keys, offW + x);
+      if (KeyOps<K>::hi(key) != whi) continue;
+      if (field(key, p.wg_shift, p.wg_mask) - 1 != ti || field(key, p.ts_shift, p.ts_mask) - 1 != tj)
+        continue;
+      if (sum_n(key, p) != n_t || key_time(key, p, cfg_t) != tt) continue;
+      atomicMin(reinterpret_cast<unsigned long long*>(&ctrl->wkey_lo),
+                (unsigned long long)KeyOps<K>::lo(key));
+    }
+    if (!grid_sync(A)) return;
+  } else if (gtid == 0) {
+    ctrl->wkey_hi = 0;
+  }
+  {
+    const uint64_t wlo = ld_relaxed_u64(&ctrl->wkey_lo);
+    const uint64_t whi = sizeof(K) == 16 ? ld_relaxed_u64(&ctrl->wkey_hi) : 0;
+    for (uint64_t x = gtid; x < Ww; x += nthreads) {
+      const K key = KeyOps<K>::load(A.log_keys, offW + x);
+      if (KeyOps<K>::lo(key) == wlo && KeyOps<K>::hi(key) == whi) ctrl->widx = x;
+    }
+  }
+  if (!grid_sync(A)) return;
+  // trace: follow parent indices from the witness back to s0
+  if (gtid == 0) {
+    uint64_t idx = ld_relaxed_u64(&ctrl->widx);
+    if (idx >= Ww) {  // cannot happen when the level is intact; never walk from it
+      set_error(ctrl, MC_ERR_FRONTIER);
+      return;
+    }
+    uint32_t l = wl;
+    for (;;) {
+      const uint64_t at = ld_relaxed_u64(&A.off[l]) + idx;
+      const K key = KeyOps<K>::load(A.log_keys, at);
+      A.trace[2 * l] = KeyOps<K>::lo(key);
+      A.trace[2 * l + 1] = KeyOps<K>::hi(key);
+      if (l == 0) break;
+      idx = __ldcg(A.log_par + at);
+      --l;
+    }
+    ctrl->witness_level = wl;
+    ctrl->trace_len = wl + 1;
+  }
+}
+
+// ------------------------------------------------------------------ simulation (T_ini)
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t ctr) {
+  return mix64(seed + (ctr + 1) * 0x9E3779B97F4A7C15ull);
+}
+
+// One random run per thread (Section 4, Step 3: a simulation gives T_ini).
+__global__ void simulate_kernel(const Params p, uint64_t seed, uint32_t walks, uint64_t* t_out) {
+  const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t w = gtid; w < walks; w += nthreads) {
+    uint64_t ctr = w << 32;
+    const uint32_t i = (uint32_t)(splitmix64_at(seed, ctr++) % p.a);
+    const uint32_t j = (uint32_t)(splitmix64_at(seed, ctr++) % p.b);
+    const uint32_t cfg = i * p.b + j;
+    const uint32_t N = __ldg(p.N + cfg);
+    const uint64_t cost = __ldg(p.cost + cfg);
+    uint64_t clk[kMaxP], t[kMaxP];
+    for (uint32_t c = 0; c < p.P; ++c) {
+      t[c] = cost * __ldg(p.speed + c);
+      clk[c] = 0;
+    }
+    for (uint32_t k = 0; k < N; ++k) {
+      uint32_t c = 0;
+      if (p.rule == MC_FREE) {
+        c = (uint32_t)(splitmix64_at(seed, ctr++) % p.P);
+      } else {
+        uint64_t mn = kNone;
+        for (uint32_t u = 0; u < p.P; ++u) mn = clk[u] < mn ? clk[u] : mn;
+        uint32_t cnt = 0;
+        for (uint32_t u = 0; u < p.P; ++u) cnt += clk[u] == mn;
+        uint32_t pick = (uint32_t)(splitmix64_at(seed, ctr++) % cnt);
+        for (uint32_t u = 0; u < p.P; ++u) {
+          if (clk[u] == mn) {
+            if (pick == 0) { c = u; break; }
+            --pick;
+          }
+        }
+      }
+      clk[c] += t[c];
+    }
+    uint64_t mx = 0;
+    for (uint32_t c = 0; c < p.P; ++c) mx = clk[c] > mx ? clk[c] : mx;
+    atomicMin(reinterpret_cast<unsigned long long*>(t_out), (unsigned long long)mx);
+  }
+}
+
+// ------------------------------------------------------------------ dispatch tables
+template <class K, int RULE>
+const void* pick_tile(int tile) {
+  switch (tile) {
+    case 1: return (const void*)explore_kernel<K, 1, RULE>;
+    case 2: return (const void*)explore_kernel<K, 2, RULE>;
+    case 4: return (const void*)explore_kernel<K, 4, RULE>;
+    case 8: return (const void*)explore_kernel<K, 8, RULE>;
+    case 16: return (const void*)explore_kernel<K, 16, RULE>;
+  }
+  return nullptr;
+}
+
+const void* pick_kernel(int key_words, int tile, int rule) {
+  if (key_words == 1) return rule == MC_FREE ? pick_tile<uint64_t, MC_FREE>(tile)
+                                             : pick_tile<uint64_t, MC_GREEDY>(tile);
+  if (key_words == 2) return rule == MC_FREE ? pick_tile<u128, MC_FREE>(tile)
+                                             : pick_tile<u128, MC_GREEDY>(tile);
+  return nullptr;
+}
+
+}  // namespace
+
+int explore_kernel_occupancy(int key_words, int tile, int rule, int threads, int* blocks_per_sm) {
+  const void* f = pick_kernel(key_words, tile, rule);
+  if (!f) return -1;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, 0) == cudaSuccess
+             ? 0
+             : -1;
+}
+
+cudaError_t launch_explore(int key_words, int tile, int rule, int grid, int threads,
+                           const ExploreArgs& args, cudaStream_t stream) {
+  const void* f = pick_kernel(key_words, tile, rule);
+  if (!f) return cudaErrorInvalidValue;
+  void* params[] = {const_cast<ExploreArgs*>(&args)};
+  return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(threads), params, 0, stream);
+}
+
+cudaError_t launch_simulate(const Params& p, uint64_t seed, uint32_t walks, uint64_t* t_out,
+                            cudaStream_t stream) {
+  const int threads = 128;
+  int grid = (int)((walks + threads - 1) / threads);
+  if (grid > 1024) grid = 1024;
+  simulate_kernel<<<grid, threads, 0, stream>>>(p, seed, walks, t_out);
+  return cudaGetLastError();
+}
+
+}  // namespace mc

@@ -1,0 +1,331 @@
+"""Python binding of the explorer's C-ABI (include/mc.h).
+
+Argument marshalling only: every function forwards to the function of the
+same name in ``libmcgpu.so``; every step of a query runs in the library's
+CUDA kernels.  PyTorch supplies device memory (the caching allocator, through
+``mc_set_allocator``) and the stream.  There is no CPU fallback: if the
+library is missing or no CUDA device is usable, the calls raise.
+"""
+from __future__ import annotations
+
+import atexit
+import ctypes as C
+import os
+import threading
+import weakref
+from typing import Optional
+
+from . import build as _build
+
+MC_OK = 0
+MC_ERR_INVAL = -1
+MC_ERR_NOMEM = -2
+MC_ERR_TABLE_FULL = -3
+MC_ERR_FRONTIER = -4
+MC_ERR_TIMEOUT = -5
+MC_ERR_CUDA = -6
+MC_ERR_OVERFLOW = -7
+MC_FREE, MC_GREEDY = 0, 1
+SEARCH = {"single": 0, "lower": 1, "bisect": 2}
+NO_LIMIT = (1 << 64) - 1
+
+U32P = C.POINTER(C.c_uint32)
+
+
+class McModelDesc(C.Structure):
+    _fields_ = [("n_wg", C.c_uint32), ("n_ts", C.c_uint32), ("P", C.c_uint32),
+                ("wg_values", U32P), ("ts_values", U32P), ("n_workgroups", U32P),
+                ("cost", U32P), ("speed", U32P), ("rule", C.c_uint32), ("key_bits", C.c_uint32)]
+
+
+class McOptions(C.Structure):
+    _fields_ = [("prune", C.c_uint32), ("early_exit", C.c_uint32), ("search", C.c_uint32),
+                ("refine", C.c_uint32), ("sim_seed", C.c_uint64), ("sim_walks", C.c_uint32),
+                ("load_factor_pct", C.c_uint32), ("table_log2", C.c_uint32),
+                ("threads_per_block", C.c_uint32), ("blocks_per_sm", C.c_uint32),
+                ("max_probes", C.c_uint32), ("log_capacity", C.c_uint64),
+                ("barrier_timeout_ns", C.c_uint64), ("debug_barrier_extra", C.c_uint32),
+                ("reserved", C.c_uint32 * 7)]
+
+
+class McCheckResult(C.Structure):
+    _fields_ = [("holds", C.c_uint32), ("levels", C.c_uint32), ("states", C.c_uint64),
+                ("cex_time", C.c_uint64), ("cex_wg_index", C.c_uint32),
+                ("cex_ts_index", C.c_uint32), ("cex_wg", C.c_uint32), ("cex_ts", C.c_uint32),
+                ("cex_level", C.c_uint32), ("key_words", C.c_uint32),
+                ("cex_key", C.c_uint64 * 2)]
+
+
+class McMinResult(C.Structure):
+    _fields_ = [("t_min", C.c_uint64), ("t_ini", C.c_uint64), ("wg_index", C.c_uint32),
+                ("ts_index", C.c_uint32), ("wg", C.c_uint32), ("ts", C.c_uint32),
+                ("states", C.c_uint64), ("checks", C.c_uint32), ("level", C.c_uint32),
+                ("witness_key", C.c_uint64 * 2)]
+
+
+class McLayout(C.Structure):
+    _fields_ = [("key_bits", C.c_uint32), ("key_words", C.c_uint32), ("used_bits", C.c_uint32),
+                ("P", C.c_uint32), ("n_bits", C.c_uint32), ("ts_bits", C.c_uint32),
+                ("wg_bits", C.c_uint32), ("ts_shift", C.c_uint32), ("wg_shift", C.c_uint32),
+                ("max_level", C.c_uint32), ("n_shift", C.c_uint32 * 16),
+                ("table_slots", C.c_uint64), ("log_capacity", C.c_uint64),
+                ("max_width", C.c_uint64), ("state_bound", C.c_uint64),
+                ("device_bytes", C.c_uint64)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+_live = weakref.WeakSet()
+
+
+@atexit.register
+def _destroy_live_models():
+    # free device buffers while PyTorch (the allocator behind them) is alive
+    for m in list(_live):
+        try:
+            mc_model_destroy(m)
+        except Exception:
+            pass
+
+
+class MCError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        msg = f"{where}: {mc_strerror(code)} ({code})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True):
+    """Load libmcgpu.so, building it first when missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"CUDA library missing: {_build.LIB}")
+        L = C.CDLL(_build.LIB)
+        P = C.c_void_p
+        sig = {
+            "mc_options_default": (None, [C.POINTER(McOptions)]),
+            "mc_model_create": (C.c_int, [C.POINTER(McModelDesc), C.POINTER(McOptions), C.POINTER(P)]),
+            "mc_model_destroy": (None, [P]),
+            "mc_set_options": (C.c_int, [P, C.POINTER(McOptions)]),
+            "mc_set_stream": (C.c_int, [P, P]),
+            "mc_set_allocator": (C.c_int, [P, ALLOC_FN, FREE_FN, P]),
+            "mc_reserve": (C.c_int, [P]),
+            "mc_model_layout": (C.c_int, [P, C.POINTER(McLayout)]),
+            "mc_check": (C.c_int, [P, C.c_uint64, C.POINTER(McCheckResult), C.POINTER(P)]),
+            "mc_min_time": (C.c_int, [P, C.POINTER(McMinResult), C.POINTER(P)]),
+            "mc_count_states": (C.c_int, [P, C.POINTER(C.c_uint64)]),
+            "mc_simulate": (C.c_int, [P, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64)]),
+            "mc_last_widths": (C.c_int, [P, C.POINTER(C.c_uint64), C.c_uint32, C.POINTER(C.c_uint32)]),
+            "mc_trace_length": (C.c_int, [P]),
+            "mc_trace_key_words": (C.c_uint32, [P]),
+            "mc_trace_states": (C.POINTER(C.c_uint64), [P]),
+            "mc_trace_free": (None, [P]),
+            "mc_strerror": (C.c_char_p, [C.c_int]),
+            "mc_last_error": (C.c_char_p, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def mc_strerror(code: int) -> str:
+    return load(build=False).mc_strerror(code).decode() if _lib else f"error {code}"
+
+
+def mc_options_default(**overrides) -> McOptions:
+    o = McOptions()
+    load().mc_options_default(C.byref(o))
+    for k, v in overrides.items():
+        if k == "search" and isinstance(v, str):
+            v = SEARCH[v]
+        setattr(o, k, int(v))
+    return o
+
+
+class Model:
+    """Owns an ``mc_model*``; destroyed with ``mc_model_destroy``."""
+
+    def __init__(self, handle: int, spec=None):
+        self.handle = C.c_void_p(handle)
+        self.spec = spec
+        self._callbacks = None
+        self._layout = None
+        _live.add(self)
+
+    def __del__(self):
+        try:
+            mc_model_destroy(self)
+        except Exception:
+            pass
+
+    def _check(self, rc: int, where: str):
+        if rc != MC_OK:
+            detail = ""
+            if self.handle:
+                detail = load(build=False).mc_last_error(self.handle).decode()
+            raise MCError(rc, where, detail)
+
+
+def _u32(xs):
+    return (C.c_uint32 * len(xs))(*[int(x) for x in xs])
+
+
+def mc_model_create(spec, options: Optional[McOptions] = None, allocator: Optional[str] = "torch",
+                    stream=None) -> Model:
+    """Create a model from a ``workloads.ModelSpec`` (or any object with the
+    same fields).  ``allocator``: "torch" (PyTorch caching allocator),
+    "cuda" (the library's cudaMalloc) or None (same as "cuda")."""
+    L = load()
+    arrs = (_u32(spec.wg_values), _u32(spec.ts_values), _u32(spec.n_workgroups), _u32(spec.cost),
+            _u32(spec.speed))
+    d = McModelDesc(len(spec.wg_values), len(spec.ts_values), spec.P, arrs[0], arrs[1], arrs[2],
+                    arrs[3], arrs[4], spec.rule, getattr(spec, "key_bits", 0))
+    h = C.c_void_p()
+    rc = L.mc_model_create(C.byref(d), C.byref(options) if options is not None else None, C.byref(h))
+    if rc != MC_OK:
+        raise MCError(rc, "mc_model_create")
+    m = Model(h.value, spec)
+    if allocator == "torch":
+        mc_set_allocator(m, "torch")
+    if stream is not None:
+        mc_set_stream(m, stream)
+    return m
+
+
+def mc_model_destroy(model: Model):
+    if model.handle and model.handle.value:
+        load(build=False).mc_model_destroy(model.handle)
+        model.handle = C.c_void_p()
+
+
+def mc_set_options(model: Model, options: McOptions):
+    model._check(load().mc_set_options(model.handle, C.byref(options)), "mc_set_options")
+
+
+def mc_set_stream(model: Model, stream):
+    """``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    raw = getattr(stream, "cuda_stream", stream)
+    model._check(load().mc_set_stream(model.handle, C.c_void_p(raw or 0)), "mc_set_stream")
+
+
+def mc_set_allocator(model: Model, kind: str = "torch"):
+    """Route the model's device allocations through PyTorch's caching allocator."""
+    if kind != "torch":
+        raise ValueError("only the 'torch' allocator can be installed from Python")
+    import torch
+
+    device = torch.cuda.current_device()
+
+    def _alloc(nbytes, stream, _ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, _nbytes, _stream, _ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    cbs = (ALLOC_FN(_alloc), FREE_FN(_free))
+    model._callbacks = cbs
+    model._check(load().mc_set_allocator(model.handle, cbs[0], cbs[1], None), "mc_set_allocator")
+
+
+def mc_reserve(model: Model):
+    model._check(load().mc_reserve(model.handle), "mc_reserve")
+
+
+def mc_model_layout(model: Model) -> dict:
+    lay = McLayout()
+    model._check(load().mc_model_layout(model.handle, C.byref(lay)), "mc_model_layout")
+    out = {k: getattr(lay, k) for k, _t in McLayout._fields_ if k != "n_shift"}
+    out["n_shift"] = list(lay.n_shift[: lay.P])
+    model._layout = out
+    return out
+
+
+def _take_trace(h: C.c_void_p):
+    if not h.value:
+        return None
+    L = load(build=False)
+    n = L.mc_trace_length(h)
+    w = L.mc_trace_key_words(h)
+    ptr = L.mc_trace_states(h)
+    words = [ptr[k] for k in range(n * w)]
+    L.mc_trace_free(h)
+    if w == 1:
+        return words
+    return [words[2 * k] | (words[2 * k + 1] << 64) for k in range(n)]
+
+
+def mc_check(model: Model, T: int, trace: bool = True) -> dict:
+    r = McCheckResult()
+    h = C.c_void_p()
+    rc = load().mc_check(model.handle, int(T) & NO_LIMIT, C.byref(r), C.byref(h) if trace else None)
+    model._check(rc, "mc_check")
+    out = {"holds": bool(r.holds), "states": r.states, "levels": r.levels}
+    if not r.holds:
+        key = r.cex_key[0] | (r.cex_key[1] << 64)
+        out.update(cex_time=r.cex_time, cex_i=r.cex_wg_index, cex_j=r.cex_ts_index, cex_wg=r.cex_wg,
+                   cex_ts=r.cex_ts, cex_level=r.cex_level, cex_key=key)
+        if trace:
+            out["trace"] = _take_trace(h)
+    return out
+
+
+def mc_min_time(model: Model, trace: bool = True) -> dict:
+    r = McMinResult()
+    h = C.c_void_p()
+    rc = load().mc_min_time(model.handle, C.byref(r), C.byref(h) if trace else None)
+    model._check(rc, "mc_min_time")
+    out = {"t_min": r.t_min, "t_ini": r.t_ini, "i": r.wg_index, "j": r.ts_index, "wg": r.wg,
+           "ts": r.ts, "states": r.states, "checks": r.checks, "level": r.level,
+           "witness_key": r.witness_key[0] | (r.witness_key[1] << 64)}
+    if trace:
+        out["trace"] = _take_trace(h)
+    return out
+
+
+def mc_count_states(model: Model) -> int:
+    v = C.c_uint64()
+    model._check(load().mc_count_states(model.handle, C.byref(v)), "mc_count_states")
+    return v.value
+
+
+def mc_simulate(model: Model, seed: int, walks: int = 1) -> int:
+    v = C.c_uint64()
+    model._check(load().mc_simulate(model.handle, int(seed) & NO_LIMIT, int(walks), C.byref(v)),
+                 "mc_simulate")
+    return v.value
+
+
+def mc_last_widths(model: Model, cap: int = 1 << 16) -> list:
+    buf = (C.c_uint64 * cap)()
+    n = C.c_uint32()
+    model._check(load().mc_last_widths(model.handle, buf, cap, C.byref(n)), "mc_last_widths")
+    return list(buf[: min(n.value, cap)])
+
+
+def decode_key(layout: dict, key: int):
+    """(i, j, n) of a packed state, i/j 1-based (0 = not selected yet)."""
+    i = (key >> layout["wg_shift"]) & ((1 << layout["wg_bits"]) - 1)
+    j = (key >> layout["ts_shift"]) & ((1 << layout["ts_bits"]) - 1)
+    mask = (1 << layout["n_bits"]) - 1
+    n = tuple((key >> s) & mask for s in layout["n_shift"])
+    return i, j, n

@@ -23,6 +23,7 @@ GREEDY (only the unit whose clock is smallest takes the next work-group):
 """
 from __future__ import annotations
 
+from bisect import bisect_left, bisect_right
 from math import comb
 
 
@@ -54,27 +55,33 @@ def _starts(spec, cfg, upto):
     return sorted((m * t[c], c) for c in range(spec.P) for m in range(upto + 1))
 
 
+def greedy_cfg_widths(spec, cfg):
+    """Level widths C(tie, x) of one configuration for k = 0..N."""
+    N = spec.n_workgroups[cfg]
+    values = [s for s, _c in _starts(spec, cfg, N + 1)]
+    out = []
+    for k in range(N + 1):
+        tau = values[k]
+        below = bisect_left(values, tau)
+        tie = bisect_right(values, tau) - below
+        out.append(comb(tie, k - below))
+    return out
+
+
 def greedy_level_width(spec, cfg, k) -> int:
-    starts = _starts(spec, cfg, k + 1)
-    tau = starts[k][0]
-    below = sum(1 for s, _c in starts if s < tau)
-    tie = sum(1 for s, _c in starts if s == tau)
-    return comb(tie, k - below)
+    return greedy_cfg_widths(spec, cfg)[k]
 
 
 def greedy_count(spec) -> int:
-    total = 1 + spec.a
-    for cfg, N in enumerate(spec.n_workgroups):
-        total += sum(greedy_level_width(spec, cfg, k) for k in range(N + 1))
-    return total
+    return 1 + spec.a + sum(sum(greedy_cfg_widths(spec, cfg)) for cfg in range(spec.a * spec.b))
 
 
 def greedy_widths(spec):
     n_max = max(spec.n_workgroups)
-    w = [1, spec.a]
-    for k in range(n_max + 1):
-        w.append(sum(greedy_level_width(spec, cfg, k)
-                     for cfg, N in enumerate(spec.n_workgroups) if N >= k))
+    w = [1, spec.a] + [0] * (n_max + 1)
+    for cfg in range(spec.a * spec.b):
+        for k, x in enumerate(greedy_cfg_widths(spec, cfg)):
+            w[2 + k] += x
     return w
 
 

@@ -1,0 +1,112 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+The library must load and export every function include/mc.h declares.
+Model creation is host-only (validation, key layout, closed-form sizing), so
+it is exercised here; any query without a CUDA device must fail loudly.
+"""
+import os
+import re
+
+import pytest
+
+import closed_forms as CF
+from paper_2305_09130_gb300 import mc
+from paper_2305_09130_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "mc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\**\s*(mc_[a-z_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return mc.load(build=True)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_options_default(lib):
+    o = mc.mc_options_default()
+    assert (o.prune, o.early_exit, o.search, o.refine, o.sim_walks, o.load_factor_pct) == (1, 1, 0, 1, 1, 50)
+    assert o.sim_seed == 2305091300
+
+
+def layout(spec, **kw):
+    m = mc.mc_model_create(spec, mc.mc_options_default(**kw), allocator=None)
+    return mc.mc_model_layout(m)
+
+
+def test_layout_of_named_workloads(lib):
+    l1 = layout(W.c1())
+    # i+1 in 3 bits (a=5), j+1 in 2 bits (b=3), n_c in 7 bits (N <= 64), P=2
+    assert (l1["wg_bits"], l1["ts_bits"], l1["n_bits"], l1["used_bits"]) == (3, 2, 7, 19)
+    assert (l1["key_bits"], l1["n_shift"], l1["ts_shift"], l1["wg_shift"]) == (64, [7, 0], 14, 16)
+    assert l1["state_bound"] == 8763 and l1["max_level"] == 66
+    l2 = layout(W.c2_star())
+    assert l2["used_bits"] == 4 + 3 + 4 * 7 and l2["key_bits"] == 64
+    assert l2["state_bound"] == CF.count(W.c2_star()) == 10_385_335
+    l3 = layout(W.c3_star())
+    assert l3["key_bits"] == 128 and l3["used_bits"] == 4 + 3 + 8 * 6
+    assert l3["state_bound"] == 1_072_924_481 and l3["max_width"] == 193_344_684
+    assert l3["table_slots"] == 1 << 29 and l3["log_capacity"] == 1_072_924_481
+    lit = layout(W.c3(rule=W.GREEDY))
+    assert lit["used_bits"] == 4 + 3 + 8 * 13 and lit["key_bits"] == 128
+    assert lit["state_bound"] >= CF.count(W.c3(rule=W.GREEDY))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_free_bound_is_the_exact_count(lib, seed):
+    spec = W.random_small(300 + seed, 1 + seed % 5, 3, 2, 9, rule=W.FREE)
+    lay = layout(spec)
+    assert lay["state_bound"] == CF.count(spec)
+    assert lay["max_width"] == max(CF.widths(spec)[3:])
+    g = spec.with_rule(W.GREEDY)
+    assert layout(g)["state_bound"] >= CF.count(g)
+    assert layout(g)["max_width"] >= max(CF.widths(g)[3:])
+
+
+def test_invalid_descriptions(lib):
+    ok = W.c1()
+    cases = [
+        (W.ModelSpec("n0", 2, [1], [1], [0], [1], [1, 1]), mc.MC_ERR_INVAL),
+        (W.ModelSpec("c0", 2, [1], [1], [1], [0], [1, 1]), mc.MC_ERR_INVAL),
+        (W.ModelSpec("s0", 2, [1], [1], [1], [1], [1, 0]), mc.MC_ERR_INVAL),
+        (W.ModelSpec("p17", 17, [1], [1], [1], [1], [1] * 17), mc.MC_ERR_INVAL),
+        (W.ModelSpec("rule", 2, [1], [1], [1], [1], [1, 1], 2), mc.MC_ERR_INVAL),
+        (ok.with_key_bits(32), mc.MC_ERR_INVAL),
+        (W.c3(rule=W.GREEDY).with_key_bits(64), mc.MC_ERR_OVERFLOW),
+        (W.ModelSpec("clock", 2, [1], [1], [1 << 20], [1 << 19], [2, 1]), mc.MC_ERR_OVERFLOW),
+        (W.ModelSpec("wide", 2, list(range(4096)), [1], [1] * 4096, [1] * 4096, [1, 1]), mc.MC_ERR_OVERFLOW),
+    ]
+    for spec, code in cases:
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_model_create(spec, allocator=None)
+        assert e.value.code == code, spec.name
+    with pytest.raises(mc.MCError) as e:
+        mc.mc_model_create(ok, mc.mc_options_default(load_factor_pct=95), allocator=None)
+    assert e.value.code == mc.MC_ERR_INVAL
+
+
+def test_strerror(lib):
+    assert mc.mc_strerror(mc.MC_ERR_TABLE_FULL).startswith("visited set full")
+    assert mc.mc_strerror(-99) == "unknown error"
+
+
+def test_queries_fail_loudly_without_a_gpu(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    m = mc.mc_model_create(W.c1(), allocator=None)
+    with pytest.raises(mc.MCError) as e:
+        mc.mc_count_states(m)
+    assert e.value.code == mc.MC_ERR_CUDA

@@ -1,0 +1,265 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Integer work: every count, level width, threshold decision, minimal time,
+configuration and witness state must be bit-exact.  The parent chain of a
+trace is chosen by racing inserts, so traces are checked by replay
+(tests/replay.py) rather than compared.
+"""
+import json
+import os
+
+import pytest
+
+import closed_forms as CF
+import replay as RP
+from paper_2305_09130_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FREE, GREEDY = W.FREE, W.GREEDY
+NO_LIMIT = (1 << 64) - 1
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_expected.json")
+
+
+def make(mc, spec, **opts):
+    m = mc.mc_model_create(spec, mc.mc_options_default(**opts))
+    return m
+
+
+def gpu_check(mc, model, T, prune=True, early_exit=True, trace=True):
+    mc.mc_set_options(model, mc.mc_options_default(prune=prune, early_exit=early_exit))
+    r = mc.mc_check(model, T, trace=trace)
+    lay = mc.mc_model_layout(model)
+    out = {"holds": r["holds"], "states": r["states"], "levels": r["levels"]}
+    if not r["holds"]:
+        i, j, n = RP.decode(lay, r["cex_key"])
+        assert (i - 1, j - 1) == (r["cex_i"], r["cex_j"])
+        out.update(cex_time=r["cex_time"], cex_i=r["cex_i"], cex_j=r["cex_j"],
+                   cex_level=r["cex_level"], cex_n=n)
+        if trace:
+            keys = r["trace"]
+            assert len(keys) == r["cex_level"] + 1
+            assert keys[-1] == r["cex_key"]
+            t, ti, tj, tn = RP.replay(model.spec, lay, keys, lambda t: t <= T)
+            assert (t, ti, tj, tn) == (r["cex_time"], r["cex_i"], r["cex_j"], n)
+    return out
+
+
+def gpu_min(mc, model, search, prune, seed=2305091300, walks=1, refine=True):
+    mc.mc_set_options(model, mc.mc_options_default(prune=prune, search=search, sim_seed=seed,
+                                                   sim_walks=walks, refine=refine))
+    r = mc.mc_min_time(model)
+    lay = mc.mc_model_layout(model)
+    i, j, n = RP.decode(lay, r["witness_key"])
+    assert (i - 1, j - 1) == (r["i"], r["j"])
+    keys = r["trace"]
+    assert keys[-1] == r["witness_key"] and len(keys) == r["level"] + 1
+    RP.replay(model.spec, lay, keys, lambda t: t == r["t_min"])
+    return {"t_min": r["t_min"], "t_ini": r["t_ini"], "states": r["states"], "checks": r["checks"],
+            "i": r["i"], "j": r["j"], "level": r["level"], "n": n}
+
+
+def thresholds(oracle, spec):
+    t_min = oracle.min_time(spec)["t_min"]
+    return sorted({0, 1, t_min - 1, t_min, t_min + 1, 2 * t_min, 5 * t_min, NO_LIMIT})
+
+
+# ---------------------------------------------------------------- small exact parity
+
+@pytest.mark.parametrize("name,rule", [("tiny", FREE), ("tiny", GREEDY), ("c1", FREE), ("c1", GREEDY)])
+def test_checks_match_oracle(mc, oracle, name, rule):
+    spec = W.NAMED[name](rule)
+    model = make(mc, spec)
+    assert mc.mc_count_states(model) == oracle.count(spec) == CF.count(spec)
+    assert mc.mc_last_widths(model) == CF.widths(spec)
+    for T in thresholds(oracle, spec):
+        for prune in (False, True):
+            for ee in (False, True):
+                got = gpu_check(mc, model, T, prune, ee)
+                exp = oracle.check(spec, T, prune=prune, early_exit=ee)
+                assert got == exp, (T, prune, ee)
+
+
+@pytest.mark.parametrize("name,rule", [("tiny", FREE), ("tiny", GREEDY), ("c1", FREE), ("c1", GREEDY)])
+def test_min_time_matches_oracle(mc, oracle, name, rule):
+    spec = W.NAMED[name](rule)
+    model = make(mc, spec)
+    for search in ("single", "lower", "bisect"):
+        for prune in (False, True):
+            got = gpu_min(mc, model, search, prune)
+            exp = oracle.min_time(spec, search=search, prune=prune)
+            assert got == exp, (search, prune)
+
+
+def sweep_models():
+    out = []
+    seed = 9000
+    shapes = [(1, 3, 2, 12), (2, 2, 3, 9), (3, 3, 2, 7), (4, 2, 2, 6), (5, 2, 2, 5), (6, 2, 1, 4),
+              (7, 1, 2, 4), (8, 2, 2, 3), (9, 1, 1, 3), (12, 1, 2, 2), (16, 2, 1, 2), (16, 1, 1, 3)]
+    for P, a, b, n_max in shapes:
+        for rule in (FREE, GREEDY):
+            for key_bits in (0, 128):
+                out.append(W.random_small(seed, P, a, b, n_max, cost_max=7, speed_max=3, rule=rule,
+                                          key_bits=key_bits))
+                seed += 1
+    return out
+
+
+@pytest.mark.parametrize("spec", sweep_models(), ids=lambda s: f"P{s.P}_r{s.rule}_k{s.key_bits}_{s.meta['seed']}")
+def test_random_models_match_oracle(mc, oracle, spec):
+    model = make(mc, spec)
+    assert mc.mc_model_layout(model)["key_bits"] == (spec.key_bits or 64)
+    assert mc.mc_count_states(model) == oracle.count(spec) == CF.count(spec)
+    assert mc.mc_last_widths(model) == CF.widths(spec)
+    t_min = oracle.min_time(spec)["t_min"]
+    for T in (t_min - 1, t_min, t_min + 3, 3 * t_min):
+        for prune, ee in ((True, True), (False, False), (True, False)):
+            assert gpu_check(mc, model, T, prune, ee) == oracle.check(spec, T, prune=prune, early_exit=ee)
+    for search in ("single", "lower", "bisect"):
+        assert gpu_min(mc, model, search, True) == oracle.min_time(spec, search=search, prune=True)
+
+
+def test_simulation_matches_oracle(mc, oracle):
+    for spec in (W.c1(FREE), W.c1(GREEDY), W.c2(rule=GREEDY), W.c3(rule=GREEDY), W.tiny(GREEDY)):
+        model = make(mc, spec)
+        for seed in (0, 1, 2305091300, 123456789):
+            for walks in (1, 7, 1000):
+                assert mc.mc_simulate(model, seed, walks) == oracle.simulate(spec, seed, walks)
+
+
+def test_key_width_does_not_change_results(mc):
+    spec = W.c1(FREE)
+    a = make(mc, spec)
+    b = make(mc, spec.with_key_bits(128))
+    assert mc.mc_model_layout(b)["key_words"] == 2
+    for T in (60, 79, 80, 200):
+        ra, rb = mc.mc_check(a, T, trace=False), mc.mc_check(b, T, trace=False)
+        ra.pop("cex_key", None)
+        rb.pop("cex_key", None)
+        assert ra == rb
+    assert mc.mc_min_time(a, trace=False)["t_min"] == mc.mc_min_time(b, trace=False)["t_min"]
+
+
+# ---------------------------------------------------------------- named workloads at full size
+
+def golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def test_c2_literal_greedy(mc, oracle):
+    spec = W.c2(rule=GREEDY)
+    g = golden()["c2_greedy"]
+    model = make(mc, spec)
+    assert mc.mc_count_states(model) == g["count"] == CF.count(spec)
+    assert mc.mc_last_widths(model) == CF.widths(spec)
+    for key, exp in g["min_time"].items():
+        search, prune = key.split("/prune")
+        got = gpu_min(mc, model, search, bool(int(prune)))
+        assert got == {k: exp[k] for k in got}, key
+    t_min = g["min_time"]["single/prune1"]["t_min"]
+    for T in (t_min - 1, t_min):
+        assert gpu_check(mc, model, T) == oracle.check(spec, T)
+
+
+def test_c3_literal_greedy_u128(mc, oracle):
+    spec = W.c3(rule=GREEDY)
+    g = golden()["c3_greedy"]
+    model = make(mc, spec)
+    assert mc.mc_model_layout(model)["key_words"] == 2
+    assert mc.mc_count_states(model) == g["count"] == CF.count(spec)
+    got = gpu_min(mc, model, "single", True)
+    exp = g["min_time"]["single/prune1"]
+    assert got == {k: exp[k] for k in got}
+    assert got["t_min"] == CF.tmin(spec)[0]
+
+
+def test_c2_star_full(mc):
+    spec = W.c2_star()
+    g = golden()["c2_star"]
+    model = make(mc, spec)
+    assert mc.mc_count_states(model) == 10_385_335 == g["count"]
+    assert mc.mc_last_widths(model) == CF.widths(spec)
+    t_min, argmins = CF.tmin(spec)
+    for key, exp in g["min_time"].items():
+        search, prune = key.split("/prune")
+        got = gpu_min(mc, model, search, bool(int(prune)))
+        assert got == {k: exp[k] for k in got}, key
+        assert got["t_min"] == t_min and (got["i"], got["j"]) in argmins
+
+
+def test_c3_star_full(mc):
+    """1,072,924,481 states with 128-bit keys, in the bench's launch shape."""
+    spec = W.c3_star()
+    model = make(mc, spec)
+    lay = mc.mc_model_layout(model)
+    assert lay["key_words"] == 2 and lay["max_width"] == 193_344_684
+    assert mc.mc_count_states(model) == 1_072_924_481 == CF.count(spec)
+    assert mc.mc_last_widths(model) == CF.widths(spec)
+    t_min, argmins = CF.tmin(spec)
+    got = gpu_min(mc, model, "single", True)
+    assert got["t_min"] == t_min
+    # the witness comes from the first BFS level holding a T_min terminal:
+    # the optimal configurations with the fewest work-groups
+    n_of = lambda ij: spec.n_workgroups[ij[0] * spec.b + ij[1]]
+    first = min(n_of(ij) for ij in argmins)
+    assert (got["i"], got["j"]) == min(ij for ij in argmins if n_of(ij) == first)
+    assert got["level"] == first + 2
+
+
+# ---------------------------------------------------------------- edge cases and errors
+
+def test_degenerate_models(mc, oracle):
+    cases = [
+        W.ModelSpec("one", 1, [1], [1], [1], [1], [1]),
+        W.ModelSpec("one_g", 1, [1], [1], [1], [1], [1], GREEDY),
+        W.ModelSpec("p16", 16, [1, 2], [1], [3, 1], [2, 5], list(range(1, 17))),
+        W.ModelSpec("p16g", 16, [1, 2], [1], [20, 1], [2, 5], [1] * 16, GREEDY),
+        W.ModelSpec("wide_ab", 2, list(range(1, 41)), list(range(1, 31)),
+                    [1 + (k % 3) for k in range(1200)], [1 + (k % 5) for k in range(1200)], [1, 2]),
+    ]
+    for spec in cases:
+        model = make(mc, spec)
+        assert mc.mc_count_states(model) == oracle.count(spec) == CF.count(spec), spec.name
+        for T in (0, 1, 3, NO_LIMIT):
+            assert gpu_check(mc, model, T) == oracle.check(spec, T), (spec.name, T)
+        assert gpu_min(mc, model, "single", True) == oracle.min_time(spec), spec.name
+
+
+def test_threshold_zero_keeps_only_selects(mc):
+    spec = W.c1(FREE)
+    model = make(mc, spec)
+    r = gpu_check(mc, model, 0, prune=True, early_exit=True)
+    assert r == {"holds": True, "states": 1 + spec.a + spec.a * spec.b, "levels": 3}
+
+
+def test_table_full_is_reported(mc):
+    model = make(mc, W.c1(FREE), table_log2=3, max_probes=2)
+    with pytest.raises(mc.MCError) as e:
+        mc.mc_count_states(model)
+    assert e.value.code == mc.MC_ERR_TABLE_FULL
+
+
+def test_frontier_overflow_is_reported(mc):
+    model = make(mc, W.c1(FREE), log_capacity=100)
+    with pytest.raises(mc.MCError) as e:
+        mc.mc_count_states(model)
+    assert e.value.code == mc.MC_ERR_FRONTIER
+
+
+def test_barrier_timeout_is_reported_and_context_survives(mc):
+    # every device-wide wait expects one arrival that never comes: each block
+    # gives up after 0.2 s of %globaltimer and the pass returns MC_ERR_TIMEOUT
+    model = make(mc, W.c1(FREE), debug_barrier_extra=1, barrier_timeout_ns=200_000_000)
+    with pytest.raises(mc.MCError) as e:
+        mc.mc_count_states(model)
+    assert e.value.code == mc.MC_ERR_TIMEOUT
+    fresh = make(mc, W.c1(FREE))
+    assert mc.mc_count_states(fresh) == 8763
+
+
+def test_invalid_descriptions_are_rejected(mc):
+    bad = W.ModelSpec("bad", 2, [1], [1], [0], [1], [1, 1])
+    with pytest.raises(mc.MCError) as e:
+        mc.mc_model_create(bad)
+    assert e.value.code == mc.MC_ERR_INVAL
