@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the explorer: unique states/s and time-to-optimal-config.
+
+One step = one ``mc_min_time`` query of the medium workload (C2 at G=80:
+P=4 compute units, WG in 2^0..2^8, TS in 2^0..2^4, FREE dispatch, formula
+cost, per-unit speeds U{1..3} from splitmix64 seed 2305091302; 10,385,335
+reachable states) with iterative threshold lowering and no pruning -- each
+check explores like an exhaustive verifier and stops at its first
+counterexample level, and the last check (T_min - 1, which holds) explores
+every reachable state.  A step covers every stage of the path: the WG/TS
+selects, level expansion, visited-set inserts, the property on terminals,
+the min-reduction and threshold refinement, and the witness trace.
+
+Output: one JSON line (rank 0).  ``value`` = unique states explored per
+second of device time with the model resident in HBM; ``e2e`` = the same
+metric through the public C-ABI calls from host buffers (create, query,
+destroy); ``roofline`` = the exploration kernel's algorithmic bytes per
+launch over its event-timed duration against the measured HBM copy peak;
+``cpu_baseline`` = the CPU oracle on a bounded sample of the same workload.
+
+``--impl reference`` times the CPU oracle instead (the method's plain CPU
+restatement) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2305_09130_gb300 import workloads as W  # noqa: E402
+
+METRIC = "unique states/sec"
+UNIT = "states/s"
+WORKLOAD = ("c2_star: G=80, P=4, WG 2^0..2^8, TS 2^0..2^4, FREE dispatch, cost ceil(WG/TS)*4+WG+2*TS, "
+            "speeds U{1..3} (splitmix64 seed 2305091302); 10,385,335 reachable states")
+REFERENCE_SAMPLE_T = 300     # pruned check of the same model: ~0.74M states
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SRC = os.path.join(ROOT, "paper_2305_09130_gb300", "csrc", "mc_kernels.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "explore_kernel_c2star_traffic.txt")
+
+
+# ---------------------------------------------------------------- distributed helpers
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def dist_init(world: int, use_cuda: bool):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend="nccl" if use_cuda else "gloo")
+    return dist
+
+
+def reduce_scalar(x: float, op: str, device=None) -> float:
+    """max or sum of a scalar over all ranks (identity with one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ---------------------------------------------------------------- clocks during the timed region
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], [], set()
+        with open(self.path) as f:
+            for line in f:
+                cols = [c.strip() for c in line.split(",")]
+                if len(cols) < 9:
+                    continue
+                try:
+                    sm.append(float(cols[1]))
+                    mx.append(float(cols[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(self.NAMES, cols[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline inputs
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def algorithmic_bytes_per_state(P: int, key_words: int) -> int:
+    """Per unique state: P random 32-byte bucket reads (a FREE state is
+    generated once per unit, in-degree ~ P), one 32-byte sector written back
+    for its slot, its key written to and read back from the frontier log, and
+    its 4-byte parent index."""
+    return 32 * P + 32 + 2 * 8 * key_words + 4
+
+
+def kernel_source_hash() -> str:
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic_per_launch():
+    """dram bytes per exploration launch from the committed ncu summary, or
+    None when the summary is missing or was taken on another kernel source."""
+    try:
+        fields = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip()
+        if fields.get("kernel_source_sha256_16") != kernel_source_hash():
+            return None
+        return float(fields["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- arms
+def cpu_baseline_sample(spec, t_min: int) -> dict:
+    """The oracle as it stands on the holding check check(T_min - 1) of the
+    workload without pruning: a full DFS over every reachable state."""
+    from oracle import oracle as O
+    O.build()
+    t0 = time.perf_counter()
+    r = O.check(spec, t_min - 1, prune=False, early_exit=True)
+    dt = time.perf_counter() - t0
+    return {"value": r["states"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle DFS (std::unordered_set) over check(T_min-1={t_min - 1}) of c2_star "
+                      f"without pruning: {r['states']} states in {dt:.2f} s, single thread"}
+
+
+def run_reference(args):
+    rank, world, _local = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    O.build()
+    spec = W.c2_star()
+
+    def step():
+        t0 = time.perf_counter()
+        r = O.check(spec, REFERENCE_SAMPLE_T, prune=True, early_exit=False)
+        return r["states"], time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        step()
+    states = 0
+    secs = 0.0
+    for _ in range(args.steps):
+        s, dt = step()
+        states += s
+        secs += dt
+    value = states / secs
+    sample = (f"each step: oracle DFS over check(T={REFERENCE_SAMPLE_T}) of c2_star with pruning, "
+              f"{states // max(args.steps, 1)} states, single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2305_09130_gb300 import mc
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist_init(world, True)
+    spec = W.c2_star()
+    opts = mc.mc_options_default(search=args.mode, prune=args.prune, timing=1)
+    stream = torch.cuda.Stream(device)
+    model = mc.mc_model_create(spec, opts, allocator="torch", stream=stream)
+    mc.mc_reserve(model)
+    layout = mc.mc_model_layout(model)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > 129 MB of L2
+
+    def flush_l2(k):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+
+    ref = None
+    for w in range(args.warmup):
+        flush_l2(w)
+        ref = mc.mc_min_time(model, trace=True)
+    expect = (96, 8, 4)  # T_min and (WG, TS) of this workload, from the oracle
+    if ref is not None and (ref["t_min"], ref["wg"], ref["ts"]) != expect:
+        raise SystemExit(f"wrong result {ref} != {expect}")
+
+    mc.mc_reset_stats(model)
+    torch.cuda.synchronize()
+    barrier(device)
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush_l2(k)
+        ev[k][0].record(stream)
+        r = mc.mc_min_time(model, trace=True)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier(device)
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    st = mc.mc_get_stats(model)
+    dev_ms = sum(step_ms)
+    states_local = st["states"]
+    dev_ms_max = reduce_scalar(dev_ms, "max", device)
+    states_all = reduce_scalar(states_local, "sum", device)
+    value = states_all / (dev_ms_max / 1000.0)
+
+    # roofline of the exploration kernel (events on the model's stream)
+    bps = algorithmic_bytes_per_state(spec.P, layout["key_words"])
+    launches = st["explore_launches"]
+    achieved = bps * st["states"] / (st["explore_ms"] / 1000.0) / 1e9
+    peak, peak_kind = measured_hbm_peak()
+    traffic = ncu_traffic_per_launch()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "algorithmic_bytes_per_launch": bps * st["states"] / max(launches, 1),
+                "bytes_per_state": bps, "states_per_launch": st["states"] / max(launches, 1),
+                "avg_launch_ms": st["explore_ms"] / max(launches, 1),
+                "kernel": f"explore_kernel<u{64 * layout['key_words']}, tile {4}, FREE>",
+                "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+                               if peak_kind == "measured" else "fallback 6.8 TB/s"}
+    gpu_launches = st["explore_launches"] + st["other_launches"]
+
+    # end to end through the public C-ABI from host buffers: create (H2D of
+    # the model arrays through pinned staging), query, read results, destroy
+    e2e_s = []
+    h2d = d2h = 0
+    for k in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m2 = mc.mc_model_create(spec, opts, allocator="torch", stream=stream)
+        r2 = mc.mc_min_time(m2, trace=True)
+        s2 = mc.mc_get_stats(m2)
+        mc.mc_model_destroy(m2)
+        e2e_s.append(time.perf_counter() - t0)
+        h2d += s2["h2d_bytes"]
+        d2h += s2["d2h_bytes"]
+        assert r2["t_min"] == r["t_min"]
+    e2e_total = reduce_scalar(sum(e2e_s), "max", device)
+    e2e_value = states_all / e2e_total
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded model description; no dataset)",
+        "config": {"workload": WORKLOAD,
+                   "query": f"mc_min_time search={args.mode} prune={int(args.prune)} early_exit=1 "
+                            f"(iterative threshold lowering from the simulated T_ini)",
+                   "l2": "flushed between steps (256 MiB write, untimed)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "states_per_step": states_local / args.steps,
+                   "checks_per_step": r["checks"]},
+        "time_to_optimal_config_ms": dev_ms_max / args.steps,
+        "result": {"t_min": r["t_min"], "wg": r["wg"], "ts": r["ts"], "t_ini": r["t_ini"]},
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
+                "d2h_bytes_per_step": d2h // args.steps,
+                "ms_per_step": 1000.0 * e2e_total / args.steps},
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(spec, r["t_min"])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    mc.mc_model_destroy(model)
+    return 0
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--mode", choices=["single", "lower", "bisect"], default="lower")
+    p.add_argument("--prune", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    args = p.parse_args(argv)
+    if args.warmup < 3:
+        p.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -107,7 +107,7 @@ typedef struct {
   uint32_t load_factor_pct;     /* visited-set load-factor cap, 10..90       */
   uint32_t table_log2;          /* 0: size the visited set from the bound;
                                    else 2^table_log2 slots                   */
-  uint32_t threads_per_block;   /* 0: 256; else 64..1024, multiple of 32     */
+  uint32_t threads_per_block;   /* 0: 256; else 64..256, multiple of 32      */
   uint32_t blocks_per_sm;       /* 0: occupancy maximum                      */
   uint32_t max_probes;          /* 0: whole table; else bucket probe limit   */
   uint64_t log_capacity;        /* 0: closed-form bound; else states kept in
@@ -117,7 +117,9 @@ typedef struct {
                                    expect that many extra arrivals, so it
                                    times out and the query returns
                                    MC_ERR_TIMEOUT.  Keep 0.                 */
-  uint32_t reserved[7];
+  uint32_t timing;              /* 1: time every exploration kernel with CUDA
+                                   events on the model's stream (mc_get_stats) */
+  uint32_t reserved[6];
 } mc_options;
 
 /* Result of mc_check (Section 4, Step 2: Phi = G(FIN -> time > T)). */
@@ -167,11 +169,22 @@ typedef struct {
   uint64_t device_bytes; /* device memory the model needs                  */
 } mc_layout;
 
+/* Counters accumulated over the model's queries (reset by mc_reset_stats). */
+typedef struct {
+  uint64_t explore_launches; /* exploration kernel launches                  */
+  uint64_t other_launches;   /* simulation kernel launches                   */
+  uint64_t states;           /* unique states summed over those launches     */
+  uint64_t h2d_bytes;        /* host -> device bytes copied                  */
+  uint64_t d2h_bytes;        /* device -> host bytes copied                  */
+  double explore_ms;         /* summed CUDA-event time of the exploration
+                                kernels (only with mc_options.timing = 1)    */
+} mc_stats;
+
 typedef void* (*mc_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*mc_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
 
 /* Fill *opt with the defaults: prune 1, early_exit 1, search SINGLE,
- * refine 1, sim_seed 2305091300, sim_walks 1, load_factor_pct 50, the rest 0. */
+ * refine 1, sim_seed 2305091300, sim_walks 1, load_factor_pct 25, the rest 0. */
 void mc_options_default(mc_options* opt);
 
 /* Validate and copy the description; compute the key layout and the
@@ -234,6 +247,12 @@ int mc_simulate(mc_model* m, uint64_t seed, uint32_t walks, uint64_t* t_ini);
 /* Per-level widths of the model's last exploration; *n receives the level
  * count and up to cap widths are copied.  Errors: INVAL, CUDA. */
 int mc_last_widths(mc_model* m, uint64_t* out, uint32_t cap, uint32_t* n);
+
+/* Copy the model's counters into *out.  Errors: INVAL. */
+int mc_get_stats(const mc_model* m, mc_stats* out);
+
+/* Zero the model's counters.  Errors: INVAL. */
+int mc_reset_stats(mc_model* m);
 
 /* Trace accessors: states s0 .. witness, each key_words u64 ({lo, hi}). */
 int mc_trace_length(const mc_trace* t);

@@ -86,11 +86,16 @@ struct mc_model {
   uint32_t* d_log_par = nullptr;
   uint8_t* d_ctrl_block = nullptr;
   Ctrl* d_ctrl = nullptr;
-  uint64_t *d_width = nullptr, *d_off = nullptr, *d_best = nullptr, *d_trace = nullptr;
+  uint32_t* d_bar = nullptr;
+  uint64_t *d_levels = nullptr, *d_off = nullptr, *d_trace = nullptr;
   uint64_t *d_tini = nullptr, *d_tmin = nullptr;
   Ctrl* h_ctrl = nullptr;       // pinned [kSlots]
   uint64_t* h_trace = nullptr;  // pinned [(max_level + 2) * 2]
   uint64_t* h_scalar = nullptr; // pinned [4]
+  uint32_t* h_params = nullptr; // pinned staging of N, cost, speed
+  cudaEvent_t ev[2 * kSlots] = {};
+  bool ev_pending[kSlots] = {};
+  mc_stats stats{};
   std::string last_err;
   uint32_t last_levels = 0;
   Params params{};
@@ -148,9 +153,15 @@ void release(mc_model* m) {
   if (m->h_ctrl) cudaFreeHost(m->h_ctrl);
   if (m->h_trace) cudaFreeHost(m->h_trace);
   if (m->h_scalar) cudaFreeHost(m->h_scalar);
+  if (m->h_params) cudaFreeHost(m->h_params);
+  for (cudaEvent_t& e : m->ev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
   m->h_ctrl = nullptr;
   m->h_trace = nullptr;
   m->h_scalar = nullptr;
+  m->h_params = nullptr;
   m->reserved = false;
 }
 
@@ -158,7 +169,7 @@ bool valid_options(const mc_options* o) {
   if (o->load_factor_pct < 10 || o->load_factor_pct > 90) return false;
   if (o->sim_walks == 0) return false;
   if (o->search > MC_SEARCH_BISECT) return false;
-  if (o->threads_per_block && (o->threads_per_block < 64 || o->threads_per_block > 512 ||
+  if (o->threads_per_block && (o->threads_per_block < 64 || o->threads_per_block > mc::kThreads ||
                                o->threads_per_block % 32))
     return false;
   if (o->table_log2 && (o->table_log2 < 3 || o->table_log2 > 40)) return false;
@@ -184,7 +195,7 @@ int size_buffers(mc_model* m) {
   if (slots < per_bucket) slots = per_bucket;
   m->table_slots = slots;
   const uint64_t key_bytes = 8ull * m->key_words;
-  const uint64_t ctrl_bytes = sizeof(Ctrl) + 8ull * (m->max_level + 2) * 5 + 64;
+  const uint64_t ctrl_bytes = 256 + mc::kBarBytes + 8ull * (m->max_level + 2) * 5 + 64;
   uint64_t total = mul_sat(slots, key_bytes);
   total = add_sat(total, mul_sat(m->log_cap, key_bytes + 4));
   total = add_sat(total, ctrl_bytes + 4ull * (2ull * m->a * m->b + m->P));
@@ -207,7 +218,7 @@ int reserve(mc_model* m) {
     m->last_err = "device lacks cooperative launch";
     return MC_ERR_CUDA;
   }
-  m->threads = m->opt.threads_per_block ? (int)m->opt.threads_per_block : 256;
+  m->threads = m->opt.threads_per_block ? (int)m->opt.threads_per_block : (int)mc::kThreads;
   int bps = 0;
   if (mc::explore_kernel_occupancy(m->key_words, m->tile, m->rule, m->threads, &bps) || bps < 1) {
     m->last_err = "occupancy query failed";
@@ -224,7 +235,7 @@ int reserve(mc_model* m) {
   m->d_log_keys = dev_alloc(m, m->log_cap * key_bytes);
   m->d_log_par = (uint32_t*)dev_alloc(m, m->log_cap * 4);
   const size_t L2 = m->max_level + 2;
-  const size_t ctrl_bytes = 256 + 8 * L2 * 3 + 16 * L2 + 64;
+  const size_t ctrl_bytes = 256 + mc::kBarBytes + 16 * L2 + 8 * L2 + 16 * L2 + 64;
   m->d_ctrl_block = (uint8_t*)dev_alloc(m, ctrl_bytes);
   if (!m->d_params || !m->d_table || !m->d_log_keys || !m->d_log_par || !m->d_ctrl_block) {
     release(m);
@@ -233,11 +244,11 @@ int reserve(mc_model* m) {
   uint8_t* q = m->d_ctrl_block;
   m->d_ctrl = (Ctrl*)q;
   q += 256;
-  m->d_width = (uint64_t*)q;
-  q += 8 * L2;
+  m->d_bar = (uint32_t*)q;
+  q += mc::kBarBytes;
+  m->d_levels = (uint64_t*)q;
+  q += 16 * L2;
   m->d_off = (uint64_t*)q;
-  q += 8 * L2;
-  m->d_best = (uint64_t*)q;
   q += 8 * L2;
   m->d_trace = (uint64_t*)q;
   q += 16 * L2;
@@ -246,16 +257,18 @@ int reserve(mc_model* m) {
 
   if (cudaMallocHost((void**)&m->h_ctrl, sizeof(Ctrl) * kSlots) != cudaSuccess ||
       cudaMallocHost((void**)&m->h_trace, 16 * L2) != cudaSuccess ||
-      cudaMallocHost((void**)&m->h_scalar, 32) != cudaSuccess) {
+      cudaMallocHost((void**)&m->h_scalar, 32) != cudaSuccess ||
+      cudaMallocHost((void**)&m->h_params, np * 4) != cudaSuccess) {
     cudaGetLastError();
     release(m);
     return MC_ERR_NOMEM;
   }
-  std::vector<uint32_t> host(np);
-  std::copy(m->N.begin(), m->N.end(), host.begin());
-  std::copy(m->cost.begin(), m->cost.end(), host.begin() + (size_t)m->a * m->b);
-  std::copy(m->speed.begin(), m->speed.end(), host.begin() + 2ull * m->a * m->b);
-  MC_CUDA(m, cudaMemcpyAsync(m->d_params, host.data(), np * 4, cudaMemcpyHostToDevice, m->stream));
+  for (cudaEvent_t& e : m->ev) MC_CUDA(m, cudaEventCreate(&e));
+  std::copy(m->N.begin(), m->N.end(), m->h_params);
+  std::copy(m->cost.begin(), m->cost.end(), m->h_params + (size_t)m->a * m->b);
+  std::copy(m->speed.begin(), m->speed.end(), m->h_params + 2ull * m->a * m->b);
+  MC_CUDA(m, cudaMemcpyAsync(m->d_params, m->h_params, np * 4, cudaMemcpyHostToDevice, m->stream));
+  m->stats.h2d_bytes += np * 4;
   MC_CUDA(m, cudaStreamSynchronize(m->stream));
 
   Params& p = m->params;
@@ -300,31 +313,46 @@ int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, 
   A.log_par = m->d_log_par;
   A.log_cap = m->log_cap;
   A.ctrl = m->d_ctrl;
-  A.width = m->d_width;
+  A.levels = m->d_levels;
   A.off = m->d_off;
-  A.best = m->d_best;
   A.trace = m->d_trace;
   A.T = T;
   A.T_src = T_src;
   A.T_delta = delta;
   A.tmin_out = tmin_out;
-  A.barrier_target = (uint32_t)m->grid + m->opt.debug_barrier_extra;
+  A.barrier_extra = m->opt.debug_barrier_extra;
+  A.bar_groups = m->d_bar;
   A.timeout_ns = m->opt.barrier_timeout_ns ? m->opt.barrier_timeout_ns : 60ull * 1000000000ull;
-  MC_CUDA(m, cudaMemsetAsync(m->d_ctrl, 0, sizeof(Ctrl), m->stream));
+  MC_CUDA(m, cudaMemsetAsync(m->d_ctrl, 0, 256 + mc::kBarBytes, m->stream));
+  if (m->opt.timing) MC_CUDA(m, cudaEventRecord(m->ev[2 * slot], m->stream));
   MC_CUDA(m, mc::launch_explore(m->key_words, m->tile, m->rule, m->grid, m->threads, A, m->stream));
+  if (m->opt.timing) {
+    MC_CUDA(m, cudaEventRecord(m->ev[2 * slot + 1], m->stream));
+    m->ev_pending[slot] = true;
+  }
   MC_CUDA(m, cudaMemcpyAsync(&m->h_ctrl[slot], m->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost,
                              m->stream));
+  m->stats.d2h_bytes += sizeof(Ctrl);
+  m->stats.explore_launches += 1;
   return MC_OK;
 }
 
 int sync(mc_model* m) {
   MC_CUDA(m, cudaStreamSynchronize(m->stream));
+  for (int s = 0; s < kSlots; ++s) {
+    if (!m->ev_pending[s]) continue;
+    float ms = 0.f;
+    MC_CUDA(m, cudaEventElapsedTime(&ms, m->ev[2 * s], m->ev[2 * s + 1]));
+    m->stats.explore_ms += ms;
+    m->ev_pending[s] = false;
+  }
   return MC_OK;
 }
 
 int pass_error(mc_model* m, int slot) {
   const Ctrl& c = m->h_ctrl[slot];
   m->last_levels = c.levels;
+  m->stats.states += c.states;
   return c.err ? (int)c.err : MC_OK;  // the kernel stores the negative MC_ERR_* code
 }
 
@@ -368,6 +396,7 @@ void fill_check(const mc_model* m, const Ctrl& c, mc_check_result* out) {
 int run_simulation(mc_model* m, uint64_t seed, uint32_t walks, uint64_t* dst) {
   MC_CUDA(m, cudaMemsetAsync(dst, 0xFF, 8, m->stream));
   MC_CUDA(m, mc::launch_simulate(m->params, seed, walks, dst, m->stream));
+  m->stats.other_launches += 1;
   return MC_OK;
 }
 
@@ -390,7 +419,7 @@ void mc_options_default(mc_options* o) {
   o->refine = 1;
   o->sim_seed = 2305091300ull;
   o->sim_walks = 1;
-  o->load_factor_pct = 50;
+  o->load_factor_pct = 25;
 }
 
 int mc_model_create(const mc_model_desc* d, const mc_options* opt, mc_model** out) {
@@ -553,7 +582,10 @@ int mc_check(mc_model* m, uint64_t T, mc_check_result* out, mc_trace** cex) {
   MC_TRY(reserve(m));
   MC_TRY(enqueue_pass(m, T, nullptr, 0, m->opt.prune, m->opt.early_exit, true, nullptr, 0));
   const size_t L2 = m->max_level + 2;
-  if (cex) MC_CUDA(m, cudaMemcpyAsync(m->h_trace, m->d_trace, 16 * L2, cudaMemcpyDeviceToHost, m->stream));
+  if (cex) {
+    MC_CUDA(m, cudaMemcpyAsync(m->h_trace, m->d_trace, 16 * L2, cudaMemcpyDeviceToHost, m->stream));
+    m->stats.d2h_bytes += 16 * L2;
+  }
   MC_TRY(sync(m));
   MC_TRY(pass_error(m, 0));
   fill_check(m, m->h_ctrl[0], out);
@@ -578,6 +610,7 @@ int mc_simulate(mc_model* m, uint64_t seed, uint32_t walks, uint64_t* t_ini) {
   MC_TRY(reserve(m));
   MC_TRY(run_simulation(m, seed, walks, m->d_tini));
   MC_CUDA(m, cudaMemcpyAsync(m->h_scalar, m->d_tini, 8, cudaMemcpyDeviceToHost, m->stream));
+  m->stats.d2h_bytes += 8;
   MC_TRY(sync(m));
   *t_ini = m->h_scalar[0];
   return MC_OK;
@@ -606,7 +639,11 @@ int mc_min_time(mc_model* m, mc_min_result* out, mc_trace** trace) {
     MC_TRY(enqueue_pass(m, 0, m->d_tmin, 0, prune, ee, true, nullptr, slot));
     final_slot = slot;
     MC_CUDA(m, cudaMemcpyAsync(m->h_scalar, m->d_tini, 8, cudaMemcpyDeviceToHost, m->stream));
-    if (trace) MC_CUDA(m, cudaMemcpyAsync(m->h_trace, m->d_trace, 16 * L2, cudaMemcpyDeviceToHost, m->stream));
+    m->stats.d2h_bytes += 8;
+    if (trace) {
+      MC_CUDA(m, cudaMemcpyAsync(m->h_trace, m->d_trace, 16 * L2, cudaMemcpyDeviceToHost, m->stream));
+      m->stats.d2h_bytes += 16 * L2;
+    }
     MC_TRY(sync(m));
     out->t_ini = m->h_scalar[0];
     for (int s = 0; s <= final_slot; ++s) {
@@ -624,6 +661,7 @@ int mc_min_time(mc_model* m, mc_min_result* out, mc_trace** trace) {
     }
   } else {
     MC_CUDA(m, cudaMemcpyAsync(m->h_scalar, m->d_tini, 8, cudaMemcpyDeviceToHost, m->stream));
+    m->stats.d2h_bytes += 8;
     MC_TRY(sync(m));
     out->t_ini = m->h_scalar[0];
     // run one check, keep its header in `slot`
@@ -674,6 +712,7 @@ int mc_min_time(mc_model* m, mc_min_result* out, mc_trace** trace) {
     final_slot = last;
     if (trace) {
       MC_CUDA(m, cudaMemcpyAsync(m->h_trace, m->d_trace, 16 * L2, cudaMemcpyDeviceToHost, m->stream));
+      m->stats.d2h_bytes += 16 * L2;
       MC_TRY(sync(m));
     }
   }
@@ -696,8 +735,23 @@ int mc_last_widths(mc_model* m, uint64_t* out, uint32_t cap, uint32_t* n) {
   if (!m->reserved || cap == 0) return MC_OK;
   DeviceGuard g(m->device);
   const uint32_t k = std::min(cap, *n);
-  MC_CUDA(m, cudaMemcpyAsync(out, m->d_width, 8ull * k, cudaMemcpyDeviceToHost, m->stream));
+  std::vector<uint64_t> rec(2ull * k);
+  MC_CUDA(m, cudaMemcpyAsync(rec.data(), m->d_levels, 16ull * k, cudaMemcpyDeviceToHost, m->stream));
+  m->stats.d2h_bytes += 16ull * k;
   MC_TRY(sync(m));
+  for (uint32_t l = 0; l < k; ++l) out[l] = rec[2 * l];
+  return MC_OK;
+}
+
+int mc_get_stats(const mc_model* m, mc_stats* out) {
+  if (!m || !out) return MC_ERR_INVAL;
+  *out = m->stats;
+  return MC_OK;
+}
+
+int mc_reset_stats(mc_model* m) {
+  if (!m) return MC_ERR_INVAL;
+  m->stats = mc_stats{};
   return MC_OK;
 }
 

@@ -11,6 +11,13 @@ constexpr uint32_t kMaxP = 16;
 constexpr uint64_t kNone = ~0ull;          // "no value" for packed minima
 constexpr int kPackIdxBits = 12;           // i and j fields of a packed (time, i, j)
 constexpr uint32_t kNoParent = 0xFFFFFFFFu;
+constexpr uint32_t kThreads = 256;         // exploration kernel block size (maximum)
+constexpr uint32_t kWarpCap = 128;         // winners staged per warp before a flush
+constexpr uint32_t kBarGroups = 16;        // first-level counters of the device-wide barrier
+constexpr uint32_t kBarTop = kBarGroups;   // 128-byte line of the top counter
+constexpr uint32_t kBarGen = kBarGroups + 1;    // line of the generation word
+constexpr uint32_t kBarAbort = kBarGroups + 2;  // line of the abort flag
+constexpr size_t kBarBytes = (kBarGroups + 4) * 128;
 
 // Packed (time, i, j) used for device-side min-reductions: time < 2^40,
 // i, j < 2^12.
@@ -43,9 +50,7 @@ struct Params {
 // Per-pass control block header (device memory, zeroed before each pass).
 struct Ctrl {
   uint32_t err;           // first error code of the pass (0 = none)
-  uint32_t bar_count;     // device-wide barrier arrivals
-  uint32_t bar_gen;       // device-wide barrier generation
-  uint32_t bar_abort;     // set when a barrier wait timed out
+  uint32_t pad0[3];
   uint32_t levels;        // last explored level + 1
   uint32_t stop_level;    // first level holding a violating terminal (0 = none)
   uint32_t witness_level; // level the witness was taken from (0 = none)
@@ -73,16 +78,16 @@ struct ExploreArgs {
   uint32_t* log_par;      // parent index inside the previous level
   uint64_t log_cap;
   Ctrl* ctrl;
-  uint64_t* width;        // [max_level + 2] kept states per level
+  uint64_t* levels;       // [max_level + 2] x {kept states, min packed violating terminal}
   uint64_t* off;          // [max_level + 2] first log entry of each level
-  uint64_t* best;         // [max_level + 2] min packed violating terminal per level
   uint64_t* trace;        // [(max_level + 1) * 2] trace keys {lo, hi}
   uint64_t T;             // threshold, unless T_src is set
   const uint64_t* T_src;  // device threshold source (T = *T_src + T_delta)
   int64_t T_delta;
   uint64_t* tmin_out;     // if set: receives pack_time(best_pack) at the end
-  uint32_t barrier_target;// arrivals that complete a device-wide barrier
+  uint32_t barrier_extra; // extra top-level arrivals a barrier waits for (test hook)
   uint32_t pad;
+  uint32_t* bar_groups;   // kBarGroups counters, 128 bytes apart (zeroed per pass)
   uint64_t timeout_ns;
 };
 

@@ -50,6 +50,14 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
 __device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void ld_relaxed_v2u64(const uint64_t* p, uint64_t& a, uint64_t& b) {
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -205,36 +213,46 @@ __device__ int visited_insert(K* table, uint64_t bucket_mask, uint32_t max_probe
 }
 
 // ------------------------------------------------------------------ device-wide barrier
-// All blocks are co-resident (cooperative launch).  Each wait is bounded by
+// All blocks are co-resident (cooperative launch).  Arrivals are counted in
+// two levels -- kBarGroups group counters, then a top counter, each in its
+// own 128-byte line -- so hundreds of blocks do not serialise on one address.
+// Counters only grow: the k-th barrier of a pass (k = 1, 2, ...) completes
+// when a group counter reaches k * members and the top counter k * groups,
+// and the last arriver publishes generation k with a release store.  Every
+// block passes the same sequence of barriers, so each tracks k itself.
+// Arrivals use acquire-release atomics after __syncthreads, waiters an
+// acquire load, so no separate fences are needed.  Each wait is bounded by
 // timeout_ns of %globaltimer; on expiry the block records MC_ERR_TIMEOUT,
-// raises bar_abort so the other waiters leave too, and returns false.
-__device__ bool grid_sync(const ExploreArgs& A) {
+// raises the abort flag so the other waiters leave too, and returns false.
+__device__ bool grid_sync(const ExploreArgs& A, uint32_t& epoch) {
   __shared__ uint32_t s_ok;
-  Ctrl* ctrl = A.ctrl;
   __syncthreads();
+  const uint32_t target = ++epoch;
   if (threadIdx.x == 0) {
     uint32_t ok = 1;
-    uint32_t gen = ld_acquire_u32(&ctrl->bar_gen);
-    __threadfence();
-    uint32_t arrived = atomicAdd(&ctrl->bar_count, 1u) + 1;
-    if (arrived == A.barrier_target) {
-      atomicExch(&ctrl->bar_count, 0u);
-      st_release_u32(&ctrl->bar_gen, gen + 1);
-    } else {
-      uint64_t t0 = globaltimer();
-      uint32_t spins = 0;
-      while (ld_acquire_u32(&ctrl->bar_gen) == gen) {
-        if (ld_relaxed_u32(&ctrl->bar_abort)) { ok = 0; break; }
-        if ((++spins & 15u) == 0 && globaltimer() - t0 > A.timeout_ns) {
-          set_error(ctrl, MC_ERR_TIMEOUT);
-          atomicExch(&ctrl->bar_abort, 1u);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
+    const uint32_t groups = gridDim.x < kBarGroups ? gridDim.x : kBarGroups;
+    const uint32_t g = blockIdx.x % groups;
+    const uint32_t members = gridDim.x / groups + (g < gridDim.x % groups ? 1u : 0u);
+    uint32_t* bar = A.bar_groups;
+    uint32_t* top = bar + kBarTop * 32;
+    uint32_t* gen = bar + kBarGen * 32;
+    uint32_t* abort_flag = bar + kBarAbort * 32;
+    if (atom_add_acq_rel(bar + g * 32, 1u) + 1 == members * target) {
+      if (atom_add_acq_rel(top, 1u) + 1 == groups * target && A.barrier_extra == 0)
+        st_release_u32(gen, target);
     }
-    __threadfence();
+    const uint64_t t0 = globaltimer();
+    uint32_t spins = 0;
+    while (ld_acquire_u32(gen) < target) {
+      if (ld_relaxed_u32(abort_flag)) { ok = 0; break; }
+      if ((++spins & 15u) == 0 && globaltimer() - t0 > A.timeout_ns) {
+        set_error(A.ctrl, MC_ERR_TIMEOUT);
+        atomicExch(abort_flag, 1u);
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
     s_ok = ok;
   }
   __syncthreads();
@@ -262,31 +280,69 @@ __device__ __forceinline__ uint64_t tile_min(uint64_t v) {
 }
 
 // ------------------------------------------------------------------ expansion of one level
+// Winners are staged per warp in shared memory.  A warp whose buffer is
+// nearly full reserves log slots with one global atomicAdd and copies the
+// buffer out coalesced; at the end of the level the block reserves one range
+// for the remainders of all its warps.  Within a level no block-wide
+// synchronisation happens, so warps run their rounds independently.
+template <class K>
+struct Stage {
+  K keys[kThreads / 32][kWarpCap];
+  uint32_t par[kThreads / 32][kWarpCap];
+  uint32_t fill[kThreads / 32];
+  unsigned long long base;
+};
+
+template <class K>
+__device__ __forceinline__ void copy_out(const ExploreArgs& A, const K* keys, const uint32_t* par,
+                                         uint32_t n, uint64_t at0, uint32_t lane) {
+  for (uint32_t x = lane; x < n; x += 32) {
+    const uint64_t at = at0 + x;
+    if (at < A.log_cap) {
+      KeyOps<K>::store(A.log_keys, at, keys[x]);
+      A.log_par[at] = par[x];
+    } else {
+      set_error(A.ctrl, MC_ERR_FRONTIER);
+    }
+  }
+}
+
 // A tile of TILE >= P lanes handles one state; lane c proposes the successor
 // in which unit c takes the next work-group (Listings 4-5): FREE allows every
 // unit, GREEDY only the units with the smallest clock.  Successors are
-// inserted into the visited set; winners are appended to the next level of
-// the frontier log (warp-aggregated), and a winner that is terminal (FIN,
-// Listing 4) with time <= T updates the level's minimum packed
-// (time, i, j) -- the property G(FIN -> time > T) of Step 2.
+// inserted into the visited set; winners are staged and appended to the next
+// level of the frontier log, and a winner that is terminal (FIN, Listing 4)
+// with time <= T updates the level's minimum packed (time, i, j) -- the
+// property G(FIN -> time > T) of Step 2.  The key of the next round is loaded
+// before the current round's probes so its latency overlaps them.
 template <class K, int TILE, int RULE>
-__device__ __forceinline__ void expand_level(const ExploreArgs& A, uint64_t T, uint32_t L,
-                                             uint64_t offL, uint64_t W, uint64_t offN) {
+__device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st, uint64_t T,
+                                             uint32_t L, uint64_t offL, uint64_t W, uint64_t offN) {
   const Params& p = A.p;
   const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warp = threadIdx.x >> 5;
   const uint32_t c = lane & (TILE - 1);
   constexpr uint32_t kTilesPerWarp = 32 / TILE;
   const uint64_t warp_gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const uint64_t stride = (((uint64_t)gridDim.x * blockDim.x) >> 5) * kTilesPerWarp;
   const uint32_t k_cur = L - 2;  // sum of n at level L
   const uint32_t c_shift = (p.P - 1 - (c < p.P ? c : 0)) * p.n_bits;
   const uint64_t speed_c = c < p.P ? __ldg(p.speed + c) : 0;
   K* table = reinterpret_cast<K*>(A.table);
+  K* wkeys = st.keys[warp];
+  uint32_t* wpar = st.par[warp];
+  uint64_t* lvl_next = A.levels + 2 * (L + 1);  // {width, best} of level L+1
+  uint64_t cached_best = kNone;
+  uint32_t fill = 0;  // warp-uniform
 
-  for (uint64_t base = warp_gid * kTilesPerWarp; base < W; base += n_warps * kTilesPerWarp) {
-    const uint64_t s = base + lane / TILE;
+  uint64_t base = warp_gid * kTilesPerWarp;
+  const uint64_t my = lane / TILE;
+  K key_next = base + my < W ? KeyOps<K>::load(A.log_keys, offL + base + my) : (K)0;
+  for (; base < W; base += stride) {
+    const uint64_t s = base + my;
     const bool valid = s < W;
-    K key = valid ? KeyOps<K>::load(A.log_keys, offL + s) : (K)0;
+    const K key = key_next;
+    if (s + stride < W) key_next = KeyOps<K>::load(A.log_keys, offL + s + stride);
     uint32_t i = 0, j = 0, r = 0;
     uint64_t t_c = 0, clk = 0;
     if (valid) {
@@ -317,20 +373,12 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, uint64_t T, u
     }
     const uint32_t m = __ballot_sync(0xffffffffu, won);
     if (m) {
-      const uint32_t leader = __ffs(m) - 1;
-      unsigned long long pos0 = 0;
-      if (lane == leader) pos0 = atomicAdd(reinterpret_cast<unsigned long long*>(&A.width[L + 1]),
-                                           (unsigned long long)__popc(m));
-      pos0 = __shfl_sync(0xffffffffu, pos0, leader);
       if (won) {
-        const uint64_t at = offN + pos0 + __popc(m & ((1u << lane) - 1u));
-        if (at < A.log_cap) {
-          KeyOps<K>::store(A.log_keys, at, succ);
-          A.log_par[at] = (uint32_t)s;
-        } else {
-          set_error(A.ctrl, MC_ERR_FRONTIER);
-        }
+        const uint32_t at = fill + __popc(m & ((1u << lane) - 1u));
+        wkeys[at] = succ;
+        wpar[at] = (uint32_t)s;
       }
+      fill += __popc(m);
       // Step 2: a terminal winner with time <= T violates G(FIN -> time > T)
       uint64_t pk = (won && r == 1 && succ_time <= T) ? pack_tij(succ_time, i, j) : kNone;
 #pragma unroll
@@ -338,19 +386,53 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, uint64_t T, u
         const uint64_t w = __shfl_xor_sync(0xffffffffu, pk, o);
         pk = w < pk ? w : pk;
       }
-      if (lane == 0 && pk != kNone && pk < ld_relaxed_u64(&A.best[L + 1]))
-        atomicMin(reinterpret_cast<unsigned long long*>(&A.best[L + 1]), (unsigned long long)pk);
+      if (lane == 0 && pk < cached_best) {
+        cached_best = ld_relaxed_u64(lvl_next + 1);
+        if (pk < cached_best) {
+          atomicMin(reinterpret_cast<unsigned long long*>(lvl_next + 1), (unsigned long long)pk);
+          cached_best = pk;
+        }
+      }
+      // each round adds at most 32 winners to the warp's buffer
+      if (fill > kWarpCap - 32) {
+        __syncwarp();
+        unsigned long long b = 0;
+        if (lane == 0)
+          b = atomicAdd(reinterpret_cast<unsigned long long*>(lvl_next), (unsigned long long)fill);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        copy_out<K>(A, wkeys, wpar, fill, offN + b, lane);
+        __syncwarp();
+        fill = 0;
+      }
     }
+  }
+  // end of level: one reservation per block for the warps' remainders
+  if (lane == 0) st.fill[warp] = fill;
+  __syncthreads();
+  const uint32_t nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) {
+    uint32_t total = 0;
+    for (uint32_t w = 0; w < nw; ++w) total += st.fill[w];
+    st.base = total ? atomicAdd(reinterpret_cast<unsigned long long*>(lvl_next), (unsigned long long)total)
+                    : 0ull;
+  }
+  __syncthreads();
+  if (fill) {
+    uint64_t at0 = offN + st.base;
+    for (uint32_t w = 0; w < warp; ++w) at0 += st.fill[w];
+    copy_out<K>(A, wkeys, wpar, fill, at0, lane);
   }
 }
 
 // ------------------------------------------------------------------ the exploration pass
 template <class K, int TILE, int RULE>
-__global__ void __launch_bounds__(512) explore_kernel(const ExploreArgs A) {
+__global__ void __launch_bounds__(kThreads) explore_kernel(const ExploreArgs A) {
   const Params& p = A.p;
   Ctrl* ctrl = A.ctrl;
   const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  __shared__ Stage<K> stage;
+  uint32_t epoch = 0;  // device-wide barriers passed in this pass
 
   uint64_t T = A.T;
   if (A.T_src) T = ld_relaxed_u64(A.T_src) + (uint64_t)A.T_delta;
@@ -362,9 +444,9 @@ __global__ void __launch_bounds__(512) explore_kernel(const ExploreArgs A) {
     const uint64_t n16 = A.table_u64 / 2;
     for (uint64_t x = gtid; x < n16; x += nthreads) tb[x] = make_ulonglong2(0, 0);
     for (uint64_t l = gtid; l < (uint64_t)p.max_level + 2; l += nthreads) {
-      A.width[l] = l == 0 ? 1 : l == 1 ? p.a : l == 2 ? (uint64_t)p.a * p.b : 0;
+      A.levels[2 * l] = l == 0 ? 1 : l == 1 ? p.a : l == 2 ? (uint64_t)p.a * p.b : 0;
+      A.levels[2 * l + 1] = kNone;
       A.off[l] = l == 0 ? 0 : l == 1 ? 1 : l == 2 ? 1 + (uint64_t)p.a : 0;
-      A.best[l] = kNone;
     }
     const uint64_t n_init = 1 + (uint64_t)p.a + (uint64_t)p.a * p.b;
     for (uint64_t x = gtid; x < n_init; x += nthreads) {
@@ -390,25 +472,27 @@ __global__ void __launch_bounds__(512) explore_kernel(const ExploreArgs A) {
       ctrl->widx = kNone;
     }
   }
-  if (!grid_sync(A)) return;
+  if (!grid_sync(A, epoch)) return;
 
   // level loop (one device-wide barrier per level)
   uint32_t last = 2;
   uint64_t off_last = 1 + (uint64_t)p.a;
+  uint64_t W = (uint64_t)p.a * p.b;
   for (;;) {
     const uint32_t L = last;
-    const uint64_t W = ld_relaxed_u64(&A.width[L]);
     if (L >= p.max_level) break;  // the deepest level holds only terminals
     const uint64_t offN = off_last + W;
     if (gtid == 0) A.off[L + 1] = offN;
-    expand_level<K, TILE, RULE>(A, T, L, off_last, W, offN);
-    if (!grid_sync(A)) return;
+    expand_level<K, TILE, RULE>(A, stage, T, L, off_last, W, offN);
+    if (!grid_sync(A, epoch)) return;
     if (ld_relaxed_u32(&ctrl->err)) break;
-    const uint64_t Wn = ld_relaxed_u64(&A.width[L + 1]);
+    uint64_t Wn, Bn;  // width and violating minimum of level L+1, one 16-byte load
+    ld_relaxed_v2u64(A.levels + 2 * (L + 1), Wn, Bn);
     if (Wn == 0) break;
     last = L + 1;
     off_last = offN;
-    if (A.early_exit && ld_relaxed_u64(&A.best[last]) != kNone) break;
+    W = Wn;
+    if (A.early_exit && Bn != kNone) break;
   }
   if (ld_relaxed_u32(&ctrl->err)) return;
 
@@ -418,7 +502,7 @@ __global__ void __launch_bounds__(512) explore_kernel(const ExploreArgs A) {
   uint32_t wl = 0;
   uint64_t best_all = kNone;
   if (A.early_exit) {
-    best_all = ld_relaxed_u64(&A.best[last]);
+    best_all = ld_relaxed_u64(A.levels + 2 * last + 1);
     wl = best_all != kNone ? last : 0;
   } else {
     __shared__ unsigned long long s_best;
@@ -429,7 +513,7 @@ __global__ void __launch_bounds__(512) explore_kernel(const ExploreArgs A) {
     }
     __syncthreads();
     for (uint32_t l = 3 + threadIdx.x; l <= last; l += blockDim.x) {
-      const uint64_t b = ld_relaxed_u64(&A.best[l]);
+      const uint64_t b = ld_relaxed_u64(A.levels + 2 * l + 1);
       if (b != kNone) {
         atomicMin(&s_best, (unsigned long long)b);
         atomicMin(&s_wl, l);
@@ -441,19 +525,19 @@ __global__ void __launch_bounds__(512) explore_kernel(const ExploreArgs A) {
   }
   if (gtid == 0) {
     ctrl->levels = last + 1;
-    ctrl->states = off_last + ld_relaxed_u64(&A.width[last]);
+    ctrl->states = off_last + W;
     ctrl->stop_level = wl;
     ctrl->best_pack = best_all;
-    ctrl->wpack = wl ? ld_relaxed_u64(&A.best[wl]) : kNone;
+    ctrl->wpack = wl ? ld_relaxed_u64(A.levels + 2 * wl + 1) : kNone;
     if (A.tmin_out && best_all != kNone) *A.tmin_out = pack_time(best_all);
   }
   if (!A.want_witness || wl == 0) return;
 
   // witness: the violating terminal of level wl with the smallest key among
   // those with the level's minimum (time, i, j)
-  const uint64_t target = ld_relaxed_u64(&A.best[wl]);
+  const uint64_t target = ld_relaxed_u64(A.levels + 2 * wl + 1);
   const uint64_t offW = ld_relaxed_u64(&A.off[wl]);
-  const uint64_t Ww = ld_relaxed_u64(&A.width[wl]);
+  const uint64_t Ww = ld_relaxed_u64(A.levels + 2 * wl);
   const uint32_t ti = pack_i(target), tj = pack_j(target);
   const uint64_t tt = pack_time(target);
   const uint32_t cfg_t = ti * p.b + tj;
@@ -470,7 +554,7 @@ __global__ void __launch_bounds__(512) explore_kernel(const ExploreArgs A) {
       atomicMin(reinterpret_cast<unsigned long long*>(&ctrl->wkey_hi),
                 (unsigned long long)KeyOps<K>::hi(key));
   }
-  if (!grid_sync(A)) return;
+  if (!grid_sync(A, epoch)) return;
   if (sizeof(K) == 16) {
     const uint64_t whi = ld_relaxed_u64(&ctrl->wkey_hi);
     for (uint64_t x = gtid; x < Ww; x += nthreads) {
@@ -482,7 +566,7 @@ __global__ void __launch_bounds__(512) explore_kernel(const ExploreArgs A) {
       atomicMin(reinterpret_cast<unsigned long long*>(&ctrl->wkey_lo),
                 (unsigned long long)KeyOps<K>::lo(key));
     }
-    if (!grid_sync(A)) return;
+    if (!grid_sync(A, epoch)) return;
   } else if (gtid == 0) {
     ctrl->wkey_hi = 0;
   }
@@ -494,7 +578,7 @@ __global__ void __launch_bounds__(512) explore_kernel(const ExploreArgs A) {
       if (KeyOps<K>::lo(key) == wlo && KeyOps<K>::hi(key) == whi) ctrl->widx = x;
     }
   }
-  if (!grid_sync(A)) return;
+  if (!grid_sync(A, epoch)) return;
   // trace: follow parent indices from the witness back to s0
   if (gtid == 0) {
     uint64_t idx = ld_relaxed_u64(&ctrl->widx);

@@ -45,7 +45,7 @@ class McOptions(C.Structure):
                 ("threads_per_block", C.c_uint32), ("blocks_per_sm", C.c_uint32),
                 ("max_probes", C.c_uint32), ("log_capacity", C.c_uint64),
                 ("barrier_timeout_ns", C.c_uint64), ("debug_barrier_extra", C.c_uint32),
-                ("reserved", C.c_uint32 * 7)]
+                ("timing", C.c_uint32), ("reserved", C.c_uint32 * 6)]
 
 
 class McCheckResult(C.Structure):
@@ -71,6 +71,12 @@ class McLayout(C.Structure):
                 ("table_slots", C.c_uint64), ("log_capacity", C.c_uint64),
                 ("max_width", C.c_uint64), ("state_bound", C.c_uint64),
                 ("device_bytes", C.c_uint64)]
+
+
+class McStats(C.Structure):
+    _fields_ = [("explore_launches", C.c_uint64), ("other_launches", C.c_uint64),
+                ("states", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
+                ("explore_ms", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -130,6 +136,8 @@ def load(build: bool = True):
             "mc_count_states": (C.c_int, [P, C.POINTER(C.c_uint64)]),
             "mc_simulate": (C.c_int, [P, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64)]),
             "mc_last_widths": (C.c_int, [P, C.POINTER(C.c_uint64), C.c_uint32, C.POINTER(C.c_uint32)]),
+            "mc_get_stats": (C.c_int, [P, C.POINTER(McStats)]),
+            "mc_reset_stats": (C.c_int, [P]),
             "mc_trace_length": (C.c_int, [P]),
             "mc_trace_key_words": (C.c_uint32, [P]),
             "mc_trace_states": (C.POINTER(C.c_uint64), [P]),
@@ -320,6 +328,16 @@ def mc_last_widths(model: Model, cap: int = 1 << 16) -> list:
     n = C.c_uint32()
     model._check(load().mc_last_widths(model.handle, buf, cap, C.byref(n)), "mc_last_widths")
     return list(buf[: min(n.value, cap)])
+
+
+def mc_get_stats(model: Model) -> dict:
+    st = McStats()
+    model._check(load().mc_get_stats(model.handle, C.byref(st)), "mc_get_stats")
+    return {k: getattr(st, k) for k, _t in McStats._fields_}
+
+
+def mc_reset_stats(model: Model):
+    model._check(load().mc_reset_stats(model.handle), "mc_reset_stats")
 
 
 def decode_key(layout: dict, key: int):

@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_options_default(lib):
     o = mc.mc_options_default()
-    assert (o.prune, o.early_exit, o.search, o.refine, o.sim_walks, o.load_factor_pct) == (1, 1, 0, 1, 1, 50)
+    assert (o.prune, o.early_exit, o.search, o.refine, o.sim_walks, o.load_factor_pct) == (1, 1, 0, 1, 1, 25)
     assert o.sim_seed == 2305091300
 
 
@@ -58,7 +58,7 @@ def test_layout_of_named_workloads(lib):
     l3 = layout(W.c3_star())
     assert l3["key_bits"] == 128 and l3["used_bits"] == 4 + 3 + 8 * 6
     assert l3["state_bound"] == 1_072_924_481 and l3["max_width"] == 193_344_684
-    assert l3["table_slots"] == 1 << 29 and l3["log_capacity"] == 1_072_924_481
+    assert l3["table_slots"] == 1 << 30 and l3["log_capacity"] == 1_072_924_481
     lit = layout(W.c3(rule=W.GREEDY))
     assert lit["used_bits"] == 4 + 3 + 8 * 13 and lit["key_bits"] == 128
     assert lit["state_bound"] >= CF.count(W.c3(rule=W.GREEDY))
