@@ -260,6 +260,30 @@ uint32_t mc_trace_key_words(const mc_trace* t);
 const uint64_t* mc_trace_states(const mc_trace* t);
 void mc_trace_free(mc_trace* t);
 
+/* ------------------------------------------------- no-allocation variant
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- a host framework that owns the device's
+ * memory budget and offers no allocator, a serving path where an allocation
+ * could block or fail, a plugin that may only launch on a stream it is
+ * given.  It answers the same question as mc_check(T) for the model
+ * described by `desc` (host memory, read during the call; options: `prune`,
+ * `early_exit`, load factor 25%) and writes *out (host memory); no trace.
+ *
+ * Every scratch buffer comes from one static device array of
+ * MC_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that
+ * loads the library holds until exit.  The call allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.  Its first call on
+ * a device looks the array's device address up (cudaGetSymbolAddress, with
+ * that device current), so make that first call before any stream capture.
+ * Work runs on `stream` (a cudaStream_t, NULL = legacy default stream) and
+ * the call returns after it finished.  Calls share the array: calls that
+ * overlap on the GPU race.  Errors: INVAL, OVERFLOW (as mc_model_create),
+ * NOMEM when the model's visited set, frontier log and tables need more than
+ * MC_NOALLOC_SCRATCH_BYTES, TABLE_FULL, FRONTIER, TIMEOUT, CUDA. */
+#define MC_NOALLOC_SCRATCH_BYTES (32ull << 20)
+int mc_check_noalloc(const mc_model_desc* desc, uint64_t T, uint32_t prune, uint32_t early_exit,
+                     void* stream, mc_check_result* out);
+
 /* Static name of an error code. */
 const char* mc_strerror(int code);
 

@@ -137,6 +137,8 @@ def load(build: bool = True):
             "mc_simulate": (C.c_int, [P, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64)]),
             "mc_last_widths": (C.c_int, [P, C.POINTER(C.c_uint64), C.c_uint32, C.POINTER(C.c_uint32)]),
             "mc_get_stats": (C.c_int, [P, C.POINTER(McStats)]),
+            "mc_check_noalloc": (C.c_int, [C.POINTER(McModelDesc), C.c_uint64, C.c_uint32, C.c_uint32,
+                                           P, C.POINTER(McCheckResult)]),
             "mc_reset_stats": (C.c_int, [P]),
             "mc_trace_length": (C.c_int, [P]),
             "mc_trace_key_words": (C.c_uint32, [P]),
@@ -338,6 +340,28 @@ def mc_get_stats(model: Model) -> dict:
 
 def mc_reset_stats(model: Model):
     model._check(load().mc_reset_stats(model.handle), "mc_reset_stats")
+
+
+def mc_check_noalloc(spec, T: int, prune: bool = True, early_exit: bool = True, stream=None) -> dict:
+    """mc_check for callers that cannot allocate device memory: the library's
+    static scratch array holds every buffer (models up to
+    MC_NOALLOC_SCRATCH_BYTES of scratch).  Same fields as mc_check, no trace."""
+    arrs = (_u32(spec.wg_values), _u32(spec.ts_values), _u32(spec.n_workgroups), _u32(spec.cost),
+            _u32(spec.speed))
+    d = McModelDesc(len(spec.wg_values), len(spec.ts_values), spec.P, arrs[0], arrs[1], arrs[2],
+                    arrs[3], arrs[4], spec.rule, getattr(spec, "key_bits", 0))
+    raw = getattr(stream, "cuda_stream", stream)
+    r = McCheckResult()
+    rc = load().mc_check_noalloc(C.byref(d), int(T) & NO_LIMIT, int(prune), int(early_exit),
+                                 C.c_void_p(raw or 0), C.byref(r))
+    if rc != MC_OK:
+        raise MCError(rc, "mc_check_noalloc")
+    out = {"holds": bool(r.holds), "states": r.states, "levels": r.levels}
+    if not r.holds:
+        out.update(cex_time=r.cex_time, cex_i=r.cex_wg_index, cex_j=r.cex_ts_index, cex_wg=r.cex_wg,
+                   cex_ts=r.cex_ts, cex_level=r.cex_level,
+                   cex_key=r.cex_key[0] | (r.cex_key[1] << 64))
+    return out
 
 
 def decode_key(layout: dict, key: int):
