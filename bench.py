@@ -39,6 +39,16 @@ if ROOT not in sys.path:
 
 from paper_2305_09130_gb300 import workloads as W  # noqa: E402
 
+WORKLOADS = {
+    # name: (spec factory, description)
+    "c2_star": (lambda: W.c2_star(), None),
+    "c3_star": (lambda: W.c3_star(),
+                "c3_star: G=36, P=8, WG 2^0..2^9, TS 2^0..2^5, FREE, cost U{1..16} (splitmix64 seed "
+                "2305091303), 128-bit keys; 1,072,924,481 reachable states"),
+    "c3_star_g24": (lambda: W.c3(G=24, rule=W.FREE, key_bits=128),
+                    "c3 at G=24: P=8, WG 2^0..2^9, TS 2^0..2^5, FREE, cost U{1..16} (seed 2305091303), "
+                    "128-bit keys (a reduced C3* for profiling)"),
+}
 METRIC = "unique states/sec"
 UNIT = "states/s"
 WORKLOAD = ("c2_star: G=80, P=4, WG 2^0..2^8, TS 2^0..2^4, FREE dispatch, cost ceil(WG/TS)*4+WG+2*TS, "
@@ -237,7 +247,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     dist_init(world, True)
-    spec = W.c2_star()
+    spec = WORKLOADS[args.workload][0]()
+    workload = WORKLOADS[args.workload][1] or WORKLOAD
     opts = mc.mc_options_default(search=args.mode, prune=args.prune, timing=1)
     stream = torch.cuda.Stream(device)
     model = mc.mc_model_create(spec, opts, allocator="torch", stream=stream)
@@ -249,13 +260,24 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             flush.fill_(k & 0xFF)
 
+    if args.query == "count":
+        def query():
+            return {"states": mc.mc_count_states(model), "checks": 1, "t_min": None, "wg": None,
+                    "ts": None, "t_ini": None}
+    else:
+        def query():
+            return mc.mc_min_time(model, trace=True)
+
     ref = None
     for w in range(args.warmup):
         flush_l2(w)
-        ref = mc.mc_min_time(model, trace=True)
-    expect = (96, 8, 4)  # T_min and (WG, TS) of this workload, from the oracle
-    if ref is not None and (ref["t_min"], ref["wg"], ref["ts"]) != expect:
-        raise SystemExit(f"wrong result {ref} != {expect}")
+        ref = query()
+    if args.workload == "c2_star" and args.query == "min_time":
+        expect = (96, 8, 4)  # T_min and (WG, TS) of this workload, from the oracle
+        if (ref["t_min"], ref["wg"], ref["ts"]) != expect:
+            raise SystemExit(f"wrong result {ref} != {expect}")
+    if args.query == "count" and spec.rule == W.FREE and ref["states"] != layout["state_bound"]:
+        raise SystemExit(f"wrong count {ref['states']} != {layout['state_bound']}")
 
     mc.mc_reset_stats(model)
     torch.cuda.synchronize()
@@ -268,7 +290,7 @@ def run_ours(args):
     for k in range(args.steps):
         flush_l2(k)
         ev[k][0].record(stream)
-        r = mc.mc_min_time(model, trace=True)
+        r = query()
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
@@ -287,13 +309,14 @@ def run_ours(args):
     launches = st["explore_launches"]
     achieved = bps * st["states"] / (st["explore_ms"] / 1000.0) / 1e9
     peak, peak_kind = measured_hbm_peak()
-    traffic = ncu_traffic_per_launch()
+    traffic = ncu_traffic_per_launch() if (args.workload, args.query) == ("c2_star", "min_time") else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "algorithmic_bytes_per_launch": bps * st["states"] / max(launches, 1),
                 "bytes_per_state": bps, "states_per_launch": st["states"] / max(launches, 1),
                 "avg_launch_ms": st["explore_ms"] / max(launches, 1),
-                "kernel": f"explore_kernel<u{64 * layout['key_words']}, tile {4}, FREE>",
+                "kernel": f"explore_kernel<u{64 * layout['key_words']}, tile {1 << (spec.P - 1).bit_length()}, "
+                          f"{'FREE' if spec.rule == W.FREE else 'GREEDY'}>",
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                                if peak_kind == "measured" else "fallback 6.8 TB/s"}
     gpu_launches = st["explore_launches"] + st["other_launches"]
@@ -306,7 +329,11 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         m2 = mc.mc_model_create(spec, opts, allocator="torch", stream=stream)
-        r2 = mc.mc_min_time(m2, trace=True)
+        if args.query == "count":
+            r2 = {"t_min": None}
+            mc.mc_count_states(m2)
+        else:
+            r2 = mc.mc_min_time(m2, trace=True)
         s2 = mc.mc_get_stats(m2)
         mc.mc_model_destroy(m2)
         e2e_s.append(time.perf_counter() - t0)
@@ -321,9 +348,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic (seeded model description; no dataset)",
-        "config": {"workload": WORKLOAD,
-                   "query": f"mc_min_time search={args.mode} prune={int(args.prune)} early_exit=1 "
-                            f"(iterative threshold lowering from the simulated T_ini)",
+        "config": {"workload": workload,
+                   "query": (f"mc_min_time search={args.mode} prune={int(args.prune)} early_exit=1 "
+                             f"(iterative threshold lowering from the simulated T_ini)"
+                             if args.query == "min_time" else "mc_count_states (every reachable state)"),
                    "l2": "flushed between steps (256 MiB write, untimed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "states_per_step": states_local / args.steps,
@@ -338,7 +366,8 @@ def run_ours(args):
         "clocks": clocks,
         "wall_s_timed_region": wall,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "c2_star" \
+            and args.query == "min_time":
         line["cpu_baseline"] = cpu_baseline_sample(spec, r["t_min"])
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -355,6 +384,9 @@ def main(argv=None):
     p.add_argument("--mode", choices=["single", "lower", "bisect"], default="lower")
     p.add_argument("--prune", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="c2_star",
+                   help="profiling aid; the benchmark line is c2_star")
+    p.add_argument("--query", choices=["min_time", "count"], default="min_time")
     args = p.parse_args(argv)
     if args.warmup < 3:
         p.error("--warmup must be >= 3")
