@@ -320,6 +320,21 @@ def run_ours(args):
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                                if peak_kind == "measured" else "fallback 6.8 TB/s"}
     gpu_launches = st["explore_launches"] + st["other_launches"]
+    # random-access ceilings (outside the timed region): random 32-byte sector
+    # reads over a buffer far larger than L2, and over one the size of this
+    # model's visited set (L2-resident when it fits)
+    if not args.no_random_roofline:
+        table_bytes = layout["table_slots"] * 8 * layout["key_words"]
+        hbm = mc.mc_measure_random_access(64 << 30, 200_000_000, 0)
+        l2 = mc.mc_measure_random_access(max(table_bytes, 1 << 20), 200_000_000, 0)
+        probes = spec.P * st["states"] / (st["explore_ms"] / 1000.0)
+        roofline["random_access"] = {
+            "hbm_64GiB_sector_reads_per_s": hbm["sectors_per_s"],
+            "table_sized_sector_reads_per_s": l2["sectors_per_s"],
+            "table_bytes": table_bytes,
+            "kernel_probe_reads_per_s": probes,
+            "frac_of_table_sized": probes / l2["sectors_per_s"],
+            "note": "one 32-byte bucket read per generated successor (P per state)"}
 
     # end to end through the public C-ABI from host buffers: create (H2D of
     # the model arrays through pinned staging), query, read results, destroy
@@ -384,6 +399,7 @@ def main(argv=None):
     p.add_argument("--mode", choices=["single", "lower", "bisect"], default="lower")
     p.add_argument("--prune", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-random-roofline", action="store_true")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="c2_star",
                    help="profiling aid; the benchmark line is c2_star")
     p.add_argument("--query", choices=["min_time", "count"], default="min_time")

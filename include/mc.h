@@ -260,6 +260,16 @@ uint32_t mc_trace_key_words(const mc_trace* t);
 const uint64_t* mc_trace_states(const mc_trace* t);
 void mc_trace_free(mc_trace* t);
 
+/* Random-access roofline of the current device (a measurement utility, not a
+ * step of the method): times `accesses` independent random 32-byte sector
+ * reads (op 0) or reads followed by an atomicCAS on the sector (op 1) over a
+ * freshly allocated buffer of `buffer_bytes` (use one far larger than L2), and
+ * writes the sustained sectors per second.  The visited set of an exploration
+ * larger than L2 is accessed this way, so this rate bounds its HBM regime.
+ * Allocates and frees its buffer.  Errors: INVAL, NOMEM, CUDA. */
+int mc_measure_random_access(uint64_t buffer_bytes, uint64_t accesses, int op,
+                             double* sectors_per_s, double* ms);
+
 /* ------------------------------------------------- no-allocation variant
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory -- a host framework that owns the device's

@@ -13,6 +13,10 @@ constexpr int kPackIdxBits = 12;           // i and j fields of a packed (time, 
 constexpr uint32_t kNoParent = 0xFFFFFFFFu;
 constexpr uint32_t kThreads = 256;         // exploration kernel block size (maximum)
 constexpr uint32_t kWarpCap = 128;         // winners staged per warp before a flush
+#ifndef MC_PROBE_DEPTH
+#define MC_PROBE_DEPTH 1
+#endif
+constexpr uint32_t kDepth = MC_PROBE_DEPTH; // states per tile and round (probes in flight per lane)
 constexpr uint32_t kBarGroups = 16;        // first-level counters of the device-wide barrier
 constexpr uint32_t kBarTop = kBarGroups;   // 128-byte line of the top counter
 constexpr uint32_t kBarGen = kBarGroups + 1;    // line of the generation word

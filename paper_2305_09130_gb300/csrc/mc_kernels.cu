@@ -64,6 +64,16 @@ __device__ __forceinline__ uint64_t globaltimer() {
   return t;
 }
 
+// 16-byte global -> shared copy that bypasses L1 (the visited set is written
+// by atomics at L2), then wait for all of this thread's copies.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ void set_error(Ctrl* ctrl, int code) {
   atomicCAS(&ctrl->err, 0u, (uint32_t)code);
 }
@@ -177,19 +187,24 @@ __device__ __forceinline__ void load_bucket<u128>(const u128* b, u128 (&v)[2]) {
   v[1] = ((u128)y.y << 64) | y.x;
 }
 
-// Insert `key` (sum of n fields = lvl) into the visited set.
+// Insert `key` (sum of n fields = lvl) into the visited set, starting at
+// bucket `bkt` whose 32 bytes are already in `first` (shared memory).
 // Returns 1 if this thread inserted it, 0 if it was already there, -1 when
 // the probe limit was reached.  A slot is free when it holds 0 or a key of an
 // earlier level; the first free slot of the probe sequence is taken.
 template <class K>
 __device__ int visited_insert(K* table, uint64_t bucket_mask, uint32_t max_probes, K key,
-                              uint32_t lvl, const Params& p) {
+                              uint32_t lvl, const Params& p, uint64_t bkt, const K* first) {
   constexpr int S = KeyOps<K>::kSlots;
-  uint64_t bkt = key_hash(key) & bucket_mask;
   for (uint32_t probe = 0; probe < max_probes; ++probe) {
     K* slot = table + bkt * S;
     K v[S];
-    load_bucket<K>(slot, v);
+    if (probe == 0) {
+#pragma unroll
+      for (int s = 0; s < S; ++s) v[s] = first[s];
+    } else {
+      load_bucket<K>(slot, v);
+    }
     bool hit = false;
 #pragma unroll
     for (int s = 0; s < S; ++s) hit |= (v[s] == key);
@@ -307,24 +322,31 @@ __device__ __forceinline__ void copy_out(const ExploreArgs& A, const K* keys, co
   }
 }
 
-// A tile of TILE >= P lanes handles one state; lane c proposes the successor
-// in which unit c takes the next work-group (Listings 4-5): FREE allows every
-// unit, GREEDY only the units with the smallest clock.  Successors are
-// inserted into the visited set; winners are staged and appended to the next
-// level of the frontier log, and a winner that is terminal (FIN, Listing 4)
-// with time <= T updates the level's minimum packed (time, i, j) -- the
-// property G(FIN -> time > T) of Step 2.  The key of the next round is loaded
-// before the current round's probes so its latency overlaps them.
+// A tile of TILE >= P lanes handles kDepth states per round; lane c proposes,
+// for each of them, the successor in which unit c takes the next work-group
+// (Listings 4-5): FREE allows every unit, GREEDY only the units with the
+// smallest clock.  The first visited-set bucket of every proposal is fetched
+// with cp.async into this thread's slice of shared memory, all kDepth at
+// once, so the probes are in flight together without holding registers;
+// then each is resolved (a hit is a duplicate; otherwise CAS into the first
+// free slot).  Winners are staged and appended to the next level of the
+// frontier log, and a winner that is terminal (FIN, Listing 4) with
+// time <= T updates the level's minimum packed (time, i, j) -- the property
+// G(FIN -> time > T) of Step 2.  The keys of the next round are loaded
+// before the current round's probes.
 template <class K, int TILE, int RULE>
 __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st, uint64_t T,
                                              uint32_t L, uint64_t offL, uint64_t W, uint64_t offN) {
+  constexpr int S = KeyOps<K>::kSlots;
+  constexpr uint32_t D = kDepth;
+  __shared__ __align__(16) K probe[kThreads][D][S];
   const Params& p = A.p;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
   const uint32_t c = lane & (TILE - 1);
   constexpr uint32_t kTilesPerWarp = 32 / TILE;
   const uint64_t warp_gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t stride = (((uint64_t)gridDim.x * blockDim.x) >> 5) * kTilesPerWarp;
+  const uint64_t stride = (((uint64_t)gridDim.x * blockDim.x) >> 5) * kTilesPerWarp * D;
   const uint32_t k_cur = L - 2;  // sum of n at level L
   const uint32_t c_shift = (p.P - 1 - (c < p.P ? c : 0)) * p.n_bits;
   const uint64_t speed_c = c < p.P ? __ldg(p.speed + c) : 0;
@@ -335,75 +357,105 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
   uint64_t cached_best = kNone;
   uint32_t fill = 0;  // warp-uniform
 
-  uint64_t base = warp_gid * kTilesPerWarp;
+  uint64_t base = warp_gid * kTilesPerWarp * D;
   const uint64_t my = lane / TILE;
-  K key_next = base + my < W ? KeyOps<K>::load(A.log_keys, offL + base + my) : (K)0;
-  for (; base < W; base += stride) {
-    const uint64_t s = base + my;
-    const bool valid = s < W;
-    const K key = key_next;
-    if (s + stride < W) key_next = KeyOps<K>::load(A.log_keys, offL + s + stride);
-    uint32_t i = 0, j = 0, r = 0;
-    uint64_t t_c = 0, clk = 0;
-    if (valid) {
-      i = field(key, p.wg_shift, p.wg_mask) - 1;
-      j = field(key, p.ts_shift, p.ts_mask) - 1;
-      const uint32_t cfg = i * p.b + j;
-      r = __ldg(p.N + cfg) - k_cur;
-      if (c < p.P) {
-        t_c = (uint64_t)__ldg(p.cost + cfg) * speed_c;
-        clk = (uint64_t)field(key, c_shift, p.n_mask) * t_c;
-      }
-    }
-    const uint64_t mx = tile_max<TILE>(clk);
-    bool allowed = valid && c < p.P && r > 0;
-    if (RULE == MC_GREEDY) {
-      const uint64_t mn = tile_min<TILE>((valid && c < p.P) ? clk : kNone);
-      allowed = allowed && clk == mn;
-    }
-    const uint64_t nclk = clk + t_c;
-    const uint64_t succ_time = nclk > mx ? nclk : mx;
-    if (A.prune && succ_time > T) allowed = false;
-    const K succ = key + ((K)1 << c_shift);
-    int won = 0;
-    if (allowed) {
-      const int rc = visited_insert<K>(table, A.bucket_mask, A.max_probes, succ, k_cur + 1, p);
-      if (rc < 0) set_error(A.ctrl, MC_ERR_TABLE_FULL);
-      won = rc > 0;
-    }
-    const uint32_t m = __ballot_sync(0xffffffffu, won);
-    if (m) {
-      if (won) {
-        const uint32_t at = fill + __popc(m & ((1u << lane) - 1u));
-        wkeys[at] = succ;
-        wpar[at] = (uint32_t)s;
-      }
-      fill += __popc(m);
-      // Step 2: a terminal winner with time <= T violates G(FIN -> time > T)
-      uint64_t pk = (won && r == 1 && succ_time <= T) ? pack_tij(succ_time, i, j) : kNone;
+  K key_next[D];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t w = __shfl_xor_sync(0xffffffffu, pk, o);
-        pk = w < pk ? w : pk;
-      }
-      if (lane == 0 && pk < cached_best) {
-        cached_best = ld_relaxed_u64(lvl_next + 1);
-        if (pk < cached_best) {
-          atomicMin(reinterpret_cast<unsigned long long*>(lvl_next + 1), (unsigned long long)pk);
-          cached_best = pk;
+  for (uint32_t d = 0; d < D; ++d) {
+    const uint64_t s = base + d * kTilesPerWarp + my;
+    key_next[d] = s < W ? KeyOps<K>::load(A.log_keys, offL + s) : (K)0;
+  }
+  for (; base < W; base += stride) {
+    K succ[D];
+    uint64_t succ_time[D], bkt[D];
+    uint32_t ij[D];
+    bool allowed[D], terminal[D];
+#pragma unroll
+    for (uint32_t d = 0; d < D; ++d) {
+      const uint64_t s = base + d * kTilesPerWarp + my;
+      const bool valid = s < W;
+      const K key = key_next[d];
+      if (s + stride < W) key_next[d] = KeyOps<K>::load(A.log_keys, offL + s + stride);
+      uint32_t i = 0, j = 0, r = 0;
+      uint64_t t_c = 0, clk = 0;
+      if (valid) {
+        i = field(key, p.wg_shift, p.wg_mask) - 1;
+        j = field(key, p.ts_shift, p.ts_mask) - 1;
+        const uint32_t cfg = i * p.b + j;
+        r = __ldg(p.N + cfg) - k_cur;
+        if (c < p.P) {
+          t_c = (uint64_t)__ldg(p.cost + cfg) * speed_c;
+          clk = (uint64_t)field(key, c_shift, p.n_mask) * t_c;
         }
       }
-      // each round adds at most 32 winners to the warp's buffer
-      if (fill > kWarpCap - 32) {
-        __syncwarp();
-        unsigned long long b = 0;
-        if (lane == 0)
-          b = atomicAdd(reinterpret_cast<unsigned long long*>(lvl_next), (unsigned long long)fill);
-        b = __shfl_sync(0xffffffffu, b, 0);
-        copy_out<K>(A, wkeys, wpar, fill, offN + b, lane);
-        __syncwarp();
-        fill = 0;
+      const uint64_t mx = tile_max<TILE>(clk);
+      bool ok = valid && c < p.P && r > 0;
+      if (RULE == MC_GREEDY) {
+        const uint64_t mn = tile_min<TILE>((valid && c < p.P) ? clk : kNone);
+        ok = ok && clk == mn;
       }
+      const uint64_t nclk = clk + t_c;
+      succ_time[d] = nclk > mx ? nclk : mx;
+      if (A.prune && succ_time[d] > T) ok = false;
+      allowed[d] = ok;
+      terminal[d] = r == 1;
+      ij[d] = (i << 16) | j;
+      succ[d] = key + ((K)1 << c_shift);
+      bkt[d] = key_hash(succ[d]) & A.bucket_mask;
+      if (ok) {
+        const K* src = table + bkt[d] * S;
+        cp_async16(&probe[threadIdx.x][d][0], src);
+        cp_async16(reinterpret_cast<char*>(&probe[threadIdx.x][d][0]) + 16,
+                   reinterpret_cast<const char*>(src) + 16);
+      }
+    }
+    cp_async_wait_all();
+#pragma unroll
+    for (uint32_t d = 0; d < D; ++d) {
+      const uint64_t s = base + d * kTilesPerWarp + my;
+      int won = 0;
+      if (allowed[d]) {
+        const int rc = visited_insert<K>(table, A.bucket_mask, A.max_probes, succ[d], k_cur + 1, p,
+                                         bkt[d], probe[threadIdx.x][d]);
+        if (rc < 0) set_error(A.ctrl, MC_ERR_TABLE_FULL);
+        won = rc > 0;
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, won);
+      if (m) {
+        if (won) {
+          const uint32_t at = fill + __popc(m & ((1u << lane) - 1u));
+          wkeys[at] = succ[d];
+          wpar[at] = (uint32_t)s;
+        }
+        fill += __popc(m);
+        // Step 2: a terminal winner with time <= T violates G(FIN -> time > T)
+        uint64_t pk = (won && terminal[d] && succ_time[d] <= T)
+                          ? pack_tij(succ_time[d], ij[d] >> 16, ij[d] & 0xFFFFu)
+                          : kNone;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const uint64_t w = __shfl_xor_sync(0xffffffffu, pk, o);
+          pk = w < pk ? w : pk;
+        }
+        if (lane == 0 && pk < cached_best) {
+          cached_best = ld_relaxed_u64(lvl_next + 1);
+          if (pk < cached_best) {
+            atomicMin(reinterpret_cast<unsigned long long*>(lvl_next + 1), (unsigned long long)pk);
+            cached_best = pk;
+          }
+        }
+      }
+    }
+    // each round adds at most 32 * D winners to the warp's buffer
+    if (fill > kWarpCap - 32 * D) {
+      __syncwarp();
+      unsigned long long b = 0;
+      if (lane == 0)
+        b = atomicAdd(reinterpret_cast<unsigned long long*>(lvl_next), (unsigned long long)fill);
+      b = __shfl_sync(0xffffffffu, b, 0);
+      copy_out<K>(A, wkeys, wpar, fill, offN + b, lane);
+      __syncwarp();
+      fill = 0;
     }
   }
   // end of level: one reservation per block for the warps' remainders

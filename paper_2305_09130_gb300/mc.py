@@ -137,6 +137,8 @@ def load(build: bool = True):
             "mc_simulate": (C.c_int, [P, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64)]),
             "mc_last_widths": (C.c_int, [P, C.POINTER(C.c_uint64), C.c_uint32, C.POINTER(C.c_uint32)]),
             "mc_get_stats": (C.c_int, [P, C.POINTER(McStats)]),
+            "mc_measure_random_access": (C.c_int, [C.c_uint64, C.c_uint64, C.c_int,
+                                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "mc_check_noalloc": (C.c_int, [C.POINTER(McModelDesc), C.c_uint64, C.c_uint32, C.c_uint32,
                                            P, C.POINTER(McCheckResult)]),
             "mc_reset_stats": (C.c_int, [P]),
@@ -362,6 +364,18 @@ def mc_check_noalloc(spec, T: int, prune: bool = True, early_exit: bool = True, 
                    cex_ts=r.cex_ts, cex_level=r.cex_level,
                    cex_key=r.cex_key[0] | (r.cex_key[1] << 64))
     return out
+
+
+def mc_measure_random_access(buffer_bytes: int, accesses: int, op: int = 0) -> dict:
+    """Random 32-byte sector reads (op 0) or read + CAS (op 1) per second over
+    a buffer of buffer_bytes on the current device."""
+    rate = C.c_double()
+    ms = C.c_double()
+    rc = load().mc_measure_random_access(int(buffer_bytes), int(accesses), int(op), C.byref(rate),
+                                         C.byref(ms))
+    if rc != MC_OK:
+        raise MCError(rc, "mc_measure_random_access")
+    return {"sectors_per_s": rate.value, "ms": ms.value, "gbs_32b": rate.value * 32 / 1e9}
 
 
 def decode_key(layout: dict, key: int):
