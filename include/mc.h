@@ -260,6 +260,52 @@ uint32_t mc_trace_key_words(const mc_trace* t);
 const uint64_t* mc_trace_states(const mc_trace* t);
 void mc_trace_free(mc_trace* t);
 
+/* ------------------------------------------------------------ batched queries
+ * Many models answered by one persistent launch (auto-tuning issues many
+ * queries, Section 2): every instance runs its own query program (mc_check or
+ * mc_min_time in SINGLE mode) and all of them advance in lockstep, so each
+ * device-wide barrier serves the whole batch.  Every instance uses 128-bit
+ * keys; results equal those of mc_check / mc_min_time on the same model and
+ * options (search mode SINGLE; lowering and bisection are single-model only). */
+typedef struct mc_batch mc_batch;
+typedef enum { MC_QUERY_CHECK = 0, MC_QUERY_MIN_TIME = 1 } mc_query_kind;
+typedef struct {
+  uint32_t kind;         /* mc_query_kind                                   */
+  uint32_t reserved;
+  uint64_t T;            /* threshold of MC_QUERY_CHECK                     */
+} mc_query;
+typedef struct {
+  int32_t status;        /* MC_OK or this instance's MC_ERR_*               */
+  uint32_t kind;
+  uint32_t holds;        /* check: 1 when the property holds                */
+  uint32_t levels;       /* levels of the last pass                         */
+  uint64_t states;       /* unique states over every pass                   */
+  uint32_t checks;       /* passes run                                      */
+  uint32_t level;        /* counterexample level (0 when it holds)          */
+  uint64_t time;         /* counterexample time; T_min for min-time         */
+  uint64_t t_ini;        /* min-time: the simulated bound                   */
+  uint32_t wg_index, ts_index, wg, ts;
+  uint64_t key[2];       /* packed counterexample / witness state {lo, hi}  */
+} mc_batch_result;
+
+/* Validate and lay out `n` (1..1024) models with one set of options.  Host
+ * only; device memory is taken at the first run.  Errors: as
+ * mc_model_create, INVAL, NOMEM (a model's bound does not fit). */
+int mc_batch_create(const mc_model_desc* descs, uint32_t n, const mc_options* opt, mc_batch** out);
+void mc_batch_destroy(mc_batch* b);
+int mc_batch_set_stream(mc_batch* b, void* stream);
+int mc_batch_set_allocator(mc_batch* b, mc_alloc_fn alloc, mc_free_fn free_fn, void* ctx);
+/* Device bytes of the batch's pool (visited sets, logs, level records). */
+int mc_batch_device_bytes(const mc_batch* b, uint64_t* out);
+/* Run queries[i] on model i for every i, in one launch; fills results[n].
+ * Errors: INVAL, NOMEM, TIMEOUT, CUDA; per-instance errors in status. */
+int mc_batch_run(mc_batch* b, const mc_query* queries, mc_batch_result* results);
+/* Trace of instance i's counterexample from the last run: *len states of two
+ * u64 words ({lo, hi}); up to cap states are copied.  Errors: INVAL, CUDA. */
+int mc_batch_trace(mc_batch* b, uint32_t i, uint64_t* keys, uint32_t cap, uint32_t* len);
+int mc_batch_get_stats(const mc_batch* b, mc_stats* out);
+const char* mc_batch_last_error(const mc_batch* b);
+
 /* Random-access roofline of the current device (a measurement utility, not a
  * step of the method): times `accesses` independent random 32-byte sector
  * reads (op 0) or reads followed by an atomicCAS on the sector (op 1) over a

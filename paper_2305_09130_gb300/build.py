@@ -17,8 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libmcgpu.so")
-SOURCES = ["mc_api.cu", "mc_kernels.cu", "mc_noalloc.cu", "mc_roofline.cu"]
-HEADERS = [os.path.join(CSRC, "mc_internal.h"), os.path.join(INCLUDE, "mc.h")]
+SOURCES = ["mc_api.cu", "mc_kernels.cu", "mc_batch.cu", "mc_noalloc.cu", "mc_roofline.cu"]
+HEADERS = [os.path.join(CSRC, "mc_internal.h"), os.path.join(CSRC, "mc_device.cuh"), os.path.join(INCLUDE, "mc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,813 @@
+// Batched exploration: many models answered by one persistent launch.
+//
+// Auto-tuning asks many questions (Section 2: one check per threshold, one
+// search per kernel and input size), most of them small: a single query of a
+// few thousand states per BFS level leaves the GPU idle between its
+// device-wide barriers.  Here every instance of a batch advances in lockstep:
+// between two barriers each instance does one step of its own query program,
+// and the barrier's cost is shared by all of them.
+//
+// Query programs (the single-model drivers of mc_api.cu, as state machines):
+//   check(T)    SETUP -> EXPAND ... -> [witness scans -> TRACE] -> DONE
+//   min_time    SIM -> min pass -> [certificate pass at T_min - 1] ->
+//               final pass at T_min -> witness scans -> TRACE -> DONE
+// The min pass keeps successors up to T_ini (with pruning) and records the
+// least violating terminal of every level; a pass ends after the first level
+// holding a violating terminal (early exit) or after the deepest level.
+//
+// Between steps, the block that completes a device-wide barrier runs the
+// planner before it releases the others: it advances each instance's state
+// machine from the level records the step produced and writes the prefix sum
+// of the next step's tasks.  A task is one warp's unit of work: 32/group
+// states of a level to expand (group = lanes per state), 32 log entries to
+// scan for the witness, 256 units of set-up, 32 random runs, or the trace.
+// Warps stride over the task index space; a task's instance is found by
+// binary search over the prefix cached in shared memory.
+//
+// All instances use 128-bit keys in their own layout.  Each instance has its
+// own visited set, frontier log and level records carved from one pool.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mc_device.cuh"
+
+namespace mc {
+namespace {
+
+using namespace mc::dev;
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ uint64_t ldcg64(const uint64_t* p) {
+  return __ldcg(reinterpret_cast<const unsigned long long*>(p));
+}
+
+// ------------------------------------------------------------------ planner
+uint64_t __host__ __device__ inline ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+__device__ uint64_t task_count(const BState& s, const BInst& I, const BatchArgs& A) {
+  switch (s.phase) {
+    case B_SIM: return ceil_div(A.sim_walks, 32);
+    case B_SETUP: {
+      uint64_t u = I.table_u64 / 2;
+      u = u > (uint64_t)I.p.max_level + 2 ? u : (uint64_t)I.p.max_level + 2;
+      const uint64_t init = 1 + (uint64_t)I.p.a + (uint64_t)I.p.a * I.p.b;
+      u = u > init ? u : init;
+      return ceil_div(u, kTaskUnits);
+    }
+    case B_EXPAND: return ceil_div(s.W, 32 / I.group);
+    case B_WIT_HI:
+    case B_WIT_LO:
+    case B_WIT_IDX: return ceil_div(s.W, 32);
+    case B_TRACE: return 1;
+  }
+  return 0;
+}
+
+__device__ void start_pass(BState& s, const BatchArgs& A, uint32_t pass, uint64_t T) {
+  s.pass = pass;
+  s.T = T;
+  s.prune = A.prune;
+  s.early_exit = pass == PASS_MIN ? 0 : A.early_exit;
+  s.phase = B_SETUP;
+  s.best_all = kNone;
+  s.first_viol = 0;
+}
+
+__device__ void fail(BState& s, int code) {
+  if (!s.err) s.err = (uint32_t)code;
+  s.phase = B_DONE;
+}
+
+// The pass ends with `s.L` as its last level.
+__device__ void end_pass(BState& s, const BInst& I, const BatchArgs& A) {
+  s.states += s.offL + s.W;
+  s.checks += 1;
+  s.levels = s.L + 1;
+  if (s.pass == PASS_MIN) {
+    if (s.best_all == kNone) return fail(s, MC_ERR_CUDA);  // no terminal below T_ini
+    s.t_min = pack_time(s.best_all);
+    if (A.refine) start_pass(s, A, PASS_REFINE, s.t_min - 1);
+    else start_pass(s, A, PASS_FINAL, s.t_min);
+  } else if (s.pass == PASS_REFINE) {
+    if (s.first_viol) return fail(s, MC_ERR_CUDA);  // certificate disagrees
+    start_pass(s, A, PASS_FINAL, s.t_min);
+  } else {
+    s.stop_level = s.first_viol;
+    if (!s.first_viol) {
+      s.phase = B_DONE;
+      return;
+    }
+    const uint32_t wl = s.first_viol;
+    s.wpack = ldcg64(I.levels + 2 * wl + 1);
+    s.phase = B_WIT_HI;
+    s.L = wl;
+    s.W = ldcg64(I.levels + 2 * wl);
+    s.offL = ldcg64(I.off + wl);
+    s.wkey_lo = s.wkey_hi = s.widx = kNone;
+  }
+}
+
+__device__ void advance(BState& s, const BInst& I, const BatchArgs& A) {
+  if (!s.started) {
+    s.started = 1;
+    if (I.kind == 1) {
+      s.phase = B_SIM;
+      s.t_ini = kNone;
+    } else {
+      start_pass(s, A, PASS_FINAL, I.T_query);
+    }
+    return;
+  }
+  if (s.err) {
+    s.phase = B_DONE;
+    return;
+  }
+  switch (s.phase) {
+    case B_SIM:  // the min pass keeps successors up to T_ini when pruning
+      start_pass(s, A, PASS_MIN, A.prune ? s.t_ini : kNone);
+      break;
+    case B_SETUP:
+      s.phase = B_EXPAND;
+      s.L = 2;
+      s.W = (uint64_t)I.p.a * I.p.b;
+      s.offL = 1 + (uint64_t)I.p.a;
+      break;
+    case B_EXPAND: {
+      const uint64_t Wn = ldcg64(I.levels + 2 * (s.L + 1));
+      const uint64_t Bn = ldcg64(I.levels + 2 * (s.L + 1) + 1);
+      if (Wn == 0) {
+        end_pass(s, I, A);
+        break;
+      }
+      if (Bn != kNone) {
+        s.best_all = Bn < s.best_all ? Bn : s.best_all;
+        if (!s.first_viol) s.first_viol = s.L + 1;
+      }
+      I.off[s.L + 1] = s.offL + s.W;
+      s.offL += s.W;
+      s.W = Wn;
+      s.L += 1;
+      if (s.L >= I.p.max_level || (s.early_exit && Bn != kNone)) end_pass(s, I, A);
+      break;
+    }
+    case B_WIT_HI: s.phase = B_WIT_LO; break;
+    case B_WIT_LO: s.phase = B_WIT_IDX; break;
+    case B_WIT_IDX:
+      if (s.widx >= s.W) fail(s, MC_ERR_FRONTIER);
+      else s.phase = B_TRACE;
+      break;
+    case B_TRACE:
+      s.trace_len = s.L + 1;
+      s.phase = B_DONE;
+      break;
+    default: break;
+  }
+}
+
+struct Planner {
+  const BatchArgs* A;
+  __device__ void operator()() const {
+    __shared__ uint32_t s_count[kMaxBatch];
+    __shared__ unsigned long long s_part[kThreads];
+    const uint32_t n = A->n;
+    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+    const uint32_t i0 = threadIdx.x * per, i1 = min(n, i0 + per);
+    unsigned long long local = 0;
+    for (uint32_t i = i0; i < i1; ++i) {
+      BState s;
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(A->state + i);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s);
+      for (uint32_t k = 0; k < sizeof(BState) / 8; ++k) dst[k] = __ldcg(src + k);
+      const BInst& I = A->inst[i];
+      advance(s, I, *A);
+      const uint64_t c = task_count(s, I, *A);
+      s_count[i] = (uint32_t)c;
+      local += c;
+      unsigned long long* out = reinterpret_cast<unsigned long long*>(A->state + i);
+      for (uint32_t k = 0; k < sizeof(BState) / 8; ++k) out[k] = dst[k];
+    }
+    s_part[threadIdx.x] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long run = 0;
+      for (uint32_t t = 0; t < blockDim.x; ++t) {
+        const unsigned long long v = s_part[t];
+        s_part[t] = run;
+        run += v;
+      }
+    }
+    __syncthreads();
+    unsigned long long run = s_part[threadIdx.x];
+    for (uint32_t i = i0; i < i1; ++i) {
+      A->plan_prefix[i] = run;
+      run += s_count[i];
+    }
+    if (i1 == n && i0 < n) A->plan_prefix[n] = run;
+    if (n == 0 && threadIdx.x == 0) A->plan_prefix[0] = 0;
+  }
+};
+
+// ------------------------------------------------------------------ warp staging
+struct WarpBuf {
+  u128 keys[kWarpCap];
+  uint32_t par[kWarpCap];
+};
+
+struct Staging {
+  uint32_t inst = 0xFFFFFFFFu;  // instance the buffer holds entries for
+  uint32_t fill = 0;
+  uint64_t offN = 0;            // log offset of the level being appended to
+  uint64_t* rec = nullptr;      // {width} counter of that level
+};
+
+__device__ void flush(const BatchArgs& A, Staging& sg, WarpBuf& wb, uint32_t lane) {
+  if (sg.fill == 0) return;
+  __syncwarp();
+  const BInst& I = A.inst[sg.inst];
+  unsigned long long b = 0;
+  if (lane == 0) b = atomicAdd(reinterpret_cast<unsigned long long*>(sg.rec), (unsigned long long)sg.fill);
+  b = __shfl_sync(0xffffffffu, b, 0);
+  for (uint32_t x = lane; x < sg.fill; x += 32) {
+    const uint64_t at = sg.offN + b + x;
+    if (at < I.log_cap) {
+      KeyOps<u128>::store(I.log_keys, at, wb.keys[x]);
+      I.log_par[at] = wb.par[x];
+    } else {
+      set_error(&A.state[sg.inst].err, MC_ERR_FRONTIER);
+    }
+  }
+  __syncwarp();
+  sg.fill = 0;
+}
+
+// ------------------------------------------------------------------ tasks
+__device__ void task_setup(const BatchArgs& A, uint32_t inst, uint64_t q, uint32_t lane) {
+  const BInst& I = A.inst[inst];
+  const Params& p = I.p;
+  const uint64_t n16 = I.table_u64 / 2;
+  const uint64_t nlev = (uint64_t)p.max_level + 2;
+  const uint64_t ninit = 1 + (uint64_t)p.a + (uint64_t)p.a * p.b;
+  ulonglong2* tb = reinterpret_cast<ulonglong2*>(I.table);
+  for (uint32_t k = 0; k < kTaskUnits / 32; ++k) {
+    const uint64_t u = q * kTaskUnits + k * 32 + lane;
+    if (u < n16) tb[u] = make_ulonglong2(0, 0);
+    if (u < nlev) {
+      I.levels[2 * u] = u == 0 ? 1 : u == 1 ? p.a : u == 2 ? (uint64_t)p.a * p.b : 0;
+      I.levels[2 * u + 1] = kNone;
+      I.off[u] = u == 0 ? 0 : u == 1 ? 1 : u == 2 ? 1 + (uint64_t)p.a : 0;
+    }
+    if (u < ninit) {
+      u128 key = 0;
+      uint32_t par = kNoParent;
+      if (u >= 1 && u <= p.a) {
+        key = (u128)u << p.wg_shift;
+        par = 0;
+      } else if (u > p.a) {
+        const uint64_t y = u - 1 - p.a;
+        const uint32_t i = (uint32_t)(y / p.b), j = (uint32_t)(y % p.b);
+        key = ((u128)(i + 1) << p.wg_shift) | ((u128)(j + 1) << p.ts_shift);
+        par = i;
+      }
+      KeyOps<u128>::store(I.log_keys, u, key);
+      I.log_par[u] = par;
+    }
+  }
+}
+
+__device__ void task_expand(const BatchArgs& A, uint32_t inst, const BState& s, uint64_t q,
+                            uint32_t lane, Staging& sg, WarpBuf& wb) {
+  const BInst& I = A.inst[inst];
+  const Params& p = I.p;
+  const uint32_t g = I.group;
+  const uint32_t c = lane & (g - 1);
+  const uint64_t sidx = q * (32 / g) + lane / g;
+  const bool valid = sidx < s.W;
+  const uint32_t k_cur = s.L - 2;
+  const u128 key = valid ? KeyOps<u128>::load(I.log_keys, s.offL + sidx) : (u128)0;
+  const uint32_t c_shift = (p.P - 1 - (c < p.P ? c : 0)) * p.n_bits;
+  uint32_t i = 0, j = 0, r = 0;
+  uint64_t t_c = 0, clk = 0;
+  if (valid) {
+    i = field(key, p.wg_shift, p.wg_mask) - 1;
+    j = field(key, p.ts_shift, p.ts_mask) - 1;
+    const uint32_t cfg = i * p.b + j;
+    r = __ldg(p.N + cfg) - k_cur;
+    if (c < p.P) {
+      t_c = (uint64_t)__ldg(p.cost + cfg) * __ldg(p.speed + c);
+      clk = (uint64_t)field(key, c_shift, p.n_mask) * t_c;
+    }
+  }
+  const uint64_t mx = group_max(clk, g);
+  bool allowed = valid && c < p.P && r > 0;
+  if (p.rule == MC_GREEDY) {
+    const uint64_t mn = group_min((valid && c < p.P) ? clk : kNone, g);
+    allowed = allowed && clk == mn;
+  }
+  const uint64_t nclk = clk + t_c;
+  const uint64_t succ_time = nclk > mx ? nclk : mx;
+  if (s.prune && succ_time > s.T) allowed = false;
+  const u128 succ = key + ((u128)1 << c_shift);
+  int won = 0;
+  if (allowed) {
+    const uint64_t bkt = key_hash(succ) & I.bucket_mask;
+    const int rc = visited_insert<u128>(reinterpret_cast<u128*>(I.table), I.bucket_mask, I.max_probes,
+                                        succ, k_cur + 1, p, bkt, nullptr);
+    if (rc < 0) set_error(&A.state[inst].err, MC_ERR_TABLE_FULL);
+    won = rc > 0;
+  }
+  const uint32_t m = __ballot_sync(0xffffffffu, won);
+  if (m) {
+    if (won) {
+      const uint32_t at = sg.fill + __popc(m & ((1u << lane) - 1u));
+      wb.keys[at] = succ;
+      wb.par[at] = (uint32_t)sidx;
+    }
+    sg.fill += __popc(m);
+    // Step 2: a terminal winner with time <= T violates G(FIN -> time > T)
+    const uint64_t pk = warp_min((won && r == 1 && succ_time <= s.T) ? pack_tij(succ_time, i, j) : kNone);
+    if (lane == 0 && pk != kNone)
+      atomicMin(reinterpret_cast<unsigned long long*>(sg.rec + 1), (unsigned long long)pk);
+  }
+}
+
+__device__ void task_witness(const BatchArgs& A, uint32_t inst, const BState& s, uint64_t q,
+                             uint32_t lane) {
+  const BInst& I = A.inst[inst];
+  const Params& p = I.p;
+  const uint64_t x = q * 32 + lane;
+  if (x >= s.W) return;
+  const u128 key = KeyOps<u128>::load(I.log_keys, s.offL + x);
+  const uint64_t lo = (uint64_t)key, hi = (uint64_t)(key >> 64);
+  BState* gs = A.state + inst;
+  if (s.phase == B_WIT_IDX) {
+    if (lo == s.wkey_lo && hi == s.wkey_hi) gs->widx = x;
+    return;
+  }
+  const uint32_t ti = pack_i(s.wpack), tj = pack_j(s.wpack);
+  if (field(key, p.wg_shift, p.wg_mask) - 1 != ti || field(key, p.ts_shift, p.ts_mask) - 1 != tj) return;
+  const uint32_t cfg = ti * p.b + tj;
+  if (sum_n(key, p) != __ldg(p.N + cfg) || key_time(key, p, cfg) != pack_time(s.wpack)) return;
+  if (s.phase == B_WIT_HI)
+    atomicMin(reinterpret_cast<unsigned long long*>(&gs->wkey_hi), (unsigned long long)hi);
+  else if (hi == s.wkey_hi)
+    atomicMin(reinterpret_cast<unsigned long long*>(&gs->wkey_lo), (unsigned long long)lo);
+}
+
+__device__ void task_trace(const BatchArgs& A, uint32_t inst, const BState& s, uint32_t lane) {
+  if (lane != 0) return;
+  const BInst& I = A.inst[inst];
+  uint64_t idx = s.widx;
+  uint32_t l = s.L;
+  for (;;) {
+    const uint64_t at = ldcg64(I.off + l) + idx;
+    const u128 key = KeyOps<u128>::load(I.log_keys, at);
+    I.trace[2 * l] = (uint64_t)key;
+    I.trace[2 * l + 1] = (uint64_t)(key >> 64);
+    if (l == 0) break;
+    idx = __ldcg(I.log_par + at);
+    --l;
+  }
+}
+
+__device__ void task_sim(const BatchArgs& A, uint32_t inst, uint64_t q, uint32_t lane) {
+  const uint64_t w = q * 32 + lane;
+  if (w >= A.sim_walks) return;
+  const uint64_t t = simulate_walk(A.inst[inst].p, A.sim_seed, w);
+  atomicMin(reinterpret_cast<unsigned long long*>(&A.state[inst].t_ini), (unsigned long long)t);
+}
+
+// The fields of BState a task reads (written by the planner before the step).
+__device__ void load_state(const BState* g, BState& s) {
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(g);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s);
+#pragma unroll 4
+  for (uint32_t k = 0; k < sizeof(BState) / 8; ++k) dst[k] = __ldcg(src + k);
+}
+
+__global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs A) {
+  __shared__ unsigned long long s_prefix[kMaxBatch + 1];
+  __shared__ WarpBuf s_buf[kThreads / 32];
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warp = threadIdx.x >> 5;
+  const uint64_t warp_gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const Barrier bar{A.bar_lines, A.err, A.barrier_extra, A.timeout_ns};
+  const Planner planner{&A};
+  uint32_t epoch = 0;
+  if (!grid_sync(bar, epoch, planner)) return;  // first plan
+  for (;;) {
+    for (uint32_t i = threadIdx.x; i <= A.n; i += blockDim.x) s_prefix[i] = __ldcg(
+        reinterpret_cast<const unsigned long long*>(A.plan_prefix) + i);
+    __syncthreads();
+    const uint64_t total = s_prefix[A.n];
+    if (total == 0) break;
+    Staging sg;
+    BState s;
+    uint32_t cur = 0xFFFFFFFFu;
+    for (uint64_t t = warp_gid; t < total; t += n_warps) {
+      // instance of task t: last i with prefix[i] <= t (warp-uniform)
+      uint32_t lo = 0, hi = A.n;
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_prefix[mid] <= t) lo = mid;
+        else hi = mid;
+      }
+      const uint32_t inst = lo;
+      const uint64_t q = t - s_prefix[inst];
+      if (inst != cur) {
+        load_state(A.state + inst, s);
+        cur = inst;
+      }
+      switch (s.phase) {
+        case B_EXPAND:
+          if (sg.inst != inst) {
+            flush(A, sg, s_buf[warp], lane);
+            sg.inst = inst;
+            sg.offN = s.offL + s.W;
+            sg.rec = A.inst[inst].levels + 2 * (s.L + 1);
+          }
+          task_expand(A, inst, s, q, lane, sg, s_buf[warp]);
+          if (sg.fill > kWarpCap - 32) flush(A, sg, s_buf[warp], lane);
+          break;
+        case B_SETUP: task_setup(A, inst, q, lane); break;
+        case B_SIM: task_sim(A, inst, q, lane); break;
+        case B_WIT_HI:
+        case B_WIT_LO:
+        case B_WIT_IDX: task_witness(A, inst, s, q, lane); break;
+        case B_TRACE: task_trace(A, inst, s, lane); break;
+        default: break;
+      }
+    }
+    flush(A, sg, s_buf[warp], lane);
+    if (!grid_sync(bar, epoch, planner)) return;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_batch(int grid, int threads, const BatchArgs& args, cudaStream_t stream) {
+  void* params[] = {const_cast<BatchArgs*>(&args)};
+  return cudaLaunchCooperativeKernel((const void*)batch_kernel, dim3(grid), dim3(threads), params, 0,
+                                     stream);
+}
+
+int batch_kernel_occupancy(int threads, int* blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void*)batch_kernel,
+                                                       threads, 0) == cudaSuccess
+             ? 0
+             : -1;
+}
+
+}  // namespace mc
+
+// ====================================================================== host API
+namespace {
+
+struct BatchBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+uint64_t al256(uint64_t x) { return (x + 255) & ~255ull; }
+
+}  // namespace
+
+struct mc_batch {
+  uint32_t n = 0;
+  mc_options opt{};
+  std::vector<mc::BInst> inst;        // host copy; pointers filled at reserve
+  std::vector<mc_layout> lay;
+  std::vector<std::vector<uint32_t>> params;  // N, cost, speed per instance
+  std::vector<std::vector<uint32_t>> wg, ts;
+  std::vector<uint64_t> pool_off;     // byte offset of each instance's region
+  uint64_t pool_bytes = 0;
+  bool reserved = false;
+  int device = -1, grid = 0, threads = 0;
+  cudaStream_t stream = nullptr;
+  mc_alloc_fn alloc = nullptr;
+  mc_free_fn dealloc = nullptr;
+  void* actx = nullptr;
+  std::vector<BatchBuf> bufs;
+  uint8_t* d_pool = nullptr;
+  mc::BInst* d_inst = nullptr;
+  mc::BState* d_state = nullptr;
+  uint64_t* d_prefix = nullptr;
+  uint32_t* d_ctrl = nullptr;         // err word, then the barrier lines
+  std::vector<mc::BState> h_state;
+  cudaEvent_t ev[2] = {};
+  mc_stats stats{};
+  std::string last_err;
+};
+
+namespace {
+
+int bfail(mc_batch* b, cudaError_t e, const char* what) {
+  b->last_err = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return MC_ERR_CUDA;
+}
+
+#define MCB_CUDA(b, call)                                  \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return bfail((b), e_, #call);   \
+  } while (0)
+
+void* balloc(mc_batch* b, size_t bytes) {
+  bytes = al256(bytes ? bytes : 256);
+  void* p = nullptr;
+  if (b->alloc) p = b->alloc(bytes, (void*)b->stream, b->actx);
+  else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) b->bufs.push_back({p, bytes});
+  return p;
+}
+
+void brelease(mc_batch* b) {
+  if (!b->bufs.empty()) {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (b->device >= 0 && prev != b->device) cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    for (const BatchBuf& x : b->bufs) {
+      if (b->dealloc) b->dealloc(x.ptr, x.bytes, (void*)b->stream, b->actx);
+      else cudaFree(x.ptr);
+    }
+    b->bufs.clear();
+    if (b->device >= 0 && prev >= 0 && prev != b->device) cudaSetDevice(prev);
+  }
+  for (cudaEvent_t& e : b->ev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
+  b->reserved = false;
+}
+
+int breserve(mc_batch* b) {
+  if (b->reserved) return MC_OK;
+  MCB_CUDA(b, cudaGetDevice(&b->device));
+  int sms = 0, coop = 0, bps = 0;
+  MCB_CUDA(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+  MCB_CUDA(b, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->device));
+  b->threads = (int)mc::kThreads;
+  if (!coop || mc::batch_kernel_occupancy(b->threads, &bps) || bps < 1) {
+    b->last_err = "cooperative launch unavailable";
+    cudaGetLastError();
+    return MC_ERR_CUDA;
+  }
+  if (b->opt.blocks_per_sm) bps = std::min<int>(bps, (int)b->opt.blocks_per_sm);
+  b->grid = sms * bps;
+  b->d_pool = (uint8_t*)balloc(b, b->pool_bytes);
+  b->d_inst = (mc::BInst*)balloc(b, sizeof(mc::BInst) * b->n);
+  b->d_state = (mc::BState*)balloc(b, sizeof(mc::BState) * b->n);
+  b->d_prefix = (uint64_t*)balloc(b, 8ull * (b->n + 1));
+  b->d_ctrl = (uint32_t*)balloc(b, 256 + mc::kBarBytes);
+  if (!b->d_pool || !b->d_inst || !b->d_state || !b->d_prefix || !b->d_ctrl) {
+    brelease(b);
+    return MC_ERR_NOMEM;
+  }
+  for (cudaEvent_t& e : b->ev) MCB_CUDA(b, cudaEventCreate(&e));
+  // carve each instance's region and upload its tables
+  for (uint32_t i = 0; i < b->n; ++i) {
+    const mc_layout& L = b->lay[i];
+    mc::BInst& I = b->inst[i];
+    uint8_t* q = b->d_pool + b->pool_off[i];
+    const uint32_t* hp = b->params[i].data();
+    const size_t np = b->params[i].size();
+    MCB_CUDA(b, cudaMemcpyAsync(q, hp, np * 4, cudaMemcpyHostToDevice, b->stream));
+    b->stats.h2d_bytes += np * 4;
+    const uint64_t ab = (uint64_t)I.p.a * I.p.b;
+    I.p.N = (const uint32_t*)q;
+    I.p.cost = (const uint32_t*)q + ab;
+    I.p.speed = (const uint32_t*)q + 2 * ab;
+    q += al256(np * 4);
+    const uint64_t L2 = L.max_level + 2;
+    I.levels = (uint64_t*)q;
+    q += al256(16 * L2);
+    I.off = (uint64_t*)q;
+    q += al256(8 * L2);
+    I.trace = (uint64_t*)q;
+    q += al256(16 * L2);
+    I.table = q;
+    q += al256(16 * L.table_slots);
+    I.log_keys = q;
+    q += al256(16 * L.log_capacity);
+    I.log_par = (uint32_t*)q;
+  }
+  MCB_CUDA(b, cudaStreamSynchronize(b->stream));
+  b->reserved = true;
+  return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mc_batch_create(const mc_model_desc* descs, uint32_t n, const mc_options* opt, mc_batch** out) {
+  if (!descs || !out || n == 0 || n > mc::kMaxBatch) return MC_ERR_INVAL;
+  *out = nullptr;
+  mc_options o;
+  if (opt) o = *opt;
+  else mc_options_default(&o);
+  mc_batch* b = new (std::nothrow) mc_batch;
+  if (!b) return MC_ERR_NOMEM;
+  b->n = n;
+  b->opt = o;
+  b->inst.resize(n);
+  b->lay.resize(n);
+  b->params.resize(n);
+  b->wg.resize(n);
+  b->ts.resize(n);
+  b->pool_off.resize(n);
+  b->h_state.resize(n);
+  uint64_t off = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    mc_model_desc d = descs[i];
+    d.key_bits = 128;  // every instance of a batch uses 128-bit keys
+    mc_model* m = nullptr;
+    int rc = mc_model_create(&d, &o, &m);
+    if (rc) {
+      delete b;
+      return rc;
+    }
+    mc_layout& L = b->lay[i];
+    rc = mc_model_layout(m, &L);
+    mc_model_destroy(m);
+    if (rc) {
+      delete b;
+      return rc;
+    }
+    if (L.log_capacity == UINT64_MAX || L.table_slots == 0) {
+      delete b;
+      return MC_ERR_NOMEM;
+    }
+    const uint64_t ab = (uint64_t)d.n_wg * d.n_ts;
+    std::vector<uint32_t>& pr = b->params[i];
+    pr.assign(d.n_workgroups, d.n_workgroups + ab);
+    pr.insert(pr.end(), d.cost, d.cost + ab);
+    for (uint32_t c = 0; c < d.P; ++c) pr.push_back(d.speed ? d.speed[c] : 1);
+    if (d.wg_values) b->wg[i].assign(d.wg_values, d.wg_values + d.n_wg);
+    if (d.ts_values) b->ts[i].assign(d.ts_values, d.ts_values + d.n_ts);
+    mc::BInst& I = b->inst[i];
+    std::memset(&I, 0, sizeof(I));
+    mc::Params& p = I.p;
+    p.a = d.n_wg;
+    p.b = d.n_ts;
+    p.P = d.P;
+    p.rule = d.rule;
+    p.n_bits = L.n_bits;
+    p.ts_shift = L.ts_shift;
+    p.wg_shift = L.wg_shift;
+    p.ts_mask = (1u << L.ts_bits) - 1;
+    p.wg_mask = (1u << L.wg_bits) - 1;
+    p.max_level = L.max_level;
+    p.n_mask = (1ull << L.n_bits) - 1;
+    const uint32_t nf = d.P * L.n_bits;
+    p.swar_ok = nf <= 64;
+    p.swar_mask = nf >= 64 ? ~0ull : ((1ull << nf) - 1);
+    for (uint32_t t = 0; t < d.P && t * L.n_bits < 64; ++t) p.swar_mul |= 1ull << (t * L.n_bits);
+    I.bucket_mask = L.table_slots / 2 - 1;
+    I.table_u64 = L.table_slots * 2;
+    I.log_cap = L.log_capacity;
+    I.max_probes = o.max_probes ? o.max_probes
+                                : (uint32_t)std::min<uint64_t>(L.table_slots / 2, 0xFFFFFFFFu);
+    I.group = 1;
+    while (I.group < d.P) I.group <<= 1;
+    const uint64_t L2 = L.max_level + 2;
+    b->pool_off[i] = off;
+    off += al256(pr.size() * 4) + al256(16 * L2) + al256(8 * L2) + al256(16 * L2) +
+           al256(16 * L.table_slots) + al256(16 * L.log_capacity) + al256(4 * L.log_capacity);
+  }
+  b->pool_bytes = off;
+  *out = b;
+  return MC_OK;
+}
+
+void mc_batch_destroy(mc_batch* b) {
+  if (!b) return;
+  brelease(b);
+  delete b;
+}
+
+int mc_batch_set_stream(mc_batch* b, void* stream) {
+  if (!b) return MC_ERR_INVAL;
+  b->stream = (cudaStream_t)stream;
+  return MC_OK;
+}
+
+int mc_batch_set_allocator(mc_batch* b, mc_alloc_fn alloc, mc_free_fn free_fn, void* ctx) {
+  if (!b || !alloc || !free_fn || b->reserved) return MC_ERR_INVAL;
+  b->alloc = alloc;
+  b->dealloc = free_fn;
+  b->actx = ctx;
+  return MC_OK;
+}
+
+int mc_batch_device_bytes(const mc_batch* b, uint64_t* out) {
+  if (!b || !out) return MC_ERR_INVAL;
+  *out = b->pool_bytes;
+  return MC_OK;
+}
+
+int mc_batch_run(mc_batch* b, const mc_query* queries, mc_batch_result* results) {
+  if (!b || !queries || !results) return MC_ERR_INVAL;
+  for (uint32_t i = 0; i < b->n; ++i)
+    if (queries[i].kind > MC_QUERY_MIN_TIME) return MC_ERR_INVAL;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (b->device >= 0 && prev != b->device) cudaSetDevice(b->device);
+  int rc = breserve(b);
+  if (rc) return rc;
+  for (uint32_t i = 0; i < b->n; ++i) {
+    b->inst[i].kind = queries[i].kind;
+    b->inst[i].T_query = queries[i].T;
+  }
+  mc::BatchArgs A{};
+  A.inst = b->d_inst;
+  A.state = b->d_state;
+  A.n = b->n;
+  A.refine = b->opt.refine;
+  A.plan_prefix = b->d_prefix;
+  A.err = b->d_ctrl;
+  A.bar_lines = b->d_ctrl + 64;
+  A.barrier_extra = b->opt.debug_barrier_extra;
+  A.sim_walks = b->opt.sim_walks;
+  A.sim_seed = b->opt.sim_seed;
+  A.timeout_ns = b->opt.barrier_timeout_ns ? b->opt.barrier_timeout_ns : 60ull * 1000000000ull;
+  A.prune = b->opt.prune;
+  A.early_exit = b->opt.early_exit;
+  MCB_CUDA(b, cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(mc::BInst) * b->n,
+                              cudaMemcpyHostToDevice, b->stream));
+  MCB_CUDA(b, cudaMemsetAsync(b->d_state, 0, sizeof(mc::BState) * b->n, b->stream));
+  MCB_CUDA(b, cudaMemsetAsync(b->d_ctrl, 0, 256 + mc::kBarBytes, b->stream));
+  b->stats.h2d_bytes += sizeof(mc::BInst) * b->n;
+  if (b->opt.timing) MCB_CUDA(b, cudaEventRecord(b->ev[0], b->stream));
+  MCB_CUDA(b, mc::launch_batch(b->grid, b->threads, A, b->stream));
+  if (b->opt.timing) MCB_CUDA(b, cudaEventRecord(b->ev[1], b->stream));
+  uint32_t err = 0;
+  MCB_CUDA(b, cudaMemcpyAsync(b->h_state.data(), b->d_state, sizeof(mc::BState) * b->n,
+                              cudaMemcpyDeviceToHost, b->stream));
+  MCB_CUDA(b, cudaMemcpyAsync(&err, b->d_ctrl, 4, cudaMemcpyDeviceToHost, b->stream));
+  MCB_CUDA(b, cudaStreamSynchronize(b->stream));
+  b->stats.d2h_bytes += sizeof(mc::BState) * b->n + 4;
+  b->stats.explore_launches += 1;
+  if (b->opt.timing) {
+    float ms = 0.f;
+    MCB_CUDA(b, cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+    b->stats.explore_ms += ms;
+  }
+  if (b->device >= 0 && prev >= 0 && prev != b->device) cudaSetDevice(prev);
+  if (err) return (int)err;
+  for (uint32_t i = 0; i < b->n; ++i) {
+    const mc::BState& s = b->h_state[i];
+    mc_batch_result& r = results[i];
+    std::memset(&r, 0, sizeof(r));
+    r.status = s.err ? (int)s.err : (s.phase == mc::B_DONE ? MC_OK : MC_ERR_CUDA);
+    r.kind = queries[i].kind;
+    r.states = s.states;
+    r.checks = s.checks;
+    r.levels = s.levels;
+    r.t_ini = queries[i].kind == MC_QUERY_MIN_TIME ? s.t_ini : 0;
+    r.holds = s.stop_level == 0;
+    b->stats.states += s.states;
+    if (s.stop_level) {
+      r.time = mc::pack_time(s.wpack);
+      r.wg_index = mc::pack_i(s.wpack);
+      r.ts_index = mc::pack_j(s.wpack);
+      r.wg = b->wg[i].empty() ? r.wg_index : b->wg[i][r.wg_index];
+      r.ts = b->ts[i].empty() ? r.ts_index : b->ts[i][r.ts_index];
+      r.level = s.stop_level;
+      r.key[0] = s.wkey_lo;
+      r.key[1] = s.wkey_hi;
+    }
+  }
+  return MC_OK;
+}
+
+int mc_batch_trace(mc_batch* b, uint32_t i, uint64_t* keys, uint32_t cap, uint32_t* len) {
+  if (!b || !len || i >= b->n || (!keys && cap)) return MC_ERR_INVAL;
+  const mc::BState& s = b->h_state[i];
+  *len = s.trace_len;
+  if (!b->reserved || s.trace_len == 0 || cap == 0) return MC_OK;
+  const uint32_t k = std::min(cap, s.trace_len);
+  MCB_CUDA(b, cudaMemcpyAsync(keys, b->inst[i].trace, 16ull * k, cudaMemcpyDeviceToHost, b->stream));
+  MCB_CUDA(b, cudaStreamSynchronize(b->stream));
+  b->stats.d2h_bytes += 16ull * k;
+  return MC_OK;
+}
+
+int mc_batch_get_stats(const mc_batch* b, mc_stats* out) {
+  if (!b || !out) return MC_ERR_INVAL;
+  *out = b->stats;
+  return MC_OK;
+}
+
+const char* mc_batch_last_error(const mc_batch* b) { return b ? b->last_err.c_str() : ""; }
+
+}  // extern "C"

@@ -103,3 +103,91 @@ cudaError_t launch_simulate(const Params& p, uint64_t seed, uint32_t walks, uint
                             cudaStream_t stream);
 
 }  // namespace mc
+
+// ---------------------------------------------------------------------------
+// Batched exploration (mc_batch.cu): many models advance in lockstep inside
+// one persistent launch.  Keys are 128-bit for every instance.
+namespace mc {
+
+constexpr uint32_t kMaxBatch = 1024;     // instances per batch launch
+constexpr uint32_t kTaskUnits = 256;     // units one set-up task initialises (8 per lane)
+
+// Phase of one instance between two device-wide barriers.
+enum BPhase : uint32_t {
+  B_DONE = 0,
+  B_SIM = 1,      // random runs for T_ini (min-time queries)
+  B_SETUP = 2,    // clear the visited set, write levels 0..2
+  B_EXPAND = 3,   // expand level L into L+1
+  B_WIT_HI = 4,   // witness scan of level L: smallest high key word
+  B_WIT_LO = 5,   //   smallest low word among those
+  B_WIT_IDX = 6,  //   its index in the level
+  B_TRACE = 7,    // parent walk into the trace buffer
+};
+
+// Pass of a query: min-time runs 1 (minimum), 2 (certificate T_min - 1) and
+// 3 (counterexample at T_min); a check runs 3 at its own T.
+enum BPass : uint32_t { PASS_NONE = 0, PASS_MIN = 1, PASS_REFINE = 2, PASS_FINAL = 3 };
+
+// Per instance, fixed for a launch.
+struct BInst {
+  Params p;
+  void* table;
+  uint64_t bucket_mask;
+  uint64_t table_u64;
+  void* log_keys;         // u128 keys
+  uint32_t* log_par;
+  uint64_t log_cap;
+  uint64_t* levels;       // [max_level + 2] x {width, min packed violating terminal}
+  uint64_t* off;          // [max_level + 2]
+  uint64_t* trace;        // [(max_level + 2) * 2]
+  uint32_t max_probes;
+  uint32_t group;         // lanes per state: next power of two >= P
+  uint32_t kind;          // MC_QUERY_*
+  uint32_t pad;
+  uint64_t T_query;       // threshold of a check query
+};
+
+// Per instance, rewritten by the planner at every barrier; the witness words
+// and err are also updated by atomics during a step.
+struct BState {
+  uint32_t phase;         // BPhase
+  uint32_t pass;          // BPass
+  uint32_t L;             // level expanded (B_EXPAND) or scanned (witness phases)
+  uint32_t err;           // first error of this instance
+  uint64_t W;             // width of level L
+  uint64_t offL;          // log offset of level L
+  uint64_t T;             // threshold of the current pass
+  uint32_t prune, early_exit;
+  uint32_t started;       // 0 until the first plan
+  uint32_t checks;        // passes finished
+  uint64_t t_ini;         // least simulated terminal time (atomicMin)
+  uint64_t t_min;         // minimum of the min pass
+  uint64_t states;        // unique states over finished passes
+  uint64_t best_all;      // min packed violating terminal over the pass's levels
+  uint32_t first_viol;    // first level of the pass with a violating terminal
+  uint32_t levels;        // levels of the last finished pass
+  uint32_t stop_level;    // counterexample level of the final pass (0: holds)
+  uint32_t trace_len;
+  uint64_t wpack;         // packed (time, i, j) of the counterexample
+  uint64_t wkey_lo, wkey_hi, widx;
+};
+
+struct BatchArgs {
+  BInst* inst;
+  BState* state;
+  uint32_t n;
+  uint32_t refine;
+  uint64_t* plan_prefix;  // [n + 1] task prefix of the current step
+  uint32_t* err;          // launch-wide error word (barrier timeout)
+  uint32_t* bar_lines;    // device-wide barrier lines
+  uint32_t barrier_extra;
+  uint32_t sim_walks;
+  uint64_t sim_seed;
+  uint64_t timeout_ns;
+  uint32_t prune, early_exit;
+};
+
+cudaError_t launch_batch(int grid, int threads, const BatchArgs& args, cudaStream_t stream);
+int batch_kernel_occupancy(int threads, int* blocks_per_sm);
+
+}  // namespace mc

@@ -23,276 +23,12 @@
 // and nothing is cleared between levels.
 #include <cstdint>
 
-#include "mc_internal.h"
-#include "mc.h"
+#include "mc_device.cuh"
 
 namespace mc {
 namespace {
 
-typedef unsigned __int128 u128;
-
-// ------------------------------------------------------------------ memory
-__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
-  uint64_t v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* p, uint32_t v) {
-  uint32_t old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
-}
-__device__ __forceinline__ void ld_relaxed_v2u64(const uint64_t* p, uint64_t& a, uint64_t& b) {
-  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
-}
-__device__ __forceinline__ uint64_t globaltimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// 16-byte global -> shared copy that bypasses L1 (the visited set is written
-// by atomics at L2), then wait for all of this thread's copies.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
-__device__ __forceinline__ void set_error(Ctrl* ctrl, int code) {
-  atomicCAS(&ctrl->err, 0u, (uint32_t)code);
-}
-
-// ------------------------------------------------------------------ keys
-template <class K>
-struct KeyOps;
-
-template <>
-struct KeyOps<uint64_t> {
-  static constexpr int kSlots = 4;  // keys per 32-byte bucket
-  __device__ static uint64_t load(const void* base, uint64_t i) {
-    return __ldcg(reinterpret_cast<const unsigned long long*>(base) + i);
-  }
-  __device__ static void store(void* base, uint64_t i, uint64_t k) {
-    reinterpret_cast<unsigned long long*>(base)[i] = k;
-  }
-  __device__ static uint64_t lo(uint64_t k) { return k; }
-  __device__ static uint64_t hi(uint64_t) { return 0; }
-};
-
-template <>
-struct KeyOps<u128> {
-  static constexpr int kSlots = 2;
-  __device__ static u128 load(const void* base, uint64_t i) {
-    ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(base) + i);
-    return ((u128)v.y << 64) | v.x;
-  }
-  __device__ static void store(void* base, uint64_t i, u128 k) {
-    reinterpret_cast<ulonglong2*>(base)[i] = make_ulonglong2((uint64_t)k, (uint64_t)(k >> 64));
-  }
-  __device__ static uint64_t lo(u128 k) { return (uint64_t)k; }
-  __device__ static uint64_t hi(u128 k) { return (uint64_t)(k >> 64); }
-};
-
-// splitmix64 output function (Steele, Lea, Flood 2014)
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-__device__ __forceinline__ uint64_t key_hash(uint64_t k) { return mix64(k); }
-__device__ __forceinline__ uint64_t key_hash(u128 k) {
-  return mix64((uint64_t)k ^ mix64((uint64_t)(k >> 64) + 0x9E3779B97F4A7C15ull));
-}
-
-template <class K>
-__device__ __forceinline__ uint32_t field(K key, uint32_t shift, uint64_t mask) {
-  return (uint32_t)((uint64_t)(key >> shift) & mask);
-}
-
-// sum of the n_c fields of a key = its BFS level - 2
-template <class K>
-__device__ __forceinline__ uint32_t sum_n(K key, const Params& p) {
-  if (p.swar_ok) {
-    uint64_t x = (uint64_t)key & p.swar_mask;
-    return (uint32_t)(((x * p.swar_mul) >> ((p.P - 1) * p.n_bits)) & p.n_mask);
-  }
-  uint32_t s = 0;
-  for (uint32_t c = 0; c < p.P; ++c) s += field(key, (p.P - 1 - c) * p.n_bits, p.n_mask);
-  return s;
-}
-
-// model time of a key (max over units of n_c * cost * speed_c)
-template <class K>
-__device__ __forceinline__ uint64_t key_time(K key, const Params& p, uint32_t cfg) {
-  uint64_t c0 = __ldg(p.cost + cfg);
-  uint64_t mx = 0;
-  for (uint32_t c = 0; c < p.P; ++c) {
-    uint64_t t = (uint64_t)field(key, (p.P - 1 - c) * p.n_bits, p.n_mask) * c0 * __ldg(p.speed + c);
-    mx = t > mx ? t : mx;
-  }
-  return mx;
-}
-
-// ------------------------------------------------------------------ visited set
-__device__ __forceinline__ u128 cas128(u128* addr, u128 cmp, u128 val) {
-  uint64_t olo, ohi;
-  asm volatile(
-      "{\n\t.reg .b128 c, v, o;\n\t"
-      "mov.b128 c, {%2, %3};\n\t"
-      "mov.b128 v, {%4, %5};\n\t"
-      "atom.relaxed.gpu.global.cas.b128 o, [%6], c, v;\n\t"
-      "mov.b128 {%0, %1}, o;\n\t}"
-      : "=l"(olo), "=l"(ohi)
-      : "l"((uint64_t)cmp), "l"((uint64_t)(cmp >> 64)), "l"((uint64_t)val),
-        "l"((uint64_t)(val >> 64)), "l"(addr)
-      : "memory");
-  return ((u128)ohi << 64) | olo;
-}
-
-__device__ __forceinline__ uint64_t slot_cas(uint64_t* addr, uint64_t cmp, uint64_t val) {
-  return atomicCAS(reinterpret_cast<unsigned long long*>(addr), cmp, val);
-}
-__device__ __forceinline__ u128 slot_cas(u128* addr, u128 cmp, u128 val) { return cas128(addr, cmp, val); }
-
-template <class K>
-__device__ __forceinline__ void load_bucket(const K* b, K (&v)[KeyOps<K>::kSlots]);
-
-template <>
-__device__ __forceinline__ void load_bucket<uint64_t>(const uint64_t* b, uint64_t (&v)[4]) {
-  ulonglong2 x = __ldcg(reinterpret_cast<const ulonglong2*>(b));
-  ulonglong2 y = __ldcg(reinterpret_cast<const ulonglong2*>(b) + 1);
-  v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
-}
-template <>
-__device__ __forceinline__ void load_bucket<u128>(const u128* b, u128 (&v)[2]) {
-  ulonglong2 x = __ldcg(reinterpret_cast<const ulonglong2*>(b));
-  ulonglong2 y = __ldcg(reinterpret_cast<const ulonglong2*>(b) + 1);
-  v[0] = ((u128)x.y << 64) | x.x;
-  v[1] = ((u128)y.y << 64) | y.x;
-}
-
-// Insert `key` (sum of n fields = lvl) into the visited set, starting at
-// bucket `bkt` whose 32 bytes are already in `first` (shared memory).
-// Returns 1 if this thread inserted it, 0 if it was already there, -1 when
-// the probe limit was reached.  A slot is free when it holds 0 or a key of an
-// earlier level; the first free slot of the probe sequence is taken.
-template <class K>
-__device__ int visited_insert(K* table, uint64_t bucket_mask, uint32_t max_probes, K key,
-                              uint32_t lvl, const Params& p, uint64_t bkt, const K* first) {
-  constexpr int S = KeyOps<K>::kSlots;
-  for (uint32_t probe = 0; probe < max_probes; ++probe) {
-    K* slot = table + bkt * S;
-    K v[S];
-    if (probe == 0) {
-#pragma unroll
-      for (int s = 0; s < S; ++s) v[s] = first[s];
-    } else {
-      load_bucket<K>(slot, v);
-    }
-    bool hit = false;
-#pragma unroll
-    for (int s = 0; s < S; ++s) hit |= (v[s] == key);
-    if (hit) return 0;
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      K cur = v[s];
-      // a slot changes at most once per level (free -> a key of this
-      // level), so two CAS attempts settle it; the bound is defensive
-      for (int tries = 0; tries < 3; ++tries) {
-        if (cur == key) return 0;
-        if (cur != (K)0 && sum_n(cur, p) >= lvl) break;  // taken this level
-        K old = slot_cas(slot + s, cur, key);
-        if (old == cur) return 1;
-        cur = old;
-      }
-    }
-    bkt = (bkt + 1) & bucket_mask;
-  }
-  return -1;
-}
-
-// ------------------------------------------------------------------ device-wide barrier
-// All blocks are co-resident (cooperative launch).  Arrivals are counted in
-// two levels -- kBarGroups group counters, then a top counter, each in its
-// own 128-byte line -- so hundreds of blocks do not serialise on one address.
-// Counters only grow: the k-th barrier of a pass (k = 1, 2, ...) completes
-// when a group counter reaches k * members and the top counter k * groups,
-// and the last arriver publishes generation k with a release store.  Every
-// block passes the same sequence of barriers, so each tracks k itself.
-// Arrivals use acquire-release atomics after __syncthreads, waiters an
-// acquire load, so no separate fences are needed.  Each wait is bounded by
-// timeout_ns of %globaltimer; on expiry the block records MC_ERR_TIMEOUT,
-// raises the abort flag so the other waiters leave too, and returns false.
-__device__ bool grid_sync(const ExploreArgs& A, uint32_t& epoch) {
-  __shared__ uint32_t s_ok;
-  __syncthreads();
-  const uint32_t target = ++epoch;
-  if (threadIdx.x == 0) {
-    uint32_t ok = 1;
-    const uint32_t groups = gridDim.x < kBarGroups ? gridDim.x : kBarGroups;
-    const uint32_t g = blockIdx.x % groups;
-    const uint32_t members = gridDim.x / groups + (g < gridDim.x % groups ? 1u : 0u);
-    uint32_t* bar = A.bar_groups;
-    uint32_t* top = bar + kBarTop * 32;
-    uint32_t* gen = bar + kBarGen * 32;
-    uint32_t* abort_flag = bar + kBarAbort * 32;
-    if (atom_add_acq_rel(bar + g * 32, 1u) + 1 == members * target) {
-      if (atom_add_acq_rel(top, 1u) + 1 == groups * target && A.barrier_extra == 0)
-        st_release_u32(gen, target);
-    }
-    const uint64_t t0 = globaltimer();
-    uint32_t spins = 0;
-    while (ld_acquire_u32(gen) < target) {
-      if (ld_relaxed_u32(abort_flag)) { ok = 0; break; }
-      if ((++spins & 15u) == 0 && globaltimer() - t0 > A.timeout_ns) {
-        set_error(A.ctrl, MC_ERR_TIMEOUT);
-        atomicExch(abort_flag, 1u);
-        ok = 0;
-        break;
-      }
-      __nanosleep(32);
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-// ------------------------------------------------------------------ tile reductions
-template <int TILE>
-__device__ __forceinline__ uint64_t tile_max(uint64_t v) {
-#pragma unroll
-  for (int o = TILE / 2; o > 0; o >>= 1) {
-    uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = w > v ? w : v;
-  }
-  return v;
-}
-template <int TILE>
-__device__ __forceinline__ uint64_t tile_min(uint64_t v) {
-#pragma unroll
-  for (int o = TILE / 2; o > 0; o >>= 1) {
-    uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = w < v ? w : v;
-  }
-  return v;
-}
+using namespace mc::dev;
 
 // ------------------------------------------------------------------ expansion of one level
 // Winners are staged per warp in shared memory.  A warp whose buffer is
@@ -485,6 +221,7 @@ __global__ void __launch_bounds__(kThreads) explore_kernel(const ExploreArgs A) 
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
   __shared__ Stage<K> stage;
   uint32_t epoch = 0;  // device-wide barriers passed in this pass
+  const Barrier bar{A.bar_groups, &A.ctrl->err, A.barrier_extra, A.timeout_ns};
 
   uint64_t T = A.T;
   if (A.T_src) T = ld_relaxed_u64(A.T_src) + (uint64_t)A.T_delta;
@@ -524,7 +261,7 @@ __global__ void __launch_bounds__(kThreads) explore_kernel(const ExploreArgs A) 
       ctrl->widx = kNone;
     }
   }
-  if (!grid_sync(A, epoch)) return;
+  if (!grid_sync(bar, epoch)) return;
 
   // level loop (one device-wide barrier per level)
   uint32_t last = 2;
@@ -536,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) explore_kernel(const ExploreArgs A) 
     const uint64_t offN = off_last + W;
     if (gtid == 0) A.off[L + 1] = offN;
     expand_level<K, TILE, RULE>(A, stage, T, L, off_last, W, offN);
-    if (!grid_sync(A, epoch)) return;
+    if (!grid_sync(bar, epoch)) return;
     if (ld_relaxed_u32(&ctrl->err)) break;
     uint64_t Wn, Bn;  // width and violating minimum of level L+1, one 16-byte load
     ld_relaxed_v2u64(A.levels + 2 * (L + 1), Wn, Bn);
@@ -606,7 +343,7 @@ __global__ void __launch_bounds__(kThreads) explore_kernel(const ExploreArgs A) 
       atomicMin(reinterpret_cast<unsigned long long*>(&ctrl->wkey_hi),
                 (unsigned long long)KeyOps<K>::hi(key));
   }
-  if (!grid_sync(A, epoch)) return;
+  if (!grid_sync(bar, epoch)) return;
   if (sizeof(K) == 16) {
     const uint64_t whi = ld_relaxed_u64(&ctrl->wkey_hi);
     for (uint64_t x = gtid; x < Ww; x += nthreads) {
@@ -618,7 +355,7 @@ __global__ void __launch_bounds__(kThreads) explore_kernel(const ExploreArgs A) 
       atomicMin(reinterpret_cast<unsigned long long*>(&ctrl->wkey_lo),
                 (unsigned long long)KeyOps<K>::lo(key));
     }
-    if (!grid_sync(A, epoch)) return;
+    if (!grid_sync(bar, epoch)) return;
   } else if (gtid == 0) {
     ctrl->wkey_hi = 0;
   }
@@ -630,7 +367,7 @@ __global__ void __launch_bounds__(kThreads) explore_kernel(const ExploreArgs A) 
       if (KeyOps<K>::lo(key) == wlo && KeyOps<K>::hi(key) == whi) ctrl->widx = x;
     }
   }
-  if (!grid_sync(A, epoch)) return;
+  if (!grid_sync(bar, epoch)) return;
   // trace: follow parent indices from the witness back to s0
   if (gtid == 0) {
     uint64_t idx = ld_relaxed_u64(&ctrl->widx);
@@ -654,49 +391,13 @@ __global__ void __launch_bounds__(kThreads) explore_kernel(const ExploreArgs A) 
 }
 
 // ------------------------------------------------------------------ simulation (T_ini)
-__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t ctr) {
-  return mix64(seed + (ctr + 1) * 0x9E3779B97F4A7C15ull);
-}
-
 // One random run per thread (Section 4, Step 3: a simulation gives T_ini).
 __global__ void simulate_kernel(const Params p, uint64_t seed, uint32_t walks, uint64_t* t_out) {
   const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t w = gtid; w < walks; w += nthreads) {
-    uint64_t ctr = w << 32;
-    const uint32_t i = (uint32_t)(splitmix64_at(seed, ctr++) % p.a);
-    const uint32_t j = (uint32_t)(splitmix64_at(seed, ctr++) % p.b);
-    const uint32_t cfg = i * p.b + j;
-    const uint32_t N = __ldg(p.N + cfg);
-    const uint64_t cost = __ldg(p.cost + cfg);
-    uint64_t clk[kMaxP], t[kMaxP];
-    for (uint32_t c = 0; c < p.P; ++c) {
-      t[c] = cost * __ldg(p.speed + c);
-      clk[c] = 0;
-    }
-    for (uint32_t k = 0; k < N; ++k) {
-      uint32_t c = 0;
-      if (p.rule == MC_FREE) {
-        c = (uint32_t)(splitmix64_at(seed, ctr++) % p.P);
-      } else {
-        uint64_t mn = kNone;
-        for (uint32_t u = 0; u < p.P; ++u) mn = clk[u] < mn ? clk[u] : mn;
-        uint32_t cnt = 0;
-        for (uint32_t u = 0; u < p.P; ++u) cnt += clk[u] == mn;
-        uint32_t pick = (uint32_t)(splitmix64_at(seed, ctr++) % cnt);
-        for (uint32_t u = 0; u < p.P; ++u) {
-          if (clk[u] == mn) {
-            if (pick == 0) { c = u; break; }
-            --pick;
-          }
-        }
-      }
-      clk[c] += t[c];
-    }
-    uint64_t mx = 0;
-    for (uint32_t c = 0; c < p.P; ++c) mx = clk[c] > mx ? clk[c] : mx;
-    atomicMin(reinterpret_cast<unsigned long long*>(t_out), (unsigned long long)mx);
-  }
+  for (uint64_t w = gtid; w < walks; w += nthreads)
+    atomicMin(reinterpret_cast<unsigned long long*>(t_out),
+              (unsigned long long)simulate_walk(p, seed, w));
 }
 
 // ------------------------------------------------------------------ dispatch tables

@@ -79,6 +79,20 @@ class McStats(C.Structure):
                 ("explore_ms", C.c_double)]
 
 
+class McQuery(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("reserved", C.c_uint32), ("T", C.c_uint64)]
+
+
+class McBatchResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("kind", C.c_uint32), ("holds", C.c_uint32),
+                ("levels", C.c_uint32), ("states", C.c_uint64), ("checks", C.c_uint32),
+                ("level", C.c_uint32), ("time", C.c_uint64), ("t_ini", C.c_uint64),
+                ("wg_index", C.c_uint32), ("ts_index", C.c_uint32), ("wg", C.c_uint32),
+                ("ts", C.c_uint32), ("key", C.c_uint64 * 2)]
+
+
+MC_QUERY_CHECK, MC_QUERY_MIN_TIME = 0, 1
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -137,6 +151,17 @@ def load(build: bool = True):
             "mc_simulate": (C.c_int, [P, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64)]),
             "mc_last_widths": (C.c_int, [P, C.POINTER(C.c_uint64), C.c_uint32, C.POINTER(C.c_uint32)]),
             "mc_get_stats": (C.c_int, [P, C.POINTER(McStats)]),
+            "mc_batch_create": (C.c_int, [C.POINTER(McModelDesc), C.c_uint32, C.POINTER(McOptions),
+                                          C.POINTER(P)]),
+            "mc_batch_destroy": (None, [P]),
+            "mc_batch_set_stream": (C.c_int, [P, P]),
+            "mc_batch_set_allocator": (C.c_int, [P, ALLOC_FN, FREE_FN, P]),
+            "mc_batch_device_bytes": (C.c_int, [P, C.POINTER(C.c_uint64)]),
+            "mc_batch_run": (C.c_int, [P, C.POINTER(McQuery), C.POINTER(McBatchResult)]),
+            "mc_batch_trace": (C.c_int, [P, C.c_uint32, C.POINTER(C.c_uint64), C.c_uint32,
+                                         C.POINTER(C.c_uint32)]),
+            "mc_batch_get_stats": (C.c_int, [P, C.POINTER(McStats)]),
+            "mc_batch_last_error": (C.c_char_p, [P]),
             "mc_measure_random_access": (C.c_int, [C.c_uint64, C.c_uint64, C.c_int,
                                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "mc_check_noalloc": (C.c_int, [C.POINTER(McModelDesc), C.c_uint64, C.c_uint32, C.c_uint32,
@@ -376,6 +401,119 @@ def mc_measure_random_access(buffer_bytes: int, accesses: int, op: int = 0) -> d
     if rc != MC_OK:
         raise MCError(rc, "mc_measure_random_access")
     return {"sectors_per_s": rate.value, "ms": ms.value, "gbs_32b": rate.value * 32 / 1e9}
+
+
+class Batch:
+    """Owns an ``mc_batch*`` (many models answered by one launch)."""
+
+    def __init__(self, handle: int, specs):
+        self.handle = C.c_void_p(handle)
+        self.specs = specs
+        self._callbacks = None
+        self._keep = None
+        _live.add(self)
+
+    def __del__(self):
+        try:
+            mc_batch_destroy(self)
+        except Exception:
+            pass
+
+    def _check(self, rc: int, where: str):
+        if rc != MC_OK:
+            detail = load(build=False).mc_batch_last_error(self.handle).decode() if self.handle else ""
+            raise MCError(rc, where, detail)
+
+
+def _descs(specs):
+    keep = []
+    arr = (McModelDesc * len(specs))()
+    for k, spec in enumerate(specs):
+        a = (_u32(spec.wg_values), _u32(spec.ts_values), _u32(spec.n_workgroups), _u32(spec.cost),
+             _u32(spec.speed))
+        keep.append(a)
+        arr[k] = McModelDesc(len(spec.wg_values), len(spec.ts_values), spec.P, a[0], a[1], a[2], a[3],
+                             a[4], spec.rule, 128)
+    return arr, keep
+
+
+def mc_batch_create(specs, options: Optional[McOptions] = None, allocator: Optional[str] = "torch",
+                    stream=None) -> Batch:
+    L = load()
+    arr, keep = _descs(specs)
+    h = C.c_void_p()
+    rc = L.mc_batch_create(arr, len(specs), C.byref(options) if options is not None else None,
+                           C.byref(h))
+    if rc != MC_OK:
+        raise MCError(rc, "mc_batch_create")
+    b = Batch(h.value, list(specs))
+    if allocator == "torch":
+        import torch
+
+        device = torch.cuda.current_device()
+
+        def _alloc(nbytes, strm, _ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(strm or 0))
+            except Exception:
+                return None
+
+        def _free(ptr, _nbytes, _strm, _ctx):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        b._callbacks = (ALLOC_FN(_alloc), FREE_FN(_free))
+        b._check(L.mc_batch_set_allocator(b.handle, b._callbacks[0], b._callbacks[1], None),
+                 "mc_batch_set_allocator")
+    if stream is not None:
+        raw = getattr(stream, "cuda_stream", stream)
+        b._check(L.mc_batch_set_stream(b.handle, C.c_void_p(raw or 0)), "mc_batch_set_stream")
+    return b
+
+
+def mc_batch_destroy(batch: Batch):
+    if batch.handle and batch.handle.value:
+        load(build=False).mc_batch_destroy(batch.handle)
+        batch.handle = C.c_void_p()
+
+
+def mc_batch_device_bytes(batch: Batch) -> int:
+    v = C.c_uint64()
+    batch._check(load().mc_batch_device_bytes(batch.handle, C.byref(v)), "mc_batch_device_bytes")
+    return v.value
+
+
+def mc_batch_run(batch: Batch, queries) -> list:
+    """queries: list of ("check", T) or ("min_time", None); one per model."""
+    n = len(batch.specs)
+    q = (McQuery * n)()
+    for k, (kind, T) in enumerate(queries):
+        q[k] = McQuery(MC_QUERY_MIN_TIME if kind == "min_time" else MC_QUERY_CHECK, 0,
+                       int(T or 0) & NO_LIMIT)
+    res = (McBatchResult * n)()
+    batch._check(load().mc_batch_run(batch.handle, q, res), "mc_batch_run")
+    out = []
+    for r in res:
+        d = {"status": r.status, "kind": "min_time" if r.kind == 1 else "check", "holds": bool(r.holds),
+             "levels": r.levels, "states": r.states, "checks": r.checks, "level": r.level,
+             "time": r.time, "t_ini": r.t_ini, "i": r.wg_index, "j": r.ts_index, "wg": r.wg,
+             "ts": r.ts, "key": r.key[0] | (r.key[1] << 64)}
+        out.append(d)
+    return out
+
+
+def mc_batch_trace(batch: Batch, i: int) -> list:
+    n = C.c_uint32()
+    L = load()
+    batch._check(L.mc_batch_trace(batch.handle, i, None, 0, C.byref(n)), "mc_batch_trace")
+    buf = (C.c_uint64 * (2 * max(n.value, 1)))()
+    batch._check(L.mc_batch_trace(batch.handle, i, buf, n.value, C.byref(n)), "mc_batch_trace")
+    return [buf[2 * k] | (buf[2 * k + 1] << 64) for k in range(n.value)]
+
+
+def mc_batch_get_stats(batch: Batch) -> dict:
+    st = McStats()
+    batch._check(load().mc_batch_get_stats(batch.handle, C.byref(st)), "mc_batch_get_stats")
+    return {k: getattr(st, k) for k, _t in McStats._fields_}
 
 
 def decode_key(layout: dict, key: int):

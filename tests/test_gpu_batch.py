@@ -1,0 +1,123 @@
+"""Batched exploration (one persistent launch for many models) against the
+CPU oracle, the closed forms and the single-model entry points.
+
+Integer results, tolerance zero: per instance the decision, counts, levels,
+counterexample or minimum, configuration and witness state; traces replay.
+"""
+import pytest
+
+import closed_forms as CF
+import replay as RP
+from paper_2305_09130_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+NO_LIMIT = (1 << 64) - 1
+
+
+def layout128(mc, spec):
+    m = mc.mc_model_create(spec.with_key_bits(128), allocator=None)
+    return mc.mc_model_layout(m)
+
+
+def mixed_specs():
+    specs = [W.tiny(W.FREE), W.tiny(W.GREEDY), W.c1(W.FREE), W.c1(W.GREEDY)]
+    seed = 7000
+    shapes = [(1, 2, 2, 9), (2, 3, 2, 8), (3, 2, 2, 6), (4, 2, 3, 5), (5, 2, 1, 5), (6, 1, 2, 4),
+              (8, 2, 2, 3), (12, 1, 1, 3), (16, 1, 2, 2)]
+    for P, a, b, n_max in shapes:
+        for rule in (W.FREE, W.GREEDY):
+            specs.append(W.random_small(seed, P, a, b, n_max, cost_max=7, speed_max=3, rule=rule))
+            seed += 1
+    return specs
+
+
+def make_queries(specs, t_mins):
+    rng = W.SplitMix64(2305091399)
+    q = []
+    for spec, t in zip(specs, t_mins):
+        if rng.uniform(0, 1):
+            q.append(("min_time", None))
+        else:
+            q.append(("check", max(0, round(t * rng.uniform(800, 1200) / 1000))))
+    return q
+
+
+def check_against_oracle(mc, oracle, spec, query, r):
+    lay = layout128(mc, spec)
+    assert r["status"] == 0
+    if query[0] == "check":
+        T = query[1]
+        exp = oracle.check(spec, T)
+        got = {"holds": r["holds"], "states": r["states"], "levels": r["levels"]}
+        if not r["holds"]:
+            i, j, n = RP.decode(lay, r["key"])
+            got.update(cex_time=r["time"], cex_i=r["i"], cex_j=r["j"], cex_level=r["level"], cex_n=n)
+            assert (i - 1, j - 1) == (r["i"], r["j"])
+        assert got == exp
+    else:
+        exp = oracle.min_time(spec)
+        i, j, n = RP.decode(lay, r["key"])
+        got = {"t_min": r["time"], "t_ini": r["t_ini"], "states": r["states"], "checks": r["checks"],
+               "i": r["i"], "j": r["j"], "level": r["level"], "n": n}
+        assert got == exp
+
+
+def test_batch_matches_oracle(mc, oracle):
+    specs = mixed_specs()
+    t_mins = [oracle.min_time(s)["t_min"] for s in specs]
+    queries = make_queries(specs, t_mins)
+    assert {k for k, _ in queries} == {"check", "min_time"}
+    b = mc.mc_batch_create(specs)
+    for _run in range(2):  # the pool is reused; results must not depend on its contents
+        res = mc.mc_batch_run(b, queries)
+        for k, (spec, q, r) in enumerate(zip(specs, queries, res)):
+            check_against_oracle(mc, oracle, spec, q, r)
+            if q[0] == "min_time" or not r["holds"]:
+                keys = mc.mc_batch_trace(b, k)
+                assert len(keys) == r["level"] + 1 and keys[-1] == r["key"]
+                bound = r["time"]
+                RP.replay(spec, layout128(mc, spec), keys,
+                          (lambda t, b_=bound: t == b_) if q[0] == "min_time" else (lambda t, T=q[1]: t <= T))
+
+
+def test_batch_equals_single_model_queries(mc):
+    specs = W.c4_instances(96)
+    t_mins = [CF.tmin(s)[0] for s in specs]
+    queries = [("min_time", None) if s.meta["query"] else ("check", round(t * s.meta["t_frac_milli"] / 1000))
+               for s, t in zip(specs, t_mins)]
+    b = mc.mc_batch_create(specs)
+    res = mc.mc_batch_run(b, queries)
+    for spec, q, r, t_min in zip(specs, queries, res, t_mins):
+        assert r["status"] == 0
+        m = mc.mc_model_create(spec.with_key_bits(128))
+        if q[0] == "min_time":
+            s = mc.mc_min_time(m, trace=False)
+            assert (r["time"], r["t_ini"], r["i"], r["j"], r["states"], r["checks"], r["level"], r["key"]) == \
+                   (s["t_min"], s["t_ini"], s["i"], s["j"], s["states"], s["checks"], s["level"], s["witness_key"])
+            assert r["time"] == t_min
+        else:
+            s = mc.mc_check(m, q[1], trace=False)
+            assert r["holds"] == s["holds"] == (q[1] < t_min)
+            assert (r["states"], r["levels"]) == (s["states"], s["levels"])
+            if not s["holds"]:
+                assert (r["time"], r["i"], r["j"], r["level"], r["key"]) == \
+                       (s["cex_time"], s["cex_i"], s["cex_j"], s["cex_level"], s["cex_key"])
+        mc.mc_model_destroy(m)
+
+
+def test_batch_errors_are_per_instance(mc):
+    specs = [W.c1(W.FREE), W.tiny(W.GREEDY)]
+    b = mc.mc_batch_create(specs, mc.mc_options_default(table_log2=3, max_probes=1))
+    res = mc.mc_batch_run(b, [("check", NO_LIMIT), ("min_time", None)])
+    assert [r["status"] for r in res] == [mc.MC_ERR_TABLE_FULL, mc.MC_ERR_TABLE_FULL]
+
+
+def test_batch_barrier_timeout(mc):
+    b = mc.mc_batch_create([W.c1(W.FREE)], mc.mc_options_default(debug_barrier_extra=1,
+                                                                    barrier_timeout_ns=200_000_000))
+    with pytest.raises(mc.MCError) as e:
+        mc.mc_batch_run(b, [("min_time", None)])
+    assert e.value.code == mc.MC_ERR_TIMEOUT
+    ok = mc.mc_batch_create([W.c1(W.FREE)])
+    assert mc.mc_batch_run(ok, [("min_time", None)])[0]["time"] == 80
