@@ -390,6 +390,106 @@ def run_ours(args):
     return 0
 
 
+def percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
+def run_c4(args):
+    """Batched queries: 256 uneven models (G = 2^U{6..12}, P in {2,4,8}, WG
+    2^0..2^8, TS 2^0..2^4, cost U{1..16}, speeds U{1..3}, GREEDY), half
+    min-time and half check at round(U[0.8,1.2] x T_min), answered by one
+    persistent launch, against the same queries one at a time."""
+    import torch
+
+    from paper_2305_09130_gb300 import mc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist_init(world, True)
+    specs = W.c4_instances(256)
+    opts = mc.mc_options_default(timing=1)
+    stream = torch.cuda.Stream(device)
+    batch = mc.mc_batch_create(specs, opts, stream=stream)
+    # the check thresholds are fractions of each instance's optimum: take the
+    # optima from an untimed all-min-time run
+    optima = [r["time"] for r in mc.mc_batch_run(batch, [("min_time", None)] * len(specs))]
+    queries = [("min_time", None) if sp.meta["query"] else
+               ("check", round(t * sp.meta["t_frac_milli"] / 1000)) for sp, t in zip(specs, optima)]
+    for _ in range(args.warmup):
+        ref = mc.mc_batch_run(batch, queries)
+    torch.cuda.synchronize()
+    barrier(device)
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    states = 0
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        res = mc.mc_batch_run(batch, queries)
+        ev[k][1].record(stream)
+        states += sum(r["states"] for r in res)
+        assert [r["status"] for r in res] == [0] * len(res)
+        assert [(r["time"], r["states"]) for r in res] == [(r["time"], r["states"]) for r in ref]
+    torch.cuda.synchronize()
+    barrier(device)
+    clocks = sampler.stop()
+    batch_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_ms = sum(batch_ms)
+    dev_ms_max = reduce_scalar(dev_ms, "max", device)
+    states_all = reduce_scalar(states, "sum", device)
+    value = states_all / (dev_ms_max / 1000.0)
+
+    # one query at a time on the single-model entry points (models created
+    # untimed); latency of query k when all arrive together = sum of the
+    # service times of queries 0..k
+    models = [mc.mc_model_create(sp.with_key_bits(128), opts, stream=stream) for sp in specs]
+    for m in models:
+        mc.mc_reserve(m)
+    service = []
+    seq_states = 0
+    for m, (kind, T) in zip(models, queries):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = mc.mc_min_time(m, trace=False) if kind == "min_time" else mc.mc_check(m, T, trace=False)
+        b.record(stream)
+        b.synchronize()
+        service.append(a.elapsed_time(b))
+        seq_states += r["states"]
+    seq_total = sum(service)
+    cum, acc = [], 0.0
+    for x in service:
+        acc += x
+        cum.append(acc)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u128", "data": "synthetic (seeded model descriptions)",
+        "config": {"workload": "c4: 256 instances, G=2^U{6..12}, P in {2,4,8}, WG 2^0..2^8, TS 2^0..2^4, "
+                               "cost U{1..16}, speeds U{1..3} (splitmix64 seed 2305091304), GREEDY; "
+                               "half mc_min_time, half mc_check at round(U[0.8,1.2] x T_min)",
+                   "query": "one mc_batch_run per step (one persistent launch)",
+                   "states_per_step": states / args.steps},
+        "batched": {"ms_per_batch": dev_ms_max / args.steps, "states_per_s": value,
+                    "query_latency_ms_p50": percentile(batch_ms, 50),
+                    "query_latency_ms_p99": percentile(batch_ms, 99)},
+        "sequential": {"ms_total": seq_total, "states_per_s": seq_states / (seq_total / 1000.0),
+                       "service_ms_p50": percentile(service, 50), "service_ms_p99": percentile(service, 99),
+                       "latency_all_arrive_together_ms_p50": percentile(cum, 50),
+                       "latency_all_arrive_together_ms_p99": percentile(cum, 99)},
+        "speedup_vs_sequential": seq_total / (dev_ms_max / args.steps),
+        "gpu_launches": args.steps, "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     p.add_argument("--gpus", type=int, default=1)
@@ -400,7 +500,7 @@ def main(argv=None):
     p.add_argument("--prune", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-random-roofline", action="store_true")
-    p.add_argument("--workload", choices=sorted(WORKLOADS), default="c2_star",
+    p.add_argument("--workload", choices=sorted(WORKLOADS) + ["c4"], default="c2_star",
                    help="profiling aid; the benchmark line is c2_star")
     p.add_argument("--query", choices=["min_time", "count"], default="min_time")
     args = p.parse_args(argv)
@@ -408,6 +508,8 @@ def main(argv=None):
         p.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c4":
+        return run_c4(args)
     return run_ours(args)
 
 
