@@ -306,6 +306,47 @@ int mc_batch_trace(mc_batch* b, uint32_t i, uint64_t* keys, uint32_t cap, uint32
 int mc_batch_get_stats(const mc_batch* b, mc_stats* out);
 const char* mc_batch_last_error(const mc_batch* b);
 
+/* ------------------------------------------------------------ served queries
+ * A request loop (no counterpart in the paper's tooling, which runs one SPIN
+ * verification per process): queries for models of different sizes are
+ * submitted as they arrive and answered by a persistent device loop that
+ * keeps up to `slots` of them on the GPU at once.  A request is admitted when
+ * a slot is free and the device pool has room for its visited set, frontier
+ * log and tables (closed-form bound); requests admitted while others run
+ * join the device loop at its next step, so their work overlaps.  Results
+ * equal those of mc_batch_run / mc_check / mc_min_time for the same model.
+ * A host thread of the library admits, harvests and relaunches; the device
+ * loop exits after `idle_ns` without work and is relaunched on demand. */
+typedef struct mc_server mc_server;
+typedef struct {
+  uint32_t slots;        /* requests on the device at once, 1..1024        */
+  uint32_t reserved0;
+  uint64_t pool_bytes;   /* device memory for the requests' buffers        */
+  uint64_t idle_ns;      /* device loop's wait for new work (0: 2 ms)      */
+  uint64_t reserved[4];
+} mc_server_config;
+typedef struct {
+  uint64_t ticket;
+  mc_batch_result result;
+  double submit_s;       /* host steady-clock seconds: submitted,          */
+  double admit_s;        /*   posted to the device,                        */
+  double done_s;         /*   result harvested                             */
+} mc_server_result;
+
+/* Allocate the pool and mailboxes, start the host thread.  Errors: INVAL,
+ * NOMEM, CUDA. */
+int mc_server_create(const mc_server_config* cfg, const mc_options* opt, mc_server** out);
+/* Queue one query on a model (copied).  Errors: INVAL, OVERFLOW, NOMEM (the
+ * model does not fit the pool at all), or the server's fatal error. */
+int mc_server_submit(mc_server* s, const mc_model_desc* desc, const mc_query* q, uint64_t* ticket);
+/* Take up to cap finished results, waiting up to wait_ms for the first. */
+int mc_server_poll(mc_server* s, mc_server_result* out, uint32_t cap, uint32_t* n, uint32_t wait_ms);
+/* Queued and running requests, device-loop launches; returns the server's
+ * fatal error (0 if none). */
+int mc_server_status(mc_server* s, uint32_t* queued, uint32_t* running, uint64_t* launches);
+/* Stop the device loop (requests in flight are abandoned) and free all. */
+void mc_server_destroy(mc_server* s);
+
 /* Random-access roofline of the current device (a measurement utility, not a
  * step of the method): times `accesses` independent random 32-byte sector
  * reads (op 0) or reads followed by an atomicCAS on the sector (op 1) over a

@@ -45,6 +45,17 @@ __device__ __forceinline__ uint64_t ldcg64(const uint64_t* p) {
   return __ldcg(reinterpret_cast<const unsigned long long*>(p));
 }
 
+// Copies of BInst / BState read from L2: in served mode a slot's request (and
+// the tables it points to) can change between steps, so nothing may come
+// from a stale L1 line.
+template <class T>
+__device__ void load_cg(const T* g, T& out) {
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(g);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&out);
+#pragma unroll 4
+  for (uint32_t k = 0; k < sizeof(T) / 8; ++k) dst[k] = __ldcg(src + k);
+}
+
 // ------------------------------------------------------------------ planner
 uint64_t __host__ __device__ inline ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 
@@ -168,46 +179,130 @@ __device__ void advance(BState& s, const BInst& I, const BatchArgs& A) {
   }
 }
 
+// Served mode: publish a finished slot's result to its host-mapped outbox
+// entry (fields first, then the sequence number with release semantics).
+__device__ void publish(const BatchArgs& A, uint32_t i, BState& s) {
+  OutboxEntry* o = A.serve.outbox + i;
+  o->status = s.err ? (int32_t)s.err : MC_OK;
+  o->holds = s.stop_level == 0;
+  o->levels = s.levels;
+  o->states = s.states;
+  o->checks = s.checks;
+  o->level = s.stop_level;
+  o->time = s.stop_level ? pack_time(s.wpack) : 0;
+  o->t_ini = s.t_ini;
+  o->wpack = s.wpack;
+  o->key_lo = s.wkey_lo;
+  o->key_hi = s.wkey_hi;
+  __threadfence_system();
+  st_release_sys_u32(&o->seq, s.seq);
+  s.published = 1;
+}
+
+// Served mode: take slot i's newly posted request (if any) into the device.
+__device__ void admit(const BatchArgs& A, uint32_t i, BState& s) {
+  const InboxEntry* e = A.serve.inbox + i;
+  const uint32_t seq = ld_acquire_sys_u32(&e->seq);
+  if (seq == 0 || seq == s.seq) return;
+  const volatile unsigned long long* src = reinterpret_cast<const volatile unsigned long long*>(&e->inst);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(A.inst + i);
+  for (uint32_t k = 0; k < sizeof(BInst) / 8; ++k) dst[k] = src[k];
+  unsigned long long* z = reinterpret_cast<unsigned long long*>(&s);
+  for (uint32_t k = 0; k < sizeof(BState) / 8; ++k) z[k] = 0;
+  s.seq = seq;
+}
+
 struct Planner {
   const BatchArgs* A;
-  __device__ void operator()() const {
+
+  // Advance every slot; returns the number of tasks of the next step and
+  // writes their prefix.
+  __device__ unsigned long long plan() const {
     __shared__ uint32_t s_count[kMaxBatch];
     __shared__ unsigned long long s_part[kThreads];
+    __shared__ unsigned long long s_total;
+    const bool serve = A->serve.inbox != nullptr;
     const uint32_t n = A->n;
     const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
     const uint32_t i0 = threadIdx.x * per, i1 = min(n, i0 + per);
     unsigned long long local = 0;
     for (uint32_t i = i0; i < i1; ++i) {
       BState s;
-      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(A->state + i);
-      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s);
-      for (uint32_t k = 0; k < sizeof(BState) / 8; ++k) dst[k] = __ldcg(src + k);
-      const BInst& I = A->inst[i];
-      advance(s, I, *A);
-      const uint64_t c = task_count(s, I, *A);
+      load_cg(A->state + i, s);
+      uint64_t c = 0;
+      if (serve) admit(*A, i, s);
+      if (!serve || (s.seq != 0 && !s.published)) {
+        BInst I;
+        load_cg(A->inst + i, I);
+        advance(s, I, *A);
+        c = task_count(s, I, *A);
+        if (serve && s.phase == B_DONE) publish(*A, i, s);
+      }
       s_count[i] = (uint32_t)c;
       local += c;
       unsigned long long* out = reinterpret_cast<unsigned long long*>(A->state + i);
-      for (uint32_t k = 0; k < sizeof(BState) / 8; ++k) out[k] = dst[k];
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&s);
+      for (uint32_t k = 0; k < sizeof(BState) / 8; ++k) out[k] = src[k];
     }
-    s_part[threadIdx.x] = local;
+    // block-wide exclusive scan of the per-thread sums
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    unsigned long long incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (uint32_t)o) incl += v;
+    }
+    if (lane == 31) s_part[warp] = incl;
     __syncthreads();
     if (threadIdx.x == 0) {
       unsigned long long run = 0;
-      for (uint32_t t = 0; t < blockDim.x; ++t) {
-        const unsigned long long v = s_part[t];
-        s_part[t] = run;
+      for (uint32_t w = 0; w < (blockDim.x >> 5); ++w) {
+        const unsigned long long v = s_part[w];
+        s_part[w] = run;
         run += v;
       }
+      s_total = run;
     }
     __syncthreads();
-    unsigned long long run = s_part[threadIdx.x];
+    unsigned long long run = s_part[warp] + incl - local;
     for (uint32_t i = i0; i < i1; ++i) {
       A->plan_prefix[i] = run;
       run += s_count[i];
     }
-    if (i1 == n && i0 < n) A->plan_prefix[n] = run;
-    if (n == 0 && threadIdx.x == 0) A->plan_prefix[0] = 0;
+    if (threadIdx.x == 0) A->plan_prefix[n] = s_total;
+    const unsigned long long total = s_total;
+    __syncthreads();
+    return total;
+  }
+
+  // Served mode with nothing to do: wait (bounded by idle_ns) until a
+  // request is posted or the host asks to stop.  True when one was posted.
+  __device__ bool wait_for_requests() const {
+    const uint32_t n = A->n;
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+      int found = 0;
+      for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint32_t seq = ld_acquire_sys_u32(&A->serve.inbox[i].seq);
+        if (seq != 0 && seq != __ldcg(&A->state[i].seq)) found = 1;
+      }
+      const int stop = threadIdx.x == 0 ? (int)ld_acquire_sys_u32(A->serve.stop) : 0;
+      if (__syncthreads_or(stop)) return false;
+      if (__syncthreads_or(found)) return true;
+      if (globaltimer() - t0 > A->serve.idle_ns) return false;
+      __nanosleep(2000);
+    }
+  }
+
+  __device__ void operator()() const {
+    for (;;) {
+      const unsigned long long total = plan();
+      if (!A->serve.inbox || total > 0) {
+        if (A->serve.inbox && threadIdx.x == 0 && ld_acquire_sys_u32(A->serve.stop))
+          A->plan_prefix[A->n] = 0;  // the host is shutting the loop down
+        return;
+      }
+      if (!wait_for_requests()) return;  // total stays 0: the loop exits
+    }
   }
 };
 
@@ -227,15 +322,18 @@ struct Staging {
 __device__ void flush(const BatchArgs& A, Staging& sg, WarpBuf& wb, uint32_t lane) {
   if (sg.fill == 0) return;
   __syncwarp();
-  const BInst& I = A.inst[sg.inst];
+  void* log_keys = (void*)__ldcg(reinterpret_cast<const unsigned long long*>(&A.inst[sg.inst].log_keys));
+  uint32_t* log_par =
+      (uint32_t*)__ldcg(reinterpret_cast<const unsigned long long*>(&A.inst[sg.inst].log_par));
+  const uint64_t log_cap = __ldcg(reinterpret_cast<const unsigned long long*>(&A.inst[sg.inst].log_cap));
   unsigned long long b = 0;
   if (lane == 0) b = atomicAdd(reinterpret_cast<unsigned long long*>(sg.rec), (unsigned long long)sg.fill);
   b = __shfl_sync(0xffffffffu, b, 0);
   for (uint32_t x = lane; x < sg.fill; x += 32) {
     const uint64_t at = sg.offN + b + x;
-    if (at < I.log_cap) {
-      KeyOps<u128>::store(I.log_keys, at, wb.keys[x]);
-      I.log_par[at] = wb.par[x];
+    if (at < log_cap) {
+      KeyOps<u128>::store(log_keys, at, wb.keys[x]);
+      log_par[at] = wb.par[x];
     } else {
       set_error(&A.state[sg.inst].err, MC_ERR_FRONTIER);
     }
@@ -245,8 +343,7 @@ __device__ void flush(const BatchArgs& A, Staging& sg, WarpBuf& wb, uint32_t lan
 }
 
 // ------------------------------------------------------------------ tasks
-__device__ void task_setup(const BatchArgs& A, uint32_t inst, uint64_t q, uint32_t lane) {
-  const BInst& I = A.inst[inst];
+__device__ void task_setup(const BatchArgs& A, const BInst& I, uint64_t q, uint32_t lane) {
   const Params& p = I.p;
   const uint64_t n16 = I.table_u64 / 2;
   const uint64_t nlev = (uint64_t)p.max_level + 2;
@@ -278,9 +375,8 @@ __device__ void task_setup(const BatchArgs& A, uint32_t inst, uint64_t q, uint32
   }
 }
 
-__device__ void task_expand(const BatchArgs& A, uint32_t inst, const BState& s, uint64_t q,
-                            uint32_t lane, Staging& sg, WarpBuf& wb) {
-  const BInst& I = A.inst[inst];
+__device__ void task_expand(const BatchArgs& A, uint32_t inst, const BInst& I, const BState& s,
+                            uint64_t q, uint32_t lane, Staging& sg, WarpBuf& wb) {
   const Params& p = I.p;
   const uint32_t g = I.group;
   const uint32_t c = lane & (g - 1);
@@ -295,9 +391,9 @@ __device__ void task_expand(const BatchArgs& A, uint32_t inst, const BState& s, 
     i = field(key, p.wg_shift, p.wg_mask) - 1;
     j = field(key, p.ts_shift, p.ts_mask) - 1;
     const uint32_t cfg = i * p.b + j;
-    r = __ldg(p.N + cfg) - k_cur;
+    r = __ldcg(p.N + cfg) - k_cur;
     if (c < p.P) {
-      t_c = (uint64_t)__ldg(p.cost + cfg) * __ldg(p.speed + c);
+      t_c = (uint64_t)__ldcg(p.cost + cfg) * __ldcg(p.speed + c);
       clk = (uint64_t)field(key, c_shift, p.n_mask) * t_c;
     }
   }
@@ -334,9 +430,8 @@ __device__ void task_expand(const BatchArgs& A, uint32_t inst, const BState& s, 
   }
 }
 
-__device__ void task_witness(const BatchArgs& A, uint32_t inst, const BState& s, uint64_t q,
-                             uint32_t lane) {
-  const BInst& I = A.inst[inst];
+__device__ void task_witness(const BatchArgs& A, uint32_t inst, const BInst& I, const BState& s,
+                             uint64_t q, uint32_t lane) {
   const Params& p = I.p;
   const uint64_t x = q * 32 + lane;
   if (x >= s.W) return;
@@ -350,16 +445,16 @@ __device__ void task_witness(const BatchArgs& A, uint32_t inst, const BState& s,
   const uint32_t ti = pack_i(s.wpack), tj = pack_j(s.wpack);
   if (field(key, p.wg_shift, p.wg_mask) - 1 != ti || field(key, p.ts_shift, p.ts_mask) - 1 != tj) return;
   const uint32_t cfg = ti * p.b + tj;
-  if (sum_n(key, p) != __ldg(p.N + cfg) || key_time(key, p, cfg) != pack_time(s.wpack)) return;
+  if (sum_n(key, p) != __ldcg(p.N + cfg) || key_time<u128, true>(key, p, cfg) != pack_time(s.wpack))
+    return;
   if (s.phase == B_WIT_HI)
     atomicMin(reinterpret_cast<unsigned long long*>(&gs->wkey_hi), (unsigned long long)hi);
   else if (hi == s.wkey_hi)
     atomicMin(reinterpret_cast<unsigned long long*>(&gs->wkey_lo), (unsigned long long)lo);
 }
 
-__device__ void task_trace(const BatchArgs& A, uint32_t inst, const BState& s, uint32_t lane) {
+__device__ void task_trace(const BInst& I, const BState& s, uint32_t lane) {
   if (lane != 0) return;
-  const BInst& I = A.inst[inst];
   uint64_t idx = s.widx;
   uint32_t l = s.L;
   for (;;) {
@@ -373,10 +468,10 @@ __device__ void task_trace(const BatchArgs& A, uint32_t inst, const BState& s, u
   }
 }
 
-__device__ void task_sim(const BatchArgs& A, uint32_t inst, uint64_t q, uint32_t lane) {
+__device__ void task_sim(const BatchArgs& A, uint32_t inst, const BInst& I, uint64_t q, uint32_t lane) {
   const uint64_t w = q * 32 + lane;
   if (w >= A.sim_walks) return;
-  const uint64_t t = simulate_walk(A.inst[inst].p, A.sim_seed, w);
+  const uint64_t t = simulate_walk<true>(I.p, A.sim_seed, w);
   atomicMin(reinterpret_cast<unsigned long long*>(&A.state[inst].t_ini), (unsigned long long)t);
 }
 
@@ -407,6 +502,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs A) {
     if (total == 0) break;
     Staging sg;
     BState s;
+    BInst I;
     uint32_t cur = 0xFFFFFFFFu;
     for (uint64_t t = warp_gid; t < total; t += n_warps) {
       // instance of task t: last i with prefix[i] <= t (warp-uniform)
@@ -420,6 +516,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs A) {
       const uint64_t q = t - s_prefix[inst];
       if (inst != cur) {
         load_state(A.state + inst, s);
+        load_cg(A.inst + inst, I);
         cur = inst;
       }
       switch (s.phase) {
@@ -428,17 +525,17 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs A) {
             flush(A, sg, s_buf[warp], lane);
             sg.inst = inst;
             sg.offN = s.offL + s.W;
-            sg.rec = A.inst[inst].levels + 2 * (s.L + 1);
+            sg.rec = I.levels + 2 * (s.L + 1);
           }
-          task_expand(A, inst, s, q, lane, sg, s_buf[warp]);
+          task_expand(A, inst, I, s, q, lane, sg, s_buf[warp]);
           if (sg.fill > kWarpCap - 32) flush(A, sg, s_buf[warp], lane);
           break;
-        case B_SETUP: task_setup(A, inst, q, lane); break;
-        case B_SIM: task_sim(A, inst, q, lane); break;
+        case B_SETUP: task_setup(A, I, q, lane); break;
+        case B_SIM: task_sim(A, inst, I, q, lane); break;
         case B_WIT_HI:
         case B_WIT_LO:
-        case B_WIT_IDX: task_witness(A, inst, s, q, lane); break;
-        case B_TRACE: task_trace(A, inst, s, lane); break;
+        case B_WIT_IDX: task_witness(A, inst, I, s, q, lane); break;
+        case B_TRACE: task_trace(I, s, lane); break;
         default: break;
       }
     }
@@ -549,6 +646,72 @@ void brelease(mc_batch* b) {
   b->reserved = false;
 }
 
+// Layout, tables and region size of one model as a batch or server instance.
+int describe_instance(const mc_model_desc& d_in, const mc_options& o, mc::BInst& I, mc_layout& L,
+                      std::vector<uint32_t>& pr, uint64_t& region_bytes) {
+  mc_model_desc d = d_in;
+  d.key_bits = 128;  // every instance uses 128-bit keys
+  mc_model* m = nullptr;
+  int rc = mc_model_create(&d, &o, &m);
+  if (rc) return rc;
+  rc = mc_model_layout(m, &L);
+  mc_model_destroy(m);
+  if (rc) return rc;
+  if (L.log_capacity == UINT64_MAX || L.table_slots == 0) return MC_ERR_NOMEM;
+  const uint64_t ab = (uint64_t)d.n_wg * d.n_ts;
+  pr.assign(d.n_workgroups, d.n_workgroups + ab);
+  pr.insert(pr.end(), d.cost, d.cost + ab);
+  for (uint32_t c = 0; c < d.P; ++c) pr.push_back(d.speed ? d.speed[c] : 1);
+  std::memset(&I, 0, sizeof(I));
+  mc::Params& p = I.p;
+  p.a = d.n_wg;
+  p.b = d.n_ts;
+  p.P = d.P;
+  p.rule = d.rule;
+  p.n_bits = L.n_bits;
+  p.ts_shift = L.ts_shift;
+  p.wg_shift = L.wg_shift;
+  p.ts_mask = (1u << L.ts_bits) - 1;
+  p.wg_mask = (1u << L.wg_bits) - 1;
+  p.max_level = L.max_level;
+  p.n_mask = (1ull << L.n_bits) - 1;
+  const uint32_t nf = d.P * L.n_bits;
+  p.swar_ok = nf <= 64;
+  p.swar_mask = nf >= 64 ? ~0ull : ((1ull << nf) - 1);
+  for (uint32_t t = 0; t < d.P && t * L.n_bits < 64; ++t) p.swar_mul |= 1ull << (t * L.n_bits);
+  I.bucket_mask = L.table_slots / 2 - 1;
+  I.table_u64 = L.table_slots * 2;
+  I.log_cap = L.log_capacity;
+  I.max_probes = o.max_probes ? o.max_probes : (uint32_t)std::min<uint64_t>(L.table_slots / 2, 0xFFFFFFFFu);
+  I.group = 1;
+  while (I.group < d.P) I.group <<= 1;
+  const uint64_t L2 = L.max_level + 2;
+  region_bytes = al256(pr.size() * 4) + al256(16 * L2) + al256(8 * L2) + al256(16 * L2) +
+                 al256(16 * L.table_slots) + al256(16 * L.log_capacity) + al256(4 * L.log_capacity);
+  return MC_OK;
+}
+
+// Point an instance at its region: [tables][levels][off][trace][visited set][log keys][log parents].
+void place_instance(mc::BInst& I, const mc_layout& L, uint8_t* q, size_t n_params) {
+  const uint64_t ab = (uint64_t)I.p.a * I.p.b;
+  I.p.N = (const uint32_t*)q;
+  I.p.cost = (const uint32_t*)q + ab;
+  I.p.speed = (const uint32_t*)q + 2 * ab;
+  q += al256(n_params * 4);
+  const uint64_t L2 = L.max_level + 2;
+  I.levels = (uint64_t*)q;
+  q += al256(16 * L2);
+  I.off = (uint64_t*)q;
+  q += al256(8 * L2);
+  I.trace = (uint64_t*)q;
+  q += al256(16 * L2);
+  I.table = q;
+  q += al256(16 * L.table_slots);
+  I.log_keys = q;
+  q += al256(16 * L.log_capacity);
+  I.log_par = (uint32_t*)q;
+}
+
 int breserve(mc_batch* b) {
   if (b->reserved) return MC_OK;
   MCB_CUDA(b, cudaGetDevice(&b->device));
@@ -575,30 +738,11 @@ int breserve(mc_batch* b) {
   for (cudaEvent_t& e : b->ev) MCB_CUDA(b, cudaEventCreate(&e));
   // carve each instance's region and upload its tables
   for (uint32_t i = 0; i < b->n; ++i) {
-    const mc_layout& L = b->lay[i];
-    mc::BInst& I = b->inst[i];
     uint8_t* q = b->d_pool + b->pool_off[i];
-    const uint32_t* hp = b->params[i].data();
     const size_t np = b->params[i].size();
-    MCB_CUDA(b, cudaMemcpyAsync(q, hp, np * 4, cudaMemcpyHostToDevice, b->stream));
+    MCB_CUDA(b, cudaMemcpyAsync(q, b->params[i].data(), np * 4, cudaMemcpyHostToDevice, b->stream));
     b->stats.h2d_bytes += np * 4;
-    const uint64_t ab = (uint64_t)I.p.a * I.p.b;
-    I.p.N = (const uint32_t*)q;
-    I.p.cost = (const uint32_t*)q + ab;
-    I.p.speed = (const uint32_t*)q + 2 * ab;
-    q += al256(np * 4);
-    const uint64_t L2 = L.max_level + 2;
-    I.levels = (uint64_t*)q;
-    q += al256(16 * L2);
-    I.off = (uint64_t*)q;
-    q += al256(8 * L2);
-    I.trace = (uint64_t*)q;
-    q += al256(16 * L2);
-    I.table = q;
-    q += al256(16 * L.table_slots);
-    I.log_keys = q;
-    q += al256(16 * L.log_capacity);
-    I.log_par = (uint32_t*)q;
+    place_instance(b->inst[i], b->lay[i], q, np);
   }
   MCB_CUDA(b, cudaStreamSynchronize(b->stream));
   b->reserved = true;
@@ -628,61 +772,17 @@ int mc_batch_create(const mc_model_desc* descs, uint32_t n, const mc_options* op
   b->h_state.resize(n);
   uint64_t off = 0;
   for (uint32_t i = 0; i < n; ++i) {
-    mc_model_desc d = descs[i];
-    d.key_bits = 128;  // every instance of a batch uses 128-bit keys
-    mc_model* m = nullptr;
-    int rc = mc_model_create(&d, &o, &m);
+    const mc_model_desc& d = descs[i];
+    uint64_t bytes = 0;
+    const int rc = describe_instance(d, o, b->inst[i], b->lay[i], b->params[i], bytes);
     if (rc) {
       delete b;
       return rc;
     }
-    mc_layout& L = b->lay[i];
-    rc = mc_model_layout(m, &L);
-    mc_model_destroy(m);
-    if (rc) {
-      delete b;
-      return rc;
-    }
-    if (L.log_capacity == UINT64_MAX || L.table_slots == 0) {
-      delete b;
-      return MC_ERR_NOMEM;
-    }
-    const uint64_t ab = (uint64_t)d.n_wg * d.n_ts;
-    std::vector<uint32_t>& pr = b->params[i];
-    pr.assign(d.n_workgroups, d.n_workgroups + ab);
-    pr.insert(pr.end(), d.cost, d.cost + ab);
-    for (uint32_t c = 0; c < d.P; ++c) pr.push_back(d.speed ? d.speed[c] : 1);
     if (d.wg_values) b->wg[i].assign(d.wg_values, d.wg_values + d.n_wg);
     if (d.ts_values) b->ts[i].assign(d.ts_values, d.ts_values + d.n_ts);
-    mc::BInst& I = b->inst[i];
-    std::memset(&I, 0, sizeof(I));
-    mc::Params& p = I.p;
-    p.a = d.n_wg;
-    p.b = d.n_ts;
-    p.P = d.P;
-    p.rule = d.rule;
-    p.n_bits = L.n_bits;
-    p.ts_shift = L.ts_shift;
-    p.wg_shift = L.wg_shift;
-    p.ts_mask = (1u << L.ts_bits) - 1;
-    p.wg_mask = (1u << L.wg_bits) - 1;
-    p.max_level = L.max_level;
-    p.n_mask = (1ull << L.n_bits) - 1;
-    const uint32_t nf = d.P * L.n_bits;
-    p.swar_ok = nf <= 64;
-    p.swar_mask = nf >= 64 ? ~0ull : ((1ull << nf) - 1);
-    for (uint32_t t = 0; t < d.P && t * L.n_bits < 64; ++t) p.swar_mul |= 1ull << (t * L.n_bits);
-    I.bucket_mask = L.table_slots / 2 - 1;
-    I.table_u64 = L.table_slots * 2;
-    I.log_cap = L.log_capacity;
-    I.max_probes = o.max_probes ? o.max_probes
-                                : (uint32_t)std::min<uint64_t>(L.table_slots / 2, 0xFFFFFFFFu);
-    I.group = 1;
-    while (I.group < d.P) I.group <<= 1;
-    const uint64_t L2 = L.max_level + 2;
     b->pool_off[i] = off;
-    off += al256(pr.size() * 4) + al256(16 * L2) + al256(8 * L2) + al256(16 * L2) +
-           al256(16 * L.table_slots) + al256(16 * L.log_capacity) + al256(4 * L.log_capacity);
+    off += bytes;
   }
   b->pool_bytes = off;
   *out = b;
@@ -809,5 +909,399 @@ int mc_batch_get_stats(const mc_batch* b, mc_stats* out) {
 }
 
 const char* mc_batch_last_error(const mc_batch* b) { return b ? b->last_err.c_str() : ""; }
+
+}  // extern "C"
+
+// ====================================================================== served queries
+// A request loop over the batched engine: the device runs the persistent
+// lockstep loop with slots; its planner admits requests the host posts into
+// host-mapped inbox entries at every barrier and publishes finished results
+// to host-mapped outbox entries, so requests that arrive while others are
+// on the GPU join them at the next step.  A host thread (the pump) admits
+// queued requests when a slot and enough of the device pool are free
+// (first fit over the pool, by each request's closed-form bound), harvests
+// results, and relaunches the device loop when it has exited after being
+// idle.  Visited sets, frontier logs and tables stay resident in the pool.
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// First fit over [0, size), offsets and sizes multiples of 256 bytes.
+struct RegionAlloc {
+  std::map<uint64_t, uint64_t> free_;  // offset -> bytes
+  void init(uint64_t size) {
+    free_.clear();
+    free_[0] = size;
+  }
+  bool alloc(uint64_t bytes, uint64_t* off) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      *off = it->first;
+      const uint64_t rest = it->second - bytes, o2 = it->first + bytes;
+      free_.erase(it);
+      if (rest) free_[o2] = rest;
+      return true;
+    }
+    return false;
+  }
+  void release(uint64_t off, uint64_t bytes) {
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+struct Request {
+  uint64_t ticket = 0;
+  mc_query q{};
+  mc::BInst inst{};
+  mc_layout lay{};
+  std::vector<uint32_t> params, wg, ts;
+  uint64_t bytes = 0;
+  double t_submit = 0;
+};
+
+struct SlotInfo {
+  bool busy = false;
+  uint32_t seq = 0;
+  uint64_t off = 0;
+  double t_admit = 0;
+  Request req;
+};
+
+}  // namespace
+
+struct mc_server {
+  mc_server_config cfg{};
+  mc_options opt{};
+  int device = -1, grid = 0, threads = 0;
+  cudaStream_t stream = nullptr, copy = nullptr;
+  uint8_t* d_pool = nullptr;
+  mc::BInst* d_inst = nullptr;
+  mc::BState* d_state = nullptr;
+  uint64_t* d_prefix = nullptr;
+  uint32_t* d_ctrl = nullptr;
+  mc::InboxEntry *h_inbox = nullptr, *d_inbox = nullptr;
+  mc::OutboxEntry *h_outbox = nullptr, *d_outbox = nullptr;
+  uint32_t *h_stop = nullptr, *d_stop = nullptr;
+  cudaEvent_t kdone = nullptr;
+  bool kernel_running = false;
+  uint64_t launches = 0;
+  std::mutex mu;
+  std::condition_variable cv_done;
+  std::deque<Request> queue;
+  std::vector<SlotInfo> slots;
+  RegionAlloc pool;
+  std::deque<mc_server_result> done;
+  uint64_t next_ticket = 1;
+  uint32_t next_seq = 1;
+  std::thread pump;
+  std::atomic<bool> shutdown{false};
+  int fatal = 0;
+  std::string last_err;
+};
+
+namespace {
+
+void finish_slot(mc_server* S, uint32_t i, const mc::OutboxEntry& o, int status_override) {
+  SlotInfo& sl = S->slots[i];
+  mc_server_result res;
+  std::memset(&res, 0, sizeof(res));
+  res.ticket = sl.req.ticket;
+  mc_batch_result& r = res.result;
+  r.status = status_override ? status_override : o.status;
+  r.kind = sl.req.q.kind;
+  r.holds = o.holds;
+  r.levels = o.levels;
+  r.states = o.states;
+  r.checks = o.checks;
+  r.level = o.level;
+  r.time = o.time;
+  r.t_ini = sl.req.q.kind == MC_QUERY_MIN_TIME ? o.t_ini : 0;
+  if (o.level) {
+    r.wg_index = mc::pack_i(o.wpack);
+    r.ts_index = mc::pack_j(o.wpack);
+    r.wg = sl.req.wg.empty() ? r.wg_index : sl.req.wg[r.wg_index];
+    r.ts = sl.req.ts.empty() ? r.ts_index : sl.req.ts[r.ts_index];
+    r.key[0] = o.key_lo;
+    r.key[1] = o.key_hi;
+  }
+  res.submit_s = sl.req.t_submit;
+  res.admit_s = sl.t_admit;
+  res.done_s = now_s();
+  S->done.push_back(res);
+  S->pool.release(sl.off, sl.req.bytes);
+  sl.busy = false;
+}
+
+int launch_server(mc_server* S) {
+  mc::BatchArgs A{};
+  A.inst = S->d_inst;
+  A.state = S->d_state;
+  A.n = S->cfg.slots;
+  A.refine = S->opt.refine;
+  A.plan_prefix = S->d_prefix;
+  A.err = S->d_ctrl;
+  A.bar_lines = S->d_ctrl + 64;
+  A.barrier_extra = 0;
+  A.sim_walks = S->opt.sim_walks;
+  A.sim_seed = S->opt.sim_seed;
+  A.timeout_ns = S->opt.barrier_timeout_ns ? S->opt.barrier_timeout_ns : 60ull * 1000000000ull;
+  A.prune = S->opt.prune;
+  A.early_exit = S->opt.early_exit;
+  A.serve.inbox = S->d_inbox;
+  A.serve.outbox = S->d_outbox;
+  A.serve.stop = S->d_stop;
+  A.serve.idle_ns = S->cfg.idle_ns ? S->cfg.idle_ns : 2000000ull;
+  if (cudaMemsetAsync(S->d_ctrl, 0, 256 + mc::kBarBytes, S->stream) != cudaSuccess ||
+      mc::launch_batch(S->grid, S->threads, A, S->stream) != cudaSuccess ||
+      cudaEventRecord(S->kdone, S->stream) != cudaSuccess) {
+    S->last_err = cudaGetErrorString(cudaGetLastError());
+    return MC_ERR_CUDA;
+  }
+  S->kernel_running = true;
+  S->launches += 1;
+  return MC_OK;
+}
+
+void pump_loop(mc_server* S) {
+  cudaSetDevice(S->device);
+  const uint32_t n = S->cfg.slots;
+  while (!S->shutdown.load()) {
+    bool progress = false;
+    {
+      std::lock_guard<std::mutex> g(S->mu);
+      // harvest published results
+      for (uint32_t i = 0; i < n; ++i) {
+        SlotInfo& sl = S->slots[i];
+        if (!sl.busy) continue;
+        if (__atomic_load_n(&S->h_outbox[i].seq, __ATOMIC_ACQUIRE) != sl.seq) continue;
+        mc::OutboxEntry o = S->h_outbox[i];
+        finish_slot(S, i, o, 0);
+        progress = true;
+      }
+      // admit queued requests in arrival order while a slot and pool room are free
+      uint32_t scan = 0;
+      while (!S->queue.empty() && !S->fatal) {
+        while (scan < n && S->slots[scan].busy) ++scan;
+        if (scan == n) break;
+        Request& req = S->queue.front();
+        uint64_t off = 0;
+        if (!S->pool.alloc(req.bytes, &off)) break;
+        uint8_t* base = S->d_pool + off;
+        place_instance(req.inst, req.lay, base, req.params.size());
+        req.inst.kind = req.q.kind;
+        req.inst.T_query = req.q.T;
+        if (cudaMemcpyAsync(base, req.params.data(), req.params.size() * 4, cudaMemcpyHostToDevice,
+                            S->copy) != cudaSuccess ||
+            cudaStreamSynchronize(S->copy) != cudaSuccess) {
+          S->fatal = MC_ERR_CUDA;
+          S->last_err = cudaGetErrorString(cudaGetLastError());
+          S->pool.release(off, req.bytes);
+          break;
+        }
+        mc::InboxEntry& e = S->h_inbox[scan];
+        std::memcpy((void*)&e.inst, &req.inst, sizeof(mc::BInst));
+        const uint32_t seq = S->next_seq++;
+        if (S->next_seq == 0) S->next_seq = 1;
+        __atomic_store_n(&e.seq, seq, __ATOMIC_RELEASE);
+        SlotInfo& sl = S->slots[scan];
+        sl.busy = true;
+        sl.seq = seq;
+        sl.off = off;
+        sl.t_admit = now_s();
+        sl.req = std::move(req);
+        S->queue.pop_front();
+        progress = true;
+      }
+      // keep the device loop running while a slot is busy
+      bool any_busy = false;
+      for (uint32_t i = 0; i < n && !any_busy; ++i) any_busy = S->slots[i].busy;
+      if (S->kernel_running) {
+        const cudaError_t q = cudaEventQuery(S->kdone);
+        if (q == cudaSuccess) {
+          S->kernel_running = false;
+          uint32_t err = 0;
+          if (cudaMemcpyAsync(&err, S->d_ctrl, 4, cudaMemcpyDeviceToHost, S->copy) == cudaSuccess &&
+              cudaStreamSynchronize(S->copy) == cudaSuccess && err)
+            S->fatal = (int)err;
+        } else if (q != cudaErrorNotReady) {
+          S->fatal = MC_ERR_CUDA;
+          S->last_err = cudaGetErrorString(q);
+          S->kernel_running = false;
+        }
+      }
+      if (S->fatal) {  // fail every request in flight or queued
+        mc::OutboxEntry none{};
+        for (uint32_t i = 0; i < n; ++i)
+          if (S->slots[i].busy) finish_slot(S, i, none, S->fatal);
+        while (!S->queue.empty()) {
+          mc_server_result res;
+          std::memset(&res, 0, sizeof(res));
+          res.ticket = S->queue.front().ticket;
+          res.result.status = S->fatal;
+          res.result.kind = S->queue.front().q.kind;
+          res.submit_s = S->queue.front().t_submit;
+          res.done_s = now_s();
+          S->done.push_back(res);
+          S->queue.pop_front();
+        }
+        progress = true;
+      } else if (any_busy && !S->kernel_running) {
+        if (launch_server(S)) S->fatal = MC_ERR_CUDA;
+      }
+    }
+    if (progress) S->cv_done.notify_all();
+    else std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+void server_free(mc_server* S) {
+  if (S->h_stop) __atomic_store_n(S->h_stop, 1u, __ATOMIC_RELEASE);
+  if (S->stream) cudaStreamSynchronize(S->stream);
+  if (S->d_pool) cudaFree(S->d_pool);
+  if (S->d_inst) cudaFree(S->d_inst);
+  if (S->d_state) cudaFree(S->d_state);
+  if (S->d_prefix) cudaFree(S->d_prefix);
+  if (S->d_ctrl) cudaFree(S->d_ctrl);
+  if (S->h_inbox) cudaFreeHost(S->h_inbox);
+  if (S->h_outbox) cudaFreeHost(S->h_outbox);
+  if (S->h_stop) cudaFreeHost(S->h_stop);
+  if (S->kdone) cudaEventDestroy(S->kdone);
+  if (S->stream) cudaStreamDestroy(S->stream);
+  if (S->copy) cudaStreamDestroy(S->copy);
+}
+
+}  // namespace
+
+extern "C" {
+
+int mc_server_create(const mc_server_config* cfg, const mc_options* opt, mc_server** out) {
+  if (!cfg || !out || cfg->slots == 0 || cfg->slots > mc::kMaxBatch || cfg->pool_bytes < (1u << 20))
+    return MC_ERR_INVAL;
+  *out = nullptr;
+  mc_server* S = new (std::nothrow) mc_server;
+  if (!S) return MC_ERR_NOMEM;
+  S->cfg = *cfg;
+  if (opt) S->opt = *opt;
+  else mc_options_default(&S->opt);
+  const uint32_t n = cfg->slots;
+  S->slots.resize(n);
+  S->pool.init(cfg->pool_bytes);
+  int sms = 0, coop = 0, bps = 0;
+  auto bad = [&](int code) {
+    cudaGetLastError();
+    server_free(S);
+    delete S;
+    return code;
+  };
+  if (cudaGetDevice(&S->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, S->device) != cudaSuccess || !coop)
+    return bad(MC_ERR_CUDA);
+  S->threads = (int)mc::kThreads;
+  if (mc::batch_kernel_occupancy(S->threads, &bps) || bps < 1) return bad(MC_ERR_CUDA);
+  if (S->opt.blocks_per_sm) bps = std::min<int>(bps, (int)S->opt.blocks_per_sm);
+  S->grid = sms * bps;
+  if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&S->kdone, cudaEventDisableTiming) != cudaSuccess)
+    return bad(MC_ERR_CUDA);
+  if (cudaMalloc(&S->d_pool, cfg->pool_bytes) != cudaSuccess ||
+      cudaMalloc(&S->d_inst, sizeof(mc::BInst) * n) != cudaSuccess ||
+      cudaMalloc(&S->d_state, sizeof(mc::BState) * n) != cudaSuccess ||
+      cudaMalloc(&S->d_prefix, 8ull * (n + 1)) != cudaSuccess ||
+      cudaMalloc(&S->d_ctrl, 256 + mc::kBarBytes) != cudaSuccess)
+    return bad(MC_ERR_NOMEM);
+  if (cudaHostAlloc((void**)&S->h_inbox, sizeof(mc::InboxEntry) * n, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc((void**)&S->h_outbox, sizeof(mc::OutboxEntry) * n, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc((void**)&S->h_stop, 64, cudaHostAllocMapped) != cudaSuccess)
+    return bad(MC_ERR_NOMEM);
+  std::memset(S->h_inbox, 0, sizeof(mc::InboxEntry) * n);
+  std::memset(S->h_outbox, 0, sizeof(mc::OutboxEntry) * n);
+  std::memset(S->h_stop, 0, 64);
+  if (cudaHostGetDevicePointer((void**)&S->d_inbox, S->h_inbox, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&S->d_outbox, S->h_outbox, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&S->d_stop, S->h_stop, 0) != cudaSuccess ||
+      cudaMemsetAsync(S->d_state, 0, sizeof(mc::BState) * n, S->stream) != cudaSuccess ||
+      cudaStreamSynchronize(S->stream) != cudaSuccess)
+    return bad(MC_ERR_CUDA);
+  S->pump = std::thread(pump_loop, S);
+  *out = S;
+  return MC_OK;
+}
+
+int mc_server_submit(mc_server* S, const mc_model_desc* desc, const mc_query* q, uint64_t* ticket) {
+  if (!S || !desc || !q || q->kind > MC_QUERY_MIN_TIME) return MC_ERR_INVAL;
+  Request req;
+  req.t_submit = now_s();
+  req.q = *q;
+  int rc = describe_instance(*desc, S->opt, req.inst, req.lay, req.params, req.bytes);
+  if (rc) return rc;
+  if (req.bytes > S->cfg.pool_bytes) return MC_ERR_NOMEM;
+  if (desc->wg_values) req.wg.assign(desc->wg_values, desc->wg_values + desc->n_wg);
+  if (desc->ts_values) req.ts.assign(desc->ts_values, desc->ts_values + desc->n_ts);
+  std::lock_guard<std::mutex> g(S->mu);
+  if (S->fatal) return S->fatal;
+  req.ticket = S->next_ticket++;
+  if (ticket) *ticket = req.ticket;
+  S->queue.push_back(std::move(req));
+  return MC_OK;
+}
+
+int mc_server_poll(mc_server* S, mc_server_result* out, uint32_t cap, uint32_t* n, uint32_t wait_ms) {
+  if (!S || !n || (!out && cap)) return MC_ERR_INVAL;
+  std::unique_lock<std::mutex> g(S->mu);
+  if (S->done.empty() && wait_ms)
+    S->cv_done.wait_for(g, std::chrono::milliseconds(wait_ms), [&] { return !S->done.empty(); });
+  uint32_t k = 0;
+  while (k < cap && !S->done.empty()) {
+    out[k++] = S->done.front();
+    S->done.pop_front();
+  }
+  *n = k;
+  return MC_OK;
+}
+
+int mc_server_status(mc_server* S, uint32_t* queued, uint32_t* running, uint64_t* launches) {
+  if (!S) return MC_ERR_INVAL;
+  std::lock_guard<std::mutex> g(S->mu);
+  if (queued) *queued = (uint32_t)S->queue.size();
+  if (running) {
+    uint32_t r = 0;
+    for (const SlotInfo& sl : S->slots) r += sl.busy;
+    *running = r;
+  }
+  if (launches) *launches = S->launches;
+  return S->fatal;
+}
+
+void mc_server_destroy(mc_server* S) {
+  if (!S) return;
+  S->shutdown.store(true);
+  if (S->pump.joinable()) S->pump.join();
+  server_free(S);
+  delete S;
+}
 
 }  // extern "C"

@@ -41,6 +41,17 @@ __device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* p, uint32_t v) {
 __device__ __forceinline__ void ld_relaxed_v2u64(const uint64_t* p, uint64_t& a, uint64_t& b) {
   asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
+__device__ __forceinline__ uint32_t ld_acquire_sys_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t* p) {
+  return *reinterpret_cast<const volatile uint64_t*>(p);
+}
 __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -121,13 +132,20 @@ __device__ __forceinline__ uint32_t sum_n(K key, const Params& p) {
   return s;
 }
 
+// Model-table load: through the read-only cache when the tables are fixed for
+// the launch (CG = false), from L2 when a persistent loop may swap them (CG).
+template <bool CG>
+__device__ __forceinline__ uint32_t ldp(const uint32_t* p) {
+  return CG ? __ldcg(p) : __ldg(p);
+}
+
 // model time of a key (max over units of n_c * cost * speed_c)
-template <class K>
+template <class K, bool CG = false>
 __device__ __forceinline__ uint64_t key_time(K key, const Params& p, uint32_t cfg) {
-  uint64_t c0 = __ldg(p.cost + cfg);
+  uint64_t c0 = ldp<CG>(p.cost + cfg);
   uint64_t mx = 0;
   for (uint32_t c = 0; c < p.P; ++c) {
-    uint64_t t = (uint64_t)field(key, (p.P - 1 - c) * p.n_bits, p.n_mask) * c0 * __ldg(p.speed + c);
+    uint64_t t = (uint64_t)field(key, (p.P - 1 - c) * p.n_bits, p.n_mask) * c0 * ldp<CG>(p.speed + c);
     mx = t > mx ? t : mx;
   }
   return mx;
@@ -344,16 +362,17 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t ctr) {
 // gives T_ini).  Walk w draws splitmix64 outputs number (w << 32) + 0, 1, ...:
 // the WG index, the TS index, then per work-group the unit among the allowed
 // ones in index order.  Returns the terminal's model time.
+template <bool CG = false>
 __device__ inline uint64_t simulate_walk(const Params& p, uint64_t seed, uint64_t w) {
   uint64_t ctr = w << 32;
   const uint32_t i = (uint32_t)(splitmix64_at(seed, ctr++) % p.a);
   const uint32_t j = (uint32_t)(splitmix64_at(seed, ctr++) % p.b);
   const uint32_t cfg = i * p.b + j;
-  const uint32_t N = __ldg(p.N + cfg);
-  const uint64_t cost = __ldg(p.cost + cfg);
+  const uint32_t N = ldp<CG>(p.N + cfg);
+  const uint64_t cost = ldp<CG>(p.cost + cfg);
   uint64_t clk[kMaxP], t[kMaxP];
   for (uint32_t c = 0; c < p.P; ++c) {
-    t[c] = cost * __ldg(p.speed + c);
+    t[c] = cost * ldp<CG>(p.speed + c);
     clk[c] = 0;
   }
   for (uint32_t k = 0; k < N; ++k) {

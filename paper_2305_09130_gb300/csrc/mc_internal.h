@@ -170,6 +170,31 @@ struct BState {
   uint32_t trace_len;
   uint64_t wpack;         // packed (time, i, j) of the counterexample
   uint64_t wkey_lo, wkey_hi, widx;
+  uint32_t seq;           // served mode: request number held by this slot
+  uint32_t published;     // served mode: result written to the outbox
+};
+
+// Served mode: host-mapped request and result mailboxes, one per slot.
+struct InboxEntry {
+  BInst inst;             // the request (pointers into the device pool)
+  uint32_t seq;           // written last by the host (release); 0 = empty
+  uint32_t pad[3];
+};
+struct OutboxEntry {
+  uint32_t seq;           // written last by the device (release)
+  int32_t status;
+  uint32_t holds, levels;
+  uint64_t states;
+  uint32_t checks, level;
+  uint64_t time, t_ini, wpack;
+  uint64_t key_lo, key_hi;
+};
+struct ServeArgs {
+  InboxEntry* inbox;      // device view of host memory
+  OutboxEntry* outbox;
+  uint32_t* stop;         // host sets 1 to end the loop
+  uint32_t pad;
+  uint64_t idle_ns;       // wait for new requests this long before exiting
 };
 
 struct BatchArgs {
@@ -185,6 +210,7 @@ struct BatchArgs {
   uint64_t sim_seed;
   uint64_t timeout_ns;
   uint32_t prune, early_exit;
+  ServeArgs serve;        // inbox == nullptr: a plain batch
 };
 
 cudaError_t launch_batch(int grid, int threads, const BatchArgs& args, cudaStream_t stream);

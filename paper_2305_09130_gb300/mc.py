@@ -93,6 +93,16 @@ class McBatchResult(C.Structure):
 
 MC_QUERY_CHECK, MC_QUERY_MIN_TIME = 0, 1
 
+
+class McServerConfig(C.Structure):
+    _fields_ = [("slots", C.c_uint32), ("reserved0", C.c_uint32), ("pool_bytes", C.c_uint64),
+                ("idle_ns", C.c_uint64), ("reserved", C.c_uint64 * 4)]
+
+
+class McServerResult(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("result", McBatchResult), ("submit_s", C.c_double),
+                ("admit_s", C.c_double), ("done_s", C.c_double)]
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -162,6 +172,14 @@ def load(build: bool = True):
                                          C.POINTER(C.c_uint32)]),
             "mc_batch_get_stats": (C.c_int, [P, C.POINTER(McStats)]),
             "mc_batch_last_error": (C.c_char_p, [P]),
+            "mc_server_create": (C.c_int, [C.POINTER(McServerConfig), C.POINTER(McOptions), C.POINTER(P)]),
+            "mc_server_submit": (C.c_int, [P, C.POINTER(McModelDesc), C.POINTER(McQuery),
+                                           C.POINTER(C.c_uint64)]),
+            "mc_server_poll": (C.c_int, [P, C.POINTER(McServerResult), C.c_uint32, C.POINTER(C.c_uint32),
+                                         C.c_uint32]),
+            "mc_server_status": (C.c_int, [P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                           C.POINTER(C.c_uint64)]),
+            "mc_server_destroy": (None, [P]),
             "mc_measure_random_access": (C.c_int, [C.c_uint64, C.c_uint64, C.c_int,
                                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "mc_check_noalloc": (C.c_int, [C.POINTER(McModelDesc), C.c_uint64, C.c_uint32, C.c_uint32,
@@ -491,14 +509,7 @@ def mc_batch_run(batch: Batch, queries) -> list:
                        int(T or 0) & NO_LIMIT)
     res = (McBatchResult * n)()
     batch._check(load().mc_batch_run(batch.handle, q, res), "mc_batch_run")
-    out = []
-    for r in res:
-        d = {"status": r.status, "kind": "min_time" if r.kind == 1 else "check", "holds": bool(r.holds),
-             "levels": r.levels, "states": r.states, "checks": r.checks, "level": r.level,
-             "time": r.time, "t_ini": r.t_ini, "i": r.wg_index, "j": r.ts_index, "wg": r.wg,
-             "ts": r.ts, "key": r.key[0] | (r.key[1] << 64)}
-        out.append(d)
-    return out
+    return [_batch_result(r) for r in res]
 
 
 def mc_batch_trace(batch: Batch, i: int) -> list:
@@ -514,6 +525,75 @@ def mc_batch_get_stats(batch: Batch) -> dict:
     st = McStats()
     batch._check(load().mc_batch_get_stats(batch.handle, C.byref(st)), "mc_batch_get_stats")
     return {k: getattr(st, k) for k, _t in McStats._fields_}
+
+
+def _batch_result(r) -> dict:
+    return {"status": r.status, "kind": "min_time" if r.kind == 1 else "check", "holds": bool(r.holds),
+            "levels": r.levels, "states": r.states, "checks": r.checks, "level": r.level,
+            "time": r.time, "t_ini": r.t_ini, "i": r.wg_index, "j": r.ts_index, "wg": r.wg, "ts": r.ts,
+            "key": r.key[0] | (r.key[1] << 64)}
+
+
+class Server:
+    """Owns an ``mc_server*`` (a request loop over a persistent device loop)."""
+
+    def __init__(self, handle: int):
+        self.handle = C.c_void_p(handle)
+        _live.add(self)
+
+    def __del__(self):
+        try:
+            mc_server_destroy(self)
+        except Exception:
+            pass
+
+
+def mc_server_create(slots: int, pool_bytes: int, options: Optional[McOptions] = None,
+                     idle_ns: int = 0) -> Server:
+    cfg = McServerConfig(int(slots), 0, int(pool_bytes), int(idle_ns))
+    h = C.c_void_p()
+    rc = load().mc_server_create(C.byref(cfg), C.byref(options) if options is not None else None,
+                                 C.byref(h))
+    if rc != MC_OK:
+        raise MCError(rc, "mc_server_create")
+    return Server(h.value)
+
+
+def mc_server_submit(server: Server, spec, kind: str, T: Optional[int] = None) -> int:
+    arr, keep = _descs([spec])
+    q = McQuery(MC_QUERY_MIN_TIME if kind == "min_time" else MC_QUERY_CHECK, 0, int(T or 0) & NO_LIMIT)
+    t = C.c_uint64()
+    rc = load().mc_server_submit(server.handle, arr, C.byref(q), C.byref(t))
+    if rc != MC_OK:
+        raise MCError(rc, "mc_server_submit")
+    return t.value
+
+
+def mc_server_poll(server: Server, cap: int = 1024, wait_ms: int = 0) -> list:
+    buf = (McServerResult * cap)()
+    n = C.c_uint32()
+    rc = load().mc_server_poll(server.handle, buf, cap, C.byref(n), int(wait_ms))
+    if rc != MC_OK:
+        raise MCError(rc, "mc_server_poll")
+    out = []
+    for k in range(n.value):
+        r = buf[k]
+        d = _batch_result(r.result)
+        d.update(ticket=r.ticket, submit_s=r.submit_s, admit_s=r.admit_s, done_s=r.done_s)
+        out.append(d)
+    return out
+
+
+def mc_server_status(server: Server) -> dict:
+    q, r, l = C.c_uint32(), C.c_uint32(), C.c_uint64()
+    fatal = load().mc_server_status(server.handle, C.byref(q), C.byref(r), C.byref(l))
+    return {"queued": q.value, "running": r.value, "launches": l.value, "fatal": fatal}
+
+
+def mc_server_destroy(server: Server):
+    if server.handle and server.handle.value:
+        load(build=False).mc_server_destroy(server.handle)
+        server.handle = C.c_void_p()
 
 
 def decode_key(layout: dict, key: int):

@@ -1,0 +1,99 @@
+"""Served queries (continuous batching): results equal the single-model
+entry points, alone and in a mix (tolerance zero), and requests submitted
+while others run are admitted into the running device loop."""
+import time
+
+import pytest
+
+from paper_2305_09130_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("status", "holds", "levels", "states", "checks", "level", "time", "t_ini", "i", "j", "key")
+
+
+def single(mc, spec, kind, T):
+    m = mc.mc_model_create(spec.with_key_bits(128))
+    if kind == "min_time":
+        r = mc.mc_min_time(m, trace=False)
+        out = {"status": 0, "holds": False, "levels": None, "states": r["states"], "checks": r["checks"],
+               "level": r["level"], "time": r["t_min"], "t_ini": r["t_ini"], "i": r["i"], "j": r["j"],
+               "key": r["witness_key"]}
+    else:
+        r = mc.mc_check(m, T, trace=False)
+        out = {"status": 0, "holds": r["holds"], "levels": r["levels"], "states": r["states"], "checks": 1,
+               "level": r.get("cex_level", 0), "time": r.get("cex_time", 0), "t_ini": 0,
+               "i": r.get("cex_i", 0), "j": r.get("cex_j", 0), "key": r.get("cex_key", 0)}
+    mc.mc_model_destroy(m)
+    return out
+
+
+def collect(mc, srv, n, timeout_s=120):
+    got = {}
+    t0 = time.time()
+    while len(got) < n:
+        for r in mc.mc_server_poll(srv, wait_ms=50):
+            got[r["ticket"]] = r
+        assert time.time() - t0 < timeout_s, mc.mc_server_status(srv)
+    return got
+
+
+def mix():
+    specs = [W.c1(W.FREE), W.c1(W.GREEDY), W.tiny(W.GREEDY), W.c2(rule=W.GREEDY)]
+    specs += W.c4_instances(24, seed=2305091377)
+    queries = []
+    for k, s in enumerate(specs):
+        queries.append(("min_time", None) if k % 2 == 0 else ("check", 40 + 13 * k))
+    return specs, queries
+
+
+def test_served_results_equal_alone_and_in_mix(mc):
+    specs, queries = mix()
+    srv = mc.mc_server_create(slots=8, pool_bytes=4 << 30)
+    tickets = {mc.mc_server_submit(srv, s, k, T): idx for idx, (s, (k, T)) in enumerate(zip(specs, queries))}
+    got = collect(mc, srv, len(specs))
+    for t, idx in tickets.items():
+        r = got[t]
+        exp = single(mc, specs[idx], *queries[idx])
+        for key in KEYS:
+            if exp[key] is not None:
+                assert r[key] == exp[key], (idx, key, r, exp)
+        assert r["submit_s"] <= r["admit_s"] <= r["done_s"]
+    # the same query alone on a fresh server gives the same answer
+    alone = mc.mc_server_create(slots=1, pool_bytes=1 << 30)
+    for idx in (0, 3, 9):
+        t = mc.mc_server_submit(alone, specs[idx], *queries[idx])
+        r = collect(mc, alone, 1)[t]
+        assert {k: r[k] for k in KEYS} == {k: got[list(tickets)[idx]][k] for k in KEYS}
+    mc.mc_server_destroy(alone)
+    st = mc.mc_server_status(srv)
+    assert st["fatal"] == 0 and st["queued"] == 0 and st["running"] == 0
+    mc.mc_server_destroy(srv)
+
+
+def test_requests_join_a_running_device_loop(mc):
+    # a long GREEDY search is running when small queries arrive: they are
+    # admitted into the same device loop and finish first
+    long_spec = W.c3(rule=W.GREEDY)
+    srv = mc.mc_server_create(slots=16, pool_bytes=8 << 30, options=mc.mc_options_default(prune=0))
+    t_long = mc.mc_server_submit(srv, long_spec, "min_time")
+    time.sleep(0.01)
+    small = [mc.mc_server_submit(srv, W.c1(W.FREE), "check", 80) for _ in range(6)]
+    got = collect(mc, srv, 7)
+    L = got[t_long]
+    assert L["status"] == 0
+    for t in small:
+        r = got[t]
+        assert r["status"] == 0 and not r["holds"] and r["time"] == 80
+        assert r["admit_s"] < L["done_s"] and r["done_s"] < L["done_s"]
+    st = mc.mc_server_status(srv)
+    assert st["launches"] >= 1 and st["fatal"] == 0
+    mc.mc_server_destroy(srv)
+
+
+def test_server_rejects_models_larger_than_its_pool(mc):
+    srv = mc.mc_server_create(slots=2, pool_bytes=1 << 20)
+    with pytest.raises(mc.MCError) as e:
+        mc.mc_server_submit(srv, W.c2_star(), "check", 95)
+    assert e.value.code == mc.MC_ERR_NOMEM
+    mc.mc_server_destroy(srv)
