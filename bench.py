@@ -26,6 +26,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -490,6 +491,109 @@ def run_c4(args):
     return 0
 
 
+def run_c5(args):
+    """Served queries: Poisson arrivals of min-time queries on models drawn as
+    the large single query (G=4096, P=8, WG 2^0..2^9, TS 2^0..2^5, cost
+    U{1..16} with a new seed per query, GREEDY, 128-bit keys), at each rate of
+    --rates, answered by the request loop (mc_server_*), against the same
+    arrivals served one query at a time on the single-model entry point."""
+    import torch
+
+    from paper_2305_09130_gb300 import mc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    rates = [float(x) for x in args.rates.split(",")]
+    rng = W.SplitMix64(2305091305)
+    free_b, _tot = torch.cuda.mem_get_info()
+    pool = int(min(free_b * 0.6, 120 << 30))
+    srv = mc.mc_server_create(slots=args.slots, pool_bytes=pool)
+
+    def make_query(k):
+        return W.c3(G=4096, rule=W.GREEDY, seed=2305091305 * 1000003 + k, key_bits=128)
+
+    # one-query-at-a-time service times on a sample of the same query stream
+    sample = [make_query(10_000_000 + k) for k in range(args.c5_sample)]
+    service, service_states = [], []
+    for sp in sample:
+        m = mc.mc_model_create(sp)
+        mc.mc_reserve(m)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        r = mc.mc_min_time(m, trace=False)
+        b.record()
+        b.synchronize()
+        service.append(a.elapsed_time(b) / 1000.0)
+        service_states.append(r["states"])
+        mc.mc_model_destroy(m)
+
+    sweep = []
+    qid = 0
+    for rate in rates:
+        n = int(min(args.c5_queries, max(20, rate * args.c5_seconds)))
+        arrivals, t = [], 0.0
+        for _ in range(n):
+            u = (rng.next() >> 11) / float(1 << 53)
+            t += -math.log(1.0 - u) / rate
+            arrivals.append(t)
+        specs = [make_query(qid + k) for k in range(n)]
+        qid += n
+        got = {}
+        t0 = time.perf_counter()
+        for k in range(n):
+            while time.perf_counter() - t0 < arrivals[k]:
+                for r in mc.mc_server_poll(srv, wait_ms=0):
+                    got[r["ticket"]] = r
+                time.sleep(0.0002)
+            mc.mc_server_submit(srv, specs[k], "min_time")
+        while len(got) < n:
+            for r in mc.mc_server_poll(srv, wait_ms=20):
+                got[r["ticket"]] = r
+            if time.perf_counter() - t0 > arrivals[-1] + 600:
+                raise SystemExit(f"served run at {rate}/s did not finish: {mc.mc_server_status(srv)}")
+        res = list(got.values())
+        assert all(r["status"] == 0 for r in res)
+        lat = [1000.0 * (r["done_s"] - r["submit_s"]) for r in res]
+        first = min(r["submit_s"] for r in res)
+        last = max(r["done_s"] for r in res)
+        # the same arrivals served FIFO one at a time, service times cycling
+        # through the measured sample
+        clock, seq_lat = 0.0, []
+        for k, a in enumerate(arrivals):
+            start = max(clock, a)
+            clock = start + service[k % len(service)]
+            seq_lat.append(1000.0 * (clock - a))
+        sweep.append({
+            "rate_per_s": rate, "queries": n,
+            "served": {"throughput_qps": n / (last - first), "latency_ms_p50": percentile(lat, 50),
+                       "latency_ms_p99": percentile(lat, 99),
+                       "states_per_s": sum(r["states"] for r in res) / (last - first)},
+            "sequential": {"throughput_qps": n / (clock - arrivals[0]) if clock > arrivals[0] else None,
+                           "latency_ms_p50": percentile(seq_lat, 50), "latency_ms_p99": percentile(seq_lat, 99)},
+        })
+    status = mc.mc_server_status(srv)
+    mc.mc_server_destroy(srv)
+    top = sweep[-1]
+    line = {
+        "metric": "served queries: throughput with p50/p99 latency", "value": top["served"]["throughput_qps"],
+        "unit": "queries/s", "n_gpus": 1, "steps": len(rates), "warmup": 0,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u128", "data": "synthetic (seeded model per query)",
+        "config": {"workload": "c5: min-time queries on G=4096, P=8, WG 2^0..2^9, TS 2^0..2^5, "
+                               "cost U{1..16} (new splitmix64 seed per query), GREEDY, 128-bit keys; "
+                               "Poisson arrivals", "slots": args.slots, "pool_bytes": pool,
+                   "sequential_service_ms_mean": 1000.0 * sum(service) / len(service),
+                   "sequential_sample": len(service),
+                   "note": "sequential latencies: the same arrival times served FIFO one at a time, with "
+                           "service times cycling through the measured single-query sample"},
+        "sweep": sweep, "device_loop_launches": status["launches"],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     p.add_argument("--gpus", type=int, default=1)
@@ -500,7 +604,12 @@ def main(argv=None):
     p.add_argument("--prune", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-random-roofline", action="store_true")
-    p.add_argument("--workload", choices=sorted(WORKLOADS) + ["c4"], default="c2_star",
+    p.add_argument("--rates", default="10,30,100,300,1000", help="c5 arrival rates (queries/s)")
+    p.add_argument("--slots", type=int, default=512, help="c5 requests on the device at once")
+    p.add_argument("--c5-seconds", type=float, default=6.0, help="c5 arrivals per rate span")
+    p.add_argument("--c5-queries", type=int, default=10000, help="c5 queries per rate at most")
+    p.add_argument("--c5-sample", type=int, default=48, help="c5 single-query service sample")
+    p.add_argument("--workload", choices=sorted(WORKLOADS) + ["c4", "c5"], default="c2_star",
                    help="profiling aid; the benchmark line is c2_star")
     p.add_argument("--query", choices=["min_time", "count"], default="min_time")
     args = p.parse_args(argv)
@@ -510,6 +619,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "c4":
         return run_c4(args)
+    if args.workload == "c5":
+        return run_c5(args)
     return run_ours(args)
 
 

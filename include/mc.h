@@ -178,6 +178,8 @@ typedef struct {
   uint64_t d2h_bytes;        /* device -> host bytes copied                  */
   double explore_ms;         /* summed CUDA-event time of the exploration
                                 kernels (only with mc_options.timing = 1)    */
+  uint64_t device_steps;     /* device-wide barrier steps: BFS levels of the
+                                passes, or lockstep steps of a batch launch  */
 } mc_stats;
 
 typedef void* (*mc_alloc_fn)(size_t bytes, void* stream, void* ctx);

@@ -353,6 +353,7 @@ int pass_error(mc_model* m, int slot) {
   const Ctrl& c = m->h_ctrl[slot];
   m->last_levels = c.levels;
   m->stats.states += c.states;
+  m->stats.device_steps += c.levels;
   return c.err ? (int)c.err : MC_OK;  // the kernel stores the negative MC_ERR_* code
 }
 
@@ -495,14 +496,21 @@ int mc_model_create(const mc_model_desc* d, const mc_options* opt, mc_model** ou
   //           after k dispatches only the units tied at the next start time
   //           can differ.
   const uint64_t greedy_cap = binom_sat(m->P, m->P / 2);
+  // configurations with N_ij >= k, for every k (suffix sums of a histogram)
+  std::vector<uint64_t> at_least(n_max + 2, 0);
+  for (size_t k = 0; k < ab; ++k) at_least[m->N[k]] += 1;
+  for (int64_t k = (int64_t)n_max - 1; k >= 0; --k) at_least[k] += at_least[k + 1];
   uint64_t total = add_sat(1 + (uint64_t)m->a, ab);
   uint64_t widest = 0;
+  uint64_t per_free = 1;  // C(k+P-1, P-1), updated incrementally (saturating)
   for (uint32_t k = 1; k <= n_max; ++k) {
-    uint64_t cnt = 0;
-    for (size_t c = 0; c < ab; ++c) cnt += m->N[c] >= k;
-    uint64_t per = binom_sat((uint64_t)k + m->P - 1, m->P - 1);
+    if (per_free != UINT64_MAX) {
+      const unsigned __int128 nx = (unsigned __int128)per_free * (k + m->P - 1) / k;
+      per_free = nx > (unsigned __int128)UINT64_MAX ? UINT64_MAX : (uint64_t)nx;
+    }
+    uint64_t per = per_free;
     if (m->rule == MC_GREEDY) per = std::min(per, greedy_cap);
-    const uint64_t w = mul_sat(per, cnt);
+    const uint64_t w = mul_sat(per, at_least[k]);
     widest = std::max(widest, w);
     total = add_sat(total, w);
   }

@@ -225,12 +225,18 @@ struct Planner {
     const uint32_t n = A->n;
     const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
     const uint32_t i0 = threadIdx.x * per, i1 = min(n, i0 + per);
+    // served mode: the doorbell read issued now is consumed at the end, so
+    // its trip to host memory overlaps this plan; the inbox is scanned only
+    // in a plan that follows a doorbell change
+    uint32_t db = 0;
+    if (serve && threadIdx.x == 0) db = *reinterpret_cast<const volatile uint32_t*>(A->serve.doorbell);
+    const bool scan_inbox = serve && __ldcg(A->serve.seen + 1) != 0;
     unsigned long long local = 0;
     for (uint32_t i = i0; i < i1; ++i) {
       BState s;
       load_cg(A->state + i, s);
       uint64_t c = 0;
-      if (serve) admit(*A, i, s);
+      if (scan_inbox) admit(*A, i, s);
       if (!serve || (s.seq != 0 && !s.published)) {
         BInst I;
         load_cg(A->inst + i, I);
@@ -268,28 +274,49 @@ struct Planner {
       A->plan_prefix[i] = run;
       run += s_count[i];
     }
-    if (threadIdx.x == 0) A->plan_prefix[n] = s_total;
+    if (threadIdx.x == 0) {
+      A->plan_prefix[n] = s_total;
+      if (serve) {
+        A->serve.seen[1] = db != __ldcg(A->serve.seen) ? 1u : 0u;
+        A->serve.seen[0] = db;
+      }
+    }
     const unsigned long long total = s_total;
     __syncthreads();
     return total;
   }
 
-  // Served mode with nothing to do: wait (bounded by idle_ns) until a
-  // request is posted or the host asks to stop.  True when one was posted.
+  // Served mode with nothing to do: wait (bounded by idle_ns) until the host
+  // posts a request or asks to stop.  True when one was posted (the next
+  // plan then scans the inbox).
   __device__ bool wait_for_requests() const {
-    const uint32_t n = A->n;
+    __shared__ uint32_t s_state;
     const uint64_t t0 = globaltimer();
     for (;;) {
-      int found = 0;
-      for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const uint32_t seq = ld_acquire_sys_u32(&A->serve.inbox[i].seq);
-        if (seq != 0 && seq != __ldcg(&A->state[i].seq)) found = 1;
+      if (threadIdx.x == 0) {
+        s_state = 0;
+        if (ld_acquire_sys_u32(A->serve.stop)) {
+          s_state = 2;
+        } else if (__ldcg(A->serve.seen + 1) != 0) {
+          s_state = 1;
+        } else {
+          const uint32_t db = ld_acquire_sys_u32(A->serve.doorbell);
+          if (db != __ldcg(A->serve.seen)) {
+            A->serve.seen[0] = db;
+            A->serve.seen[1] = 1;
+            s_state = 1;
+          } else if (globaltimer() - t0 > A->serve.idle_ns) {
+            s_state = 3;
+          } else {
+            __nanosleep(1000);
+          }
+        }
       }
-      const int stop = threadIdx.x == 0 ? (int)ld_acquire_sys_u32(A->serve.stop) : 0;
-      if (__syncthreads_or(stop)) return false;
-      if (__syncthreads_or(found)) return true;
-      if (globaltimer() - t0 > A->serve.idle_ns) return false;
-      __nanosleep(2000);
+      __syncthreads();
+      const uint32_t st = s_state;
+      __syncthreads();
+      if (st == 1) return true;
+      if (st >= 2) return false;
     }
   }
 
@@ -499,7 +526,10 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs A) {
         reinterpret_cast<const unsigned long long*>(A.plan_prefix) + i);
     __syncthreads();
     const uint64_t total = s_prefix[A.n];
-    if (total == 0) break;
+    if (total == 0) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) A.err[1] = epoch;  // steps of this launch
+      break;
+    }
     Staging sg;
     BState s;
     BInst I;
@@ -850,13 +880,15 @@ int mc_batch_run(mc_batch* b, const mc_query* queries, mc_batch_result* results)
   if (b->opt.timing) MCB_CUDA(b, cudaEventRecord(b->ev[0], b->stream));
   MCB_CUDA(b, mc::launch_batch(b->grid, b->threads, A, b->stream));
   if (b->opt.timing) MCB_CUDA(b, cudaEventRecord(b->ev[1], b->stream));
-  uint32_t err = 0;
+  uint32_t ctrl2[2] = {0, 0};  // launch error word, steps of the launch
   MCB_CUDA(b, cudaMemcpyAsync(b->h_state.data(), b->d_state, sizeof(mc::BState) * b->n,
                               cudaMemcpyDeviceToHost, b->stream));
-  MCB_CUDA(b, cudaMemcpyAsync(&err, b->d_ctrl, 4, cudaMemcpyDeviceToHost, b->stream));
+  MCB_CUDA(b, cudaMemcpyAsync(ctrl2, b->d_ctrl, 8, cudaMemcpyDeviceToHost, b->stream));
   MCB_CUDA(b, cudaStreamSynchronize(b->stream));
-  b->stats.d2h_bytes += sizeof(mc::BState) * b->n + 4;
+  b->stats.d2h_bytes += sizeof(mc::BState) * b->n + 8;
   b->stats.explore_launches += 1;
+  b->stats.device_steps += ctrl2[1];
+  const uint32_t err = ctrl2[0];
   if (b->opt.timing) {
     float ms = 0.f;
     MCB_CUDA(b, cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
@@ -1004,6 +1036,8 @@ struct mc_server {
   mc::InboxEntry *h_inbox = nullptr, *d_inbox = nullptr;
   mc::OutboxEntry *h_outbox = nullptr, *d_outbox = nullptr;
   uint32_t *h_stop = nullptr, *d_stop = nullptr;
+  uint32_t *h_doorbell = nullptr, *d_doorbell = nullptr;  // inside the h_stop allocation
+  uint32_t* d_seen = nullptr;
   cudaEvent_t kdone = nullptr;
   bool kernel_running = false;
   uint64_t launches = 0;
@@ -1072,6 +1106,8 @@ int launch_server(mc_server* S) {
   A.serve.inbox = S->d_inbox;
   A.serve.outbox = S->d_outbox;
   A.serve.stop = S->d_stop;
+  A.serve.doorbell = S->d_doorbell;
+  A.serve.seen = S->d_seen;
   A.serve.idle_ns = S->cfg.idle_ns ? S->cfg.idle_ns : 2000000ull;
   if (cudaMemsetAsync(S->d_ctrl, 0, 256 + mc::kBarBytes, S->stream) != cudaSuccess ||
       mc::launch_batch(S->grid, S->threads, A, S->stream) != cudaSuccess ||
@@ -1125,6 +1161,7 @@ void pump_loop(mc_server* S) {
         const uint32_t seq = S->next_seq++;
         if (S->next_seq == 0) S->next_seq = 1;
         __atomic_store_n(&e.seq, seq, __ATOMIC_RELEASE);
+        __atomic_add_fetch(S->h_doorbell, 1u, __ATOMIC_RELEASE);
         SlotInfo& sl = S->slots[scan];
         sl.busy = true;
         sl.seq = seq;
@@ -1184,6 +1221,7 @@ void server_free(mc_server* S) {
   if (S->d_state) cudaFree(S->d_state);
   if (S->d_prefix) cudaFree(S->d_prefix);
   if (S->d_ctrl) cudaFree(S->d_ctrl);
+  if (S->d_seen) cudaFree(S->d_seen);
   if (S->h_inbox) cudaFreeHost(S->h_inbox);
   if (S->h_outbox) cudaFreeHost(S->h_outbox);
   if (S->h_stop) cudaFreeHost(S->h_stop);
@@ -1231,7 +1269,8 @@ int mc_server_create(const mc_server_config* cfg, const mc_options* opt, mc_serv
       cudaMalloc(&S->d_inst, sizeof(mc::BInst) * n) != cudaSuccess ||
       cudaMalloc(&S->d_state, sizeof(mc::BState) * n) != cudaSuccess ||
       cudaMalloc(&S->d_prefix, 8ull * (n + 1)) != cudaSuccess ||
-      cudaMalloc(&S->d_ctrl, 256 + mc::kBarBytes) != cudaSuccess)
+      cudaMalloc(&S->d_ctrl, 256 + mc::kBarBytes) != cudaSuccess ||
+      cudaMalloc(&S->d_seen, 256) != cudaSuccess)
     return bad(MC_ERR_NOMEM);
   if (cudaHostAlloc((void**)&S->h_inbox, sizeof(mc::InboxEntry) * n, cudaHostAllocMapped) != cudaSuccess ||
       cudaHostAlloc((void**)&S->h_outbox, sizeof(mc::OutboxEntry) * n, cudaHostAllocMapped) != cudaSuccess ||
@@ -1240,9 +1279,12 @@ int mc_server_create(const mc_server_config* cfg, const mc_options* opt, mc_serv
   std::memset(S->h_inbox, 0, sizeof(mc::InboxEntry) * n);
   std::memset(S->h_outbox, 0, sizeof(mc::OutboxEntry) * n);
   std::memset(S->h_stop, 0, 64);
+  S->h_doorbell = S->h_stop + 8;  // its own 32 bytes of the same mapped allocation
   if (cudaHostGetDevicePointer((void**)&S->d_inbox, S->h_inbox, 0) != cudaSuccess ||
       cudaHostGetDevicePointer((void**)&S->d_outbox, S->h_outbox, 0) != cudaSuccess ||
       cudaHostGetDevicePointer((void**)&S->d_stop, S->h_stop, 0) != cudaSuccess ||
+      !(S->d_doorbell = S->d_stop + 8) ||
+      cudaMemsetAsync(S->d_seen, 0, 256, S->stream) != cudaSuccess ||
       cudaMemsetAsync(S->d_state, 0, sizeof(mc::BState) * n, S->stream) != cudaSuccess ||
       cudaStreamSynchronize(S->stream) != cudaSuccess)
     return bad(MC_ERR_CUDA);

@@ -280,10 +280,9 @@ __device__ bool grid_sync(const Barrier& B, uint32_t& epoch, const Serial& seria
     if (s_release) {
       serial();
       __syncthreads();
-      if (threadIdx.x == 0) {
-        __threadfence();
-        st_release_u32(gen, target);
-      }
+      // the block's writes are ordered before thread 0's release by the
+      // barrier above (release is cumulative)
+      if (threadIdx.x == 0) st_release_u32(gen, target);
     }
   }
   if (threadIdx.x == 0) {

@@ -193,7 +193,9 @@ struct ServeArgs {
   InboxEntry* inbox;      // device view of host memory
   OutboxEntry* outbox;
   uint32_t* stop;         // host sets 1 to end the loop
-  uint32_t pad;
+  uint32_t* doorbell;     // host-mapped: bumped after every post
+  uint32_t* seen;         // device memory: [0] last doorbell value read,
+                          // [1] 1 when the inbox is to be scanned at the next plan
   uint64_t idle_ns;       // wait for new requests this long before exiting
 };
 
