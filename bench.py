@@ -46,6 +46,9 @@ WORKLOADS = {
     "c3_star": (lambda: W.c3_star(),
                 "c3_star: G=36, P=8, WG 2^0..2^9, TS 2^0..2^5, FREE, cost U{1..16} (splitmix64 seed "
                 "2305091303), 128-bit keys; 1,072,924,481 reachable states"),
+    "c3": (lambda: W.c3(rule=W.GREEDY),
+           "c3: G=4096, P=8, WG 2^0..2^9, TS 2^0..2^5, GREEDY, cost U{1..16} (splitmix64 seed "
+           "2305091303), 128-bit keys"),
     "c3_star_g24": (lambda: W.c3(G=24, rule=W.FREE, key_bits=128),
                     "c3 at G=24: P=8, WG 2^0..2^9, TS 2^0..2^5, FREE, cost U{1..16} (seed 2305091303), "
                     "128-bit keys (a reduced C3* for profiling)"),
@@ -399,6 +402,45 @@ def percentile(xs, q):
     return xs[k]
 
 
+def run_swarm(args):
+    """Swarm search (Section 5) on a workload: rounds of random runs on the
+    GPU, the first trail's time and optimality against the exact T_min, as in
+    the paper's Table 1 (first trail, optimality of the first trail)."""
+    import torch
+
+    from paper_2305_09130_gb300 import mc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    spec = WORKLOADS[args.workload][0]()
+    m = mc.mc_model_create(spec, mc.mc_options_default(timing=1))
+    t_min = mc.mc_min_time(m, trace=False)["t_min"]
+    walks = args.swarm_walks
+    mc.mc_swarm(m, 1, walks, max_rounds=2, trace=False)  # warm-up
+    runs = []
+    for k in range(args.steps):
+        runs.append(mc.mc_swarm(m, 2305091300 + k, walks, max_rounds=64, trace=True))
+    best = runs[-1]
+    line = {
+        "metric": "swarm search: random runs per second, first-trail time and optimality",
+        "value": sum(r["walks"] for r in runs) / (sum(r["total_ms"] for r in runs) / 1000.0),
+        "unit": "runs/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+        "ms_per_step": sum(r["total_ms"] for r in runs) / len(runs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload][1] or WORKLOAD, "walks_per_round": walks,
+                   "stop": "after the first round without a run at or below best - 1 (at most 64 rounds)"},
+        "t_min_exact": t_min,
+        "runs": [{"first_trail_ms": r["first_trail_ms"], "total_ms": r["total_ms"], "rounds": r["rounds"],
+                  "first_time": r["first_time"], "best_time": r["best_time"],
+                  "first_trail_optimality": t_min / r["first_time"],
+                  "final_optimality": t_min / r["best_time"], "wg": r["wg"], "ts": r["ts"]} for r in runs],
+        "trace_states": len(best["trace"]),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_c4(args):
     """Batched queries: 256 uneven models (G = 2^U{6..12}, P in {2,4,8}, WG
     2^0..2^8, TS 2^0..2^4, cost U{1..16}, speeds U{1..3}, GREEDY), half
@@ -413,7 +455,15 @@ def run_c4(args):
     device = torch.device("cuda", local)
     dist_init(world, True)
     specs = W.c4_instances(256)
-    opts = mc.mc_options_default(timing=1)
+    from paper_2305_09130_gb300 import autotune as AT
+    probe = mc.mc_batch_create(specs)
+    optima0 = [r["time"] for r in mc.mc_batch_run(probe, [("min_time", None)] * len(specs))]
+    mc.mc_batch_destroy(probe)
+    queries0 = [("min_time", None) if sp.meta["query"] else
+                ("check", round(t * sp.meta["t_frac_milli"] / 1000)) for sp, t in zip(specs, optima0)]
+    tuned = AT.tune_batch(specs, queries0, space={"blocks_per_sm": [0, 1, 2], "load_factor_pct": [25, 50]},
+                          reps=1, cache={}, path=os.path.join(tempfile.gettempdir(), "mc_autotune_c4.json"))
+    opts = mc.mc_options_default(timing=1, **tuned["options"])
     stream = torch.cuda.Stream(device)
     batch = mc.mc_batch_create(specs, opts, stream=stream)
     # the check thresholds are fractions of each instance's optimum: take the
@@ -475,6 +525,7 @@ def run_c4(args):
                                "cost U{1..16}, speeds U{1..3} (splitmix64 seed 2305091304), GREEDY; "
                                "half mc_min_time, half mc_check at round(U[0.8,1.2] x T_min)",
                    "query": "one mc_batch_run per step (one persistent launch)",
+                   "autotuned_options": tuned["options"], "autotune_ms": tuned["timings"],
                    "states_per_step": states / args.steps},
         "batched": {"ms_per_batch": dev_ms_max / args.steps, "states_per_s": value,
                     "query_latency_ms_p50": percentile(batch_ms, 50),
@@ -611,7 +662,8 @@ def main(argv=None):
     p.add_argument("--c5-sample", type=int, default=48, help="c5 single-query service sample")
     p.add_argument("--workload", choices=sorted(WORKLOADS) + ["c4", "c5"], default="c2_star",
                    help="profiling aid; the benchmark line is c2_star")
-    p.add_argument("--query", choices=["min_time", "count"], default="min_time")
+    p.add_argument("--query", choices=["min_time", "count", "swarm"], default="min_time")
+    p.add_argument("--swarm-walks", type=int, default=1 << 20, help="random runs per swarm round")
     args = p.parse_args(argv)
     if args.warmup < 3:
         p.error("--warmup must be >= 3")
@@ -619,6 +671,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "c4":
         return run_c4(args)
+    if args.query == "swarm":
+        return run_swarm(args)
     if args.workload == "c5":
         return run_c5(args)
     return run_ours(args)

@@ -246,6 +246,31 @@ int mc_count_states(mc_model* m, uint64_t* out);
  * order (x % count).  Errors: INVAL, NOMEM, CUDA. */
 int mc_simulate(mc_model* m, uint64_t seed, uint32_t walks, uint64_t* t_ini);
 
+/* Swarm search (Section 5): a first round of `walks_per_round` random runs
+ * (the swarm checking G(!FIN): every run that terminates is a counterexample)
+ * gives the first trail; each further round runs as many fresh random runs
+ * cut as soon as a clock passes T-1, T the best time so far (the swarm
+ * checking the over-time property at T-1).  The search stops after the first
+ * round that finds nothing -- the paper's stopping criterion -- or after
+ * max_rounds.  Runs are the walks of mc_simulate: round r uses walks
+ * r*walks_per_round .. (r+1)*walks_per_round-1 of `seed`.  Not a proof of
+ * optimality: compare with mc_min_time.  *trace (NULL ok) receives the best
+ * run.  Errors: INVAL (walks_per_round 0 or above 2^24), NOMEM, CUDA. */
+typedef struct {
+  uint64_t best_time;     /* least terminal time found                      */
+  uint64_t first_time;    /* least time of the first round                  */
+  uint32_t wg_index, ts_index, wg, ts;   /* configuration of the best run   */
+  uint32_t rounds;        /* rounds run (the last one found nothing unless
+                             max_rounds stopped the search)                 */
+  uint32_t key_words;
+  uint64_t walks;         /* random runs made                               */
+  uint64_t best_walk;     /* walk index of the best run                     */
+  double first_trail_ms;  /* host time from the call to the first round's end */
+  double total_ms;        /* host time of the whole search                  */
+} mc_swarm_result;
+int mc_swarm(mc_model* m, uint64_t seed, uint32_t walks_per_round, uint32_t max_rounds,
+             mc_swarm_result* out, mc_trace** trace);
+
 /* Per-level widths of the model's last exploration; *n receives the level
  * count and up to cap widths are copied.  Errors: INVAL, CUDA. */
 int mc_last_widths(mc_model* m, uint64_t* out, uint32_t cap, uint32_t* n);

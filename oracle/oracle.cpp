@@ -273,7 +273,7 @@ uint64_t splitmix64_at(uint64_t seed, uint64_t ctr) {
 // Walk w draws from counters (w << 32) + 0, 1, 2, ...: the WG index, the TS
 // index, then one draw per dispatched work-group picking among the allowed
 // units in index order.
-uint64_t simulate_walk(const Model& m, uint64_t seed, uint32_t w) {
+uint64_t simulate_walk(const Model& m, uint64_t seed, uint64_t w) {
   uint64_t ctr = (uint64_t)w << 32;
   State s;
   s.n.assign(m.P, 0);
@@ -307,6 +307,18 @@ int oracle_count(const or_model* mm, uint64_t* out) {
   int rc = oracle_check(mm, kNoLimit, 0, 0, &r, nullptr, 0);
   if (rc == 0) *out = r.states;
   return rc;
+}
+
+// One random run (walk number w of `seed`): its terminal time and (i, j).
+int oracle_walk(const or_model* mm, uint64_t seed, uint64_t w, uint64_t* time, uint32_t* i,
+                uint32_t* j) {
+  if (!mm || !time || !i || !j) return -1;
+  Model m = load(mm);
+  uint64_t ctr = w << 32;
+  *i = (uint32_t)(splitmix64_at(seed, ctr++) % m.a);
+  *j = (uint32_t)(splitmix64_at(seed, ctr++) % m.b);
+  *time = simulate_walk(m, seed, w);
+  return 0;
 }
 
 int oracle_simulate(const or_model* mm, uint64_t seed, uint32_t walks, uint64_t* t_ini) {

@@ -11,7 +11,9 @@ with the host C++ compiler and exposes:
 * ``simulate(spec, seed, walks)`` -- T_ini from random runs (Section 4,
   Step 3: a simulation gives the initial bound);
 * ``min_time(spec, search, ...)`` -- Step 3 (search for T_min) and Step 4
-  (the configuration of the last counterexample).
+  (the configuration of the last counterexample);
+* ``walk(spec, seed, w)`` and ``swarm(spec, seed, walks, rounds)`` -- the
+  random runs and the swarm search of Section 5.
 """
 from __future__ import annotations
 
@@ -70,7 +72,10 @@ def lib():
                                           C.POINTER(C.c_uint64)]
             L.oracle_min_time.argtypes = [C.POINTER(OrModel), C.c_int, C.c_int, C.c_int, C.c_int,
                                           C.c_uint64, C.c_uint32, C.POINTER(OrMin)]
-            for f in (L.oracle_check, L.oracle_count, L.oracle_simulate, L.oracle_min_time):
+            L.oracle_walk.argtypes = [C.POINTER(OrModel), C.c_uint64, C.c_uint64, C.POINTER(C.c_uint64),
+                                      C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+            for f in (L.oracle_check, L.oracle_count, L.oracle_simulate, L.oracle_min_time,
+                      L.oracle_walk):
                 f.restype = C.c_int
             _lib = L
     return _lib
@@ -114,6 +119,39 @@ def simulate(spec, seed: int, walks: int = 1) -> int:
     if lib().oracle_simulate(C.byref(m), seed & NO_LIMIT, walks, C.byref(out)) != 0:
         raise ValueError("oracle_simulate failed")
     return out.value
+
+
+def walk(spec, seed: int, w: int):
+    """(time, i, j) of random run number w of `seed` (Section 5's swarm runs)."""
+    m, _keep = _model(spec)
+    t, i, j = C.c_uint64(), C.c_uint32(), C.c_uint32()
+    if lib().oracle_walk(C.byref(m), seed & NO_LIMIT, w, C.byref(t), C.byref(i), C.byref(j)) != 0:
+        raise ValueError("oracle_walk failed")
+    return t.value, i.value, j.value
+
+
+def swarm(spec, seed: int, walks_per_round: int, max_rounds: int) -> dict:
+    """Section 5's swarm search over the same runs: round 0 takes the least
+    terminal time of its runs; each later round looks for a run ending at or
+    below (best - 1) and the search stops after a round that finds none."""
+    bound = None
+    out = {"rounds": 0, "walks": 0}
+    for r in range(max_rounds):
+        base = r * walks_per_round
+        found = None
+        for k in range(walks_per_round):
+            t, i, j = walk(spec, seed, base + k)
+            if (bound is None or t <= bound) and (found is None or (t, k) < found[:2]):
+                found = (t, k, i, j)
+        out["rounds"] = r + 1
+        out["walks"] += walks_per_round
+        if found is None:
+            break
+        out.update(best_time=found[0], best_walk=base + found[1], i=found[2], j=found[3])
+        if r == 0:
+            out["first_time"] = found[0]
+        bound = found[0] - 1
+    return out
 
 
 def min_time(spec, search: str = "single", prune: bool = True, early_exit: bool = True,

@@ -4,6 +4,7 @@
 // a query runs in the kernels of mc_kernels.cu; this file only enqueues them
 // on the model's stream and reads back a few words of results.
 #include <algorithm>
+#include <chrono>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -734,6 +735,74 @@ int mc_min_time(mc_model* m, mc_min_result* out, mc_trace** trace) {
   out->witness_key[0] = c.wkey_lo;
   out->witness_key[1] = m->key_words == 2 ? c.wkey_hi : 0;
   MC_TRY(make_trace(m, c, trace));
+  return MC_OK;
+}
+
+int mc_swarm(mc_model* m, uint64_t seed, uint32_t walks_per_round, uint32_t max_rounds,
+             mc_swarm_result* out, mc_trace** trace) {
+  if (!m || !out || walks_per_round == 0 || walks_per_round > (1u << 24) || max_rounds == 0)
+    return MC_ERR_INVAL;
+  if (trace) *trace = nullptr;
+  std::memset(out, 0, sizeof(*out));
+  DeviceGuard g(m->device);
+  MC_TRY(reserve(m));
+  const auto t0 = std::chrono::steady_clock::now();
+  auto ms_since = [&]() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  };
+  int sms = 0;
+  MC_CUDA(m, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+  unsigned long long* best = reinterpret_cast<unsigned long long*>(m->d_tmin);
+  uint64_t bound = UINT64_MAX;
+  for (uint32_t r = 0; r < max_rounds; ++r) {
+    MC_CUDA(m, cudaMemsetAsync(best, 0xFF, 8, m->stream));
+    MC_CUDA(m, mc::launch_swarm(m->params, seed, (uint64_t)r * walks_per_round, walks_per_round, bound,
+                                best, sms * 8, m->stream));
+    m->stats.other_launches += 1;
+    MC_CUDA(m, cudaMemcpyAsync(m->h_scalar, best, 8, cudaMemcpyDeviceToHost, m->stream));
+    m->stats.d2h_bytes += 8;
+    MC_TRY(sync(m));
+    out->rounds = r + 1;
+    out->walks += walks_per_round;
+    const uint64_t v = m->h_scalar[0];
+    if (v == UINT64_MAX) break;  // nothing at or below the bound: stop
+    out->best_time = v >> 24;
+    out->best_walk = (uint64_t)r * walks_per_round + (v & 0xFFFFFFu);
+    if (r == 0) {
+      out->first_time = out->best_time;
+      out->first_trail_ms = ms_since();
+    }
+    if (out->best_time == 0) break;
+    bound = out->best_time - 1;
+  }
+  if (out->first_time == 0) {  // cannot happen: every run terminates
+    m->last_err = "swarm found no terminal";
+    return MC_ERR_CUDA;
+  }
+  // replay the best run: its states give the configuration and the trace
+  uint32_t* d_len = reinterpret_cast<uint32_t*>(m->d_tini);
+  MC_CUDA(m, mc::launch_replay_walk(m->params, seed, out->best_walk, (int)m->key_words, m->d_trace,
+                                    d_len, m->stream));
+  m->stats.other_launches += 1;
+  const size_t L2 = m->max_level + 2;
+  MC_CUDA(m, cudaMemcpyAsync(m->h_scalar, d_len, 4, cudaMemcpyDeviceToHost, m->stream));
+  MC_CUDA(m, cudaMemcpyAsync(m->h_trace, m->d_trace, 16 * L2, cudaMemcpyDeviceToHost, m->stream));
+  m->stats.d2h_bytes += 4 + 16 * L2;
+  MC_TRY(sync(m));
+  out->total_ms = ms_since();
+  const uint32_t len = (uint32_t)(m->h_scalar[0] & 0xFFFFFFFFu);
+  const uint64_t k2lo = m->h_trace[4], k2hi = m->h_trace[5];  // state 2: (i+1, j+1, 0)
+  const unsigned __int128 k2 = ((unsigned __int128)k2hi << 64) | k2lo;
+  out->wg_index = (uint32_t)((k2 >> m->wg_shift) & ((1u << m->wg_bits) - 1)) - 1;
+  out->ts_index = (uint32_t)((k2 >> m->ts_shift) & ((1u << m->ts_bits) - 1)) - 1;
+  out->wg = wg_value(m, out->wg_index);
+  out->ts = ts_value(m, out->ts_index);
+  out->key_words = m->key_words;
+  if (trace) {
+    mc::Ctrl c{};
+    c.trace_len = len;
+    MC_TRY(make_trace(m, c, trace));
+  }
   return MC_OK;
 }
 

@@ -358,15 +358,19 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t ctr) {
 }
 
 // One random run of the model (Section 4, Step 3: SPIN's simulation mode
-// gives T_ini).  Walk w draws splitmix64 outputs number (w << 32) + 0, 1, ...:
-// the WG index, the TS index, then per work-group the unit among the allowed
-// ones in index order.  Returns the terminal's model time.
+// gives T_ini; Section 5: a swarm is many such runs).  Walk w draws
+// splitmix64 outputs number (w << 32) + 0, 1, ...: the WG index, the TS index,
+// then per work-group the unit among the allowed ones in index order.
+// Returns the terminal's model time, or kNone when some clock passes `bound`
+// first (the run cannot end at or below it).  *cfg receives i * b + j.
 template <bool CG = false>
-__device__ inline uint64_t simulate_walk(const Params& p, uint64_t seed, uint64_t w) {
+__device__ inline uint64_t walk_time(const Params& p, uint64_t seed, uint64_t w, uint64_t bound,
+                                     uint32_t* cfg_out = nullptr) {
   uint64_t ctr = w << 32;
   const uint32_t i = (uint32_t)(splitmix64_at(seed, ctr++) % p.a);
   const uint32_t j = (uint32_t)(splitmix64_at(seed, ctr++) % p.b);
   const uint32_t cfg = i * p.b + j;
+  if (cfg_out) *cfg_out = cfg;
   const uint32_t N = ldp<CG>(p.N + cfg);
   const uint64_t cost = ldp<CG>(p.cost + cfg);
   uint64_t clk[kMaxP], t[kMaxP];
@@ -392,10 +396,16 @@ __device__ inline uint64_t simulate_walk(const Params& p, uint64_t seed, uint64_
       }
     }
     clk[c] += t[c];
+    if (clk[c] > bound) return kNone;
   }
   uint64_t mx = 0;
   for (uint32_t c = 0; c < p.P; ++c) mx = clk[c] > mx ? clk[c] : mx;
   return mx;
+}
+
+template <bool CG = false>
+__device__ inline uint64_t simulate_walk(const Params& p, uint64_t seed, uint64_t w) {
+  return walk_time<CG>(p, seed, w, kNone);
 }
 
 }  // namespace dev

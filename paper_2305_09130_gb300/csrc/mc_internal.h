@@ -101,6 +101,10 @@ cudaError_t launch_explore(int key_words, int tile, int rule, int grid, int thre
                            const ExploreArgs& args, cudaStream_t stream);
 cudaError_t launch_simulate(const Params& p, uint64_t seed, uint32_t walks, uint64_t* t_out,
                             cudaStream_t stream);
+cudaError_t launch_swarm(const Params& p, uint64_t seed, uint64_t w0, uint32_t walks, uint64_t bound,
+                         unsigned long long* best, int grid, cudaStream_t stream);
+cudaError_t launch_replay_walk(const Params& p, uint64_t seed, uint64_t w, int key_words,
+                               uint64_t* trace, uint32_t* len, cudaStream_t stream);
 
 }  // namespace mc
 

@@ -73,6 +73,13 @@ class McLayout(C.Structure):
                 ("device_bytes", C.c_uint64)]
 
 
+class McSwarmResult(C.Structure):
+    _fields_ = [("best_time", C.c_uint64), ("first_time", C.c_uint64), ("wg_index", C.c_uint32),
+                ("ts_index", C.c_uint32), ("wg", C.c_uint32), ("ts", C.c_uint32), ("rounds", C.c_uint32),
+                ("key_words", C.c_uint32), ("walks", C.c_uint64), ("best_walk", C.c_uint64),
+                ("first_trail_ms", C.c_double), ("total_ms", C.c_double)]
+
+
 class McStats(C.Structure):
     _fields_ = [("explore_launches", C.c_uint64), ("other_launches", C.c_uint64),
                 ("states", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
@@ -159,6 +166,8 @@ def load(build: bool = True):
             "mc_min_time": (C.c_int, [P, C.POINTER(McMinResult), C.POINTER(P)]),
             "mc_count_states": (C.c_int, [P, C.POINTER(C.c_uint64)]),
             "mc_simulate": (C.c_int, [P, C.c_uint64, C.c_uint32, C.POINTER(C.c_uint64)]),
+            "mc_swarm": (C.c_int, [P, C.c_uint64, C.c_uint32, C.c_uint32, C.POINTER(McSwarmResult),
+                                   C.POINTER(P)]),
             "mc_last_widths": (C.c_int, [P, C.POINTER(C.c_uint64), C.c_uint32, C.POINTER(C.c_uint32)]),
             "mc_get_stats": (C.c_int, [P, C.POINTER(McStats)]),
             "mc_batch_create": (C.c_int, [C.POINTER(McModelDesc), C.c_uint32, C.POINTER(McOptions),
@@ -368,6 +377,19 @@ def mc_simulate(model: Model, seed: int, walks: int = 1) -> int:
     model._check(load().mc_simulate(model.handle, int(seed) & NO_LIMIT, int(walks), C.byref(v)),
                  "mc_simulate")
     return v.value
+
+
+def mc_swarm(model: Model, seed: int, walks_per_round: int, max_rounds: int = 64,
+             trace: bool = True) -> dict:
+    r = McSwarmResult()
+    h = C.c_void_p()
+    model._check(load().mc_swarm(model.handle, int(seed) & NO_LIMIT, int(walks_per_round),
+                                 int(max_rounds), C.byref(r), C.byref(h) if trace else None), "mc_swarm")
+    out = {k: getattr(r, k) for k, _t in McSwarmResult._fields_}
+    out["i"], out["j"] = out.pop("wg_index"), out.pop("ts_index")
+    if trace:
+        out["trace"] = _take_trace(h)
+    return out
 
 
 def mc_last_widths(model: Model, cap: int = 1 << 16) -> list:

@@ -167,3 +167,18 @@ def test_simulation_draws_its_configuration(oracle):
         # many walks reach the optimum of a tiny model
         best = min(t for _i, _j, t in BF.schedules(spec))
         assert oracle.simulate(spec, seed, 4000) == best
+
+
+def test_swarm_runs_are_schedules_and_never_beat_tmin(oracle):
+    # every swarm run is a complete schedule of its configuration, so its
+    # time is one of the brute-force terminal times and never below T_min
+    for spec in tiny_models()[:8]:
+        sched = BF.schedules(spec)
+        best = min(t for _i, _j, t in sched)
+        for w in range(40):
+            t, i, j = oracle.walk(spec, 99, w)
+            assert t in {tt for ii, jj, tt in sched if (ii, jj) == (i, j)}
+        sw = oracle.swarm(spec, 99, 64, 30)
+        assert sw["best_time"] >= best and sw["first_time"] >= sw["best_time"]
+        # many runs per round reach the optimum of a tiny model
+        assert oracle.swarm(spec, 99, 4000, 30)["best_time"] == best
