@@ -61,7 +61,7 @@ extern "C" {
 #define MC_ERR_TIMEOUT (-5)    /* a device-side wait exceeded its limit     */
 #define MC_ERR_CUDA (-6)       /* CUDA runtime error (see mc_last_error)    */
 #define MC_ERR_OVERFLOW (-7)   /* key wider than 128 bits, clock >= 2^40,
-                                  a level wider than 2^32, or a, b > 4095   */
+                                  a level wider than 2^31, or a, b > 4095   */
 
 typedef enum { MC_FREE = 0, MC_GREEDY = 1 } mc_rule;
 

@@ -182,7 +182,8 @@ int size_buffers(mc_model* m) {
   const uint64_t n_init = 1 + (uint64_t)m->a + (uint64_t)m->a * m->b;
   m->log_cap = m->opt.log_capacity ? std::max(m->opt.log_capacity, n_init) : m->state_bound;
   if (m->log_cap == UINT64_MAX) return MC_ERR_NOMEM;
-  if (std::min(m->max_width, m->log_cap) >= (1ull << 32)) return MC_ERR_OVERFLOW;
+  // level widths travel in 31 bits of the device-wide barrier's word
+  if (std::min(m->max_width, m->log_cap) >= (1ull << 31)) return MC_ERR_OVERFLOW;
   const uint64_t per_bucket = m->key_words == 1 ? 4 : 2;
   uint64_t slots;
   if (m->opt.table_log2) {

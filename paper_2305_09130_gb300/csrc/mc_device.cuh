@@ -235,16 +235,19 @@ __device__ int visited_insert(K* table, uint64_t bucket_mask, uint32_t max_probe
 // two levels -- kBarGroups group counters, then a top counter, each in its
 // own 128-byte line -- so hundreds of blocks do not serialise on one address.
 // Counters only grow: the k-th barrier of a launch (k = 1, 2, ...) completes
-// when a group counter reaches k * members and the top counter k * groups,
-// and the last arriver publishes generation k with a release store.  Every
-// block passes the same sequence of barriers, so each tracks k itself.
-// Arrivals use acquire-release atomics after __syncthreads, waiters an
-// acquire load, so no separate fences are needed.  With a serial section,
-// the releasing block runs it (all its threads, after every other block has
-// arrived) before it publishes the generation.  Each wait is bounded by
-// timeout_ns of %globaltimer; on expiry the block records MC_ERR_TIMEOUT in
-// *err, raises the abort flag so the other waiters leave too, and returns
-// false.
+// when a group counter reaches k * members and the top counter k * groups.
+// The last arriver publishes a 64-bit word: generation k in the high half and
+// a 32-bit payload in the low half, with a release store; the waiters poll it
+// with acquire loads, so the payload reaches every block with the load that
+// ends its wait.  (A value every block needs after the barrier -- the next
+// level's width -- is read once by the releaser instead of by hundreds of
+// blocks at once from a line the step just updated with atomics, which
+// doubled the barrier's cost.)  Every block passes the same sequence of
+// barriers, so each tracks k itself.  Arrivals use acquire-release atomics
+// after __syncthreads.  With a serial section, the releasing block runs it
+// (all its threads) before publishing.  Each wait is bounded by timeout_ns of
+// %globaltimer; on expiry the block records MC_ERR_TIMEOUT in *err, raises
+// the abort flag so the other waiters leave too, and returns false.
 struct Barrier {
   uint32_t* lines;      // kBarGroups + 4 lines of 128 bytes, zeroed per launch
   uint32_t* err;        // error word of the launch
@@ -255,14 +258,29 @@ struct Barrier {
 struct NoSerial {
   __device__ void operator()() const {}
 };
+struct NoPayload {
+  __device__ uint32_t operator()() const { return 0; }
+};
 
-template <class Serial = NoSerial>
-__device__ bool grid_sync(const Barrier& B, uint32_t& epoch, const Serial& serial = Serial()) {
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Returns false on timeout/abort; *payload (if given) receives the releaser's
+// payload of this barrier.
+template <class Serial = NoSerial, class Payload = NoPayload>
+__device__ bool grid_sync(const Barrier& B, uint32_t& epoch, const Serial& serial = Serial(),
+                          const Payload& payload_fn = Payload(), uint32_t* payload = nullptr) {
   constexpr bool kSerial = !std::is_same<Serial, NoSerial>::value;
-  __shared__ uint32_t s_ok, s_release;
+  __shared__ uint32_t s_ok, s_release, s_payload;
   __syncthreads();
   const uint32_t target = ++epoch;
-  uint32_t* gen = B.lines + kBarGen * 32;
+  uint64_t* gen = reinterpret_cast<uint64_t*>(B.lines + kBarGen * 32);
   if (threadIdx.x == 0) {
     s_release = 0;
     const uint32_t groups = gridDim.x < kBarGroups ? gridDim.x : kBarGroups;
@@ -271,7 +289,7 @@ __device__ bool grid_sync(const Barrier& B, uint32_t& epoch, const Serial& seria
     if (atom_add_acq_rel(B.lines + g * 32, 1u) + 1 == members * target) {
       if (atom_add_acq_rel(B.lines + kBarTop * 32, 1u) + 1 == groups * target && B.extra == 0) {
         if (kSerial) s_release = 1;
-        else st_release_u32(gen, target);
+        else st_release_u64(gen, ((uint64_t)target << 32) | payload_fn());
       }
     }
   }
@@ -282,7 +300,7 @@ __device__ bool grid_sync(const Barrier& B, uint32_t& epoch, const Serial& seria
       __syncthreads();
       // the block's writes are ordered before thread 0's release by the
       // barrier above (release is cumulative)
-      if (threadIdx.x == 0) st_release_u32(gen, target);
+      if (threadIdx.x == 0) st_release_u64(gen, ((uint64_t)target << 32) | payload_fn());
     }
   }
   if (threadIdx.x == 0) {
@@ -290,7 +308,8 @@ __device__ bool grid_sync(const Barrier& B, uint32_t& epoch, const Serial& seria
     uint32_t* abort_flag = B.lines + kBarAbort * 32;
     const uint64_t t0 = globaltimer();
     uint32_t spins = 0;
-    while (ld_acquire_u32(gen) < target) {
+    uint64_t w;
+    while (((w = ld_acquire_u64(gen)) >> 32) < target) {
       if (ld_relaxed_u32(abort_flag)) { ok = 0; break; }
       if ((++spins & 15u) == 0 && globaltimer() - t0 > B.timeout_ns) {
         set_error(B.err, MC_ERR_TIMEOUT);
@@ -300,9 +319,11 @@ __device__ bool grid_sync(const Barrier& B, uint32_t& epoch, const Serial& seria
       }
       __nanosleep(32);
     }
+    s_payload = (uint32_t)w;
     s_ok = ok;
   }
   __syncthreads();
+  if (payload) *payload = s_payload;
   return s_ok != 0;
 }
 

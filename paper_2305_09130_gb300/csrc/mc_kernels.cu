@@ -72,7 +72,8 @@ __device__ __forceinline__ void copy_out(const ExploreArgs& A, const K* keys, co
 // before the current round's probes.
 template <class K, int TILE, int RULE>
 __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st, uint64_t T,
-                                             uint32_t L, uint64_t offL, uint64_t W, uint64_t offN) {
+                                             uint32_t L, uint64_t offL, uint64_t W, uint64_t offN,
+                                             const K (&first)[kDepth], bool have_first) {
   constexpr int S = KeyOps<K>::kSlots;
   constexpr uint32_t D = kDepth;
   __shared__ __align__(16) K probe[kThreads][D][S];
@@ -99,7 +100,7 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
 #pragma unroll
   for (uint32_t d = 0; d < D; ++d) {
     const uint64_t s = base + d * kTilesPerWarp + my;
-    key_next[d] = s < W ? KeyOps<K>::load(A.log_keys, offL + s) : (K)0;
+    key_next[d] = s < W ? (have_first ? first[d] : KeyOps<K>::load(A.log_keys, offL + s)) : (K)0;
   }
   for (; base < W; base += stride) {
     K succ[D];
@@ -267,21 +268,51 @@ __global__ void __launch_bounds__(kThreads) explore_kernel(const ExploreArgs A) 
   uint32_t last = 2;
   uint64_t off_last = 1 + (uint64_t)p.a;
   uint64_t W = (uint64_t)p.a * p.b;
+  // this thread's first keys of a level sit at fixed positions from the
+  // level's start, so after each barrier they are loaded together with the
+  // level's record rather than after it (positions past the level's end
+  // read stale log entries that are never used; they stay inside the log)
+  const uint64_t first_pos = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32 *
+                             (32 / TILE) * kDepth + (threadIdx.x & 31u) / TILE;
+  K first[kDepth];
+  bool have_first = false;
   for (;;) {
     const uint32_t L = last;
     if (L >= p.max_level) break;  // the deepest level holds only terminals
     const uint64_t offN = off_last + W;
     if (gtid == 0) A.off[L + 1] = offN;
-    expand_level<K, TILE, RULE>(A, stage, T, L, off_last, W, offN);
-    if (!grid_sync(bar, epoch)) return;
-    if (ld_relaxed_u32(&ctrl->err)) break;
-    uint64_t Wn, Bn;  // width and violating minimum of level L+1, one 16-byte load
-    ld_relaxed_v2u64(A.levels + 2 * (L + 1), Wn, Bn);
+    expand_level<K, TILE, RULE>(A, stage, T, L, off_last, W, offN, first, have_first);
+    // the releaser reads level L+1's record and the error word once and
+    // publishes (width << 1) | stop, stop = error or early exit
+    const uint64_t* rec = A.levels + 2 * (L + 1);
+    const uint32_t* errp = &ctrl->err;
+    const uint32_t early = A.early_exit;
+    auto level_word = [rec, errp, early]() -> uint32_t {
+      uint64_t w, b;
+      ld_relaxed_v2u64(rec, w, b);
+      const bool stop = ld_relaxed_u32(errp) != 0 || (early && b != kNone);
+      return ((uint32_t)w << 1) | (stop ? 1u : 0u);
+    };
+    uint32_t word = 0;
+    if (!grid_sync(bar, epoch, NoSerial(), level_word, &word)) return;
+#pragma unroll
+    for (uint32_t d = 0; d < kDepth; ++d) {
+      const uint64_t at = offN + first_pos + d * (32 / TILE);
+      first[d] = KeyOps<K>::load(A.log_keys, at < A.log_cap ? at : A.log_cap - 1);
+    }
+    have_first = true;
+    const uint64_t Wn = word >> 1;
+    if (word & 1u) {  // an error, or level L+1 holds a violating terminal
+      if (ld_relaxed_u32(&ctrl->err)) break;
+      last = L + 1;
+      off_last = offN;
+      W = Wn;
+      break;
+    }
     if (Wn == 0) break;
     last = L + 1;
     off_last = offN;
     W = Wn;
-    if (A.early_exit && Bn != kNone) break;
   }
   if (ld_relaxed_u32(&ctrl->err)) return;
 
