@@ -38,6 +38,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+from paper_2305_09130_gb300 import pe_workloads as PW  # noqa: E402
 from paper_2305_09130_gb300 import workloads as W  # noqa: E402
 
 WORKLOADS = {
@@ -441,6 +442,143 @@ def run_swarm(args):
     return 0
 
 
+PE_WORKLOADS = {
+    # name: (spec factory, description, expected (t_min, wg, ts) from the oracle,
+    #        T of the oracle's bounded sample)
+    "pe_abstract": (lambda: PW.pe_abstract(16, P=4, np_=4, gmt=1),
+                    "PE-level model of the abstract kernel (Listings 2, 9): size 16, 4 units x 4 PEs, "
+                    "GMT 1, WG and TS in {2, 4, 8}; every PE mark, barrier arrival, release, dispatch "
+                    "and clock tick interleaved; 37,040,200 reachable states over 1,295 BFS levels",
+                    None, 6),
+    "pe_minimum": (lambda: PW.pe_minimum(64, P=4, np_=4, gmt=2),
+                   "PE-level model of the Minimum kernel (Listings 11-16): size 64, 4 units x 4 PEs, "
+                   "GMT 2, WG and TS in 2^1..2^5; 3,178,678 reachable states over 3,859 BFS levels",
+                   None, 40),
+}
+
+
+def run_pe(args):
+    """The processing-element level model: one step = one mc_pe_min_time (a
+    full exploration for T_min, the certificate check at T_min - 1 and the
+    counterexample check at T_min), or one mc_pe_count_states."""
+    import torch
+
+    from paper_2305_09130_gb300 import mc
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist_init(world, True)
+    spec = PE_WORKLOADS[args.workload][0]()
+    desc = PE_WORKLOADS[args.workload][1]
+    opts = mc.mc_options_default(timing=1)
+    stream = torch.cuda.Stream(device)
+    model = mc.mc_pe_model_create(spec, opts, stream=stream.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+
+    def flush_l2(k):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+
+    if args.query == "count":
+        def query(m):
+            return {"states": mc.mc_pe_count_states(m), "t_min": None, "wg": None, "ts": None, "checks": 1}
+    else:
+        def query(m):
+            return mc.mc_pe_min_time(m, trace=True)
+    ref = None
+    for w in range(args.warmup):  # the first warm-up also grows the buffers to fit
+        flush_l2(w)
+        ref = query(model)
+    lay = mc.mc_pe_model_layout(model)
+    mc.mc_pe_reset_stats(model)
+    torch.cuda.synchronize()
+    barrier(device)
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush_l2(k)
+        ev[k][0].record(stream)
+        r = query(model)
+        ev[k][1].record(stream)
+        assert r["t_min"] == ref["t_min"]
+    torch.cuda.synchronize()
+    barrier(device)
+    clocks = sampler.stop()
+    st = mc.mc_pe_get_stats(model)
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    dev_ms_max = reduce_scalar(dev_ms, "max", device)
+    states_all = reduce_scalar(st["states"], "sum", device)
+    value = states_all / (dev_ms_max / 1000.0)
+    # per unique state: one 32-byte bucket probe per generated successor, one
+    # 32-byte slot write-back, the 16-byte key written to and read back from
+    # the frontier log, the 4-byte parent index
+    probes_per_state = st["probes"] / max(st["states"], 1)
+    bps = 32 * probes_per_state + 32 + 2 * 16 + 4
+    launches = st["explore_launches"]
+    achieved = bps * st["states"] / (st["explore_ms"] / 1000.0) / 1e9
+    peak, peak_kind = measured_hbm_peak()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "bytes_per_state": bps, "probes_per_state": probes_per_state,
+                "algorithmic_bytes_per_launch": bps * st["states"] / max(launches, 1),
+                "avg_launch_ms": st["explore_ms"] / max(launches, 1),
+                "levels_per_launch": st["device_steps"] / max(launches, 1),
+                "kernel": f"pe_explore_kernel<tile {lay['tile']}>",
+                "peak_source": f"{peak_kind} HBM copy bandwidth"}
+    # end to end through the public C-ABI from host buffers
+    e2e_s, h2d, d2h = [], 0, 0
+    big = {"log_capacity": lay["log_capacity"], "table_log2": lay["table_slots"].bit_length() - 1}
+    for k in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m2 = mc.mc_pe_model_create(spec, mc.mc_options_default(**big), stream=stream.cuda_stream)
+        r2 = query(m2)
+        s2 = mc.mc_pe_get_stats(m2)
+        mc.mc_pe_model_destroy(m2)
+        e2e_s.append(time.perf_counter() - t0)
+        h2d += s2["h2d_bytes"]
+        d2h += s2["d2h_bytes"]
+        assert r2["t_min"] == ref["t_min"]
+    e2e_total = reduce_scalar(sum(e2e_s), "max", device)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u128",
+        "data": "synthetic (model description from the kernels' listings; no dataset)",
+        "config": {"workload": desc,
+                   "query": "mc_pe_min_time (full pass, check(T_min-1), check(T_min)), prune=1 early_exit=1"
+                   if args.query == "min_time" else "mc_pe_count_states",
+                   "l2": "flushed between steps (256 MiB write, untimed)",
+                   "states_per_step": st["states"] / args.steps},
+        "time_to_optimal_config_ms": dev_ms_max / args.steps,
+        "result": {"t_min": ref["t_min"], "wg": ref["wg"], "ts": ref["ts"]},
+        "roofline": roofline,
+        "e2e": {"value": states_all / e2e_total, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
+                "d2h_bytes_per_step": d2h // args.steps, "ms_per_step": 1000.0 * e2e_total / args.steps},
+        "gpu_launches": st["explore_launches"],
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.build()
+        T = PE_WORKLOADS[args.workload][3]
+        t0 = time.perf_counter()
+        rs = O.pe_check(spec, T, prune=True, early_exit=False)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": rs["states"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"oracle BFS (std::unordered_set) over check(T={T}) of the same "
+                                          f"model with pruning: {rs['states']} states in {dt:.2f} s, "
+                                          f"single thread"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    mc.mc_pe_model_destroy(model)
+    return 0
+
+
 def run_c4(args):
     """Batched queries: 256 uneven models (G = 2^U{6..12}, P in {2,4,8}, WG
     2^0..2^8, TS 2^0..2^4, cost U{1..16}, speeds U{1..3}, GREEDY), half
@@ -660,7 +798,8 @@ def main(argv=None):
     p.add_argument("--c5-seconds", type=float, default=6.0, help="c5 arrivals per rate span")
     p.add_argument("--c5-queries", type=int, default=10000, help="c5 queries per rate at most")
     p.add_argument("--c5-sample", type=int, default=48, help="c5 single-query service sample")
-    p.add_argument("--workload", choices=sorted(WORKLOADS) + ["c4", "c5"], default="c2_star",
+    p.add_argument("--workload", choices=sorted(WORKLOADS) + ["c4", "c5"] + sorted(PE_WORKLOADS),
+                   default="c2_star",
                    help="profiling aid; the benchmark line is c2_star")
     p.add_argument("--query", choices=["min_time", "count", "swarm"], default="min_time")
     p.add_argument("--swarm-walks", type=int, default=1 << 20, help="random runs per swarm round")
@@ -675,6 +814,8 @@ def main(argv=None):
         return run_swarm(args)
     if args.workload == "c5":
         return run_c5(args)
+    if args.workload in PE_WORKLOADS:
+        return run_pe(args)
     return run_ours(args)
 
 

@@ -180,6 +180,8 @@ typedef struct {
                                 kernels (only with mc_options.timing = 1)    */
   uint64_t device_steps;     /* device-wide barrier steps: BFS levels of the
                                 passes, or lockstep steps of a batch launch  */
+  uint64_t probes;           /* successors generated, each one visited-set
+                                probe (PE-level model, mc_pe.h, only)        */
 } mc_stats;
 
 typedef void* (*mc_alloc_fn)(size_t bytes, void* stream, void* ctx);

@@ -13,7 +13,9 @@ with the host C++ compiler and exposes:
 * ``min_time(spec, search, ...)`` -- Step 3 (search for T_min) and Step 4
   (the configuration of the last counterexample);
 * ``walk(spec, seed, w)`` and ``swarm(spec, seed, walks, rounds)`` -- the
-  random runs and the swarm search of Section 5.
+  random runs and the swarm search of Section 5;
+* ``pe_check``, ``pe_count``, ``pe_min_time`` -- the same queries on the
+  processing-element level model (``oracle_pe.cpp``).
 """
 from __future__ import annotations
 
@@ -23,7 +25,7 @@ import subprocess
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "oracle.cpp")
+SRCS = [os.path.join(HERE, "oracle.cpp"), os.path.join(HERE, "oracle_pe.cpp")]
 LIB = os.path.join(HERE, "liboracle.so")
 NO_LIMIT = (1 << 64) - 1
 SEARCH = {"single": 0, "lower": 1, "bisect": 2}
@@ -34,9 +36,10 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/liboracle.so (host code only)."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+    stale = not os.path.exists(LIB) or any(os.path.getmtime(LIB) < os.path.getmtime(s) for s in SRCS)
+    if force or stale:
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", SRC, "-o", tmp])
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", *SRCS, "-o", tmp])
         os.replace(tmp, LIB)
     return LIB
 
@@ -59,6 +62,24 @@ class OrMin(C.Structure):
                 ("level", C.c_uint32), ("n", C.c_uint32 * 16)]
 
 
+class OrPeModel(C.Structure):
+    _fields_ = [("a", C.c_uint32), ("b", C.c_uint32), ("P", C.c_uint32),
+                ("N", C.POINTER(C.c_uint32)), ("pes", C.POINTER(C.c_uint32)),
+                ("prog_off", C.POINTER(C.c_uint32)), ("seg_ticks", C.POINTER(C.c_uint32)),
+                ("seg_pes", C.POINTER(C.c_uint32))]
+
+
+class OrPeCheck(C.Structure):
+    _fields_ = [("holds", C.c_uint32), ("levels", C.c_uint32), ("states", C.c_uint64),
+                ("cex_time", C.c_uint64), ("cex_i", C.c_uint32), ("cex_j", C.c_uint32),
+                ("cex_level", C.c_uint32), ("pad", C.c_uint32)]
+
+
+class OrPeMin(C.Structure):
+    _fields_ = [("t_min", C.c_uint64), ("states", C.c_uint64), ("checks", C.c_uint32),
+                ("i", C.c_uint32), ("j", C.c_uint32), ("level", C.c_uint32)]
+
+
 def lib():
     global _lib
     with _lock:
@@ -74,8 +95,13 @@ def lib():
                                           C.c_uint64, C.c_uint32, C.POINTER(OrMin)]
             L.oracle_walk.argtypes = [C.POINTER(OrModel), C.c_uint64, C.c_uint64, C.POINTER(C.c_uint64),
                                       C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+            L.oracle_pe_check.argtypes = [C.POINTER(OrPeModel), C.c_uint64, C.c_int, C.c_int,
+                                          C.POINTER(OrPeCheck), C.POINTER(C.c_uint64), C.c_uint32]
+            L.oracle_pe_count.argtypes = [C.POINTER(OrPeModel), C.POINTER(C.c_uint64)]
+            L.oracle_pe_min_time.argtypes = [C.POINTER(OrPeModel), C.c_int, C.c_int, C.c_int,
+                                             C.POINTER(OrPeMin)]
             for f in (L.oracle_check, L.oracle_count, L.oracle_simulate, L.oracle_min_time,
-                      L.oracle_walk):
+                      L.oracle_walk, L.oracle_pe_check, L.oracle_pe_count, L.oracle_pe_min_time):
                 f.restype = C.c_int
             _lib = L
     return _lib
@@ -164,3 +190,45 @@ def min_time(spec, search: str = "single", prune: bool = True, early_exit: bool 
         raise ValueError(f"oracle_min_time failed ({rc})")
     return {"t_min": r.t_min, "t_ini": r.t_ini, "states": r.states, "checks": r.checks,
             "i": r.i, "j": r.j, "level": r.level, "n": list(r.n[: spec.P])}
+
+
+# ---------------------------------------------------------------- PE-level model
+def _pe_model(spec):
+    arr = lambda xs: (C.c_uint32 * max(1, len(xs)))(*xs)
+    off, ticks, pes = spec.flat()
+    keep = (arr(spec.n_workgroups), arr(spec.pes), arr(off), arr(ticks), arr(pes))
+    return OrPeModel(spec.a, spec.b, spec.P, *keep), keep
+
+
+def pe_check(spec, T: int, prune: bool = True, early_exit: bool = True, widths: int = 0) -> dict:
+    """G(FIN -> time > T) on the processing-element level model."""
+    m, _keep = _pe_model(spec)
+    r = OrPeCheck()
+    w = (C.c_uint64 * max(widths, 1))()
+    rc = lib().oracle_pe_check(C.byref(m), T & NO_LIMIT, int(prune), int(early_exit), C.byref(r),
+                               w if widths else None, widths)
+    if rc != 0:
+        raise ValueError(f"oracle_pe_check failed ({rc})")
+    out = {"holds": bool(r.holds), "states": r.states, "levels": r.levels}
+    if not r.holds:
+        out.update(cex_time=r.cex_time, cex_i=r.cex_i, cex_j=r.cex_j, cex_level=r.cex_level)
+    if widths:
+        out["widths"] = list(w[: r.levels])
+    return out
+
+
+def pe_count(spec) -> int:
+    m, _keep = _pe_model(spec)
+    out = C.c_uint64()
+    if lib().oracle_pe_count(C.byref(m), C.byref(out)) != 0:
+        raise ValueError("oracle_pe_count failed")
+    return out.value
+
+
+def pe_min_time(spec, prune: bool = True, early_exit: bool = True, refine: bool = True) -> dict:
+    m, _keep = _pe_model(spec)
+    r = OrPeMin()
+    if lib().oracle_pe_min_time(C.byref(m), int(prune), int(early_exit), int(refine), C.byref(r)) != 0:
+        raise ValueError("oracle_pe_min_time failed")
+    return {"t_min": r.t_min, "states": r.states, "checks": r.checks, "i": r.i, "j": r.j,
+            "level": r.level}

@@ -1,6 +1,6 @@
 """Build of the CUDA library libmcgpu.so (sm_103a only), in-tree.
 
-The two translation units are compiled in parallel with nvcc and linked into
+The translation units are compiled in parallel with nvcc and linked into
 ``paper_2305_09130_gb300/_lib/libmcgpu.so`` with the CUDA runtime linked
 statically.  Rebuilds only when a source or header is newer than the library.
 """
@@ -17,8 +17,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libmcgpu.so")
-SOURCES = ["mc_api.cu", "mc_kernels.cu", "mc_batch.cu", "mc_noalloc.cu", "mc_roofline.cu"]
-HEADERS = [os.path.join(CSRC, "mc_internal.h"), os.path.join(CSRC, "mc_device.cuh"), os.path.join(INCLUDE, "mc.h")]
+SOURCES = ["mc_api.cu", "mc_kernels.cu", "mc_batch.cu", "mc_noalloc.cu", "mc_roofline.cu", "mc_pe.cu"]
+HEADERS = [os.path.join(CSRC, "mc_internal.h"), os.path.join(CSRC, "mc_device.cuh"),
+           os.path.join(INCLUDE, "mc.h"), os.path.join(INCLUDE, "mc_pe.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

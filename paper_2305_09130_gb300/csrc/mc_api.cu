@@ -57,11 +57,6 @@ uint64_t mul_sat(uint64_t a, uint64_t b) {
 
 }  // namespace
 
-struct mc_trace {
-  uint32_t words = 1;
-  std::vector<uint64_t> keys;
-};
-
 struct mc_model {
   // description
   uint32_t a = 0, b = 0, P = 0, rule = 0;

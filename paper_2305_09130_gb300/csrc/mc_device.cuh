@@ -189,15 +189,15 @@ __device__ __forceinline__ void load_bucket<u128>(const u128* b, u128 (&v)[2]) {
   v[1] = ((u128)y.y << 64) | y.x;
 }
 
-// Insert `key` (sum of n fields = lvl) into the visited set, starting at
-// bucket `bkt`, whose 32 bytes are already in `first` (shared memory) unless
-// `first` is null.
+// Insert `key` (BFS level lvl, as level_of reports it for any key) into the
+// visited set, starting at bucket `bkt`, whose 32 bytes are already in
+// `first` (shared memory) unless `first` is null.
 // Returns 1 if this thread inserted it, 0 if it was already there, -1 when
 // the probe limit was reached.  A slot is free when it holds 0 or a key of an
 // earlier level; the first free slot of the probe sequence is taken.
-template <class K>
-__device__ int visited_insert(K* table, uint64_t bucket_mask, uint32_t max_probes, K key,
-                              uint32_t lvl, const Params& p, uint64_t bkt, const K* first) {
+template <class K, class LevelOf>
+__device__ int visited_insert_lv(K* table, uint64_t bucket_mask, uint32_t max_probes, K key,
+                                 uint32_t lvl, const LevelOf& level_of, uint64_t bkt, const K* first) {
   constexpr int S = KeyOps<K>::kSlots;
   for (uint32_t probe = 0; probe < max_probes; ++probe) {
     K* slot = table + bkt * S;
@@ -219,7 +219,7 @@ __device__ int visited_insert(K* table, uint64_t bucket_mask, uint32_t max_probe
       // level), so two CAS attempts settle it; the bound is defensive
       for (int tries = 0; tries < 3; ++tries) {
         if (cur == key) return 0;
-        if (cur != (K)0 && sum_n(cur, p) >= lvl) break;  // taken this level
+        if (cur != (K)0 && level_of(cur) >= lvl) break;  // taken this level
         K old = slot_cas(slot + s, cur, key);
         if (old == cur) return 1;
         cur = old;
@@ -228,6 +228,15 @@ __device__ int visited_insert(K* table, uint64_t bucket_mask, uint32_t max_probe
     bkt = (bkt + 1) & bucket_mask;
   }
   return -1;
+}
+
+// The cost-table model's keys: the level is 2 + sum(n), so `lvl` here is the
+// sum of the n fields.
+template <class K>
+__device__ __forceinline__ int visited_insert(K* table, uint64_t bucket_mask, uint32_t max_probes, K key,
+                                              uint32_t lvl, const Params& p, uint64_t bkt, const K* first) {
+  return visited_insert_lv<K>(table, bucket_mask, max_probes, key, lvl,
+                              [&p](K k) { return sum_n(k, p); }, bkt, first);
 }
 
 // ------------------------------------------------------------------ device-wide barrier

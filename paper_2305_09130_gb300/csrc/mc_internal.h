@@ -3,7 +3,16 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
+
+// A counterexample or witness path returned through the C-ABI (mc_trace is
+// opaque in mc.h): `words` u64 per state, states s0 .. the last one.
+struct mc_trace {
+  uint32_t words = 1;
+  std::vector<uint64_t> keys;
+};
 
 namespace mc {
 
@@ -66,6 +75,7 @@ struct Ctrl {
   uint64_t widx;          // witness index inside its level
   uint64_t wpack;         // packed (time, i, j) of the first violating level
   uint64_t T;             // threshold the pass used
+  uint64_t probes;        // successors generated (PE-level explorer only)
 };
 
 // Everything one exploration pass needs.

@@ -83,7 +83,7 @@ class McSwarmResult(C.Structure):
 class McStats(C.Structure):
     _fields_ = [("explore_launches", C.c_uint64), ("other_launches", C.c_uint64),
                 ("states", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
-                ("explore_ms", C.c_double), ("device_steps", C.c_uint64)]
+                ("explore_ms", C.c_double), ("device_steps", C.c_uint64), ("probes", C.c_uint64)]
 
 
 class McQuery(C.Structure):
@@ -110,6 +110,25 @@ class McServerResult(C.Structure):
     _fields_ = [("ticket", C.c_uint64), ("result", McBatchResult), ("submit_s", C.c_double),
                 ("admit_s", C.c_double), ("done_s", C.c_double)]
 
+class McPeModelDesc(C.Structure):
+    _fields_ = [("n_wg", C.c_uint32), ("n_ts", C.c_uint32), ("P", C.c_uint32),
+                ("wg_values", C.POINTER(C.c_uint32)), ("ts_values", C.POINTER(C.c_uint32)),
+                ("n_workgroups", C.POINTER(C.c_uint32)), ("pes", C.POINTER(C.c_uint32)),
+                ("prog_off", C.POINTER(C.c_uint32)), ("seg_ticks", C.POINTER(C.c_uint32)),
+                ("seg_pes", C.POINTER(C.c_uint32))]
+
+
+class McPeLayout(C.Structure):
+    _fields_ = [("used_bits", C.c_uint32), ("P", C.c_uint32), ("wg_bits", C.c_uint32),
+                ("ts_bits", C.c_uint32), ("level_bits", C.c_uint32), ("unit_bits", C.c_uint32),
+                ("n_bits", C.c_uint32), ("pc_bits", C.c_uint32), ("mask_bits", C.c_uint32),
+                ("tile", C.c_uint32), ("wg_shift", C.c_uint32), ("ts_shift", C.c_uint32),
+                ("level_shift", C.c_uint32), ("max_level", C.c_uint32),
+                ("unit_shift", C.c_uint32 * 8), ("max_steps", C.c_uint64),
+                ("table_slots", C.c_uint64), ("log_capacity", C.c_uint64),
+                ("device_bytes", C.c_uint64)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -123,7 +142,10 @@ def _destroy_live_models():
     # free device buffers while PyTorch (the allocator behind them) is alive
     for m in list(_live):
         try:
-            mc_model_destroy(m)
+            if isinstance(m, PeModel):
+                mc_pe_model_destroy(m)
+            else:
+                mc_model_destroy(m)
         except Exception:
             pass
 
@@ -194,6 +216,19 @@ def load(build: bool = True):
             "mc_check_noalloc": (C.c_int, [C.POINTER(McModelDesc), C.c_uint64, C.c_uint32, C.c_uint32,
                                            P, C.POINTER(McCheckResult)]),
             "mc_reset_stats": (C.c_int, [P]),
+            "mc_pe_model_create": (C.c_int, [C.POINTER(McPeModelDesc), C.POINTER(McOptions),
+                                             C.POINTER(P)]),
+            "mc_pe_model_destroy": (None, [P]),
+            "mc_pe_set_stream": (C.c_int, [P, P]),
+            "mc_pe_model_layout": (C.c_int, [P, C.POINTER(McPeLayout)]),
+            "mc_pe_check": (C.c_int, [P, C.c_uint64, C.POINTER(McCheckResult), C.POINTER(P)]),
+            "mc_pe_min_time": (C.c_int, [P, C.POINTER(McMinResult), C.POINTER(P)]),
+            "mc_pe_count_states": (C.c_int, [P, C.POINTER(C.c_uint64)]),
+            "mc_pe_last_widths": (C.c_int, [P, C.POINTER(C.c_uint64), C.c_uint32,
+                                            C.POINTER(C.c_uint32)]),
+            "mc_pe_get_stats": (C.c_int, [P, C.POINTER(McStats)]),
+            "mc_pe_reset_stats": (C.c_int, [P]),
+            "mc_pe_last_error": (C.c_char_p, [P]),
             "mc_trace_length": (C.c_int, [P]),
             "mc_trace_key_words": (C.c_uint32, [P]),
             "mc_trace_states": (C.POINTER(C.c_uint64), [P]),
@@ -625,3 +660,122 @@ def decode_key(layout: dict, key: int):
     mask = (1 << layout["n_bits"]) - 1
     n = tuple((key >> s) & mask for s in layout["n_shift"])
     return i, j, n
+
+
+# ---------------------------------------------------------------- PE-level model
+class PeModel(Model):
+    """Owns an ``mc_pe_model*``; destroyed with ``mc_pe_model_destroy``."""
+
+    def __del__(self):
+        try:
+            mc_pe_model_destroy(self)
+        except Exception:
+            pass
+
+    def _check(self, rc: int, where: str):
+        if rc != MC_OK:
+            detail = ""
+            if self.handle:
+                detail = load(build=False).mc_pe_last_error(self.handle).decode()
+            raise MCError(rc, where, detail)
+
+
+def mc_pe_model_create(spec, options: Optional[McOptions] = None, stream=None) -> PeModel:
+    """Create a PE-level model from a ``pe_workloads.PeSpec``."""
+    L = load()
+    off, ticks, pes = spec.flat()
+    arrs = (_u32(spec.wg_values), _u32(spec.ts_values), _u32(spec.n_workgroups), _u32(spec.pes),
+            _u32(off), _u32(ticks), _u32(pes))
+    d = McPeModelDesc(spec.a, spec.b, spec.P, *arrs)
+    h = C.c_void_p()
+    rc = L.mc_pe_model_create(C.byref(d), C.byref(options) if options is not None else None, C.byref(h))
+    if rc != MC_OK:
+        raise MCError(rc, "mc_pe_model_create")
+    m = PeModel(h.value, spec)
+    if stream is None:
+        import torch
+
+        if torch.cuda.is_available():
+            stream = torch.cuda.current_stream().cuda_stream
+    if stream is not None:
+        m._check(L.mc_pe_set_stream(m.handle, C.c_void_p(int(stream))), "mc_pe_set_stream")
+    return m
+
+
+def mc_pe_model_destroy(model: PeModel):
+    if model.handle and model.handle.value:
+        load(build=False).mc_pe_model_destroy(model.handle)
+        model.handle = C.c_void_p()
+    _live.discard(model)
+
+
+def mc_pe_model_layout(model: PeModel) -> dict:
+    lay = McPeLayout()
+    model._check(load().mc_pe_model_layout(model.handle, C.byref(lay)), "mc_pe_model_layout")
+    out = {k: getattr(lay, k) for k, _t in McPeLayout._fields_ if k != "unit_shift"}
+    out["unit_shift"] = list(lay.unit_shift[: lay.P])
+    return out
+
+
+def mc_pe_check(model: PeModel, T: int, trace: bool = True) -> dict:
+    r = McCheckResult()
+    h = C.c_void_p()
+    rc = load().mc_pe_check(model.handle, int(T) & NO_LIMIT, C.byref(r), C.byref(h) if trace else None)
+    model._check(rc, "mc_pe_check")
+    out = {"holds": bool(r.holds), "states": r.states, "levels": r.levels}
+    if not r.holds:
+        out.update(cex_time=r.cex_time, cex_i=r.cex_wg_index, cex_j=r.cex_ts_index, cex_wg=r.cex_wg,
+                   cex_ts=r.cex_ts, cex_level=r.cex_level, cex_key=r.cex_key[0] | (r.cex_key[1] << 64))
+        if trace:
+            out["trace"] = _take_trace(h)
+    return out
+
+
+def mc_pe_min_time(model: PeModel, trace: bool = True) -> dict:
+    r = McMinResult()
+    h = C.c_void_p()
+    rc = load().mc_pe_min_time(model.handle, C.byref(r), C.byref(h) if trace else None)
+    model._check(rc, "mc_pe_min_time")
+    out = {"t_min": r.t_min, "i": r.wg_index, "j": r.ts_index, "wg": r.wg, "ts": r.ts,
+           "states": r.states, "checks": r.checks, "level": r.level,
+           "witness_key": r.witness_key[0] | (r.witness_key[1] << 64)}
+    if trace:
+        out["trace"] = _take_trace(h)
+    return out
+
+
+def mc_pe_count_states(model: PeModel) -> int:
+    v = C.c_uint64()
+    model._check(load().mc_pe_count_states(model.handle, C.byref(v)), "mc_pe_count_states")
+    return v.value
+
+
+def mc_pe_last_widths(model: PeModel, cap: int = 1 << 16) -> list:
+    buf = (C.c_uint64 * cap)()
+    n = C.c_uint32()
+    model._check(load().mc_pe_last_widths(model.handle, buf, cap, C.byref(n)), "mc_pe_last_widths")
+    return list(buf[: min(n.value, cap)])
+
+
+def mc_pe_get_stats(model: PeModel) -> dict:
+    st = McStats()
+    model._check(load().mc_pe_get_stats(model.handle, C.byref(st)), "mc_pe_get_stats")
+    return {k: getattr(st, k) for k, _t in McStats._fields_}
+
+
+def mc_pe_reset_stats(model: PeModel):
+    model._check(load().mc_pe_reset_stats(model.handle), "mc_pe_reset_stats")
+
+
+def decode_pe_key(layout: dict, key: int) -> dict:
+    """Fields of a packed PE-level state: i, j (1-based, 0 = not selected),
+    level, and per unit (n, busy, pc, mask)."""
+    f = lambda shift, bits: (key >> shift) & ((1 << bits) - 1)
+    units = []
+    M, pcb = layout["mask_bits"], layout["pc_bits"]
+    for shift in layout["unit_shift"]:
+        u = f(shift, layout["unit_bits"])
+        units.append((u >> (M + pcb + 1), (u >> (M + pcb)) & 1, (u >> M) & ((1 << pcb) - 1),
+                      u & ((1 << M) - 1)))
+    return {"i": f(layout["wg_shift"], layout["wg_bits"]), "j": f(layout["ts_shift"], layout["ts_bits"]),
+            "level": f(layout["level_shift"], layout["level_bits"]), "units": units}

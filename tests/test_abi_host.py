@@ -1,6 +1,6 @@
 """Host-side checks of the C-ABI library (no GPU needed).
 
-The library must load and export every function include/mc.h declares.
+The library must load and export every function include/*.h declares.
 Model creation is host-only (validation, key layout, closed-form sizing), so
 it is exercised here; any query without a CUDA device must fail loudly.
 """
@@ -17,10 +17,15 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "mc.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\**\s*(mc_[a-z_]+)\s*\(", src, flags=re.M)
-    return sorted(set(names))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(inc, h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\**\s*(mc_[a-z_]+)\s*\(", src, flags=re.M))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -30,7 +35,7 @@ def lib():
 
 def test_every_declared_symbol_is_exported(lib):
     names = declared_functions()
-    assert len(names) >= 19
+    assert len(names) >= 19 and "mc_pe_check" in names and "mc_check_noalloc" in names
     for n in names:
         assert hasattr(lib, n), n
 
@@ -109,4 +114,65 @@ def test_queries_fail_loudly_without_a_gpu(lib):
     m = mc.mc_model_create(W.c1(), allocator=None)
     with pytest.raises(mc.MCError) as e:
         mc.mc_count_states(m)
+    assert e.value.code == mc.MC_ERR_CUDA
+
+
+# ---------------------------------------------------------------- PE-level model
+def pe_layout(spec, **kw):
+    return mc.mc_pe_model_layout(mc.mc_pe_model_create(spec, mc.mc_options_default(**kw), stream=0))
+
+
+def test_pe_layout(lib):
+    from paper_2305_09130_gb300 import pe_workloads as PW
+
+    lay = pe_layout(PW.table1_row1())
+    # a = b = 2 (WG, TS in {2, 4}); N <= 4; longest program: TS = 2, four
+    # iterations of (3 ticks, barrier, 3 ticks, barrier) and 2 ticks = 34 steps
+    assert (lay["wg_bits"], lay["ts_bits"], lay["n_bits"], lay["mask_bits"]) == (2, 2, 3, 4)
+    assert lay["max_steps"] == 34 and lay["pc_bits"] == 6 and lay["unit_bits"] == 3 + 1 + 6 + 4
+    assert lay["tile"] == 8 and lay["unit_shift"] == [0]
+    # deepest FIN: WG=2, TS=2: 4 work-groups of 26 ticks on one unit, 2 PEs
+    assert lay["max_level"] == 2 + 4 * (1 + 2 * 26 + 2 * 8 + 8) + 4 * 26
+    big = pe_layout(PW.pe_abstract(16, P=4))
+    assert big["tile"] == 32 and big["unit_shift"] == [3 * big["unit_bits"], 2 * big["unit_bits"],
+                                                        big["unit_bits"], 0]
+    assert big["used_bits"] <= 128 and big["level_shift"] == 4 * big["unit_bits"]
+
+
+def test_pe_invalid_descriptions(lib):
+    from paper_2305_09130_gb300 import pe_workloads as PW
+
+    ok = PW.table1_row1()
+
+    def variant(**kw):
+        d = dict(name="bad", P=ok.P, wg_values=ok.wg_values, ts_values=ok.ts_values,
+                 n_workgroups=ok.n_workgroups, pes=ok.pes, programs=ok.programs)
+        d.update(kw)
+        return PW.PeSpec(**d)
+
+    cases = [
+        (variant(P=0), mc.MC_ERR_INVAL),
+        (variant(P=9), mc.MC_ERR_INVAL),
+        (variant(n_workgroups=[0, 1, 1, 1]), mc.MC_ERR_INVAL),
+        (variant(pes=[9, 1, 1, 1]), mc.MC_ERR_INVAL),
+        (variant(programs=[[(1, 3)]] + ok.programs[1:], pes=[2, 2, 4, 4]), mc.MC_ERR_INVAL),
+        (variant(programs=[[]] + ok.programs[1:]), mc.MC_ERR_INVAL),
+        (variant(programs=[[(70000, 1)]] + ok.programs[1:]), mc.MC_ERR_INVAL),
+        (variant(P=8, pes=[4, 4, 4, 4]), mc.MC_ERR_INVAL),  # 8 * 4 + 8 + 1 lanes > 32
+    ]
+    for spec, code in cases:
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_pe_model_create(spec, stream=0)
+        assert e.value.code == code, spec
+
+
+def test_pe_queries_fail_loudly_without_a_gpu(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2305_09130_gb300 import pe_workloads as PW
+
+    m = mc.mc_pe_model_create(PW.table1_row1(), stream=0)
+    with pytest.raises(mc.MCError) as e:
+        mc.mc_pe_count_states(m)
     assert e.value.code == mc.MC_ERR_CUDA
