@@ -119,7 +119,11 @@ typedef struct {
                                    MC_ERR_TIMEOUT.  Keep 0.                 */
   uint32_t timing;              /* 1: time every exploration kernel with CUDA
                                    events on the model's stream (mc_get_stats) */
-  uint32_t reserved[6];
+  uint32_t lanes_per_state;     /* PE-level model (mc_pe.h) only: lanes of the
+                                   warp tile that expands one state: 4 or 8
+                                   (up to 3 successors per lane), 16 (up to
+                                   2) or 32 (1); 0 = the smallest that fits */
+  uint32_t reserved[5];
 } mc_options;
 
 /* Result of mc_check (Section 4, Step 2: Phi = G(FIN -> time > T)). */

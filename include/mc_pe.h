@@ -55,7 +55,7 @@ typedef struct mc_pe_model mc_pe_model;
 /* PE-level model description.  Per-configuration arrays are row-major
  * [i][j]; the segments of configuration k are seg_*[prog_off[k] ..
  * prog_off[k+1]-1].  Limits: a, b 1..255, P 1..8, NWE 1..8 with
- * P*max(NWE) + P + 1 <= 32 (the successor lanes of one warp), at least one
+ * P*max(NWE) + P + 1 <= 32 (the successors of one state), at least one
  * segment per program, seg_pes 1..NWE of its configuration, seg_ticks <=
  * 65535, the packed state within 128 bits. */
 typedef struct {
@@ -81,7 +81,7 @@ typedef struct {
 typedef struct {
   uint32_t used_bits, P;
   uint32_t wg_bits, ts_bits, level_bits, unit_bits;
-  uint32_t n_bits, pc_bits, mask_bits, tile;
+  uint32_t n_bits, pc_bits, mask_bits, tile;  /* tile: lanes expanding one state */
   uint32_t wg_shift, ts_shift, level_shift, max_level;
   uint32_t unit_shift[8];
   uint64_t max_steps;    /* longest program in steps                        */

@@ -1,7 +1,9 @@
 """Autotuner for the explorer's launch and table parameters, with a JSON cache.
 
 The knobs are the runtime options of ``mc_options``: threads per block,
-blocks per SM (the persistent grid) and the visited-set load factor.  A
+blocks per SM (the persistent grid) and the visited-set load factor; for the
+processing-element level model, the lanes that expand one state (a quarter,
+half or whole warp) and the grid.  A
 candidate is timed on the real query through the C-ABI (CUDA events recorded
 by the library around its kernels), every candidate must return the same
 answer as the default options (a tuning run never trades correctness), and
@@ -58,7 +60,7 @@ def signature(layout: dict, spec, query: str, batch: int = 1) -> str:
 
 def candidates(space: Optional[Dict[str, Sequence[int]]] = None) -> List[dict]:
     space = space or DEFAULT_SPACE
-    names = [k for k in KNOBS if k in space]
+    names = [k for k in KNOBS if k in space] + sorted(k for k in space if k not in KNOBS)
     return [dict(zip(names, vals)) for vals in itertools.product(*(space[k] for k in names))]
 
 
@@ -143,6 +145,51 @@ def tune_batch(specs, queries, space=None, reps: int = 2, cache: Optional[dict] 
         ms = mc.mc_batch_get_stats(b)["explore_ms"] - t0
         mc.mc_batch_destroy(b)
         return ms, [(r["status"], r["time"], r["states"], r["key"]) for r in res]
+
+    out = tune(measure, space, reps)
+    cache[sig] = {"options": out["options"], "ms": out["ms"], "when": time.time()}
+    save_cache(cache, path)
+    return {"signature": sig, **out}
+
+
+PE_SPACE = {
+    "lanes_per_state": [8, 16, 32],
+    "blocks_per_sm": [0, 1, 2],
+}
+
+
+def tune_pe(spec, query: str = "min_time", space=None, reps: int = 2, cache: Optional[dict] = None,
+            path: Optional[str] = None) -> dict:
+    """Tune the PE-level model's query ("count" or "min_time"): lanes per
+    state (the warp tile that expands one state) and the persistent grid.
+    Candidates whose tile cannot hold the model's successors are skipped."""
+    from . import mc
+
+    mc.load()
+    space = dict(space or PE_SPACE)
+    probe = mc.mc_pe_model_create(spec, stream=0)
+    lay = mc.mc_pe_model_layout(probe)
+    lanes = spec.P * lay["mask_bits"] + spec.P + 1
+    fits = lambda t: -(-lanes // t) <= (1 if t >= 32 else 2 if t == 16 else 3)
+    space["lanes_per_state"] = [t for t in space.get("lanes_per_state", [0]) if t == 0 or fits(t)]
+    sig = (f"pe|{query}|P{spec.P}|m{lay['mask_bits']}|a{spec.a}|b{spec.b}|L{lay['max_level']}"
+           f"|k{lay['used_bits']}")
+    cache = load_cache(path) if cache is None else cache
+    grown = {}
+
+    def measure(c):
+        m = mc.mc_pe_model_create(spec, mc.mc_options_default(timing=1, **c, **grown))
+        run = {"count": lambda: mc.mc_pe_count_states(m),
+               "min_time": lambda: mc.mc_pe_min_time(m, trace=False)}[query]
+        run()
+        if not grown:  # later candidates start at the grown buffer sizes
+            L = mc.mc_pe_model_layout(m)
+            grown.update(log_capacity=L["log_capacity"], table_log2=L["table_slots"].bit_length() - 1)
+        mc.mc_pe_reset_stats(m)
+        ans = run()
+        ms = mc.mc_pe_get_stats(m)["explore_ms"]
+        mc.mc_pe_model_destroy(m)
+        return ms, ans
 
     out = tune(measure, space, reps)
     cache[sig] = {"options": out["options"], "ms": out["ms"], "when": time.time()}

@@ -33,6 +33,9 @@ using namespace mc::dev;
 constexpr uint32_t kPeMaxUnits = 8;
 constexpr uint32_t kPeMaxPes = 8;
 constexpr uint32_t kBarrierBit = 1u << 16;  // step info: barrier flag | participating PEs
+// successors per lane a tile of `tile` lanes can propose: one for a whole
+// warp, two for half a warp, three for smaller tiles
+__host__ __device__ constexpr uint32_t slots_for(uint32_t tile) { return tile >= 32 ? 1 : tile == 16 ? 2 : 3; }
 
 struct PeParams {
   uint32_t a, b, P, M;          // M: mask bits per unit (largest NWE)
@@ -69,6 +72,8 @@ struct PeArgs {
   uint64_t* tmin_out;
   uint32_t* bar;
   uint64_t timeout_ns;
+  uint32_t slots;    // successors per lane: ceil(lanes / TILE) <= slots_for(TILE)
+  uint32_t pad;
 };
 
 struct Unit {
@@ -171,12 +176,70 @@ __device__ __forceinline__ void pe_copy_out(const PeArgs& A, const u128* keys, c
   }
 }
 
-// Expand level L (states offL .. offL+W-1 of the log) into level L+1.
-// *probes (lane 0 of each warp) accumulates the successors the warp generated.
+// Successor number `slot` of a decoded state (the lane roles above).  Sets
+// ok when the transition is enabled, with the successor's key (level field
+// not yet raised), its model time and whether it is FIN.
+__device__ __forceinline__ void propose(const PeParams& p, const Decoded& d, u128 key, uint32_t slot,
+                                        bool& ok, u128& succ, uint64_t& t, bool& term) {
+  const uint32_t PM = p.P * p.M;
+  ok = false;
+  term = false;
+  succ = key;
+  t = d.time;
+  if (slot < PM) {  // PE e of unit c marks the current step
+    const uint32_t c = slot / p.M, e = slot % p.M;
+    const Unit& u = d.u[c];
+    if (u.busy && e < (d.info[c] & 0xFFFFu) && !((u.mask >> e) & 1u)) {
+      ok = true;
+      succ = key ^ ((u128)(1u << e) << ((p.P - 1 - c) * p.unit_bits));
+    }
+  } else if (slot < PM + p.P) {  // unit c: barrier release, or dispatch
+    const uint32_t c = slot - PM;
+    const Unit u = d.u[c];
+    Unit v = u;
+    if (u.busy) {
+      const uint32_t pes = d.info[c] & 0xFFFFu;
+      if ((d.info[c] & kBarrierBit) && u.mask == (1u << pes) - 1u) {
+        ok = true;
+        v = step_on(u, d.S);
+        bool others_idle = true;
+        for (uint32_t x = 0; x < p.P; ++x)
+          if (x != c && d.u[x].busy) others_idle = false;
+        term = d.left == 0 && !v.busy && others_idle;
+      }
+    } else if (d.left > 0) {
+      ok = true;
+      v.n = u.n + 1;
+      v.busy = 1;
+      v.pc = 0;
+      v.mask = 0;
+    }
+    if (ok) succ = key ^ ((u128)(pack(u, p) ^ pack(v, p)) << ((p.P - 1 - c) * p.unit_bits));
+  } else if (slot == PM + p.P && d.any_busy && d.ready && !(d.left > 0 && d.any_idle)) {
+    ok = true;  // the clock ticks; every busy unit moves on
+    bool all_idle = true;
+    for (uint32_t c = 0; c < p.P; ++c) {
+      const Unit u = d.u[c];
+      if (!u.busy) continue;
+      const Unit v = step_on(u, d.S);
+      if (v.busy) all_idle = false;
+      succ ^= (u128)(pack(u, p) ^ pack(v, p)) << ((p.P - 1 - c) * p.unit_bits);
+    }
+    t = d.time + 1;
+    term = d.left == 0 && all_idle;
+  }
+}
+
+// Expand level L (states offL .. offL+W-1 of the log) into level L+1.  A tile
+// of TILE lanes owns one state; lane l proposes successors l, l + TILE, ...
+// (A.slots of them), fetches the first bucket of each with cp.async so that
+// all of its probes are in flight together, then inserts them in turn.
+// `probes` (lane 0 of each warp) accumulates the successors the warp made.
 template <int TILE>
 __device__ void pe_expand_level(const PeArgs& A, PeStage<TILE>& st, uint64_t T, uint32_t L,
                                 uint64_t offL, uint64_t W, uint64_t offN, uint64_t& probes) {
-  __shared__ __align__(16) u128 probe[kThreads][2];
+  constexpr uint32_t SL = slots_for(TILE);
+  __shared__ __align__(16) u128 probe[kThreads][SL][2];
   const PeParams& p = A.p;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
@@ -184,7 +247,7 @@ __device__ void pe_expand_level(const PeArgs& A, PeStage<TILE>& st, uint64_t T, 
   constexpr uint32_t kTilesPerWarp = 32 / TILE;
   const uint64_t warp_gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t stride = (((uint64_t)gridDim.x * blockDim.x) >> 5) * kTilesPerWarp;
-  const uint32_t PM = p.P * p.M;
+  const uint32_t slots = A.slots;
   u128* table = reinterpret_cast<u128*>(A.table);
   u128* wkeys = st.keys[warp];
   uint32_t* wpar = st.par[warp];
@@ -194,108 +257,81 @@ __device__ void pe_expand_level(const PeArgs& A, PeStage<TILE>& st, uint64_t T, 
   const u128 lvl_one = (u128)1 << p.lvl_shift;
   auto level_of = [&p](u128 k) { return pe_level(k, p); };
 
-  for (uint64_t base = warp_gid * kTilesPerWarp; base < W; base += stride) {
+  uint64_t base = warp_gid * kTilesPerWarp;
+  u128 key_next = base + lane / TILE < W ? KeyOps<u128>::load(A.log_keys, offL + base + lane / TILE) : (u128)0;
+  for (; base < W; base += stride) {
     const uint64_t s = base + lane / TILE;
     const bool valid = s < W;
-    bool ok = false, term = false;
-    u128 succ = 0;
-    uint64_t succ_time = 0;
+    const u128 key = key_next;
+    if (s + stride < W) key_next = KeyOps<u128>::load(A.log_keys, offL + s + stride);
+    bool ok[SL], term[SL];
+    u128 succ[SL];
+    uint64_t st_time[SL], bkt[SL];
     uint32_t ci = 0, cj = 0;
+    Decoded d;
     if (valid) {
-      const u128 key = KeyOps<u128>::load(A.log_keys, offL + s);
-      Decoded d;
       decode(key, p, d);
       ci = d.i;
       cj = d.j;
-      succ_time = d.time;
-      if (l < PM) {  // PE e of unit c marks the current step
-        const uint32_t c = l / p.M, e = l % p.M;
-        const Unit& u = d.u[c];
-        if (u.busy && e < (d.info[c] & 0xFFFFu) && !((u.mask >> e) & 1u)) {
-          ok = true;
-          succ = key ^ ((u128)(1u << e) << ((p.P - 1 - c) * p.unit_bits));
-        }
-      } else if (l < PM + p.P) {  // unit c: barrier release, or dispatch
-        const uint32_t c = l - PM;
-        const Unit u = d.u[c];
-        Unit v = u;
-        if (u.busy) {
-          const uint32_t pes = d.info[c] & 0xFFFFu;
-          if ((d.info[c] & kBarrierBit) && u.mask == (1u << pes) - 1u) {
-            ok = true;
-            v = step_on(u, d.S);
-            bool others_idle = true;
-            for (uint32_t x = 0; x < p.P; ++x)
-              if (x != c && d.u[x].busy) others_idle = false;
-            term = d.left == 0 && !v.busy && others_idle;
-          }
-        } else if (d.left > 0) {
-          ok = true;
-          v.n = u.n + 1;
-          v.busy = 1;
-          v.pc = 0;
-          v.mask = 0;
-        }
-        if (ok) succ = key ^ ((u128)(pack(u, p) ^ pack(v, p)) << ((p.P - 1 - c) * p.unit_bits));
-      } else if (l == PM + p.P && d.any_busy && d.ready && !(d.left > 0 && d.any_idle)) {
-        ok = true;  // the clock ticks; every busy unit moves on
-        succ = key;
-        bool all_idle = true;
-        for (uint32_t c = 0; c < p.P; ++c) {
-          const Unit u = d.u[c];
-          if (!u.busy) continue;
-          const Unit v = step_on(u, d.S);
-          if (v.busy) all_idle = false;
-          succ ^= (u128)(pack(u, p) ^ pack(v, p)) << ((p.P - 1 - c) * p.unit_bits);
-        }
-        succ_time = d.time + 1;
-        term = d.left == 0 && all_idle;
-      }
-      if (ok && A.prune && succ_time > T) ok = false;
-      succ += lvl_one;
     }
-    probes += __popc(__ballot_sync(0xffffffffu, ok));
-    uint64_t bkt = 0;
-    if (ok) {
-      bkt = key_hash(succ) & A.bucket_mask;
-      const u128* src = table + bkt * 2;
-      cp_async16(&probe[threadIdx.x][0], src);
-      cp_async16(&probe[threadIdx.x][1], src + 1);
+#pragma unroll
+    for (uint32_t k = 0; k < SL; ++k) {
+      ok[k] = false;
+      term[k] = false;
+      bkt[k] = 0;
+      st_time[k] = 0;
+      succ[k] = 0;
+      if (valid && k < slots) {
+        propose(p, d, key, l + k * TILE, ok[k], succ[k], st_time[k], term[k]);
+        if (ok[k] && A.prune && st_time[k] > T) ok[k] = false;
+        succ[k] += lvl_one;
+      }
+      probes += __popc(__ballot_sync(0xffffffffu, ok[k]));
+      if (ok[k]) {
+        bkt[k] = key_hash(succ[k]) & A.bucket_mask;
+        const u128* src = table + bkt[k] * 2;
+        cp_async16(&probe[threadIdx.x][k][0], src);
+        cp_async16(&probe[threadIdx.x][k][1], src + 1);
+      }
     }
     cp_async_wait_all();
-    int won = 0;
-    if (ok) {
-      const int rc = visited_insert_lv<u128>(table, A.bucket_mask, A.max_probes, succ, L + 1, level_of,
-                                             bkt, probe[threadIdx.x]);
-      if (rc < 0) set_error(A.ctrl, MC_ERR_TABLE_FULL);
-      won = rc > 0;
-    }
-    const uint32_t m = __ballot_sync(0xffffffffu, won);
-    if (m) {
-      if (won) {
-        const uint32_t at = fill + __popc(m & ((1u << lane) - 1u));
-        wkeys[at] = succ;
-        wpar[at] = (uint32_t)s;
+#pragma unroll
+    for (uint32_t k = 0; k < SL; ++k) {
+      int won = 0;
+      if (ok[k]) {
+        const int rc = visited_insert_lv<u128>(table, A.bucket_mask, A.max_probes, succ[k], L + 1, level_of,
+                                               bkt[k], probe[threadIdx.x][k]);
+        if (rc < 0) set_error(A.ctrl, MC_ERR_TABLE_FULL);
+        won = rc > 0;
       }
-      fill += __popc(m);
-      uint64_t pk = (won && term && succ_time <= T) ? pack_tij(succ_time, ci, cj) : kNone;
-      pk = warp_min(pk);
-      if (lane == 0 && pk < cached_best) {
-        cached_best = ld_relaxed_u64(lvl_next + 1);
-        if (pk < cached_best) {
-          atomicMin(reinterpret_cast<unsigned long long*>(lvl_next + 1), (unsigned long long)pk);
-          cached_best = pk;
+      const uint32_t m = __ballot_sync(0xffffffffu, won);
+      if (m) {
+        if (won) {
+          const uint32_t at = fill + __popc(m & ((1u << lane) - 1u));
+          wkeys[at] = succ[k];
+          wpar[at] = (uint32_t)s;
+        }
+        fill += __popc(m);
+        uint64_t pk = (won && term[k] && st_time[k] <= T) ? pack_tij(st_time[k], ci, cj) : kNone;
+        pk = warp_min(pk);
+        if (lane == 0 && pk < cached_best) {
+          cached_best = ld_relaxed_u64(lvl_next + 1);
+          if (pk < cached_best) {
+            atomicMin(reinterpret_cast<unsigned long long*>(lvl_next + 1), (unsigned long long)pk);
+            cached_best = pk;
+          }
         }
       }
-    }
-    if (fill > kWarpCap - 32) {
-      __syncwarp();
-      unsigned long long b = 0;
-      if (lane == 0) b = atomicAdd(reinterpret_cast<unsigned long long*>(lvl_next), (unsigned long long)fill);
-      b = __shfl_sync(0xffffffffu, b, 0);
-      pe_copy_out(A, wkeys, wpar, fill, offN + b, lane);
-      __syncwarp();
-      fill = 0;
+      // each slot adds at most 32 winners to the warp's buffer
+      if (fill > kWarpCap - 32) {
+        __syncwarp();
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(reinterpret_cast<unsigned long long*>(lvl_next), (unsigned long long)fill);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        pe_copy_out(A, wkeys, wpar, fill, offN + b, lane);
+        __syncwarp();
+        fill = 0;
+      }
     }
   }
   if (lane == 0) st.fill[warp] = fill;
@@ -700,6 +736,8 @@ int pe_enqueue(mc_pe_model* m, uint64_t T, const uint64_t* T_src, int64_t delta,
   A.tmin_out = tmin_out;
   A.bar = m->d_bar;
   A.timeout_ns = m->opt.barrier_timeout_ns ? m->opt.barrier_timeout_ns : 60ull * 1000000000ull;
+  const uint32_t lanes = m->P * m->M + m->P + 1;
+  A.slots = (lanes + m->lay.tile - 1) / m->lay.tile;
   static_assert(sizeof(Ctrl) <= 256, "control block header");
   PE_CUDA(m, cudaMemsetAsync(m->d_ctrl, 0, 256 + mc::kBarBytes, m->stream));
   if (m->opt.timing) PE_CUDA(m, cudaEventRecord(m->ev[2 * slot], m->stream));
@@ -884,8 +922,16 @@ int mc_pe_model_create(const mc_pe_model_desc* d, const mc_options* opt, mc_pe_m
   for (uint32_t c = 0; c < m->P; ++c) L.unit_shift[c] = (m->P - 1 - c) * L.unit_bits;
   L.max_level = (uint32_t)lvl_max;
   L.max_steps = s_max;
-  L.tile = 4;
-  while (L.tile < m->P * M + m->P + 1) L.tile <<= 1;
+  const uint32_t lanes = m->P * M + m->P + 1;
+  if (o.lanes_per_state) {
+    const uint32_t t = o.lanes_per_state;
+    if ((t != 4 && t != 8 && t != 16 && t != 32) || (lanes + t - 1) / t > mc::slots_for(t))
+      return fail(MC_ERR_INVAL);
+    L.tile = t;
+  } else {
+    L.tile = 4;
+    while ((lanes + L.tile - 1) / L.tile > mc::slots_for(L.tile)) L.tile <<= 1;
+  }
   mc::PeParams& p = m->params;
   p.a = m->a;
   p.b = m->b;

@@ -45,7 +45,8 @@ class McOptions(C.Structure):
                 ("threads_per_block", C.c_uint32), ("blocks_per_sm", C.c_uint32),
                 ("max_probes", C.c_uint32), ("log_capacity", C.c_uint64),
                 ("barrier_timeout_ns", C.c_uint64), ("debug_barrier_extra", C.c_uint32),
-                ("timing", C.c_uint32), ("reserved", C.c_uint32 * 6)]
+                ("timing", C.c_uint32), ("lanes_per_state", C.c_uint32),
+                ("reserved", C.c_uint32 * 5)]
 
 
 class McCheckResult(C.Structure):

@@ -130,11 +130,13 @@ def test_pe_layout(lib):
     # iterations of (3 ticks, barrier, 3 ticks, barrier) and 2 ticks = 34 steps
     assert (lay["wg_bits"], lay["ts_bits"], lay["n_bits"], lay["mask_bits"]) == (2, 2, 3, 4)
     assert lay["max_steps"] == 34 and lay["pc_bits"] == 6 and lay["unit_bits"] == 3 + 1 + 6 + 4
-    assert lay["tile"] == 8 and lay["unit_shift"] == [0]
+    # 4 + 1 + 1 successors: a tile of 4 lanes, two successors per lane
+    assert lay["tile"] == 4 and lay["unit_shift"] == [0]
     # deepest FIN: WG=2, TS=2: 4 work-groups of 26 ticks on one unit, 2 PEs
     assert lay["max_level"] == 2 + 4 * (1 + 2 * 26 + 2 * 8 + 8) + 4 * 26
     big = pe_layout(PW.pe_abstract(16, P=4))
-    assert big["tile"] == 32 and big["unit_shift"] == [3 * big["unit_bits"], 2 * big["unit_bits"],
+    # 16 + 4 + 1 successors: a tile of 8 lanes, three successors per lane
+    assert big["tile"] == 8 and big["unit_shift"] == [3 * big["unit_bits"], 2 * big["unit_bits"],
                                                         big["unit_bits"], 0]
     assert big["used_bits"] <= 128 and big["level_shift"] == 4 * big["unit_bits"]
 
@@ -164,6 +166,18 @@ def test_pe_invalid_descriptions(lib):
         with pytest.raises(mc.MCError) as e:
             mc.mc_pe_model_create(spec, stream=0)
         assert e.value.code == code, spec
+    # a tile too narrow for the model's successors, or not a tile width
+    cases = [
+        (PW.pe_abstract(16, P=4), 4), (PW.pe_abstract(16, P=4), 12), (PW.table1_row1(), 2),
+    ]
+    for spec, tile in cases:
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_pe_model_create(spec, mc.mc_options_default(lanes_per_state=tile), stream=0)
+        assert e.value.code == mc.MC_ERR_INVAL
+    for tile in (8, 16, 32):
+        lay = mc.mc_pe_model_layout(mc.mc_pe_model_create(PW.pe_abstract(16, P=4),
+                                                          mc.mc_options_default(lanes_per_state=tile), stream=0))
+        assert lay["tile"] == tile
 
 
 def test_pe_queries_fail_loudly_without_a_gpu(lib):

@@ -58,3 +58,8 @@ def test_tuned_options_reproduce_results(mc, tmp_path):
     m = mc.mc_model_create(spec, opts)
     assert mc.mc_min_time(m, trace=False)["t_min"] == 80
     assert json.load(open(path))[out["signature"]]["options"] == out["options"]
+
+
+def test_candidates_cover_knobs_outside_the_default_space():
+    c = AT.candidates({"lanes_per_state": [8, 16], "blocks_per_sm": [0, 1]})
+    assert sorted((x["lanes_per_state"], x["blocks_per_sm"]) for x in c) == [(8, 0), (8, 1), (16, 0), (16, 1)]

@@ -134,3 +134,25 @@ def test_pe_explicit_small_log_reports_frontier(mc):
     assert e.value.code == mc.MC_ERR_FRONTIER
     m2 = mc.mc_pe_model_create(spec)
     assert mc.mc_pe_count_states(m2) == 24301
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_pe_every_tile_width_agrees(mc, oracle, tile):
+    for spec in (PW.pe_abstract(8, P=2), PW.pe_minimum(32, P=4, np_=4, gmt=2), tiny_pe_models()[3]):
+        lanes = spec.P * max(spec.pes) + spec.P + 1
+        if -(-lanes // tile) > (1 if tile == 32 else 2 if tile == 16 else 3):
+            continue
+        m = mc.mc_pe_model_create(spec, mc.mc_options_default(lanes_per_state=tile))
+        assert mc.mc_pe_model_layout(m)["tile"] == tile
+        assert mc.mc_pe_count_states(m) == oracle.pe_count(spec)
+        r = mc.mc_pe_min_time(m)
+        e = oracle.pe_min_time(spec)
+        assert {k: r[k] for k in e} == e
+
+
+def test_pe_autotune_keeps_the_answer(mc, tmp_path):
+    from paper_2305_09130_gb300 import autotune as AT
+    spec = PW.pe_abstract(8, P=2)
+    out = AT.tune_pe(spec, space={"lanes_per_state": [8, 16, 32], "blocks_per_sm": [0, 2]}, reps=1,
+                     path=str(tmp_path / "cache.json"))
+    assert out["options"]["lanes_per_state"] in (8, 16, 32) and len(out["timings"]) >= 4
