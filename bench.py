@@ -443,17 +443,17 @@ def run_swarm(args):
 
 
 PE_WORKLOADS = {
-    # name: (spec factory, description, expected (t_min, wg, ts) from the oracle,
-    #        T of the oracle's bounded sample)
+    # name: (spec factory, description, expected (t_min, wg, ts) from the oracle
+    #        (tests/golden/pe_oracle_expected.json), T of the oracle's bounded sample)
     "pe_abstract": (lambda: PW.pe_abstract(16, P=4, np_=4, gmt=1),
-                    "PE-level model of the abstract kernel (Listings 2, 9): size 16, 4 units x 4 PEs, "
+                    "PE-level model of the abstract kernel (Listings 2, 8): size 16, 4 units x 4 PEs, "
                     "GMT 1, WG and TS in {2, 4, 8}; every PE mark, barrier arrival, release, dispatch "
                     "and clock tick interleaved; 37,040,200 reachable states over 1,295 BFS levels",
-                    None, 6),
+                    (38, 4, 8), 6),
     "pe_minimum": (lambda: PW.pe_minimum(64, P=4, np_=4, gmt=2),
-                   "PE-level model of the Minimum kernel (Listings 11-16): size 64, 4 units x 4 PEs, "
+                   "PE-level model of the Minimum kernel (Listings 10-15): size 64, 4 units x 4 PEs, "
                    "GMT 2, WG and TS in 2^1..2^5; 3,178,678 reachable states over 3,859 BFS levels",
-                   None, 40),
+                   (17, 4, 4), 17),
 }
 
 
@@ -473,7 +473,15 @@ def run_pe(args):
     dist_init(world, True)
     spec = PE_WORKLOADS[args.workload][0]()
     desc = PE_WORKLOADS[args.workload][1]
-    opts = mc.mc_options_default(timing=1)
+    # the tile that expands one state and the grid, from the autotuner (every
+    # candidate must give the same answer); outside the timed region
+    from paper_2305_09130_gb300 import autotune as AT
+    fd, cache = tempfile.mkstemp(suffix=".json")
+    os.close(fd)
+    tuned = AT.tune_pe(spec, "count" if args.query == "count" else "min_time",
+                       space={"lanes_per_state": [8, 16, 32], "blocks_per_sm": [0, 2, 3]}, reps=1, path=cache)
+    os.unlink(cache)
+    opts = mc.mc_options_default(timing=1, **tuned["options"])
     stream = torch.cuda.Stream(device)
     model = mc.mc_pe_model_create(spec, opts, stream=stream.cuda_stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
@@ -493,6 +501,9 @@ def run_pe(args):
         flush_l2(w)
         ref = query(model)
     lay = mc.mc_pe_model_layout(model)
+    expect = PE_WORKLOADS[args.workload][2]
+    if args.query == "min_time" and (ref["t_min"], ref["wg"], ref["ts"]) != expect:
+        raise SystemExit(f"wrong result {ref} != {expect}")
     mc.mc_pe_reset_stats(model)
     torch.cuda.synchronize()
     barrier(device)
@@ -531,7 +542,8 @@ def run_pe(args):
                 "peak_source": f"{peak_kind} HBM copy bandwidth"}
     # end to end through the public C-ABI from host buffers
     e2e_s, h2d, d2h = [], 0, 0
-    big = {"log_capacity": lay["log_capacity"], "table_log2": lay["table_slots"].bit_length() - 1}
+    big = dict(tuned["options"], log_capacity=lay["log_capacity"],
+               table_log2=lay["table_slots"].bit_length() - 1)
     for k in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -553,6 +565,7 @@ def run_pe(args):
                    "query": "mc_pe_min_time (full pass, check(T_min-1), check(T_min)), prune=1 early_exit=1"
                    if args.query == "min_time" else "mc_pe_count_states",
                    "l2": "flushed between steps (256 MiB write, untimed)",
+                   "autotuned": tuned["options"],
                    "states_per_step": st["states"] / args.steps},
         "time_to_optimal_config_ms": dev_ms_max / args.steps,
         "result": {"t_min": ref["t_min"], "wg": ref["wg"], "ts": ref["ts"]},

@@ -3,8 +3,8 @@
  * as mc.h (check, min-time, count) on a finer transition system that keeps
  * the processes the cost-table model folds into one number per work-group.
  *
- * Model (Section 4, Step 1, Listings 4-10; the Minimum model of Section 6,
- * Listings 11-16, is an instance with another program).  Each of P compute
+ * Model (Section 4, Step 1, Listings 3-9; the Minimum model of Section 6,
+ * Listings 10-15, is an instance with another program).  Each of P compute
  * units (`unit`) runs the work-group it was given as NWE processing elements
  * (`pex`) with one local `barrier`; the `clock` counts global time.  Per
  * configuration (WG index i, TS index j) the caller gives N_ij work-groups,
@@ -16,16 +16,16 @@
  *   select    s0 -> (i) -> (i, j, every unit idle): `select` in `main`
  *             (Listing 3);
  *   dispatch  a unit that is idle while work-groups are left takes the next
- *             one and starts its program (the device's `go`, Listing 6);
+ *             one and starts its program (the device's `go`, Listing 5);
  *   mark      a participating PE of a busy unit that has not yet marked the
  *             current step marks it: at a tick step it reports NRP_work++
- *             and waits for the clock (`long_work`, Listing 9), at a barrier
- *             step it sends `done` to the barrier (Listing 8);
+ *             and waits for the clock (`long_work`, Listing 8), at a barrier
+ *             step it sends `done` to the barrier (Listing 7);
  *   release   a unit at a barrier step whose participants have all marked
  *             moves on (the barrier's `go`);
  *   tick      when every busy unit is at a tick step with all participants
  *             marked and no unit is idle while work-groups are left, time
- *             grows by one (Listing 10) and every busy unit moves on;
+ *             grows by one (Listing 9) and every busy unit moves on;
  *   FIN       no work-group left and every unit idle (Listing 4); the model
  *             time is the number of ticks.
  *

@@ -9,7 +9,7 @@
 // obvious.
 //
 // The model keeps the processes the cost-table model folds away (Section 4,
-// Step 1, Listings 4-10): every compute unit runs a work-group as NWE
+// Step 1, Listings 3-9): every compute unit runs a work-group as NWE
 // processing elements `pex`, each of which reports every tick of its
 // `long_work` to the `clock`, and the unit's `barrier` waits for all of them.
 // Per configuration (i, j) the input gives N work-groups and one program:
@@ -19,16 +19,16 @@
 //   * s0 -> (WG i) -> (WG i, TS j, every unit idle, N work-groups left):
 //     the selects of `main` (Listing 3).
 //   * dispatch: a unit that is idle while work-groups are left takes the next
-//     one (the device's `dev_u ! go` reaches any waiting unit, Listing 6); it
+//     one (the device's `dev_u ! go` reaches any waiting unit, Listing 5); it
 //     starts at program step 0 with no PE marked.
 //   * mark: a participating PE of a busy unit that has not marked itself in
 //     the current step does so -- in a tick step it reports NRP_work++
-//     (Listing 9), at a barrier it sends `done` to the barrier (Listing 8).
+//     (Listing 8), at a barrier it sends `done` to the barrier (Listing 7).
 //   * release: a busy unit at a barrier step with every participant marked
 //     moves to its next step (the barrier's `b_pex ! go`).
 //   * tick: when every busy unit is at a tick step with every participant
 //     marked, and no unit is idle while work-groups are left, `time` grows by
-//     one (Listing 10) and every busy unit moves to its next step.
+//     one (Listing 9) and every busy unit moves to its next step.
 //   * a unit whose program ends becomes idle; FIN holds when no work-group is
 //     left and every unit is idle, and the model time is the tick count.
 // Property (Step 2): G(FIN -> time > T).

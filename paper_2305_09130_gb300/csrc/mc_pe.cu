@@ -7,7 +7,7 @@
 // handles one state: lane (c, e) for c < P, e < M proposes "PE e of unit c
 // marks", lane P*M + c proposes "unit c passes its barrier" or "unit c takes
 // the next work-group", and lane P*M + P proposes the clock tick (Listings
-// 6-10).  The rest of a pass is the level-synchronous BFS of the cost-table
+// 5-9).  The rest of a pass is the level-synchronous BFS of the cost-table
 // explorer (mc_kernels.cu): lock-free visited set with CAS on 128-bit keys,
 // frontier log with parent indices, a device-wide barrier per level, the
 // minimum packed (time, i, j) over violating FIN states per level, witness and

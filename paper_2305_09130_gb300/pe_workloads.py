@@ -2,8 +2,8 @@
 
 The processing-element (PE) level model keeps what the cost-table model folds
 away: every compute unit runs a work-group as NWE processing elements (the
-processes ``pex`` of Listing 9 and ``barrier`` of Listing 8), each PE reports
-every tick of its ``long_work`` to the ``clock`` process (Listing 10), and
+processes ``pex`` of Listing 8 and ``barrier`` of Listing 7), each PE reports
+every tick of its ``long_work`` to the ``clock`` process (Listing 9), and
 the unit's local barrier waits for all of its PEs.  What a user hands to
 ``mc_pe_model_create`` is, per configuration (WG index i, TS index j):
 
@@ -21,22 +21,22 @@ Readings (each is listed with its reason in the design doc):
 
 * ``long_work(gt, tz)`` lasts ``gt * tz + 1`` ticks: it leaves its loop once
   ``time > start_time + gt * tz`` and ``start_time`` is the time it began
-  (Listing 9 sets ``start_time`` before every call but the global-memory one
+  (Listing 8 sets ``start_time`` before every call but the global-memory one
   of the second and later iterations; the stale value is read as a slip).
-* Abstract kernel (Listings 2 and 9): N = size / WG work-groups (one element
+* Abstract kernel (Listings 2 and 8): N = size / WG work-groups (one element
   per work item), NWE = min(WG, NP); a PE serves ceil(WG / NP) work items one
-  after another (the unit re-activates it, Listing 7); each item runs
+  after another (the unit re-activates it, Listing 6); each item runs
   size / TS iterations of [global load: long_work(GMT, TS); barrier; local
   work: long_work(1, TS); barrier], then stores its result: long_work(GMT, 1).
   WG and TS range over 2^1 .. 2^(n-1) for size = 2^n (``select`` in main,
   Listing 3).  With one unit of four PEs and GMT = 1 the minimum over this
   domain at size 8 is 44 at TS = 4, WG = 4 -- the first row of Table 1.
-* Minimum kernel (Listings 11-16): N = ceil(size / (WG * TS)) work-groups,
+* Minimum kernel (Listings 10-15): N = ceil(size / (WG * TS)) work-groups,
   NWE = min(WG, NP); a PE maps ceil(WG / NP) slices of TS elements, each
   element a global read of GMT + 1 ticks, with no barrier in between; then
   one barrier, and PE 0 alone reduces the unit's NWE local minima (NWE - 1
   ticks) and writes the result to global memory (GMT ticks).  The reduction
-  is taken per work-group as in the OpenCL kernel (Listing 11).
+  is taken per work-group as in the OpenCL kernel (Listing 10).
 """
 from __future__ import annotations
 
@@ -101,7 +101,7 @@ def abstract_program(size: int, wg: int, ts: int, np_: int, gmt: int) -> List[Se
 
 def pe_abstract(size: int, P: int = 1, np_: int = 4, gmt: int = 1,
                 wg_values: Sequence[int] = (), ts_values: Sequence[int] = ()) -> PeSpec:
-    """The abstract kernel of Listings 2 and 9 on P units of np_ PEs."""
+    """The abstract kernel of Listings 2 and 8 on P units of np_ PEs."""
     wg = list(wg_values) or _pow2_domain(size)
     ts = list(ts_values) or _pow2_domain(size)
     n, pes, progs = [], [], []
@@ -127,7 +127,7 @@ def minimum_program(wg: int, ts: int, np_: int, gmt: int) -> List[Segment]:
 
 def pe_minimum(size: int, P: int = 2, np_: int = 4, gmt: int = 2,
                wg_values: Sequence[int] = (), ts_values: Sequence[int] = ()) -> PeSpec:
-    """The Minimum kernel of Listings 11-16 on P units of np_ PEs."""
+    """The Minimum kernel of Listings 10-15 on P units of np_ PEs."""
     wg = list(wg_values) or _pow2_domain(size)
     ts = list(ts_values) or _pow2_domain(size)
     n, pes, progs = [], [], []

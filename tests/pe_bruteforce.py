@@ -4,7 +4,7 @@ A third, deliberately plain implementation of the transition relation (the
 CPU oracle and the CUDA path are the other two), used to pin the oracle on
 tiny models.  States are Python tuples; nothing is packed.
 
-The model (Listings 4-10, processes ``host``, ``device``, ``unit``, ``pex``,
+The model (Listings 3-9, processes ``host``, ``device``, ``unit``, ``pex``,
 ``barrier``, ``clock``), as read for this project:
 
 * ``s0`` selects WG (level 1), then TS (level 2): configuration (i, j) with
@@ -14,11 +14,11 @@ The model (Listings 4-10, processes ``host``, ``device``, ``unit``, ``pex``,
   the configuration's program at its first step with no PE marked.
 * A program step is a clock tick of a work segment or a local barrier.  In
   either, each participating PE marks itself once, in any order: in a tick it
-  reports ``NRP_work++`` and waits for ``time`` to change (Listing 9,
+  reports ``NRP_work++`` and waits for ``time`` to change (Listing 8,
   ``long_work``), at a barrier it sends ``done`` to the ``barrier`` process
-  (Listing 8).  When all participants of a barrier are marked, the barrier
+  (Listing 7).  When all participants of a barrier are marked, the barrier
   releases them (one step: the unit moves to its next program step).
-* The clock ticks (``time++``, Listing 10) when every busy unit is in a tick
+* The clock ticks (``time++``, Listing 9) when every busy unit is in a tick
   step with all of its participants marked and no unit is idle while
   work-groups are left; every busy unit then moves to its next step.
 * A unit whose program ends becomes idle.  FIN holds when no work-group is
