@@ -714,20 +714,33 @@ def run_c5(args):
     def make_query(k):
         return W.c3(G=4096, rule=W.GREEDY, seed=2305091305 * 1000003 + k, key_bits=128)
 
-    # one-query-at-a-time service times on a sample of the same query stream
+    # one-query-at-a-time service times on a sample of the same query stream:
+    # end to end as a caller of the single-model API sees it (create the
+    # model from host arrays, mc_min_time, read the result, destroy; PyTorch's
+    # caching allocator), and the exploration's device time alone
     sample = [make_query(10_000_000 + k) for k in range(args.c5_sample)]
-    service, service_states = [], []
+    for sp in sample[:3]:  # warm the allocator and the library
+        m = mc.mc_model_create(sp)
+        mc.mc_min_time(m, trace=False)
+        mc.mc_model_destroy(m)
+    service, service_dev, service_states = [], [], []
     for sp in sample:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = mc.mc_model_create(sp)
+        r = mc.mc_min_time(m, trace=False)
+        mc.mc_model_destroy(m)
+        service.append(time.perf_counter() - t0)
+        service_states.append(r["states"])
         m = mc.mc_model_create(sp)
         mc.mc_reserve(m)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record()
-        r = mc.mc_min_time(m, trace=False)
+        mc.mc_min_time(m, trace=False)
         b.record()
         b.synchronize()
-        service.append(a.elapsed_time(b) / 1000.0)
-        service_states.append(r["states"])
+        service_dev.append(a.elapsed_time(b) / 1000.0)
         mc.mc_model_destroy(m)
 
     sweep = []
@@ -760,19 +773,27 @@ def run_c5(args):
         first = min(r["submit_s"] for r in res)
         last = max(r["done_s"] for r in res)
         # the same arrivals served FIFO one at a time, service times cycling
-        # through the measured sample
-        clock, seq_lat = 0.0, []
-        for k, a in enumerate(arrivals):
-            start = max(clock, a)
-            clock = start + service[k % len(service)]
-            seq_lat.append(1000.0 * (clock - a))
+        # through the measured sample (end to end; and device time only)
+        def fifo(times):
+            clock, out = 0.0, []
+            for k, a in enumerate(arrivals):
+                clock = max(clock, a) + times[k % len(times)]
+                out.append(1000.0 * (clock - a))
+            return clock, out
+
+        clock, seq_lat = fifo(service)
+        clock_dev, seq_lat_dev = fifo(service_dev)
         sweep.append({
             "rate_per_s": rate, "queries": n,
             "served": {"throughput_qps": n / (last - first), "latency_ms_p50": percentile(lat, 50),
                        "latency_ms_p99": percentile(lat, 99),
-                       "states_per_s": sum(r["states"] for r in res) / (last - first)},
+                       "states_per_s": sum(r["states"] for r in res) / (last - first),
+                       "ran_alone": sum(r["path"] == "alone" for r in res)},
             "sequential": {"throughput_qps": n / (clock - arrivals[0]) if clock > arrivals[0] else None,
                            "latency_ms_p50": percentile(seq_lat, 50), "latency_ms_p99": percentile(seq_lat, 99)},
+            "sequential_device_only": {
+                "throughput_qps": n / (clock_dev - arrivals[0]) if clock_dev > arrivals[0] else None,
+                "latency_ms_p50": percentile(seq_lat_dev, 50), "latency_ms_p99": percentile(seq_lat_dev, 99)},
         })
     status = mc.mc_server_status(srv)
     mc.mc_server_destroy(srv)
@@ -786,9 +807,13 @@ def run_c5(args):
                                "cost U{1..16} (new splitmix64 seed per query), GREEDY, 128-bit keys; "
                                "Poisson arrivals", "slots": args.slots, "pool_bytes": pool,
                    "sequential_service_ms_mean": 1000.0 * sum(service) / len(service),
+                   "sequential_device_ms_mean": 1000.0 * sum(service_dev) / len(service_dev),
                    "sequential_sample": len(service),
                    "note": "sequential latencies: the same arrival times served FIFO one at a time, with "
-                           "service times cycling through the measured single-query sample"},
+                           "service times cycling through the measured single-query sample; 'sequential' "
+                           "times each query end to end through the single-model C-ABI (create, "
+                           "mc_min_time, destroy), as the served latency is measured from submit to "
+                           "result; 'sequential_device_only' counts the exploration's device time alone"},
         "sweep": sweep, "device_loop_launches": status["launches"],
     }
     if rank == 0:

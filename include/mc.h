@@ -356,14 +356,23 @@ typedef struct {
   uint32_t reserved0;
   uint64_t pool_bytes;   /* device memory for the requests' buffers        */
   uint64_t idle_ns;      /* device loop's wait for new work (0: 2 ms)      */
-  uint64_t reserved[4];
+  uint64_t solo_states;  /* latency path: a request that finds the server
+                            idle (nothing on the device, nothing else
+                            queued) and whose closed-form state bound is at
+                            most this runs alone on the single-model
+                            explorer, whose BFS levels cost half a lockstep
+                            step; requests arriving meanwhile wait for it.
+                            0: 2^22 states; 1: never                        */
+  uint64_t reserved[3];
 } mc_server_config;
 typedef struct {
   uint64_t ticket;
   mc_batch_result result;
   double submit_s;       /* host steady-clock seconds: submitted,          */
-  double admit_s;        /*   posted to the device,                        */
+  double admit_s;        /*   posted to the device (or started alone),     */
   double done_s;         /*   result harvested                             */
+  uint32_t path;         /* 0: the device loop, 1: alone (solo_states)     */
+  uint32_t reserved;
 } mc_server_result;
 
 /* Allocate the pool and mailboxes, start the host thread.  Errors: INVAL,

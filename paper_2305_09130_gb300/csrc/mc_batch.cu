@@ -27,6 +27,7 @@
 // All instances use 128-bit keys in their own layout.  Each instance has its
 // own visited set, frontier log and level records carved from one pool.
 #include <algorithm>
+#include <cstddef>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -216,41 +217,64 @@ struct Planner {
   const BatchArgs* A;
 
   // Advance every slot; returns the number of tasks of the next step and
-  // writes their prefix.
+  // writes the compact plan: the instances with tasks and their prefix.  A
+  // slot with nothing to do (a finished instance; in served mode an empty or
+  // published slot while the inbox is not being scanned) is recognised from
+  // one word of its state and neither loaded nor written back.
   __device__ unsigned long long plan() const {
     __shared__ uint32_t s_count[kMaxBatch];
     __shared__ unsigned long long s_part[kThreads];
     __shared__ unsigned long long s_total;
+    constexpr uint32_t kActShift = 48;  // (active instances << 48) + tasks, scanned together
     const bool serve = A->serve.inbox != nullptr;
     const uint32_t n = A->n;
     const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
     const uint32_t i0 = threadIdx.x * per, i1 = min(n, i0 + per);
-    // served mode: the doorbell read issued now is consumed at the end, so
-    // its trip to host memory overlaps this plan; the inbox is scanned only
-    // in a plan that follows a doorbell change
+    // served mode: every 8th plan reads the doorbell (host memory, a trip of
+    // microseconds that would otherwise lengthen every step); the read issued
+    // now is consumed at the end, so it overlaps this plan, and the inbox is
+    // scanned only in a plan that follows a doorbell change.  seen[2] counts
+    // plans (only planners touch it; the barriers order them).
     uint32_t db = 0;
-    if (serve && threadIdx.x == 0) db = *reinterpret_cast<const volatile uint32_t*>(A->serve.doorbell);
+    bool read_db = false;
+    if (serve && threadIdx.x == 0) {
+      const uint32_t k = __ldcg(A->serve.seen + 2);
+      A->serve.seen[2] = k + 1;
+      read_db = (k & 7u) == 0;
+      if (read_db) db = *reinterpret_cast<const volatile uint32_t*>(A->serve.doorbell);
+    }
     const bool scan_inbox = serve && __ldcg(A->serve.seen + 1) != 0;
     unsigned long long local = 0;
     for (uint32_t i = i0; i < i1; ++i) {
-      BState s;
-      load_cg(A->state + i, s);
+      const unsigned long long* g = reinterpret_cast<const unsigned long long*>(A->state + i);
+      bool idle;
+      if (serve) {  // last word: {seq, published}
+        const unsigned long long w = __ldcg(g + sizeof(BState) / 8 - 1);
+        idle = !scan_inbox && ((uint32_t)w == 0 || (uint32_t)(w >> 32) != 0);
+      } else {      // {phase, pass} and {started, checks}
+        idle = (uint32_t)__ldcg(g) == B_DONE &&
+               (uint32_t)__ldcg(g + offsetof(BState, started) / 8) != 0;
+      }
       uint64_t c = 0;
-      if (scan_inbox) admit(*A, i, s);
-      if (!serve || (s.seq != 0 && !s.published)) {
-        BInst I;
-        load_cg(A->inst + i, I);
-        advance(s, I, *A);
-        c = task_count(s, I, *A);
-        if (serve && s.phase == B_DONE) publish(*A, i, s);
+      if (!idle) {
+        BState s;
+        load_cg(A->state + i, s);
+        if (scan_inbox) admit(*A, i, s);
+        if (!serve || (s.seq != 0 && !s.published)) {
+          BInst I;
+          load_cg(A->inst + i, I);
+          advance(s, I, *A);
+          c = task_count(s, I, *A);
+          if (serve && s.phase == B_DONE) publish(*A, i, s);
+        }
+        unsigned long long* out = reinterpret_cast<unsigned long long*>(A->state + i);
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&s);
+        for (uint32_t k = 0; k < sizeof(BState) / 8; ++k) out[k] = src[k];
       }
       s_count[i] = (uint32_t)c;
-      local += c;
-      unsigned long long* out = reinterpret_cast<unsigned long long*>(A->state + i);
-      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&s);
-      for (uint32_t k = 0; k < sizeof(BState) / 8; ++k) out[k] = src[k];
+      local += c + (c ? 1ull << kActShift : 0ull);
     }
-    // block-wide exclusive scan of the per-thread sums
+    // block-wide exclusive scan of the per-thread (active, tasks) sums
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     unsigned long long incl = local;
     for (int o = 1; o < 32; o <<= 1) {
@@ -269,19 +293,29 @@ struct Planner {
       s_total = run;
     }
     __syncthreads();
-    unsigned long long run = s_part[warp] + incl - local;
+    const unsigned long long base = s_part[warp] + incl - local;
+    const unsigned long long tmask = (1ull << kActShift) - 1;
+    uint32_t pos = (uint32_t)(base >> kActShift);
+    unsigned long long run = base & tmask;
     for (uint32_t i = i0; i < i1; ++i) {
-      A->plan_prefix[i] = run;
+      if (!s_count[i]) continue;
+      A->plan_inst[pos] = i;
+      A->plan_prefix[pos] = run;
+      ++pos;
       run += s_count[i];
     }
+    const uint32_t active = (uint32_t)(s_total >> kActShift);
+    const unsigned long long total = s_total & tmask;
     if (threadIdx.x == 0) {
-      A->plan_prefix[n] = s_total;
-      if (serve) {
+      A->plan_prefix[active] = total;
+      *A->plan_count = active;
+      if (serve && read_db) {
         A->serve.seen[1] = db != __ldcg(A->serve.seen) ? 1u : 0u;
         A->serve.seen[0] = db;
+      } else if (serve) {
+        A->serve.seen[1] = 0;  // this plan scanned the inbox if it was asked to
       }
     }
-    const unsigned long long total = s_total;
     __syncthreads();
     return total;
   }
@@ -325,7 +359,7 @@ struct Planner {
       const unsigned long long total = plan();
       if (!A->serve.inbox || total > 0) {
         if (A->serve.inbox && threadIdx.x == 0 && ld_acquire_sys_u32(A->serve.stop))
-          A->plan_prefix[A->n] = 0;  // the host is shutting the loop down
+          *A->plan_count = 0;  // the host is shutting the loop down
         return;
       }
       if (!wait_for_requests()) return;  // total stays 0: the loop exits
@@ -512,6 +546,7 @@ __device__ void load_state(const BState* g, BState& s) {
 
 __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs A) {
   __shared__ unsigned long long s_prefix[kMaxBatch + 1];
+  __shared__ uint32_t s_inst[kMaxBatch];
   __shared__ WarpBuf s_buf[kThreads / 32];
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
@@ -522,10 +557,13 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs A) {
   uint32_t epoch = 0;
   if (!grid_sync(bar, epoch, planner)) return;  // first plan
   for (;;) {
-    for (uint32_t i = threadIdx.x; i <= A.n; i += blockDim.x) s_prefix[i] = __ldcg(
-        reinterpret_cast<const unsigned long long*>(A.plan_prefix) + i);
+    const uint32_t K = __ldcg(A.plan_count);
+    for (uint32_t i = threadIdx.x; i <= K; i += blockDim.x) {
+      s_prefix[i] = __ldcg(reinterpret_cast<const unsigned long long*>(A.plan_prefix) + i);
+      if (i < K) s_inst[i] = __ldcg(A.plan_inst + i);
+    }
     __syncthreads();
-    const uint64_t total = s_prefix[A.n];
+    const uint64_t total = K ? s_prefix[K] : 0;
     if (total == 0) {
       if (blockIdx.x == 0 && threadIdx.x == 0) A.err[1] = epoch;  // steps of this launch
       break;
@@ -535,15 +573,15 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs A) {
     BInst I;
     uint32_t cur = 0xFFFFFFFFu;
     for (uint64_t t = warp_gid; t < total; t += n_warps) {
-      // instance of task t: last i with prefix[i] <= t (warp-uniform)
-      uint32_t lo = 0, hi = A.n;
+      // instance of task t: the last planned k with prefix[k] <= t (warp-uniform)
+      uint32_t lo = 0, hi = K;
       while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
         if (s_prefix[mid] <= t) lo = mid;
         else hi = mid;
       }
-      const uint32_t inst = lo;
-      const uint64_t q = t - s_prefix[inst];
+      const uint32_t inst = s_inst[lo];
+      const uint64_t q = t - s_prefix[lo];
       if (inst != cur) {
         load_state(A.state + inst, s);
         load_cg(A.inst + inst, I);
@@ -759,7 +797,7 @@ int breserve(mc_batch* b) {
   b->d_pool = (uint8_t*)balloc(b, b->pool_bytes);
   b->d_inst = (mc::BInst*)balloc(b, sizeof(mc::BInst) * b->n);
   b->d_state = (mc::BState*)balloc(b, sizeof(mc::BState) * b->n);
-  b->d_prefix = (uint64_t*)balloc(b, 8ull * (b->n + 1));
+  b->d_prefix = (uint64_t*)balloc(b, 12ull * (b->n + 1));  // prefix, instance list, count
   b->d_ctrl = (uint32_t*)balloc(b, 256 + mc::kBarBytes);
   if (!b->d_pool || !b->d_inst || !b->d_state || !b->d_prefix || !b->d_ctrl) {
     brelease(b);
@@ -864,6 +902,8 @@ int mc_batch_run(mc_batch* b, const mc_query* queries, mc_batch_result* results)
   A.n = b->n;
   A.refine = b->opt.refine;
   A.plan_prefix = b->d_prefix;
+  A.plan_inst = reinterpret_cast<uint32_t*>(b->d_prefix + b->n + 1);
+  A.plan_count = A.plan_inst + b->n;
   A.err = b->d_ctrl;
   A.bar_lines = b->d_ctrl + 64;
   A.barrier_extra = b->opt.debug_barrier_extra;
@@ -1041,6 +1081,7 @@ struct mc_server {
   cudaEvent_t kdone = nullptr;
   bool kernel_running = false;
   uint64_t launches = 0;
+  uint64_t solo_states = 0;  // requests at most this large may run alone
   std::mutex mu;
   std::condition_variable cv_done;
   std::deque<Request> queue;
@@ -1095,6 +1136,8 @@ int launch_server(mc_server* S) {
   A.n = S->cfg.slots;
   A.refine = S->opt.refine;
   A.plan_prefix = S->d_prefix;
+  A.plan_inst = reinterpret_cast<uint32_t*>(S->d_prefix + S->cfg.slots + 1);
+  A.plan_count = A.plan_inst + S->cfg.slots;
   A.err = S->d_ctrl;
   A.bar_lines = S->d_ctrl + 64;
   A.barrier_extra = 0;
@@ -1120,11 +1163,139 @@ int launch_server(mc_server* S) {
   return MC_OK;
 }
 
+// Latency path: one request on an idle server runs on the single-model
+// explorer (mc_api.cu), whose BFS level costs about half a lockstep step.
+// Its buffers come from the server's pool through a bump allocator; options
+// are the server's with search SINGLE, so every field of the result equals
+// what the device loop would report.  Returns false (request untouched) when
+// the pool has no room, and the request then takes the device loop.
+struct Bump {
+  uint8_t* base;
+  uint64_t size, used;
+};
+void* bump_alloc(size_t bytes, void*, void* ctx) {
+  Bump* b = static_cast<Bump*>(ctx);
+  const uint64_t at = (b->used + 255) & ~255ull;
+  if (at + bytes > b->size) return nullptr;
+  b->used = at + bytes;
+  return b->base + at;
+}
+void bump_free(void*, size_t, void*, void*) {}
+
+bool run_alone(mc_server* S, Request& req, mc_server_result& res) {
+  const uint64_t ab = (uint64_t)req.inst.p.a * req.inst.p.b;
+  mc_model_desc d{};
+  d.n_wg = req.inst.p.a;
+  d.n_ts = req.inst.p.b;
+  d.P = req.inst.p.P;
+  d.wg_values = req.wg.empty() ? nullptr : req.wg.data();
+  d.ts_values = req.ts.empty() ? nullptr : req.ts.data();
+  d.n_workgroups = req.params.data();
+  d.cost = req.params.data() + ab;
+  d.speed = req.params.data() + 2 * ab;
+  d.rule = req.inst.p.rule;
+  d.key_bits = 128;
+  mc_options o = S->opt;
+  o.search = MC_SEARCH_SINGLE;
+  o.timing = 0;
+  mc_model* m = nullptr;
+  if (mc_model_create(&d, &o, &m) != MC_OK) return false;
+  mc_layout L;
+  mc_model_layout(m, &L);
+  const uint64_t bytes = L.device_bytes + 16 * 256;
+  uint64_t off = 0;
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    if (!S->pool.alloc(bytes, &off)) {
+      mc_model_destroy(m);
+      return false;
+    }
+  }
+  Bump bump{S->d_pool + off, bytes, 0};
+  mc_set_allocator(m, bump_alloc, bump_free, &bump);
+  mc_set_stream(m, S->stream);
+  std::memset(&res, 0, sizeof(res));
+  res.ticket = req.ticket;
+  res.submit_s = req.t_submit;
+  res.admit_s = now_s();
+  res.path = 1;
+  mc_batch_result& r = res.result;
+  r.kind = req.q.kind;
+  if (req.q.kind == MC_QUERY_MIN_TIME) {
+    mc_min_result mr;
+    r.status = mc_min_time(m, &mr, nullptr);
+    if (r.status == MC_OK) {
+      uint32_t levels = 0;
+      mc_last_widths(m, nullptr, 0, &levels);
+      r.holds = 0;
+      r.levels = levels;
+      r.states = mr.states;
+      r.checks = mr.checks;
+      r.level = mr.level;
+      r.time = mr.t_min;
+      r.t_ini = mr.t_ini;
+      r.wg_index = mr.wg_index;
+      r.ts_index = mr.ts_index;
+      r.wg = mr.wg;
+      r.ts = mr.ts;
+      r.key[0] = mr.witness_key[0];
+      r.key[1] = mr.witness_key[1];
+    }
+  } else {
+    mc_check_result cr;
+    r.status = mc_check(m, req.q.T, &cr, nullptr);
+    if (r.status == MC_OK) {
+      r.holds = cr.holds;
+      r.levels = cr.levels;
+      r.states = cr.states;
+      r.checks = 1;
+      if (!cr.holds) {
+        r.level = cr.cex_level;
+        r.time = cr.cex_time;
+        r.wg_index = cr.cex_wg_index;
+        r.ts_index = cr.cex_ts_index;
+        r.wg = cr.cex_wg;
+        r.ts = cr.cex_ts;
+        r.key[0] = cr.cex_key[0];
+        r.key[1] = cr.cex_key[1];
+      }
+    }
+  }
+  mc_model_destroy(m);  // waits for the model's work on the server stream
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    S->pool.release(off, bytes);
+  }
+  res.done_s = now_s();
+  return true;
+}
+
 void pump_loop(mc_server* S) {
   cudaSetDevice(S->device);
   const uint32_t n = S->cfg.slots;
   while (!S->shutdown.load()) {
     bool progress = false;
+    {  // latency path for a lone request on an idle server
+      std::unique_lock<std::mutex> g(S->mu);
+      bool idle = !S->fatal && !S->kernel_running && S->queue.size() == 1 &&
+                  S->queue.front().lay.state_bound <= S->solo_states;
+      for (uint32_t i = 0; i < n && idle; ++i) idle = !S->slots[i].busy;
+      if (idle) {
+        Request req = std::move(S->queue.front());
+        S->queue.pop_front();
+        g.unlock();
+        mc_server_result res;
+        const bool ran = run_alone(S, req, res);
+        g.lock();
+        if (ran) {
+          S->done.push_back(res);
+          g.unlock();
+          S->cv_done.notify_all();
+          continue;
+        }
+        S->queue.push_front(std::move(req));  // no pool room: take the device loop
+      }
+    }
     {
       std::lock_guard<std::mutex> g(S->mu);
       // harvest published results
@@ -1243,6 +1414,7 @@ int mc_server_create(const mc_server_config* cfg, const mc_options* opt, mc_serv
   S->cfg = *cfg;
   if (opt) S->opt = *opt;
   else mc_options_default(&S->opt);
+  S->solo_states = cfg->solo_states ? cfg->solo_states : (1ull << 22);
   const uint32_t n = cfg->slots;
   S->slots.resize(n);
   S->pool.init(cfg->pool_bytes);
@@ -1268,7 +1440,7 @@ int mc_server_create(const mc_server_config* cfg, const mc_options* opt, mc_serv
   if (cudaMalloc(&S->d_pool, cfg->pool_bytes) != cudaSuccess ||
       cudaMalloc(&S->d_inst, sizeof(mc::BInst) * n) != cudaSuccess ||
       cudaMalloc(&S->d_state, sizeof(mc::BState) * n) != cudaSuccess ||
-      cudaMalloc(&S->d_prefix, 8ull * (n + 1)) != cudaSuccess ||
+      cudaMalloc(&S->d_prefix, 12ull * (n + 1)) != cudaSuccess ||
       cudaMalloc(&S->d_ctrl, 256 + mc::kBarBytes) != cudaSuccess ||
       cudaMalloc(&S->d_seen, 256) != cudaSuccess)
     return bad(MC_ERR_NOMEM);

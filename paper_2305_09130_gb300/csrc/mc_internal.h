@@ -209,7 +209,8 @@ struct ServeArgs {
   uint32_t* stop;         // host sets 1 to end the loop
   uint32_t* doorbell;     // host-mapped: bumped after every post
   uint32_t* seen;         // device memory: [0] last doorbell value read,
-                          // [1] 1 when the inbox is to be scanned at the next plan
+                          // [1] 1 when the inbox is to be scanned at the next plan,
+                          // [2] plans so far (the doorbell is read every 8th)
   uint64_t idle_ns;       // wait for new requests this long before exiting
 };
 
@@ -218,7 +219,9 @@ struct BatchArgs {
   BState* state;
   uint32_t n;
   uint32_t refine;
-  uint64_t* plan_prefix;  // [n + 1] task prefix of the current step
+  uint64_t* plan_prefix;  // [K + 1] task prefix over the step's active instances
+  uint32_t* plan_inst;    // [K] those instances (ascending), K = *plan_count
+  uint32_t* plan_count;   // K; 0 ends the launch
   uint32_t* err;          // launch-wide error word (barrier timeout)
   uint32_t* bar_lines;    // device-wide barrier lines
   uint32_t barrier_extra;

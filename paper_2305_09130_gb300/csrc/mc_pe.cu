@@ -99,13 +99,14 @@ __device__ __forceinline__ uint64_t pack(const Unit& u, const PeParams& p) {
          ((uint64_t)u.pc << p.M) | u.mask;
 }
 
-// Everything a lane needs about one state.
+// What every lane of a tile needs about its state, in scalars (the loops over
+// units are unrolled to kPeMaxUnits with a guard, so nothing is indexed at run
+// time and nothing goes to local memory).
 struct Decoded {
-  uint32_t i, j, cfg, left, S;
+  uint32_t i, j, cfg, left, S, so;
+  uint32_t busy_mask;  // bit c: unit c is busy
   uint64_t tau, time;
-  bool any_busy, any_idle, ready;
-  Unit u[kPeMaxUnits];
-  uint32_t info[kPeMaxUnits];  // step info of each busy unit (0 when idle)
+  bool ready;          // every busy unit is at a tick step with all participants marked
 };
 
 template <bool CG = false>
@@ -115,26 +116,24 @@ __device__ __forceinline__ void decode(u128 key, const PeParams& p, Decoded& d) 
   d.cfg = d.i * p.b + d.j;
   d.tau = ldp<CG>(p.tau + d.cfg);
   d.S = ldp<CG>(p.nsteps + d.cfg);
-  const uint32_t so = ldp<CG>(p.soff + d.cfg);
+  d.so = ldp<CG>(p.soff + d.cfg);
   uint32_t taken = 0;
-  d.any_busy = d.any_idle = false;
+  d.busy_mask = 0;
   d.ready = true;
   d.time = 0;
-  for (uint32_t c = 0; c < p.P; ++c) {
+#pragma unroll
+  for (uint32_t c = 0; c < kPeMaxUnits; ++c) {
+    if (c >= p.P) break;
     const Unit u = unpack(unit_field(key, p, c), p);
-    d.u[c] = u;
     taken += u.n;
     uint64_t clk;
     if (u.busy) {
-      const uint2 st = __ldg(p.step + so + u.pc);
-      d.info[c] = st.x;
-      d.any_busy = true;
+      const uint2 st = __ldg(p.step + d.so + u.pc);
+      d.busy_mask |= 1u << c;
       const uint32_t pes = st.x & 0xFFFFu;
       if ((st.x & kBarrierBit) || u.mask != (1u << pes) - 1u) d.ready = false;
       clk = (uint64_t)(u.n - 1) * d.tau + st.y;
     } else {
-      d.info[c] = 0;
-      d.any_idle = true;
       clk = (uint64_t)u.n * d.tau;
     }
     d.time = clk > d.time ? clk : d.time;
@@ -142,7 +141,10 @@ __device__ __forceinline__ void decode(u128 key, const PeParams& p, Decoded& d) 
   d.left = ldp<CG>(p.N + d.cfg) - taken;
 }
 
-__device__ __forceinline__ bool is_fin(const Decoded& d) { return d.left == 0 && !d.any_busy; }
+__device__ __forceinline__ bool is_fin(const Decoded& d) { return d.left == 0 && d.busy_mask == 0; }
+__device__ __forceinline__ bool any_idle(const Decoded& d, const PeParams& p) {
+  return d.busy_mask != (1u << p.P) - 1u;
+}
 
 // next program step of a busy unit (idle at the program's end)
 __device__ __forceinline__ Unit step_on(Unit u, uint32_t S) {
@@ -186,41 +188,43 @@ __device__ __forceinline__ void propose(const PeParams& p, const Decoded& d, u12
   term = false;
   succ = key;
   t = d.time;
-  if (slot < PM) {  // PE e of unit c marks the current step
-    const uint32_t c = slot / p.M, e = slot % p.M;
-    const Unit& u = d.u[c];
-    if (u.busy && e < (d.info[c] & 0xFFFFu) && !((u.mask >> e) & 1u)) {
-      ok = true;
-      succ = key ^ ((u128)(1u << e) << ((p.P - 1 - c) * p.unit_bits));
-    }
-  } else if (slot < PM + p.P) {  // unit c: barrier release, or dispatch
-    const uint32_t c = slot - PM;
-    const Unit u = d.u[c];
-    Unit v = u;
-    if (u.busy) {
-      const uint32_t pes = d.info[c] & 0xFFFFu;
-      if ((d.info[c] & kBarrierBit) && u.mask == (1u << pes) - 1u) {
+  if (slot < PM + p.P) {  // a mark of PE e of unit c, or unit c's release / dispatch
+    const uint32_t c = slot < PM ? slot / p.M : slot - PM;
+    const uint32_t shift = (p.P - 1 - c) * p.unit_bits;
+    const Unit u = unpack(unit_field(key, p, c), p);
+    const uint32_t info = u.busy ? __ldg(&p.step[d.so + u.pc].x) : 0u;
+    const uint32_t pes = info & 0xFFFFu;
+    if (slot < PM) {
+      const uint32_t e = slot - c * p.M;
+      if (u.busy && e < pes && !((u.mask >> e) & 1u)) {
         ok = true;
-        v = step_on(u, d.S);
-        bool others_idle = true;
-        for (uint32_t x = 0; x < p.P; ++x)
-          if (x != c && d.u[x].busy) others_idle = false;
-        term = d.left == 0 && !v.busy && others_idle;
+        succ = key ^ ((u128)(1u << e) << shift);
       }
-    } else if (d.left > 0) {
-      ok = true;
-      v.n = u.n + 1;
-      v.busy = 1;
-      v.pc = 0;
-      v.mask = 0;
+    } else {
+      Unit v = u;
+      if (u.busy) {
+        if ((info & kBarrierBit) && u.mask == (1u << pes) - 1u) {
+          ok = true;
+          v = step_on(u, d.S);
+          term = d.left == 0 && !v.busy && (d.busy_mask & ~(1u << c)) == 0;
+        }
+      } else if (d.left > 0) {
+        ok = true;
+        v.n = u.n + 1;
+        v.busy = 1;
+        v.pc = 0;
+        v.mask = 0;
+      }
+      if (ok) succ = key ^ ((u128)(pack(u, p) ^ pack(v, p)) << shift);
     }
-    if (ok) succ = key ^ ((u128)(pack(u, p) ^ pack(v, p)) << ((p.P - 1 - c) * p.unit_bits));
-  } else if (slot == PM + p.P && d.any_busy && d.ready && !(d.left > 0 && d.any_idle)) {
+  } else if (slot == PM + p.P && d.busy_mask && d.ready && !(d.left > 0 && any_idle(d, p))) {
     ok = true;  // the clock ticks; every busy unit moves on
     bool all_idle = true;
-    for (uint32_t c = 0; c < p.P; ++c) {
-      const Unit u = d.u[c];
-      if (!u.busy) continue;
+#pragma unroll
+    for (uint32_t c = 0; c < kPeMaxUnits; ++c) {
+      if (c >= p.P) break;
+      if (!((d.busy_mask >> c) & 1u)) continue;
+      const Unit u = unpack(unit_field(key, p, c), p);
       const Unit v = step_on(u, d.S);
       if (v.busy) all_idle = false;
       succ ^= (u128)(pack(u, p) ^ pack(v, p)) << ((p.P - 1 - c) * p.unit_bits);
@@ -351,8 +355,10 @@ __device__ void pe_expand_level(const PeArgs& A, PeStage<TILE>& st, uint64_t T, 
   }
 }
 
+// Register budgets: 64 per thread (4 blocks of 256 per SM) for tiles of 16
+// and 32 lanes, 85 (3 blocks) for the three-successor tiles, which spill at 64.
 template <int TILE>
-__global__ void __launch_bounds__(kThreads) pe_explore_kernel(const PeArgs A) {
+__global__ void __launch_bounds__(kThreads, TILE >= 16 ? 4 : 3) pe_explore_kernel(const PeArgs A) {
   const PeParams& p = A.p;
   Ctrl* ctrl = A.ctrl;
   const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -104,12 +104,13 @@ MC_QUERY_CHECK, MC_QUERY_MIN_TIME = 0, 1
 
 class McServerConfig(C.Structure):
     _fields_ = [("slots", C.c_uint32), ("reserved0", C.c_uint32), ("pool_bytes", C.c_uint64),
-                ("idle_ns", C.c_uint64), ("reserved", C.c_uint64 * 4)]
+                ("idle_ns", C.c_uint64), ("solo_states", C.c_uint64), ("reserved", C.c_uint64 * 3)]
 
 
 class McServerResult(C.Structure):
     _fields_ = [("ticket", C.c_uint64), ("result", McBatchResult), ("submit_s", C.c_double),
-                ("admit_s", C.c_double), ("done_s", C.c_double)]
+                ("admit_s", C.c_double), ("done_s", C.c_double), ("path", C.c_uint32),
+                ("reserved", C.c_uint32)]
 
 class McPeModelDesc(C.Structure):
     _fields_ = [("n_wg", C.c_uint32), ("n_ts", C.c_uint32), ("P", C.c_uint32),
@@ -607,8 +608,11 @@ class Server:
 
 
 def mc_server_create(slots: int, pool_bytes: int, options: Optional[McOptions] = None,
-                     idle_ns: int = 0) -> Server:
-    cfg = McServerConfig(int(slots), 0, int(pool_bytes), int(idle_ns))
+                     idle_ns: int = 0, solo_states: int = 0) -> Server:
+    """solo_states: requests that find the server idle and whose state bound
+    is at most this run alone on the single-model explorer (0: the library's
+    default, 1: never)."""
+    cfg = McServerConfig(int(slots), 0, int(pool_bytes), int(idle_ns), int(solo_states))
     h = C.c_void_p()
     rc = load().mc_server_create(C.byref(cfg), C.byref(options) if options is not None else None,
                                  C.byref(h))
@@ -637,7 +641,8 @@ def mc_server_poll(server: Server, cap: int = 1024, wait_ms: int = 0) -> list:
     for k in range(n.value):
         r = buf[k]
         d = _batch_result(r.result)
-        d.update(ticket=r.ticket, submit_s=r.submit_s, admit_s=r.admit_s, done_s=r.done_s)
+        d.update(ticket=r.ticket, submit_s=r.submit_s, admit_s=r.admit_s, done_s=r.done_s,
+                 path="alone" if r.path == 1 else "loop")
         out.append(d)
     return out
 

@@ -59,13 +59,16 @@ def test_served_results_equal_alone_and_in_mix(mc):
             if exp[key] is not None:
                 assert r[key] == exp[key], (idx, key, r, exp)
         assert r["submit_s"] <= r["admit_s"] <= r["done_s"]
-    # the same query alone on a fresh server gives the same answer
-    alone = mc.mc_server_create(slots=1, pool_bytes=1 << 30)
-    for idx in (0, 3, 9):
-        t = mc.mc_server_submit(alone, specs[idx], *queries[idx])
-        r = collect(mc, alone, 1)[t]
-        assert {k: r[k] for k in KEYS} == {k: got[list(tickets)[idx]][k] for k in KEYS}
-    mc.mc_server_destroy(alone)
+    # the same query alone on a fresh server gives the same answer, on the
+    # device loop and on the latency path for a lone request
+    for solo, path in ((1, "loop"), (0, "alone")):
+        alone = mc.mc_server_create(slots=1, pool_bytes=1 << 30, solo_states=solo)
+        for idx in (0, 3, 9):
+            t = mc.mc_server_submit(alone, specs[idx], *queries[idx])
+            r = collect(mc, alone, 1)[t]
+            assert r["path"] == path
+            assert {k: r[k] for k in KEYS} == {k: got[list(tickets)[idx]][k] for k in KEYS}
+        mc.mc_server_destroy(alone)
     st = mc.mc_server_status(srv)
     assert st["fatal"] == 0 and st["queued"] == 0 and st["running"] == 0
     mc.mc_server_destroy(srv)
@@ -75,7 +78,8 @@ def test_requests_join_a_running_device_loop(mc):
     # a long GREEDY search is running when small queries arrive: they are
     # admitted into the same device loop and finish first
     long_spec = W.c3(rule=W.GREEDY)
-    srv = mc.mc_server_create(slots=16, pool_bytes=8 << 30, options=mc.mc_options_default(prune=0))
+    srv = mc.mc_server_create(slots=16, pool_bytes=8 << 30, options=mc.mc_options_default(prune=0),
+                              solo_states=1)
     t_long = mc.mc_server_submit(srv, long_spec, "min_time")
     time.sleep(0.01)
     small = [mc.mc_server_submit(srv, W.c1(W.FREE), "check", 80) for _ in range(6)]
@@ -86,6 +90,7 @@ def test_requests_join_a_running_device_loop(mc):
         r = got[t]
         assert r["status"] == 0 and not r["holds"] and r["time"] == 80
         assert r["admit_s"] < L["done_s"] and r["done_s"] < L["done_s"]
+        assert r["path"] == "loop"
     st = mc.mc_server_status(srv)
     assert st["launches"] >= 1 and st["fatal"] == 0
     mc.mc_server_destroy(srv)
@@ -96,4 +101,25 @@ def test_server_rejects_models_larger_than_its_pool(mc):
     with pytest.raises(mc.MCError) as e:
         mc.mc_server_submit(srv, W.c2_star(), "check", 95)
     assert e.value.code == mc.MC_ERR_NOMEM
+    mc.mc_server_destroy(srv)
+
+
+def test_lone_requests_take_the_latency_path(mc):
+    # each request finds the server idle: it runs alone on the single-model
+    # explorer, with the answer of the single-model entry point; requests
+    # submitted together go through the device loop
+    srv = mc.mc_server_create(slots=8, pool_bytes=2 << 30)
+    specs, queries = mix()
+    for idx in (0, 1, 4, 5):
+        t = mc.mc_server_submit(srv, specs[idx], *queries[idx])
+        r = collect(mc, srv, 1)[t]
+        assert r["path"] == "alone"
+        exp = single(mc, specs[idx], *queries[idx])
+        for key in KEYS:
+            if exp[key] is not None:
+                assert r[key] == exp[key], (idx, key)
+    big = mc.mc_server_create(slots=8, pool_bytes=2 << 30, solo_states=1 << 12)
+    t = mc.mc_server_submit(big, specs[3], *queries[3])  # c2 literal: bound above 2^12
+    assert collect(mc, big, 1)[t]["path"] == "loop"
+    mc.mc_server_destroy(big)
     mc.mc_server_destroy(srv)
