@@ -349,7 +349,8 @@ const char* mc_batch_last_error(const mc_batch* b);
  * join the device loop at its next step, so their work overlaps.  Results
  * equal those of mc_batch_run / mc_check / mc_min_time for the same model.
  * A host thread of the library admits, harvests and relaunches; the device
- * loop exits after `idle_ns` without work and is relaunched on demand. */
+ * loop exits after `idle_ns` without work and is relaunched on demand.  The
+ * loop runs one block per SM unless mc_options.blocks_per_sm says otherwise. */
 typedef struct mc_server mc_server;
 typedef struct {
   uint32_t slots;        /* requests on the device at once, 1..1024        */
