@@ -186,6 +186,8 @@ typedef struct {
                                 passes, or lockstep steps of a batch launch  */
   uint64_t probes;           /* successors generated, each one visited-set
                                 probe (PE-level model, mc_pe.h, only)        */
+  uint64_t graph_launches;   /* batch runs replayed from the captured CUDA
+                                graph of mc_batch_run (batches only)         */
 } mc_stats;
 
 typedef void* (*mc_alloc_fn)(size_t bytes, void* stream, void* ctx);
@@ -331,6 +333,9 @@ int mc_batch_set_allocator(mc_batch* b, mc_alloc_fn alloc, mc_free_fn free_fn, v
 /* Device bytes of the batch's pool (visited sets, logs, level records). */
 int mc_batch_device_bytes(const mc_batch* b, uint64_t* out);
 /* Run queries[i] on model i for every i, in one launch; fills results[n].
+ * The first run captures its work (uploads, clears, the persistent launch,
+ * read-backs) into a CUDA graph, which later runs replay with new queries;
+ * where capture is not possible the work is enqueued directly.
  * Errors: INVAL, NOMEM, TIMEOUT, CUDA; per-instance errors in status. */
 int mc_batch_run(mc_batch* b, const mc_query* queries, mc_batch_result* results);
 /* Trace of instance i's counterexample from the last run: *len states of two

@@ -684,7 +684,14 @@ struct mc_batch {
   mc::BState* d_state = nullptr;
   uint64_t* d_prefix = nullptr;
   uint32_t* d_ctrl = nullptr;         // err word, then the barrier lines
-  std::vector<mc::BState> h_state;
+  // pinned staging: the instances uploaded, the states read back, and the
+  // launch's {error, steps} words; a run is replayed from a CUDA graph
+  mc::BInst* h_inst = nullptr;
+  mc::BState* h_state = nullptr;
+  uint32_t* h_ctrl2 = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on
+  cudaGraphExec_t graph = nullptr;
+  bool graph_tried = false;           // a refused capture leaves graph null
   cudaEvent_t ev[2] = {};
   mc_stats stats{};
   std::string last_err;
@@ -733,6 +740,17 @@ void brelease(mc_batch* b) {
     if (e) cudaEventDestroy(e);
     e = nullptr;
   }
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->h_inst) cudaFreeHost(b->h_inst);
+  if (b->h_state) cudaFreeHost(b->h_state);
+  if (b->h_ctrl2) cudaFreeHost(b->h_ctrl2);
+  b->graph = nullptr;
+  b->graph_tried = false;
+  b->cap_stream = nullptr;
+  b->h_inst = nullptr;
+  b->h_state = nullptr;
+  b->h_ctrl2 = nullptr;
   b->reserved = false;
 }
 
@@ -826,6 +844,14 @@ int breserve(mc_batch* b) {
     return MC_ERR_NOMEM;
   }
   for (cudaEvent_t& e : b->ev) MCB_CUDA(b, cudaEventCreate(&e));
+  if (cudaMallocHost((void**)&b->h_inst, sizeof(mc::BInst) * b->n) != cudaSuccess ||
+      cudaMallocHost((void**)&b->h_state, sizeof(mc::BState) * b->n) != cudaSuccess ||
+      cudaMallocHost((void**)&b->h_ctrl2, 64) != cudaSuccess) {
+    cudaGetLastError();
+    brelease(b);
+    return MC_ERR_NOMEM;
+  }
+  MCB_CUDA(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
   // carve each instance's region and upload its tables
   for (uint32_t i = 0; i < b->n; ++i) {
     uint8_t* q = b->d_pool + b->pool_off[i];
@@ -859,7 +885,6 @@ int mc_batch_create(const mc_model_desc* descs, uint32_t n, const mc_options* op
   b->wg.resize(n);
   b->ts.resize(n);
   b->pool_off.resize(n);
-  b->h_state.resize(n);
   uint64_t off = 0;
   for (uint32_t i = 0; i < n; ++i) {
     const mc_model_desc& d = descs[i];
@@ -934,19 +959,52 @@ int mc_batch_run(mc_batch* b, const mc_query* queries, mc_batch_result* results)
   A.timeout_ns = b->opt.barrier_timeout_ns ? b->opt.barrier_timeout_ns : 60ull * 1000000000ull;
   A.prune = b->opt.prune;
   A.early_exit = b->opt.early_exit;
-  MCB_CUDA(b, cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(mc::BInst) * b->n,
-                              cudaMemcpyHostToDevice, b->stream));
-  MCB_CUDA(b, cudaMemsetAsync(b->d_state, 0, sizeof(mc::BState) * b->n, b->stream));
-  MCB_CUDA(b, cudaMemsetAsync(b->d_ctrl, 0, 256 + mc::kBarBytes, b->stream));
+  std::copy(b->inst.begin(), b->inst.end(), b->h_inst);
+  // The run's sequence -- upload the instances, clear states and control,
+  // the persistent launch, read the states and {error, steps} back -- is
+  // captured once into a CUDA graph on a private stream and replayed on the
+  // batch's stream; only the pinned inputs change between runs.  Where the
+  // capture is refused, the sequence is enqueued directly.
+  auto enqueue = [&](cudaStream_t st, bool capturing) -> cudaError_t {
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(b->d_inst, b->h_inst, sizeof(mc::BInst) * b->n, cudaMemcpyHostToDevice, st)))
+      return e;
+    if ((e = cudaMemsetAsync(b->d_state, 0, sizeof(mc::BState) * b->n, st))) return e;
+    if ((e = cudaMemsetAsync(b->d_ctrl, 0, 256 + mc::kBarBytes, st))) return e;
+    if (b->opt.timing &&
+        (e = capturing ? cudaEventRecordWithFlags(b->ev[0], st, cudaEventRecordExternal) : cudaEventRecord(b->ev[0], st)))
+      return e;
+    if ((e = mc::launch_batch(b->grid, b->threads, A, st))) return e;
+    if (b->opt.timing &&
+        (e = capturing ? cudaEventRecordWithFlags(b->ev[1], st, cudaEventRecordExternal) : cudaEventRecord(b->ev[1], st)))
+      return e;
+    if ((e = cudaMemcpyAsync(b->h_state, b->d_state, sizeof(mc::BState) * b->n, cudaMemcpyDeviceToHost, st)))
+      return e;
+    return cudaMemcpyAsync(b->h_ctrl2, b->d_ctrl, 8, cudaMemcpyDeviceToHost, st);
+  };
+  if (!b->graph_tried) {
+    b->graph_tried = true;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const cudaError_t e1 = enqueue(b->cap_stream, true);
+      const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+      if (e1 == cudaSuccess && e2 == cudaSuccess && g &&
+          cudaGraphInstantiate(&b->graph, g, 0) != cudaSuccess)
+        b->graph = nullptr;
+      if (e1 != cudaSuccess || e2 != cudaSuccess) b->graph = nullptr;
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();  // a refused capture is not an error of the run
+  }
+  if (b->graph) {
+    MCB_CUDA(b, cudaGraphLaunch(b->graph, b->stream));
+    b->stats.graph_launches += 1;
+  } else {
+    MCB_CUDA(b, enqueue(b->stream, false));
+  }
   b->stats.h2d_bytes += sizeof(mc::BInst) * b->n;
-  if (b->opt.timing) MCB_CUDA(b, cudaEventRecord(b->ev[0], b->stream));
-  MCB_CUDA(b, mc::launch_batch(b->grid, b->threads, A, b->stream));
-  if (b->opt.timing) MCB_CUDA(b, cudaEventRecord(b->ev[1], b->stream));
-  uint32_t ctrl2[2] = {0, 0};  // launch error word, steps of the launch
-  MCB_CUDA(b, cudaMemcpyAsync(b->h_state.data(), b->d_state, sizeof(mc::BState) * b->n,
-                              cudaMemcpyDeviceToHost, b->stream));
-  MCB_CUDA(b, cudaMemcpyAsync(ctrl2, b->d_ctrl, 8, cudaMemcpyDeviceToHost, b->stream));
   MCB_CUDA(b, cudaStreamSynchronize(b->stream));
+  const uint32_t ctrl2[2] = {b->h_ctrl2[0], b->h_ctrl2[1]};  // launch error word, steps of the launch
   b->stats.d2h_bytes += sizeof(mc::BState) * b->n + 8;
   b->stats.explore_launches += 1;
   b->stats.device_steps += ctrl2[1];

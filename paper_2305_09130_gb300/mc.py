@@ -84,7 +84,8 @@ class McSwarmResult(C.Structure):
 class McStats(C.Structure):
     _fields_ = [("explore_launches", C.c_uint64), ("other_launches", C.c_uint64),
                 ("states", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
-                ("explore_ms", C.c_double), ("device_steps", C.c_uint64), ("probes", C.c_uint64)]
+                ("explore_ms", C.c_double), ("device_steps", C.c_uint64), ("probes", C.c_uint64),
+                ("graph_launches", C.c_uint64)]
 
 
 class McQuery(C.Structure):

@@ -79,6 +79,12 @@ def test_batch_matches_oracle(mc, oracle):
                 bound = r["time"]
                 RP.replay(spec, layout128(mc, spec), keys,
                           (lambda t, b_=bound: t == b_) if q[0] == "min_time" else (lambda t, T=q[1]: t <= T))
+    # the runs replay one captured CUDA graph; new queries reach it through
+    # its pinned inputs
+    flipped = [("min_time", None) if k == "check" else ("check", t - 1) for (k, _T), t in zip(queries, t_mins)]
+    for spec, q, r in zip(specs, flipped, mc.mc_batch_run(b, flipped)):
+        check_against_oracle(mc, oracle, spec, q, r)
+    assert mc.mc_batch_get_stats(b)["graph_launches"] == 3
 
 
 def test_batch_equals_single_model_queries(mc):
