@@ -17,7 +17,7 @@ the unit's local barrier waits for all of its PEs.  What a user hands to
 This module builds those arrays from the kernels the paper models.  It holds
 none of the explorer's arithmetic (no transition, no clock, no property).
 
-Readings (each is listed with its reason in the design doc):
+Readings of the paper used here (where it is silent or inconsistent):
 
 * ``long_work(gt, tz)`` lasts ``gt * tz + 1`` ticks: it leaves its loop once
   ``time > start_time + gt * tz`` and ``start_time`` is the time it began

@@ -8,7 +8,7 @@ per-compute-unit speed factors.  It holds none of the explorer's arithmetic:
 no transition rule, no clock, no property.  Both the CUDA path and the CPU
 oracle consume these arrays; neither imports the other.
 
-Readings of the paper used here (each is listed with its reason in the design doc):
+Readings of the paper used here (where it is silent or inconsistent):
 
 * Number of work-groups: ``N = ceil(G / WG)`` (at least 1).  The paper prints
   ``WGs = size / (WG * TS)`` (Listing 3) but its Table 1 contradicts that
