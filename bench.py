@@ -60,7 +60,8 @@ WORKLOAD = ("c2_star: G=80, P=4, WG 2^0..2^8, TS 2^0..2^4, FREE dispatch, cost c
             "speeds U{1..3} (splitmix64 seed 2305091302); 10,385,335 reachable states")
 REFERENCE_SAMPLE_T = 300     # pruned check of the same model: ~0.74M states
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SRC = os.path.join(ROOT, "paper_2305_09130_gb300", "csrc", "mc_kernels.cu")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2305_09130_gb300", "csrc", f)
+               for f in ("mc_kernels.cu", "mc_device.cuh", "mc_internal.h")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "explore_kernel_c2star_traffic.txt")
 
 
@@ -168,21 +169,27 @@ def algorithmic_bytes_per_state(P: int, key_words: int) -> int:
 
 
 def kernel_source_hash() -> str:
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for path in KERNEL_SRCS:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_launch():
+def ncu_traffic_per_launch(load_factor_pct: int):
     """dram bytes per exploration launch from the committed ncu summary, or
-    None when the summary is missing or was taken on another kernel source."""
+    None when the summary is missing or was taken on another kernel source or
+    another visited-set load factor."""
     try:
         fields = {}
         with open(TRAFFIC_FILE) as f:
             for line in f:
-                if ":" in line:
+                if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
                     fields[k.strip()] = v.strip()
         if fields.get("kernel_source_sha256_16") != kernel_source_hash():
+            return None
+        if int(fields.get("load_factor_pct", -1)) != int(load_factor_pct):
             return None
         return float(fields["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -333,7 +340,8 @@ def run_ours(args):
     launches = st["explore_launches"]
     achieved = bps * st["states"] / (st["explore_ms"] / 1000.0) / 1e9
     peak, peak_kind = measured_hbm_peak()
-    traffic = ncu_traffic_per_launch() if (args.workload, args.query) == ("c2_star", "min_time") else None
+    traffic = (ncu_traffic_per_launch(opts.load_factor_pct)
+               if (args.workload, args.query) == ("c2_star", "min_time") else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "algorithmic_bytes_per_launch": bps * st["states"] / max(launches, 1),

@@ -21,7 +21,8 @@ using mc::Params;
 
 namespace {
 
-constexpr int kSlots = 4;  // pinned per-pass result slots
+constexpr int kSlots = 4;  // per-pass result slots (device header + pinned copy)
+constexpr size_t kCtrlStride = 256 + mc::kBarBytes;  // one slot: header, then its barrier lines
 
 struct Buf {
   void* ptr = nullptr;
@@ -82,7 +83,6 @@ struct mc_model {
   uint32_t* d_log_par = nullptr;
   uint8_t* d_ctrl_block = nullptr;
   Ctrl* d_ctrl = nullptr;
-  uint32_t* d_bar = nullptr;
   uint64_t *d_levels = nullptr, *d_off = nullptr, *d_trace = nullptr;
   uint64_t *d_tini = nullptr, *d_tmin = nullptr;
   Ctrl* h_ctrl = nullptr;       // pinned [kSlots]
@@ -192,7 +192,7 @@ int size_buffers(mc_model* m) {
   if (slots < per_bucket) slots = per_bucket;
   m->table_slots = slots;
   const uint64_t key_bytes = 8ull * m->key_words;
-  const uint64_t ctrl_bytes = 256 + mc::kBarBytes + 8ull * (m->max_level + 2) * 5 + 64;
+  const uint64_t ctrl_bytes = kCtrlStride * kSlots + 8ull * (m->max_level + 2) * 5 + 64;
   uint64_t total = mul_sat(slots, key_bytes);
   total = add_sat(total, mul_sat(m->log_cap, key_bytes + 4));
   total = add_sat(total, ctrl_bytes + 4ull * (2ull * m->a * m->b + m->P));
@@ -232,17 +232,15 @@ int reserve(mc_model* m) {
   m->d_log_keys = dev_alloc(m, m->log_cap * key_bytes);
   m->d_log_par = (uint32_t*)dev_alloc(m, m->log_cap * 4);
   const size_t L2 = m->max_level + 2;
-  const size_t ctrl_bytes = 256 + mc::kBarBytes + 16 * L2 + 8 * L2 + 16 * L2 + 64;
+  const size_t ctrl_bytes = kCtrlStride * kSlots + 16 * L2 + 8 * L2 + 16 * L2 + 64;
   m->d_ctrl_block = (uint8_t*)dev_alloc(m, ctrl_bytes);
   if (!m->d_params || !m->d_table || !m->d_log_keys || !m->d_log_par || !m->d_ctrl_block) {
     release(m);
     return MC_ERR_NOMEM;
   }
   uint8_t* q = m->d_ctrl_block;
-  m->d_ctrl = (Ctrl*)q;
-  q += 256;
-  m->d_bar = (uint32_t*)q;
-  q += mc::kBarBytes;
+  m->d_ctrl = (Ctrl*)q;  // per slot: [Ctrl header, 256 B][barrier lines]
+  q += kCtrlStride * kSlots;
   m->d_levels = (uint64_t*)q;
   q += 16 * L2;
   m->d_off = (uint64_t*)q;
@@ -292,9 +290,15 @@ int reserve(mc_model* m) {
   return MC_OK;
 }
 
-// Enqueue one exploration pass; its Ctrl header lands in h_ctrl[slot].
+Ctrl* ctrl_at(mc_model* m, int slot) {
+  return reinterpret_cast<Ctrl*>(reinterpret_cast<uint8_t*>(m->d_ctrl) + kCtrlStride * slot);
+}
+
+// Enqueue one exploration pass; its Ctrl header lands in h_ctrl[slot].  With
+// `prev`, the pass takes its threshold from that slot's counterexample (see
+// ExploreArgs::prev).
 int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, bool prune,
-                 bool early_exit, bool witness, uint64_t* tmin_out, int slot) {
+                 bool early_exit, bool witness, uint64_t* tmin_out, int slot, int prev = -1) {
   ExploreArgs A{};
   A.p = m->params;
   A.table = m->d_table;
@@ -309,7 +313,8 @@ int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, 
   A.log_keys = m->d_log_keys;
   A.log_par = m->d_log_par;
   A.log_cap = m->log_cap;
-  A.ctrl = m->d_ctrl;
+  A.ctrl = ctrl_at(m, slot);
+  A.prev = prev >= 0 ? ctrl_at(m, prev) : nullptr;
   A.levels = m->d_levels;
   A.off = m->d_off;
   A.trace = m->d_trace;
@@ -318,16 +323,16 @@ int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, 
   A.T_delta = delta;
   A.tmin_out = tmin_out;
   A.barrier_extra = m->opt.debug_barrier_extra;
-  A.bar_groups = m->d_bar;
+  A.bar_groups = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(A.ctrl) + 256);
   A.timeout_ns = m->opt.barrier_timeout_ns ? m->opt.barrier_timeout_ns : 60ull * 1000000000ull;
-  MC_CUDA(m, cudaMemsetAsync(m->d_ctrl, 0, 256 + mc::kBarBytes, m->stream));
+  MC_CUDA(m, cudaMemsetAsync(A.ctrl, 0, kCtrlStride, m->stream));
   if (m->opt.timing) MC_CUDA(m, cudaEventRecord(m->ev[2 * slot], m->stream));
   MC_CUDA(m, mc::launch_explore(m->key_words, m->tile, m->rule, m->grid, m->threads, A, m->stream));
   if (m->opt.timing) {
     MC_CUDA(m, cudaEventRecord(m->ev[2 * slot + 1], m->stream));
     m->ev_pending[slot] = true;
   }
-  MC_CUDA(m, cudaMemcpyAsync(&m->h_ctrl[slot], m->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost,
+  MC_CUDA(m, cudaMemcpyAsync(&m->h_ctrl[slot], A.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost,
                              m->stream));
   m->stats.d2h_bytes += sizeof(Ctrl);
   m->stats.explore_launches += 1;
@@ -664,6 +669,46 @@ int mc_min_time(mc_model* m, mc_min_result* out, mc_trace** trace) {
       m->last_err = "certificate checks disagree with the minimum";
       return MC_ERR_CUDA;
     }
+  } else if (m->opt.search == MC_SEARCH_LOWER) {
+    // Step 3: check at T_ini, then one below each counterexample, until the
+    // property holds.  The checks are chained on the device (each takes its
+    // threshold from its predecessor's counterexample, and one after a check
+    // that held does not run) and enqueued in groups of three over four
+    // result slots, so the last failing check's header survives the next
+    // group; the host waits once per group.
+    constexpr int kGroup = 3;
+    MC_CUDA(m, cudaMemcpyAsync(m->h_scalar, m->d_tini, 8, cudaMemcpyDeviceToHost, m->stream));
+    m->stats.d2h_bytes += 8;
+    int p = 0, last = -1;
+    bool held = false;
+    while (!held) {
+      const int first = p;
+      for (int k = 0; k < kGroup; ++k, ++p) {
+        if (p == 0) MC_TRY(enqueue_pass(m, 0, m->d_tini, 0, prune, ee, true, nullptr, 0));
+        else MC_TRY(enqueue_pass(m, 0, nullptr, 0, prune, ee, true, nullptr, p % kSlots, (p - 1) % kSlots));
+      }
+      MC_TRY(sync(m));
+      for (int q = first; q < p && !held; ++q) {
+        const int slot = q % kSlots;
+        if (m->h_ctrl[slot].skipped) break;
+        MC_TRY(pass_error(m, slot));
+        out->states += m->h_ctrl[slot].states;
+        out->checks += 1;
+        if (m->h_ctrl[slot].stop_level == 0) held = true;
+        else last = slot;
+      }
+    }
+    out->t_ini = m->h_scalar[0];
+    if (last < 0) {
+      m->last_err = "search ended without a counterexample";
+      return MC_ERR_CUDA;
+    }
+    final_slot = last;
+    if (trace) {
+      MC_CUDA(m, cudaMemcpyAsync(m->h_trace, m->d_trace, 16 * L2, cudaMemcpyDeviceToHost, m->stream));
+      m->stats.d2h_bytes += 16 * L2;
+      MC_TRY(sync(m));
+    }
   } else {
     MC_CUDA(m, cudaMemcpyAsync(m->h_scalar, m->d_tini, 8, cudaMemcpyDeviceToHost, m->stream));
     m->stats.d2h_bytes += 8;
@@ -679,17 +724,7 @@ int mc_min_time(mc_model* m, mc_min_result* out, mc_trace** trace) {
       return MC_OK;
     };
     int last = -1;  // slot of the last failing check
-    if (m->opt.search == MC_SEARCH_LOWER) {
-      // Step 3: lower T below each counterexample until the property holds
-      uint64_t T = out->t_ini;
-      for (;;) {
-        const int slot = last == 0 ? 1 : 0;
-        MC_TRY(check(T, slot));
-        if (m->h_ctrl[slot].stop_level == 0) break;
-        last = slot;
-        T = mc::pack_time(m->h_ctrl[slot].wpack) - 1;
-      }
-    } else {
+    {
       // bisection (Fig. 1) between 0 (no terminal has time 0) and T_ini;
       // a counterexample at mid lowers hi to its own time
       uint64_t lo = 0, hi = out->t_ini;

@@ -63,7 +63,8 @@ struct Params {
 // Per-pass control block header (device memory, zeroed before each pass).
 struct Ctrl {
   uint32_t err;           // first error code of the pass (0 = none)
-  uint32_t pad0[3];
+  uint32_t skipped;       // 1: a chained pass that did not run (its predecessor held or failed)
+  uint32_t pad0[2];
   uint32_t levels;        // last explored level + 1
   uint32_t stop_level;    // first level holding a violating terminal (0 = none)
   uint32_t witness_level; // level the witness was taken from (0 = none)
@@ -103,6 +104,8 @@ struct ExploreArgs {
   uint32_t pad;
   uint32_t* bar_groups;   // kBarGroups counters, 128 bytes apart (zeroed per pass)
   uint64_t timeout_ns;
+  const Ctrl* prev;       // lowering chained on the device: run at (prev's counterexample
+                          // time) - 1, or not at all if prev held, failed or was skipped
 };
 
 // Launch helpers implemented in mc_kernels.cu.

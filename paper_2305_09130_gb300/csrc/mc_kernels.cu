@@ -224,8 +224,31 @@ __global__ void __launch_bounds__(kThreads) explore_kernel(const ExploreArgs A) 
   uint32_t epoch = 0;  // device-wide barriers passed in this pass
   const Barrier bar{A.bar_groups, &A.ctrl->err, A.barrier_extra, A.timeout_ns};
 
-  uint64_t T = A.T;
-  if (A.T_src) T = ld_relaxed_u64(A.T_src) + (uint64_t)A.T_delta;
+  // The threshold: given, read from the device (T_src + T_delta), or --
+  // Step 3's lowering chained on the device -- one below the predecessor's
+  // counterexample time, with no run at all once a predecessor held (or
+  // failed).  One thread per block reads those words (thousands of warps
+  // polling one line would queue at its L2 slice) and shares them.
+  __shared__ unsigned long long s_T;
+  __shared__ uint32_t s_skip;
+  if (threadIdx.x == 0) {
+    uint64_t t = A.T;
+    uint32_t skip = 0;
+    if (A.T_src) t = ld_relaxed_u64(A.T_src) + (uint64_t)A.T_delta;
+    if (A.prev) {
+      const Ctrl* q = A.prev;
+      if (ld_relaxed_u32(&q->err) || ld_relaxed_u32(&q->skipped) || ld_relaxed_u32(&q->stop_level) == 0) skip = 1;
+      else t = pack_time(ld_relaxed_u64(&q->wpack)) - 1;
+    }
+    s_T = t;
+    s_skip = skip;
+  }
+  __syncthreads();
+  if (s_skip) {
+    if (gtid == 0) ctrl->skipped = 1;
+    return;
+  }
+  const uint64_t T = s_T;
 
   // prologue: empty visited set, level arrays, levels 0..2 (the selects of
   // WG and TS, Listing 3) written directly: they are distinct by construction
