@@ -367,8 +367,12 @@ __global__ void __launch_bounds__(kThreads, TILE >= 16 ? 4 : 3) pe_explore_kerne
   uint32_t epoch = 0;
   const Barrier bar{A.bar, &A.ctrl->err, 0, A.timeout_ns};
 
-  uint64_t T = A.T;
-  if (A.T_src) T = ld_relaxed_u64(A.T_src) + (uint64_t)A.T_delta;
+  // threshold from the device when chained (one read per block: thousands of
+  // warps polling one line would queue at its L2 slice)
+  __shared__ unsigned long long s_T;
+  if (threadIdx.x == 0) s_T = A.T_src ? ld_relaxed_u64(A.T_src) + (uint64_t)A.T_delta : A.T;
+  __syncthreads();
+  const uint64_t T = s_T;
 
   // prologue: empty visited set; levels 0..2 (the selects of Listing 3)
   {
