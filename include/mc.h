@@ -361,7 +361,7 @@ typedef struct {
   uint32_t slots;        /* requests on the device at once, 1..1024        */
   uint32_t reserved0;
   uint64_t pool_bytes;   /* device memory for the requests' buffers        */
-  uint64_t idle_ns;      /* device loop's wait for new work (0: 2 ms)      */
+  uint64_t idle_ns;      /* device loop's wait for new work (0: 0.2 ms)    */
   uint64_t solo_states;  /* latency path: a request that finds the server
                             idle (nothing on the device, nothing else
                             queued) and whose closed-form state bound is at

@@ -1231,7 +1231,7 @@ int launch_server(mc_server* S) {
   A.serve.stop = S->d_stop;
   A.serve.doorbell = S->d_doorbell;
   A.serve.seen = S->d_seen;
-  A.serve.idle_ns = S->cfg.idle_ns ? S->cfg.idle_ns : 2000000ull;
+  A.serve.idle_ns = S->cfg.idle_ns ? S->cfg.idle_ns : 200000ull;
   if (cudaMemsetAsync(S->d_ctrl, 0, 256 + mc::kBarBytes, S->stream) != cudaSuccess ||
       mc::launch_batch(S->grid, S->threads, A, S->stream) != cudaSuccess ||
       cudaEventRecord(S->kdone, S->stream) != cudaSuccess) {
