@@ -1350,6 +1350,11 @@ bool run_alone(mc_server* S, Request& req, mc_server_result& res) {
   return true;
 }
 
+// Requests waiting on an idle server that still take the latency path one
+// after another (FIFO); a longer queue goes to the device loop, where the
+// requests share its steps.
+constexpr size_t kSoloQueue = 2;
+
 void pump_loop(mc_server* S) {
   cudaSetDevice(S->device);
   const uint32_t n = S->cfg.slots;
@@ -1357,7 +1362,7 @@ void pump_loop(mc_server* S) {
     bool progress = false;
     {  // latency path for a lone request on an idle server
       std::unique_lock<std::mutex> g(S->mu);
-      bool idle = !S->fatal && !S->kernel_running && S->queue.size() == 1 &&
+      bool idle = !S->fatal && !S->kernel_running && !S->queue.empty() && S->queue.size() <= kSoloQueue &&
                   S->queue.front().lay.state_bound <= S->solo_states;
       for (uint32_t i = 0; i < n && idle; ++i) idle = !S->slots[i].busy;
       if (idle) {
