@@ -861,7 +861,7 @@ def main(argv=None):
     p.add_argument("--no-random-roofline", action="store_true")
     p.add_argument("--rates", default="10,30,100,300,1000", help="c5 arrival rates (queries/s)")
     p.add_argument("--slots", type=int, default=512, help="c5 requests on the device at once")
-    p.add_argument("--c5-seconds", type=float, default=6.0, help="c5 arrivals per rate span")
+    p.add_argument("--c5-seconds", type=float, default=10.0, help="c5 arrivals per rate span")
     p.add_argument("--c5-queries", type=int, default=10000, help="c5 queries per rate at most")
     p.add_argument("--c5-sample", type=int, default=48, help="c5 single-query service sample")
     p.add_argument("--workload", choices=sorted(WORKLOADS) + ["c4", "c5"] + sorted(PE_WORKLOADS),

@@ -263,3 +263,28 @@ def test_invalid_descriptions_are_rejected(mc):
     with pytest.raises(mc.MCError) as e:
         mc.mc_model_create(bad)
     assert e.value.code == mc.MC_ERR_INVAL
+
+
+def staircase(P, b, rule):
+    """Configuration j has N = j+1 work-groups and a cost chosen so that the
+    model time falls as N grows: each lowering check stops at a shallower
+    level than the minimum, and the search takes many checks."""
+    n = [j + 1 for j in range(b)]
+    cost = [max(1, 600 // (j + 1) - 7 * j) for j in range(b)]
+    return W.ModelSpec(f"staircase_P{P}", P, [1], W.pow2_range(0, b - 1), n, cost, [1] * P, rule)
+
+
+@pytest.mark.parametrize("P,b", [(1, 12), (2, 10), (3, 9)])
+@pytest.mark.parametrize("rule", [FREE, GREEDY])
+def test_lowering_chained_over_several_groups(mc, oracle, P, b, rule):
+    # the device chains the lowering checks in groups of three over four
+    # result slots; up to eight checks here cross two group boundaries, and a
+    # group's remaining checks are skipped once one holds
+    spec = staircase(P, b, rule)
+    model = make(mc, spec)
+    for prune in (True, False):
+        exp = oracle.min_time(spec, search="lower", prune=prune)
+        assert gpu_min(mc, model, "lower", prune) == exp
+        st = mc.mc_get_stats(model)
+        assert st["explore_launches"] >= exp["checks"]
+        mc.mc_reset_stats(model)
