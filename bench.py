@@ -358,10 +358,12 @@ def run_ours(args):
     if not args.no_random_roofline:
         table_bytes = layout["table_slots"] * 8 * layout["key_words"]
         hbm = mc.mc_measure_random_access(64 << 30, 200_000_000, 0)
+        hbm_cas = mc.mc_measure_random_access(64 << 30, 200_000_000, 1)
         l2 = mc.mc_measure_random_access(max(table_bytes, 1 << 20), 200_000_000, 0)
         probes = spec.P * st["states"] / (st["explore_ms"] / 1000.0)
         roofline["random_access"] = {
             "hbm_64GiB_sector_reads_per_s": hbm["sectors_per_s"],
+            "hbm_64GiB_sector_read_cas_per_s": hbm_cas["sectors_per_s"],
             "table_sized_sector_reads_per_s": l2["sectors_per_s"],
             "table_bytes": table_bytes,
             "kernel_probe_reads_per_s": probes,
