@@ -678,9 +678,11 @@ def run_c4(args):
     value = states_all / (dev_ms_max / 1000.0)
 
     # one query at a time on the single-model entry points (models created
-    # untimed); latency of query k when all arrive together = sum of the
-    # service times of queries 0..k
-    models = [mc.mc_model_create(sp.with_key_bits(128), opts, stream=stream) for sp in specs]
+    # untimed, with the library's default launch shape -- the batch's tuned
+    # options suit its lockstep steps, not a lone query); latency of query k
+    # when all arrive together = sum of the service times of queries 0..k
+    seq_opts = mc.mc_options_default(timing=1)
+    models = [mc.mc_model_create(sp.with_key_bits(128), seq_opts, stream=stream) for sp in specs]
     for m in models:
         mc.mc_reserve(m)
     service = []
@@ -707,6 +709,7 @@ def run_c4(args):
                                "half mc_min_time, half mc_check at round(U[0.8,1.2] x T_min)",
                    "query": "one mc_batch_run per step (one persistent launch)",
                    "autotuned_options": tuned["options"], "autotune_ms": tuned["timings"],
+                   "sequential_options": "library defaults (occupancy-maximum grid, load factor 25%)",
                    "states_per_step": states / args.steps},
         "batched": {"ms_per_batch": dev_ms_max / args.steps, "states_per_s": value,
                     "query_latency_ms_p50": percentile(batch_ms, 50),
