@@ -323,7 +323,7 @@ int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, 
   A.T_delta = delta;
   A.tmin_out = tmin_out;
   A.barrier_extra = m->opt.debug_barrier_extra;
-  A.bar_groups = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(A.ctrl) + 256);
+  A.bar_lines = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(A.ctrl) + 256);
   A.timeout_ns = m->opt.barrier_timeout_ns ? m->opt.barrier_timeout_ns : 60ull * 1000000000ull;
   MC_CUDA(m, cudaMemsetAsync(A.ctrl, 0, kCtrlStride, m->stream));
   if (m->opt.timing) MC_CUDA(m, cudaEventRecord(m->ev[2 * slot], m->stream));

@@ -240,11 +240,13 @@ __device__ __forceinline__ int visited_insert(K* table, uint64_t bucket_mask, ui
 }
 
 // ------------------------------------------------------------------ device-wide barrier
-// All blocks are co-resident (cooperative launch).  Arrivals are counted in
-// two levels -- kBarGroups group counters, then a top counter, each in its
-// own 128-byte line -- so hundreds of blocks do not serialise on one address.
-// Counters only grow: the k-th barrier of a launch (k = 1, 2, ...) completes
-// when a group counter reaches k * members and the top counter k * groups.
+// All blocks are co-resident (cooperative launch).  Each block's thread 0
+// counts its arrival with one acquire-release atomic on a single counter in
+// its own 128-byte line.  (A two-level tree of 16 group counters and a top
+// counter puts a second dependent atomic on the last arriver's path; one
+// counter for all blocks measured 12% faster per level on deep, narrow
+// searches and 3% on the widest ones.)  The counter only grows: the k-th
+// barrier of a launch (k = 1, 2, ...) completes when it reaches k * blocks.
 // The last arriver publishes a 64-bit word: generation k in the high half and
 // a 32-bit payload in the low half, with a release store; the waiters poll it
 // with acquire loads, so the payload reaches every block with the load that
@@ -252,15 +254,15 @@ __device__ __forceinline__ int visited_insert(K* table, uint64_t bucket_mask, ui
 // level's width -- is read once by the releaser instead of by hundreds of
 // blocks at once from a line the step just updated with atomics, which
 // doubled the barrier's cost.)  Every block passes the same sequence of
-// barriers, so each tracks k itself.  Arrivals use acquire-release atomics
-// after __syncthreads.  With a serial section, the releasing block runs it
-// (all its threads) before publishing.  Each wait is bounded by timeout_ns of
-// %globaltimer; on expiry the block records MC_ERR_TIMEOUT in *err, raises
-// the abort flag so the other waiters leave too, and returns false.
+// barriers, so each tracks k itself.  With a serial section, the releasing
+// block runs it (all its threads) before publishing.  Each wait is bounded by
+// timeout_ns of %globaltimer; on expiry the block records MC_ERR_TIMEOUT in
+// *err, raises the abort flag so the other waiters leave too, and returns
+// false.
 struct Barrier {
-  uint32_t* lines;      // kBarGroups + 4 lines of 128 bytes, zeroed per launch
+  uint32_t* lines;      // kBarBytes / 128 lines of 128 bytes, zeroed per launch
   uint32_t* err;        // error word of the launch
-  uint32_t extra;       // extra top-level arrivals to wait for (test hook)
+  uint32_t extra;       // extra arrivals to wait for (test hook)
   uint64_t timeout_ns;
 };
 
@@ -292,14 +294,9 @@ __device__ bool grid_sync(const Barrier& B, uint32_t& epoch, const Serial& seria
   uint64_t* gen = reinterpret_cast<uint64_t*>(B.lines + kBarGen * 32);
   if (threadIdx.x == 0) {
     s_release = 0;
-    const uint32_t groups = gridDim.x < kBarGroups ? gridDim.x : kBarGroups;
-    const uint32_t g = blockIdx.x % groups;
-    const uint32_t members = gridDim.x / groups + (g < gridDim.x % groups ? 1u : 0u);
-    if (atom_add_acq_rel(B.lines + g * 32, 1u) + 1 == members * target) {
-      if (atom_add_acq_rel(B.lines + kBarTop * 32, 1u) + 1 == groups * target && B.extra == 0) {
-        if (kSerial) s_release = 1;
-        else st_release_u64(gen, ((uint64_t)target << 32) | payload_fn());
-      }
+    if (atom_add_acq_rel(B.lines + kBarCount * 32, 1u) + 1 == gridDim.x * target && B.extra == 0) {
+      if (kSerial) s_release = 1;
+      else st_release_u64(gen, ((uint64_t)target << 32) | payload_fn());
     }
   }
   if (kSerial) {

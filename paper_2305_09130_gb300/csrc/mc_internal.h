@@ -26,11 +26,12 @@ constexpr uint32_t kWarpCap = 128;         // winners staged per warp before a f
 #define MC_PROBE_DEPTH 1
 #endif
 constexpr uint32_t kDepth = MC_PROBE_DEPTH; // states per tile and round (probes in flight per lane)
-constexpr uint32_t kBarGroups = 16;        // first-level counters of the device-wide barrier
-constexpr uint32_t kBarTop = kBarGroups;   // 128-byte line of the top counter
-constexpr uint32_t kBarGen = kBarGroups + 1;    // line of the generation word
-constexpr uint32_t kBarAbort = kBarGroups + 2;  // line of the abort flag
-constexpr size_t kBarBytes = (kBarGroups + 4) * 128;
+// device-wide barrier: 128-byte lines of the arrival counter, the
+// generation word and the abort flag (one more line spare)
+constexpr uint32_t kBarCount = 0;
+constexpr uint32_t kBarGen = 1;
+constexpr uint32_t kBarAbort = 2;
+constexpr size_t kBarBytes = 4 * 128;
 
 // Packed (time, i, j) used for device-side min-reductions: time < 2^40,
 // i, j < 2^12.
@@ -100,9 +101,9 @@ struct ExploreArgs {
   const uint64_t* T_src;  // device threshold source (T = *T_src + T_delta)
   int64_t T_delta;
   uint64_t* tmin_out;     // if set: receives pack_time(best_pack) at the end
-  uint32_t barrier_extra; // extra top-level arrivals a barrier waits for (test hook)
+  uint32_t barrier_extra; // extra arrivals a barrier waits for (test hook)
   uint32_t pad;
-  uint32_t* bar_groups;   // kBarGroups counters, 128 bytes apart (zeroed per pass)
+  uint32_t* bar_lines;    // the device-wide barrier's lines (zeroed per pass)
   uint64_t timeout_ns;
   const Ctrl* prev;       // lowering chained on the device: run at (prev's counterexample
                           // time) - 1, or not at all if prev held, failed or was skipped

@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kThreads) explore_kernel(const ExploreArgs A) 
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
   __shared__ Stage<K> stage;
   uint32_t epoch = 0;  // device-wide barriers passed in this pass
-  const Barrier bar{A.bar_groups, &A.ctrl->err, A.barrier_extra, A.timeout_ns};
+  const Barrier bar{A.bar_lines, &A.ctrl->err, A.barrier_extra, A.timeout_ns};
 
   // The threshold: given, read from the device (T_src + T_delta), or --
   // Step 3's lowering chained on the device -- one below the predecessor's
