@@ -95,8 +95,9 @@ typedef struct {
  * other than SINGLE, sim_* and key options are ignored.  The visited set and
  * the frontier log start at table_log2 / log_capacity when given, else at
  * 2^20 slots and 2^22 entries, and grow fourfold (up to half the device's
- * free memory) whenever a query ends in TABLE_FULL or FRONTIER, which then
- * reruns; max_probes 0 means 64 bucket probes.  Errors: INVAL, OVERFLOW. */
+ * free memory, and the visited set up to 2^31 slots) whenever a query ends
+ * in TABLE_FULL or FRONTIER, which then reruns; max_probes 0 means 64 bucket
+ * probes.  Errors: INVAL, OVERFLOW (also table_log2 > 31). */
 int mc_pe_model_create(const mc_pe_model_desc* desc, const mc_options* opt, mc_pe_model** out);
 void mc_pe_model_destroy(mc_pe_model* m);
 int mc_pe_set_stream(mc_pe_model* m, void* stream);

@@ -177,7 +177,9 @@ int size_buffers(mc_model* m) {
   const uint64_t n_init = 1 + (uint64_t)m->a + (uint64_t)m->a * m->b;
   m->log_cap = m->opt.log_capacity ? std::max(m->opt.log_capacity, n_init) : m->state_bound;
   if (m->log_cap == UINT64_MAX) return MC_ERR_NOMEM;
-  // level widths travel in 31 bits of the device-wide barrier's word
+  // a level's width is counted in the low 32 bits of its barrier word: the
+  // winners of a level number at most its width bound and at most the
+  // visited set's slots, and at most the log's capacity reach the next level
   if (std::min(m->max_width, m->log_cap) >= (1ull << 31)) return MC_ERR_OVERFLOW;
   const uint64_t per_bucket = m->key_words == 1 ? 4 : 2;
   uint64_t slots;
@@ -190,6 +192,7 @@ int size_buffers(mc_model* m) {
     if (slots < want) return MC_ERR_NOMEM;
   }
   if (slots < per_bucket) slots = per_bucket;
+  if (m->max_width >= (1ull << 31) && slots > (1ull << 31)) return MC_ERR_OVERFLOW;
   m->table_slots = slots;
   const uint64_t key_bytes = 8ull * m->key_words;
   const uint64_t ctrl_bytes = kCtrlStride * kSlots + 8ull * (m->max_level + 2) * 5 + 64;
@@ -847,7 +850,9 @@ int mc_last_widths(mc_model* m, uint64_t* out, uint32_t cap, uint32_t* n) {
   MC_CUDA(m, cudaMemcpyAsync(rec.data(), m->d_levels, 16ull * k, cudaMemcpyDeviceToHost, m->stream));
   m->stats.d2h_bytes += 16ull * k;
   MC_TRY(sync(m));
-  for (uint32_t l = 0; l < k; ++l) out[l] = rec[2 * l];
+  // the low 32 bits of a level's word are its width (the kernel's level
+  // barrier counts arrivals in the high bits of the same word)
+  for (uint32_t l = 0; l < k; ++l) out[l] = rec[2 * l] & 0xFFFFFFFFull;
   return MC_OK;
 }
 

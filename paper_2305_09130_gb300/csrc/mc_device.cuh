@@ -315,13 +315,16 @@ __device__ bool grid_sync(const Barrier& B, uint32_t& epoch, const Serial& seria
     const uint64_t t0 = globaltimer();
     uint32_t spins = 0;
     uint64_t w;
+    // one load per spin; the abort flag and the clock every 16th
     while (((w = ld_acquire_u64(gen)) >> 32) < target) {
-      if (ld_relaxed_u32(abort_flag)) { ok = 0; break; }
-      if ((++spins & 15u) == 0 && globaltimer() - t0 > B.timeout_ns) {
-        set_error(B.err, MC_ERR_TIMEOUT);
-        atomicExch(abort_flag, 1u);
-        ok = 0;
-        break;
+      if ((++spins & 15u) == 0) {
+        if (ld_relaxed_u32(abort_flag)) { ok = 0; break; }
+        if (globaltimer() - t0 > B.timeout_ns) {
+          set_error(B.err, MC_ERR_TIMEOUT);
+          atomicExch(abort_flag, 1u);
+          ok = 0;
+          break;
+        }
       }
       __nanosleep(32);
     }
@@ -330,6 +333,71 @@ __device__ bool grid_sync(const Barrier& B, uint32_t& epoch, const Serial& seria
   }
   __syncthreads();
   if (payload) *payload = s_payload;
+  return s_ok != 0;
+}
+
+// ------------------------------------------------------------------ level barrier
+// The device-wide barrier at the end of a BFS level, fused with the level's
+// width counter.  The 64-bit word of the next level is, from the top,
+// [blocks arrived : 16][blocks that ask to stop : 16][width : 32].  During
+// the level, warps reserve frontier-log ranges by adding to the width field;
+// at the end each block (after its last reservation and log writes) adds one
+// arrival, plus one stop when its shared `flags` word has a bit of
+// stop_mask set (an error, or what ends the search; the word is cleared for
+// the next level), with a release reduction, and polls the word with acquire loads
+// until every block has arrived.  The value that ends the wait carries the
+// final width and the stop count, and every arrival is in the release
+// sequence it reads from, so each block's log writes are visible after the
+// wait.  No block releases the others: one dependent L2 round trip fewer for
+// the record read and one for the release store, per level.  Widths stay
+// below 2^31 (checked on the host), so the width field never carries.  The
+// wait is bounded like grid_sync's; `extra` adds arrivals to wait for (test
+// hook).  Returns false on timeout/abort; *value receives the final word.
+__device__ __forceinline__ void red_add_release_u64(uint64_t* p, uint64_t v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+constexpr uint32_t kLevelArriveShift = 48;
+constexpr uint32_t kLevelStopShift = 32;
+constexpr uint64_t kLevelWidthMask = 0xFFFFFFFFull;
+
+// Reserve n frontier-log entries of the level whose word this is; returns
+// the offset of the first (blocks that already arrived have raised the high
+// fields, which the offset leaves out).
+__device__ __forceinline__ uint64_t level_reserve(uint64_t* word, uint32_t n) {
+  return atomicAdd(reinterpret_cast<unsigned long long*>(word), (unsigned long long)n) & kLevelWidthMask;
+}
+
+__device__ __forceinline__ bool level_sync(const Barrier& B, uint64_t* word, uint32_t* flags,
+                                           uint32_t stop_mask, uint64_t* value) {
+  __shared__ uint32_t s_ok;
+  __shared__ unsigned long long s_v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const bool stop = (*flags & stop_mask) != 0;
+    *flags = 0;
+    red_add_release_u64(word, (1ull << kLevelArriveShift) | (stop ? 1ull << kLevelStopShift : 0ull));
+    const uint64_t target = (uint64_t)gridDim.x + B.extra;
+    uint32_t* abort_flag = B.lines + kBarAbort * 32;
+    const uint64_t t0 = globaltimer();
+    uint32_t ok = 1, spins = 0;
+    uint64_t v;
+    while (((v = ld_acquire_u64(word)) >> kLevelArriveShift) < target) {
+      if ((++spins & 15u) == 0) {
+        if (ld_relaxed_u32(abort_flag)) { ok = 0; break; }
+        if (globaltimer() - t0 > B.timeout_ns) {
+          set_error(B.err, MC_ERR_TIMEOUT);
+          atomicExch(abort_flag, 1u);
+          ok = 0;
+          break;
+        }
+      }
+      __nanosleep(32);
+    }
+    s_v = v;
+    s_ok = ok;
+  }
+  __syncthreads();
+  *value = s_v;
   return s_ok != 0;
 }
 
@@ -368,7 +436,10 @@ __device__ __forceinline__ uint64_t group_min(uint64_t v, uint32_t g) {
   }
   return v;
 }
+// Minimum over the warp; most calls have no lane with a value (kNone), and
+// one vote settles those.
 __device__ __forceinline__ uint64_t warp_min(uint64_t v) {
+  if (!__any_sync(0xffffffffu, v != kNone)) return kNone;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);

@@ -42,11 +42,15 @@ struct Stage {
   uint32_t par[kThreads / 32][kWarpCap];
   uint32_t fill[kThreads / 32];
   unsigned long long base;
+  uint32_t flags;  // this level: kFlagError | kFlagViolation
 };
+
+constexpr uint32_t kFlagError = 1;
+constexpr uint32_t kFlagViolation = 2;
 
 template <class K>
 __device__ __forceinline__ void copy_out(const ExploreArgs& A, const K* keys, const uint32_t* par,
-                                         uint32_t n, uint64_t at0, uint32_t lane) {
+                                         uint32_t n, uint64_t at0, uint32_t lane, uint32_t* flags) {
   for (uint32_t x = lane; x < n; x += 32) {
     const uint64_t at = at0 + x;
     if (at < A.log_cap) {
@@ -54,6 +58,7 @@ __device__ __forceinline__ void copy_out(const ExploreArgs& A, const K* keys, co
       A.log_par[at] = par[x];
     } else {
       set_error(A.ctrl, MC_ERR_FRONTIER);
+      atomicOr(flags, kFlagError);
     }
   }
 }
@@ -154,7 +159,10 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
       if (allowed[d]) {
         const int rc = visited_insert<K>(table, A.bucket_mask, A.max_probes, succ[d], k_cur + 1, p,
                                          bkt[d], probe[threadIdx.x][d]);
-        if (rc < 0) set_error(A.ctrl, MC_ERR_TABLE_FULL);
+        if (rc < 0) {
+          set_error(A.ctrl, MC_ERR_TABLE_FULL);
+          atomicOr(&st.flags, kFlagError);
+        }
         won = rc > 0;
       }
       const uint32_t m = __ballot_sync(0xffffffffu, won);
@@ -166,14 +174,10 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
         }
         fill += __popc(m);
         // Step 2: a terminal winner with time <= T violates G(FIN -> time > T)
-        uint64_t pk = (won && terminal[d] && succ_time[d] <= T)
-                          ? pack_tij(succ_time[d], ij[d] >> 16, ij[d] & 0xFFFFu)
-                          : kNone;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const uint64_t w = __shfl_xor_sync(0xffffffffu, pk, o);
-          pk = w < pk ? w : pk;
-        }
+        const uint64_t pk = warp_min((won && terminal[d] && succ_time[d] <= T)
+                                         ? pack_tij(succ_time[d], ij[d] >> 16, ij[d] & 0xFFFFu)
+                                         : kNone);
+        if (lane == 0 && pk != kNone) atomicOr(&st.flags, kFlagViolation);
         if (lane == 0 && pk < cached_best) {
           cached_best = ld_relaxed_u64(lvl_next + 1);
           if (pk < cached_best) {
@@ -188,9 +192,9 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
       __syncwarp();
       unsigned long long b = 0;
       if (lane == 0)
-        b = atomicAdd(reinterpret_cast<unsigned long long*>(lvl_next), (unsigned long long)fill);
+        b = level_reserve(lvl_next, fill);
       b = __shfl_sync(0xffffffffu, b, 0);
-      copy_out<K>(A, wkeys, wpar, fill, offN + b, lane);
+      copy_out<K>(A, wkeys, wpar, fill, offN + b, lane, &st.flags);
       __syncwarp();
       fill = 0;
     }
@@ -202,20 +206,19 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
   if (threadIdx.x == 0) {
     uint32_t total = 0;
     for (uint32_t w = 0; w < nw; ++w) total += st.fill[w];
-    st.base = total ? atomicAdd(reinterpret_cast<unsigned long long*>(lvl_next), (unsigned long long)total)
-                    : 0ull;
+    st.base = total ? level_reserve(lvl_next, total) : 0ull;
   }
   __syncthreads();
   if (fill) {
     uint64_t at0 = offN + st.base;
     for (uint32_t w = 0; w < warp; ++w) at0 += st.fill[w];
-    copy_out<K>(A, wkeys, wpar, fill, at0, lane);
+    copy_out<K>(A, wkeys, wpar, fill, at0, lane, &st.flags);
   }
 }
 
 // ------------------------------------------------------------------ the exploration pass
 template <class K, int TILE, int RULE>
-__global__ void __launch_bounds__(kThreads) explore_kernel(const ExploreArgs A) {
+__global__ void __launch_bounds__(kThreads, 4) explore_kernel(const ExploreArgs A) {
   const Params& p = A.p;
   Ctrl* ctrl = A.ctrl;
   const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -277,6 +280,7 @@ __global__ void __launch_bounds__(kThreads) explore_kernel(const ExploreArgs A) 
       KeyOps<K>::store(A.log_keys, x, key);
       A.log_par[x] = par;
     }
+    if (threadIdx.x == 0) stage.flags = 0;
     if (gtid == 0) {
       ctrl->T = T;
       ctrl->best_pack = kNone;
@@ -305,27 +309,21 @@ __global__ void __launch_bounds__(kThreads) explore_kernel(const ExploreArgs A) 
     const uint64_t offN = off_last + W;
     if (gtid == 0) A.off[L + 1] = offN;
     expand_level<K, TILE, RULE>(A, stage, T, L, off_last, W, offN, first, have_first);
-    // the releaser reads level L+1's record and the error word once and
-    // publishes (width << 1) | stop, stop = error or early exit
-    const uint64_t* rec = A.levels + 2 * (L + 1);
-    const uint32_t* errp = &ctrl->err;
-    const uint32_t early = A.early_exit;
-    auto level_word = [rec, errp, early]() -> uint32_t {
-      uint64_t w, b;
-      ld_relaxed_v2u64(rec, w, b);
-      const bool stop = ld_relaxed_u32(errp) != 0 || (early && b != kNone);
-      return ((uint32_t)w << 1) | (stop ? 1u : 0u);
-    };
-    uint32_t word = 0;
-    if (!grid_sync(bar, epoch, NoSerial(), level_word, &word)) return;
+    // level L+1's width word doubles as the barrier: it ends with the width
+    // and the number of blocks that saw an error or (with early exit) a
+    // violating terminal
+    uint64_t word = 0;
+    if (!level_sync(bar, A.levels + 2 * (L + 1), &stage.flags,
+                    kFlagError | (A.early_exit ? kFlagViolation : 0u), &word))
+      return;
 #pragma unroll
     for (uint32_t d = 0; d < kDepth; ++d) {
       const uint64_t at = offN + first_pos + d * (32 / TILE);
       first[d] = KeyOps<K>::load(A.log_keys, at < A.log_cap ? at : A.log_cap - 1);
     }
     have_first = true;
-    const uint64_t Wn = word >> 1;
-    if (word & 1u) {  // an error, or level L+1 holds a violating terminal
+    const uint64_t Wn = word & kLevelWidthMask;
+    if ((word >> kLevelStopShift) & 0xFFFFu) {  // an error, or level L+1 holds a violating terminal
       if (ld_relaxed_u32(&ctrl->err)) break;
       last = L + 1;
       off_last = offN;
@@ -380,7 +378,7 @@ __global__ void __launch_bounds__(kThreads) explore_kernel(const ExploreArgs A) 
   // those with the level's minimum (time, i, j)
   const uint64_t target = ld_relaxed_u64(A.levels + 2 * wl + 1);
   const uint64_t offW = ld_relaxed_u64(&A.off[wl]);
-  const uint64_t Ww = ld_relaxed_u64(A.levels + 2 * wl);
+  const uint64_t Ww = ld_relaxed_u64(A.levels + 2 * wl) & kLevelWidthMask;
   const uint32_t ti = pack_i(target), tj = pack_j(target);
   const uint64_t tt = pack_time(target);
   const uint32_t cfg_t = ti * p.b + tj;

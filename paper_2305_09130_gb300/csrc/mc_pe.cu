@@ -163,10 +163,14 @@ struct PeStage {
   uint32_t par[kThreads / 32][kWarpCap];
   uint32_t fill[kThreads / 32];
   unsigned long long base;
+  uint32_t flags;  // this level: kPeFlagError | kPeFlagViolation
 };
 
+constexpr uint32_t kPeFlagError = 1;
+constexpr uint32_t kPeFlagViolation = 2;
+
 __device__ __forceinline__ void pe_copy_out(const PeArgs& A, const u128* keys, const uint32_t* par,
-                                            uint32_t n, uint64_t at0, uint32_t lane) {
+                                            uint32_t n, uint64_t at0, uint32_t lane, uint32_t* flags) {
   for (uint32_t x = lane; x < n; x += 32) {
     const uint64_t at = at0 + x;
     if (at < A.log_cap) {
@@ -174,6 +178,7 @@ __device__ __forceinline__ void pe_copy_out(const PeArgs& A, const u128* keys, c
       A.log_par[at] = par[x];
     } else {
       set_error(A.ctrl, MC_ERR_FRONTIER);
+      atomicOr(flags, kPeFlagError);
     }
   }
 }
@@ -305,7 +310,10 @@ __device__ void pe_expand_level(const PeArgs& A, PeStage<TILE>& st, uint64_t T, 
       if (ok[k]) {
         const int rc = visited_insert_lv<u128>(table, A.bucket_mask, A.max_probes, succ[k], L + 1, level_of,
                                                bkt[k], probe[threadIdx.x][k]);
-        if (rc < 0) set_error(A.ctrl, MC_ERR_TABLE_FULL);
+        if (rc < 0) {
+          set_error(A.ctrl, MC_ERR_TABLE_FULL);
+          atomicOr(&st.flags, kPeFlagError);
+        }
         won = rc > 0;
       }
       const uint32_t m = __ballot_sync(0xffffffffu, won);
@@ -318,6 +326,7 @@ __device__ void pe_expand_level(const PeArgs& A, PeStage<TILE>& st, uint64_t T, 
         fill += __popc(m);
         uint64_t pk = (won && term[k] && st_time[k] <= T) ? pack_tij(st_time[k], ci, cj) : kNone;
         pk = warp_min(pk);
+        if (lane == 0 && pk != kNone) atomicOr(&st.flags, kPeFlagViolation);
         if (lane == 0 && pk < cached_best) {
           cached_best = ld_relaxed_u64(lvl_next + 1);
           if (pk < cached_best) {
@@ -330,9 +339,9 @@ __device__ void pe_expand_level(const PeArgs& A, PeStage<TILE>& st, uint64_t T, 
       if (fill > kWarpCap - 32) {
         __syncwarp();
         unsigned long long b = 0;
-        if (lane == 0) b = atomicAdd(reinterpret_cast<unsigned long long*>(lvl_next), (unsigned long long)fill);
+        if (lane == 0) b = level_reserve(lvl_next, fill);
         b = __shfl_sync(0xffffffffu, b, 0);
-        pe_copy_out(A, wkeys, wpar, fill, offN + b, lane);
+        pe_copy_out(A, wkeys, wpar, fill, offN + b, lane, &st.flags);
         __syncwarp();
         fill = 0;
       }
@@ -344,14 +353,13 @@ __device__ void pe_expand_level(const PeArgs& A, PeStage<TILE>& st, uint64_t T, 
   if (threadIdx.x == 0) {
     uint32_t total = 0;
     for (uint32_t w = 0; w < nw; ++w) total += st.fill[w];
-    st.base = total ? atomicAdd(reinterpret_cast<unsigned long long*>(lvl_next), (unsigned long long)total)
-                    : 0ull;
+    st.base = total ? level_reserve(lvl_next, total) : 0ull;
   }
   __syncthreads();
   if (fill) {
     uint64_t at0 = offN + st.base;
     for (uint32_t w = 0; w < warp; ++w) at0 += st.fill[w];
-    pe_copy_out(A, wkeys, wpar, fill, at0, lane);
+    pe_copy_out(A, wkeys, wpar, fill, at0, lane, &st.flags);
   }
 }
 
@@ -400,6 +408,7 @@ __global__ void __launch_bounds__(kThreads, TILE >= 16 ? 4 : 3) pe_explore_kerne
       KeyOps<u128>::store(A.log_keys, x, key);
       A.log_par[x] = par;
     }
+    if (threadIdx.x == 0) stage.flags = 0;
     if (gtid == 0) {
       ctrl->T = T;
       ctrl->best_pack = kNone;
@@ -420,19 +429,13 @@ __global__ void __launch_bounds__(kThreads, TILE >= 16 ? 4 : 3) pe_explore_kerne
     const uint64_t offN = off_last + W;
     if (gtid == 0) A.off[L + 1] = offN;
     pe_expand_level<TILE>(A, stage, T, L, off_last, W, offN, probes);
-    const uint64_t* rec = A.levels + 2 * (L + 1);
-    const uint32_t* errp = &ctrl->err;
-    const uint32_t early = A.early_exit;
-    auto level_word = [rec, errp, early]() -> uint32_t {
-      uint64_t w, b;
-      ld_relaxed_v2u64(rec, w, b);
-      const bool stop = ld_relaxed_u32(errp) != 0 || (early && b != kNone);
-      return ((uint32_t)w << 1) | (stop ? 1u : 0u);
-    };
-    uint32_t word = 0;
-    if (!grid_sync(bar, epoch, NoSerial(), level_word, &word)) return;
-    const uint64_t Wn = word >> 1;
-    if (word & 1u) {
+    // level L+1's width word is the barrier (level_sync)
+    uint64_t word = 0;
+    if (!level_sync(bar, A.levels + 2 * (L + 1), &stage.flags,
+                    kPeFlagError | (A.early_exit ? kPeFlagViolation : 0u), &word))
+      return;
+    const uint64_t Wn = word & kLevelWidthMask;
+    if ((word >> kLevelStopShift) & 0xFFFFu) {
       if (ld_relaxed_u32(&ctrl->err)) break;
       last = L + 1;
       off_last = offN;
@@ -486,7 +489,7 @@ __global__ void __launch_bounds__(kThreads, TILE >= 16 ? 4 : 3) pe_explore_kerne
   // (time, i, j), the smallest key (high word first, then low word)
   const uint64_t target = ld_relaxed_u64(A.levels + 2 * wl + 1);
   const uint64_t offW = ld_relaxed_u64(&A.off[wl]);
-  const uint64_t Ww = ld_relaxed_u64(A.levels + 2 * wl);
+  const uint64_t Ww = ld_relaxed_u64(A.levels + 2 * wl) & kLevelWidthMask;
   auto matches = [&](u128 key) {
     Decoded d;
     decode(key, p, d);
@@ -827,6 +830,9 @@ int with_growth(mc_pe_model* m, Query query) {
     const int rc = query();
     if (rc != MC_ERR_TABLE_FULL && rc != MC_ERR_FRONTIER) return rc;
     if (m->opt.table_log2 && rc == MC_ERR_TABLE_FULL) return rc;
+    // a level's width is counted in 32 bits of its barrier word and cannot
+    // exceed the visited set's slots, which stay at or below 2^31
+    if (rc == MC_ERR_TABLE_FULL && m->table_slots * 4 > (1ull << 31)) return rc;
     if (m->opt.log_capacity && rc == MC_ERR_FRONTIER) return rc;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
@@ -959,6 +965,7 @@ int mc_pe_model_create(const mc_pe_model_desc* d, const mc_options* opt, mc_pe_m
   p.ts_mask = (1u << L.ts_bits) - 1;
   p.unit_mask = L.unit_bits >= 64 ? ~0ull : (1ull << L.unit_bits) - 1;
   p.lvl_mask = (1ull << L.level_bits) - 1;
+  if (o.table_log2 > 31) return fail(MC_ERR_OVERFLOW);
   m->table_slots = o.table_log2 ? (1ull << o.table_log2) : (1ull << 20);
   if (m->table_slots < 2) m->table_slots = 2;
   const uint64_t n_init = 1 + (uint64_t)m->a + ab;
@@ -1063,7 +1070,7 @@ int mc_pe_last_widths(mc_pe_model* m, uint64_t* out, uint32_t cap, uint32_t* n) 
   PE_CUDA(m, cudaMemcpyAsync(rec.data(), m->d_levels, 16ull * k, cudaMemcpyDeviceToHost, m->stream));
   PE_CUDA(m, cudaStreamSynchronize(m->stream));
   m->stats.d2h_bytes += 16ull * k;
-  for (uint32_t l = 0; l < k; ++l) out[l] = rec[2 * l];
+  for (uint32_t l = 0; l < k; ++l) out[l] = rec[2 * l] & 0xFFFFFFFFull;  // width field of the word
   return MC_OK;
 }
 
