@@ -230,6 +230,37 @@ __device__ int visited_insert_lv(K* table, uint64_t bucket_mask, uint32_t max_pr
   return -1;
 }
 
+// The first step of an insert whose first bucket is already in shared
+// memory, split off so that a thread can issue the CAS of several inserts
+// before it waits for any: kPickDup when the key is in the bucket, kPickFull
+// when every slot holds a key of this level, else the first free slot (its
+// content in cur).  After the CAS on that slot, an old value equal to cur
+// means the insert won, equal to the key a duplicate, and anything else (the
+// slot went to another key) sends the insert to visited_insert_lv from the
+// same bucket, which rereads it.
+constexpr uint32_t kPickDup = 0xFFu;
+constexpr uint32_t kPickFull = 0xFEu;
+template <class K, class LevelOf>
+__device__ __forceinline__ uint32_t bucket_pick(const K* first, K key, uint32_t lvl, const LevelOf& level_of,
+                                                K& cur) {
+  constexpr int S = KeyOps<K>::kSlots;
+  K v[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) v[s] = first[s];
+  bool hit = false;
+#pragma unroll
+  for (int s = 0; s < S; ++s) hit |= (v[s] == key);
+  if (hit) return kPickDup;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    if (v[s] == (K)0 || level_of(v[s]) < lvl) {
+      cur = v[s];
+      return (uint32_t)s;
+    }
+  }
+  return kPickFull;
+}
+
 // The cost-table model's keys: the level is 2 + sum(n), so `lvl` here is the
 // sum of the n fields.
 template <class K>

@@ -98,6 +98,7 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
   uint64_t* lvl_next = A.levels + 2 * (L + 1);  // {width, best} of level L+1
   uint64_t cached_best = kNone;
   uint32_t fill = 0;  // warp-uniform
+  auto level_of = [&p](K k) { return sum_n(k, p); };
 
   uint64_t base = warp_gid * kTilesPerWarp * D;
   const uint64_t my = lane / TILE;
@@ -152,13 +153,35 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
       }
     }
     cp_async_wait_all();
+    // 64-bit keys: pick a slot for every proposal from the fetched bucket,
+    // issue all of their CAS, and only then look at the results, with the
+    // general insert (rereading the bucket) when the slot went to another
+    // key or the bucket is full.  128-bit keys take the general insert from
+    // the fetched bucket directly.  (Measured: the split form is 8% faster
+    // on C2 at G=80 and 2-3% slower per level with 128-bit keys.)
+    constexpr bool kSplit = sizeof(K) == 8;
+    uint32_t pick[D];
+    K cur[D], old[D];
+#pragma unroll
+    for (uint32_t d = 0; d < D; ++d) {
+      pick[d] = allowed[d] ? kPickFull : kPickDup;
+      if (kSplit && allowed[d])
+        pick[d] = bucket_pick<K>(probe[threadIdx.x][d], succ[d], k_cur + 1, level_of, cur[d]);
+    }
+#pragma unroll
+    for (uint32_t d = 0; d < D; ++d)
+      if (kSplit && pick[d] < (uint32_t)S) old[d] = slot_cas(table + bkt[d] * S + pick[d], cur[d], succ[d]);
 #pragma unroll
     for (uint32_t d = 0; d < D; ++d) {
       const uint64_t s = base + d * kTilesPerWarp + my;
       int won = 0;
-      if (allowed[d]) {
-        const int rc = visited_insert<K>(table, A.bucket_mask, A.max_probes, succ[d], k_cur + 1, p,
-                                         bkt[d], probe[threadIdx.x][d]);
+      if (kSplit && pick[d] < (uint32_t)S) {
+        if (old[d] == cur[d]) won = 1;
+        else if (old[d] != succ[d]) pick[d] = kPickFull;  // the slot went to another key
+      }
+      if (pick[d] == kPickFull) {
+        const int rc = visited_insert<K>(table, A.bucket_mask, A.max_probes, succ[d], k_cur + 1, p, bkt[d],
+                                         kSplit ? nullptr : probe[threadIdx.x][d]);
         if (rc < 0) {
           set_error(A.ctrl, MC_ERR_TABLE_FULL);
           atomicOr(&st.flags, kFlagError);
