@@ -207,9 +207,9 @@ int mc_model_create(const mc_model_desc* desc, const mc_options* opt, mc_model**
  * and its pinned host buffers.  NULL is ignored. */
 void mc_model_destroy(mc_model* m);
 
-/* Replace the options of later queries.  Options that size buffers
- * (load_factor_pct, table_log2, log_capacity) only act before the buffers
- * exist.  Errors: INVAL. */
+/* Replace the options of later queries.  Options that size buffers or the
+ * launch (load_factor_pct, table_log2, log_capacity, threads_per_block,
+ * blocks_per_sm) only act before the buffers exist.  Errors: INVAL. */
 int mc_set_options(mc_model* m, const mc_options* opt);
 
 /* CUDA stream (a cudaStream_t, NULL = legacy default stream) for every later
