@@ -49,12 +49,15 @@ __device__ __forceinline__ uint64_t ldcg64(const uint64_t* p) {
 // Copies of BInst / BState read from L2: in served mode a slot's request (and
 // the tables it points to) can change between steps, so nothing may come
 // from a stale L1 line.
+// 16-byte loads, all issued before the first is used (BInst and BState are
+// multiples of 16 bytes in 16-byte aligned arrays).
 template <class T>
-__device__ void load_cg(const T* g, T& out) {
-  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(g);
-  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&out);
-#pragma unroll 4
-  for (uint32_t k = 0; k < sizeof(T) / 8; ++k) dst[k] = __ldcg(src + k);
+__device__ __forceinline__ void load_cg(const T* g, T& out) {
+  static_assert(sizeof(T) % 16 == 0, "16-byte words");
+  const ulonglong2* src = reinterpret_cast<const ulonglong2*>(g);
+  ulonglong2* dst = reinterpret_cast<ulonglong2*>(&out);
+#pragma unroll
+  for (uint32_t k = 0; k < sizeof(T) / 16; ++k) dst[k] = __ldcg(src + k);
 }
 
 // ------------------------------------------------------------------ planner
@@ -200,14 +203,20 @@ __device__ void publish(const BatchArgs& A, uint32_t i, BState& s) {
   s.published = 1;
 }
 
-// Served mode: take slot i's newly posted request (if any) into the device.
-__device__ void admit(const BatchArgs& A, uint32_t i, BState& s) {
+// Served mode: take slot i's newly posted request (if any) into the device;
+// I receives its description.
+__device__ void admit(const BatchArgs& A, uint32_t i, BState& s, BInst& I) {
   const InboxEntry* e = A.serve.inbox + i;
   const uint32_t seq = ld_acquire_sys_u32(&e->seq);
   if (seq == 0 || seq == s.seq) return;
   const volatile unsigned long long* src = reinterpret_cast<const volatile unsigned long long*>(&e->inst);
   unsigned long long* dst = reinterpret_cast<unsigned long long*>(A.inst + i);
-  for (uint32_t k = 0; k < sizeof(BInst) / 8; ++k) dst[k] = src[k];
+  unsigned long long* loc = reinterpret_cast<unsigned long long*>(&I);
+  for (uint32_t k = 0; k < sizeof(BInst) / 8; ++k) {
+    const unsigned long long v = src[k];
+    dst[k] = v;
+    loc[k] = v;
+  }
   unsigned long long* z = reinterpret_cast<unsigned long long*>(&s);
   for (uint32_t k = 0; k < sizeof(BState) / 8; ++k) z[k] = 0;
   s.seq = seq;
@@ -246,23 +255,18 @@ struct Planner {
     const bool scan_inbox = serve && __ldcg(A->serve.seen + 1) != 0;
     unsigned long long local = 0;
     for (uint32_t i = i0; i < i1; ++i) {
-      const unsigned long long* g = reinterpret_cast<const unsigned long long*>(A->state + i);
-      bool idle;
-      if (serve) {  // last word: {seq, published}
-        const unsigned long long w = __ldcg(g + sizeof(BState) / 8 - 1);
-        idle = !scan_inbox && ((uint32_t)w == 0 || (uint32_t)(w >> 32) != 0);
-      } else {      // {phase, pass} and {started, checks}
-        idle = (uint32_t)__ldcg(g) == B_DONE &&
-               (uint32_t)__ldcg(g + offsetof(BState, started) / 8) != 0;
-      }
+      // the state and the description are loaded together (one round trip
+      // of L2 latency on the serial path, not three)
+      BState s;
+      BInst I;
+      load_cg(A->state + i, s);
+      load_cg(A->inst + i, I);
+      const bool idle = serve ? !scan_inbox && (s.seq == 0 || s.published != 0)
+                              : s.phase == B_DONE && s.started != 0;
       uint64_t c = 0;
       if (!idle) {
-        BState s;
-        load_cg(A->state + i, s);
-        if (scan_inbox) admit(*A, i, s);
+        if (scan_inbox) admit(*A, i, s, I);
         if (!serve || (s.seq != 0 && !s.published)) {
-          BInst I;
-          load_cg(A->inst + i, I);
           advance(s, I, *A);
           c = task_count(s, I, *A);
           if (serve && s.phase == B_DONE) publish(*A, i, s);
@@ -378,15 +382,17 @@ struct Staging {
   uint32_t fill = 0;
   uint64_t offN = 0;            // log offset of the level being appended to
   uint64_t* rec = nullptr;      // {width} counter of that level
+  void* log_keys = nullptr;     // that instance's frontier log
+  uint32_t* log_par = nullptr;
+  uint64_t log_cap = 0;
 };
 
 __device__ void flush(const BatchArgs& A, Staging& sg, WarpBuf& wb, uint32_t lane) {
   if (sg.fill == 0) return;
   __syncwarp();
-  void* log_keys = (void*)__ldcg(reinterpret_cast<const unsigned long long*>(&A.inst[sg.inst].log_keys));
-  uint32_t* log_par =
-      (uint32_t*)__ldcg(reinterpret_cast<const unsigned long long*>(&A.inst[sg.inst].log_par));
-  const uint64_t log_cap = __ldcg(reinterpret_cast<const unsigned long long*>(&A.inst[sg.inst].log_cap));
+  void* log_keys = sg.log_keys;
+  uint32_t* log_par = sg.log_par;
+  const uint64_t log_cap = sg.log_cap;
   unsigned long long b = 0;
   if (lane == 0) b = atomicAdd(reinterpret_cast<unsigned long long*>(sg.rec), (unsigned long long)sg.fill);
   b = __shfl_sync(0xffffffffu, b, 0);
@@ -537,12 +543,7 @@ __device__ void task_sim(const BatchArgs& A, uint32_t inst, const BInst& I, uint
 }
 
 // The fields of BState a task reads (written by the planner before the step).
-__device__ void load_state(const BState* g, BState& s) {
-  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(g);
-  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s);
-#pragma unroll 4
-  for (uint32_t k = 0; k < sizeof(BState) / 8; ++k) dst[k] = __ldcg(src + k);
-}
+__device__ __forceinline__ void load_state(const BState* g, BState& s) { load_cg(g, s); }
 
 __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs A) {
   __shared__ unsigned long long s_prefix[kMaxBatch + 1];
@@ -554,17 +555,22 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs A) {
   const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   const Barrier bar{A.bar_lines, A.err, A.barrier_extra, A.timeout_ns};
   const Planner planner{&A};
-  // A plan of one instance travels in the barrier word itself: bit 0 set,
-  // the instance in bits 1-10, its task count in bits 11-31; the blocks then
-  // skip reading the plan back from memory.
+  // The plan's size travels in the barrier word: a plan of one instance
+  // whole (bit 0 set, the instance in bits 1-10, its task count in bits
+  // 11-31), so the blocks skip reading the plan back, and a larger one as its
+  // instance count (bit 1 set, the count in bits 2-12), so the blocks read
+  // the plan in one round trip instead of two.
   const uint32_t* p_count = A.plan_count;
   const uint32_t* p_inst = A.plan_inst;
   const uint64_t* p_prefix = A.plan_prefix;
   auto plan_word = [p_count, p_inst, p_prefix]() -> uint32_t {
-    if (*p_count != 1) return 0;
-    const uint32_t inst = *p_inst;
-    const uint64_t total = p_prefix[1];
-    return (inst < 1024 && total < (1u << 21)) ? 1u | (inst << 1) | ((uint32_t)total << 11) : 0u;
+    const uint32_t k = *p_count;
+    if (k == 1) {
+      const uint32_t inst = *p_inst;
+      const uint64_t total = p_prefix[1];
+      if (inst < 1024 && total < (1u << 21)) return 1u | (inst << 1) | ((uint32_t)total << 11);
+    }
+    return k <= kMaxBatch ? 2u | (k << 2) : 0u;
   };
   uint32_t epoch = 0, word = 0;
   if (!grid_sync(bar, epoch, planner, plan_word, &word)) return;  // first plan
@@ -578,7 +584,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs A) {
         s_prefix[1] = word >> 11;
       }
     } else {
-      K = __ldcg(A.plan_count);
+      K = (word & 2u) ? (word >> 2) & 0x7FFu : __ldcg(A.plan_count);
       for (uint32_t i = threadIdx.x; i <= K; i += blockDim.x) {
         s_prefix[i] = __ldcg(reinterpret_cast<const unsigned long long*>(A.plan_prefix) + i);
         if (i < K) s_inst[i] = __ldcg(A.plan_inst + i);
@@ -616,6 +622,9 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs A) {
             sg.inst = inst;
             sg.offN = s.offL + s.W;
             sg.rec = I.levels + 2 * (s.L + 1);
+            sg.log_keys = I.log_keys;
+            sg.log_par = I.log_par;
+            sg.log_cap = I.log_cap;
           }
           task_expand(A, inst, I, s, q, lane, sg, s_buf[warp]);
           if (sg.fill > kWarpCap - 32) flush(A, sg, s_buf[warp], lane);
