@@ -150,10 +150,18 @@ __device__ void advance(BState& s, const BInst& I, const BatchArgs& A) {
       s.L = 2;
       s.W = (uint64_t)I.p.a * I.p.b;
       s.offL = 1 + (uint64_t)I.p.a;
+      s.wnext = 0;
+      s.bnext = kNone;
       break;
     case B_EXPAND: {
-      const uint64_t Wn = ldcg64(I.levels + 2 * (s.L + 1));
-      const uint64_t Bn = ldcg64(I.levels + 2 * (s.L + 1) + 1);
+      // level L+1's counters came with the state; keep them in the level
+      // records (the witness phases read them) and start the next level's
+      const uint64_t Wn = s.wnext;
+      const uint64_t Bn = s.bnext;
+      I.levels[2 * (s.L + 1)] = Wn;
+      I.levels[2 * (s.L + 1) + 1] = Bn;
+      s.wnext = 0;
+      s.bnext = kNone;
       if (Wn == 0) {
         end_pass(s, I, A);
         break;
@@ -381,7 +389,7 @@ struct Staging {
   uint32_t inst = 0xFFFFFFFFu;  // instance the buffer holds entries for
   uint32_t fill = 0;
   uint64_t offN = 0;            // log offset of the level being appended to
-  uint64_t* rec = nullptr;      // {width} counter of that level
+  uint64_t* rec = nullptr;      // {width, best} counters of that level (in the instance state)
   void* log_keys = nullptr;     // that instance's frontier log
   uint32_t* log_par = nullptr;
   uint64_t log_cap = 0;
@@ -545,7 +553,7 @@ __device__ void task_sim(const BatchArgs& A, uint32_t inst, const BInst& I, uint
 // The fields of BState a task reads (written by the planner before the step).
 __device__ __forceinline__ void load_state(const BState* g, BState& s) { load_cg(g, s); }
 
-__global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs A) {
+__global__ void __launch_bounds__(kThreads, 1) batch_kernel(const BatchArgs A) {
   __shared__ unsigned long long s_prefix[kMaxBatch + 1];
   __shared__ uint32_t s_inst[kMaxBatch];
   __shared__ WarpBuf s_buf[kThreads / 32];
@@ -621,7 +629,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs A) {
             flush(A, sg, s_buf[warp], lane);
             sg.inst = inst;
             sg.offN = s.offL + s.W;
-            sg.rec = I.levels + 2 * (s.L + 1);
+            sg.rec = &A.state[inst].wnext;  // {wnext, bnext}
             sg.log_keys = I.log_keys;
             sg.log_par = I.log_par;
             sg.log_cap = I.log_cap;

@@ -165,8 +165,8 @@ struct BInst {
   uint64_t T_query;       // threshold of a check query
 };
 
-// Per instance, rewritten by the planner at every barrier; the witness words
-// and err are also updated by atomics during a step.
+// Per instance, rewritten by the planner at every barrier; the witness words,
+// the next level's counters and err are also updated by atomics during a step.
 struct BState {
   uint32_t phase;         // BPhase
   uint32_t pass;          // BPass
@@ -188,6 +188,8 @@ struct BState {
   uint32_t trace_len;
   uint64_t wpack;         // packed (time, i, j) of the counterexample
   uint64_t wkey_lo, wkey_hi, widx;
+  uint64_t wnext;         // B_EXPAND: width of level L+1 (log reservations add to it)
+  uint64_t bnext;         // B_EXPAND: min packed violating terminal of level L+1 (atomicMin)
   uint32_t seq;           // served mode: request number held by this slot
   uint32_t published;     // served mode: result written to the outbox
 };
