@@ -232,6 +232,7 @@ __device__ void admit(const BatchArgs& A, uint32_t i, BState& s, BInst& I) {
 
 struct Planner {
   const BatchArgs* A;
+  uint32_t* word;  // shared: the barrier payload describing the plan (see batch_kernel)
 
   // Advance every slot; returns the number of tasks of the next step and
   // writes the compact plan: the instances with tasks and their prefix.  A
@@ -242,6 +243,7 @@ struct Planner {
     __shared__ uint32_t s_count[kMaxBatch];
     __shared__ unsigned long long s_part[kThreads];
     __shared__ unsigned long long s_total;
+    __shared__ uint32_t s_first;  // the first planned instance
     constexpr uint32_t kActShift = 48;  // (active instances << 48) + tasks, scanned together
     const bool serve = A->serve.inbox != nullptr;
     const uint32_t n = A->n;
@@ -313,14 +315,19 @@ struct Planner {
       if (!s_count[i]) continue;
       A->plan_inst[pos] = i;
       A->plan_prefix[pos] = run;
+      if (pos == 0) s_first = i;
       ++pos;
       run += s_count[i];
     }
+    __syncthreads();
     const uint32_t active = (uint32_t)(s_total >> kActShift);
     const unsigned long long total = s_total & tmask;
     if (threadIdx.x == 0) {
       A->plan_prefix[active] = total;
       *A->plan_count = active;
+      *word = active == 1 && s_first < 1024 && total < (1u << 21)
+                  ? 1u | (s_first << 1) | ((uint32_t)total << 11)
+                  : (active <= kMaxBatch ? 2u | (active << 2) : 0u);
       if (serve && read_db) {
         A->serve.seen[1] = db != __ldcg(A->serve.seen) ? 1u : 0u;
         A->serve.seen[0] = db;
@@ -370,8 +377,10 @@ struct Planner {
     for (;;) {
       const unsigned long long total = plan();
       if (!A->serve.inbox || total > 0) {
-        if (A->serve.inbox && threadIdx.x == 0 && ld_acquire_sys_u32(A->serve.stop))
+        if (A->serve.inbox && threadIdx.x == 0 && ld_acquire_sys_u32(A->serve.stop)) {
           *A->plan_count = 0;  // the host is shutting the loop down
+          *word = 2u;          // a plan of no instances
+        }
         return;
       }
       if (!wait_for_requests()) return;  // total stays 0: the loop exits
@@ -562,24 +571,14 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(const BatchArgs A) {
   const uint64_t warp_gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   const Barrier bar{A.bar_lines, A.err, A.barrier_extra, A.timeout_ns};
-  const Planner planner{&A};
-  // The plan's size travels in the barrier word: a plan of one instance
-  // whole (bit 0 set, the instance in bits 1-10, its task count in bits
-  // 11-31), so the blocks skip reading the plan back, and a larger one as its
-  // instance count (bit 1 set, the count in bits 2-12), so the blocks read
-  // the plan in one round trip instead of two.
-  const uint32_t* p_count = A.plan_count;
-  const uint32_t* p_inst = A.plan_inst;
-  const uint64_t* p_prefix = A.plan_prefix;
-  auto plan_word = [p_count, p_inst, p_prefix]() -> uint32_t {
-    const uint32_t k = *p_count;
-    if (k == 1) {
-      const uint32_t inst = *p_inst;
-      const uint64_t total = p_prefix[1];
-      if (inst < 1024 && total < (1u << 21)) return 1u | (inst << 1) | ((uint32_t)total << 11);
-    }
-    return k <= kMaxBatch ? 2u | (k << 2) : 0u;
-  };
+  // The plan's size travels in the barrier word, written by the planner: a
+  // plan of one instance whole (bit 0 set, the instance in bits 1-10, its
+  // task count in bits 11-31), so the blocks skip reading the plan back, and
+  // a larger one as its instance count (bit 1 set, the count in bits 2-12),
+  // so the blocks read the plan in one round trip instead of two.
+  __shared__ uint32_t s_plan_word;
+  const Planner planner{&A, &s_plan_word};
+  auto plan_word = []() -> uint32_t { return s_plan_word; };
   uint32_t epoch = 0, word = 0;
   if (!grid_sync(bar, epoch, planner, plan_word, &word)) return;  // first plan
   for (;;) {
