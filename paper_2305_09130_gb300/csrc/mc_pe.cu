@@ -105,6 +105,7 @@ __device__ __forceinline__ uint64_t pack(const Unit& u, const PeParams& p) {
 struct Decoded {
   uint32_t i, j, cfg, left, S, so;
   uint32_t busy_mask;  // bit c: unit c is busy
+  uint32_t mark_floor; // 1 + the highest marked (unit, PE) index c * M + e, 0 when nothing is marked
   uint64_t tau, time;
   bool ready;          // every busy unit is at a tick step with all participants marked
 };
@@ -119,6 +120,7 @@ __device__ __forceinline__ void decode(u128 key, const PeParams& p, Decoded& d) 
   d.so = ldp<CG>(p.soff + d.cfg);
   uint32_t taken = 0;
   d.busy_mask = 0;
+  d.mark_floor = 0;
   d.ready = true;
   d.time = 0;
 #pragma unroll
@@ -132,6 +134,7 @@ __device__ __forceinline__ void decode(u128 key, const PeParams& p, Decoded& d) 
       d.busy_mask |= 1u << c;
       const uint32_t pes = st.x & 0xFFFFu;
       if ((st.x & kBarrierBit) || u.mask != (1u << pes) - 1u) d.ready = false;
+      if (u.mask) d.mark_floor = c * p.M + (32u - __clz(u.mask));
       clk = (uint64_t)(u.n - 1) * d.tau + st.y;
     } else {
       clk = (uint64_t)u.n * d.tau;
@@ -200,8 +203,12 @@ __device__ __forceinline__ void propose(const PeParams& p, const Decoded& d, u12
     const uint32_t info = u.busy ? __ldg(&p.step[d.so + u.pc].x) : 0u;
     const uint32_t pes = info & 0xFFFFu;
     if (slot < PM) {
+      // marks are proposed only above the highest marked (unit, PE) index:
+      // a state whose highest mark is (c, e) is still reached from the state
+      // without that mark, and the other orders of the same marks only
+      // generated it again
       const uint32_t e = slot - c * p.M;
-      if (u.busy && e < pes && !((u.mask >> e) & 1u)) {
+      if (u.busy && e < pes && !((u.mask >> e) & 1u) && slot >= d.mark_floor) {
         ok = true;
         succ = key ^ ((u128)(1u << e) << shift);
       }
