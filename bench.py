@@ -178,8 +178,8 @@ def kernel_source_hash() -> str:
 
 def ncu_traffic_per_launch(load_factor_pct: int):
     """dram bytes per exploration launch from the committed ncu summary, or
-    None when the summary is missing or was taken on another kernel source or
-    another visited-set load factor."""
+    None when the summary is missing, was taken on another kernel source, or
+    holds no capture at this visited-set load factor."""
     try:
         fields = {}
         with open(TRAFFIC_FILE) as f:
@@ -189,9 +189,7 @@ def ncu_traffic_per_launch(load_factor_pct: int):
                     fields[k.strip()] = v.strip()
         if fields.get("kernel_source_sha256_16") != kernel_source_hash():
             return None
-        if int(fields.get("load_factor_pct", -1)) != int(load_factor_pct):
-            return None
-        return float(fields["dram_bytes_per_launch"])
+        return float(fields[f"dram_bytes_per_launch_lf{int(load_factor_pct)}"])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -278,7 +276,7 @@ def run_ours(args):
             best = min(best, mc.mc_get_stats(m)["explore_ms"])
         mc.mc_model_destroy(m)
         return best, ans
-    tuned = AT.tune(lf_measure, {"load_factor_pct": [15, 25]}, reps=1) if args.workload == "c2_star" else \
+    tuned = AT.tune(lf_measure, {"load_factor_pct": [10, 15, 25]}, reps=1) if args.workload == "c2_star" else \
         {"options": {}}
     opts = mc.mc_options_default(search=args.mode, prune=args.prune, timing=1, **tuned["options"])
     stream = torch.cuda.Stream(device)
