@@ -368,14 +368,17 @@ def run_ours(args):
             "frac_of_table_sized": probes / l2["sectors_per_s"],
             "note": "one 32-byte bucket read per generated successor (P per state)"}
 
-    # end to end through the public C-ABI from host buffers: create (H2D of
-    # the model arrays through pinned staging), query, read results, destroy
+    # end to end through the public C-ABI from host buffers, as a C caller
+    # makes the calls: create (H2D of the model arrays through pinned
+    # staging), query, read results, destroy; the library's own allocator and
+    # no kernel timing
+    e2e_opts = mc.mc_options_default(search=args.mode, prune=args.prune, **tuned["options"])
     e2e_s = []
     h2d = d2h = 0
     for k in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        m2 = mc.mc_model_create(spec, opts, allocator="torch", stream=stream)
+        m2 = mc.mc_model_create(spec, e2e_opts, allocator=None, stream=stream)
         if args.query == "count":
             r2 = {"t_min": None}
             mc.mc_count_states(m2)

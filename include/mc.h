@@ -37,8 +37,10 @@
  *     (default: the legacy default stream; see mc_set_stream) and return
  *     after that stream has finished the query's work.
  *   - Device memory comes from the allocator set by mc_set_allocator
- *     (default: cudaMalloc/cudaFree), allocated on the first query or by
- *     mc_reserve, and released by mc_model_destroy.
+ *     (default: the library's stream-ordered pool on the model's device,
+ *     which keeps up to 1 GiB of freed blocks for later models), allocated
+ *     on the first query or by mc_reserve, and released by
+ *     mc_model_destroy.  Pinned host staging is pooled the same way.
  *   - There is no CPU fallback: without a usable CUDA device, queries return
  *     MC_ERR_CUDA.
  */

@@ -7,17 +7,103 @@
 #include <chrono>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "mc.h"
+#include "mc_host.h"
 #include "mc_internal.h"
 
 using mc::Ctrl;
 using mc::ExploreArgs;
 using mc::kNone;
 using mc::Params;
+
+namespace mc {
+
+// Pinned host blocks, kept for reuse across models: pinning and unpinning
+// pages (cudaMallocHost / cudaFreeHost) cost tens of microseconds each, which
+// a create-query-destroy cycle would otherwise pay every time.  Blocks come
+// in power-of-two classes from 4 KiB; at most 64 MiB stay cached.
+namespace {
+std::mutex g_pinned_mu;
+std::multimap<size_t, void*> g_pinned_free;
+size_t g_pinned_cached = 0;
+constexpr size_t kPinnedCacheMax = 64ull << 20;
+
+size_t pinned_class(size_t bytes) {
+  size_t c = 4096;
+  while (c < bytes) c <<= 1;
+  return c;
+}
+}  // namespace
+
+void* pinned_alloc(size_t bytes) {
+  const size_t c = pinned_class(bytes);
+  {
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    auto it = g_pinned_free.find(c);
+    if (it != g_pinned_free.end()) {
+      void* p = it->second;
+      g_pinned_free.erase(it);
+      g_pinned_cached -= c;
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaHostAlloc(&p, c, cudaHostAllocPortable) != cudaSuccess) {  // pinned for every device
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+// The library's stream-ordered device pool of each device, made on first
+// use; freed blocks stay in it for reuse up to 1 GiB (the process's other
+// allocations and pools are left alone).
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+}  // namespace
+
+cudaMemPool_t device_pool(int dev) {
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = 1ull << 30;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+  }
+  return g_pools[dev];
+}
+
+void pinned_free(void* p, size_t bytes) {
+  const size_t c = pinned_class(bytes);
+  {
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    if (g_pinned_cached + c <= kPinnedCacheMax) {
+      g_pinned_free.emplace(c, p);
+      g_pinned_cached += c;
+      return;
+    }
+  }
+  cudaFreeHost(p);
+}
+
+}  // namespace mc
 
 namespace {
 
@@ -27,6 +113,7 @@ constexpr size_t kCtrlStride = 256 + mc::kBarBytes;  // one slot: header, then i
 struct Buf {
   void* ptr = nullptr;
   size_t bytes = 0;
+  bool pooled = false;  // from the library's stream-ordered pool
 };
 
 uint32_t bits_for(uint64_t x) {  // bits to store values 0..x
@@ -85,10 +172,12 @@ struct mc_model {
   Ctrl* d_ctrl = nullptr;
   uint64_t *d_levels = nullptr, *d_off = nullptr, *d_trace = nullptr;
   uint64_t *d_tini = nullptr, *d_tmin = nullptr;
-  Ctrl* h_ctrl = nullptr;       // pinned [kSlots]
-  uint64_t* h_trace = nullptr;  // pinned [(max_level + 2) * 2]
-  uint64_t* h_scalar = nullptr; // pinned [4]
-  uint32_t* h_params = nullptr; // pinned staging of N, cost, speed
+  uint8_t* h_block = nullptr;   // pinned host staging (from the pool), carved into:
+  size_t h_block_bytes = 0;
+  Ctrl* h_ctrl = nullptr;       // [kSlots]
+  uint64_t* h_trace = nullptr;  // [(max_level + 2) * 2]
+  uint64_t* h_scalar = nullptr; // [4]
+  uint32_t* h_params = nullptr; // staging of N, cost, speed
   cudaEvent_t ev[2 * kSlots] = {};
   bool ev_pending[kSlots] = {};
   mc_stats stats{};
@@ -98,6 +187,8 @@ struct mc_model {
 };
 
 namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 int cuda_fail(mc_model* m, cudaError_t e, const char* what) {
   m->last_err = std::string(what) + ": " + cudaGetErrorString(e);
@@ -109,6 +200,13 @@ int cuda_fail(mc_model* m, cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                              \
     if (e_ != cudaSuccess) return cuda_fail((m), e_, #call); \
   } while (0)
+
+// The timing events, made when a query first asks for timing.
+int make_events(mc_model* m) {
+  if (m->ev[0]) return MC_OK;
+  for (cudaEvent_t& e : m->ev) MC_CUDA(m, cudaEventCreate(&e));
+  return MC_OK;
+}
 
 // Makes the model's device current for the duration of a call.
 struct DeviceGuard {
@@ -122,17 +220,25 @@ struct DeviceGuard {
   }
 };
 
+// Device buffers: through the caller's allocator when one is set, else
+// stream-ordered from the library's pool on the model's device.
 void* dev_alloc(mc_model* m, size_t bytes) {
   if (bytes == 0) bytes = 256;
   bytes = (bytes + 255) & ~(size_t)255;
   void* p = nullptr;
+  bool pooled = false;
   if (m->alloc) {
     p = m->alloc(bytes, (void*)m->stream, m->actx);
-  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    p = nullptr;
+  } else {
+    cudaMemPool_t pool = mc::device_pool(m->device);
+    if (pool && cudaMallocFromPoolAsync(&p, bytes, pool, m->stream) == cudaSuccess) {
+      pooled = true;
+    } else {
+      cudaGetLastError();
+      p = nullptr;
+    }
   }
-  if (p) m->bufs.push_back({p, bytes});
+  if (p) m->bufs.push_back({p, bytes, pooled});
   return p;
 }
 
@@ -141,15 +247,14 @@ void release(mc_model* m) {
     DeviceGuard g(m->device);
     cudaStreamSynchronize(m->stream);
     for (const Buf& b : m->bufs) {
-      if (m->dealloc) m->dealloc(b.ptr, b.bytes, (void*)m->stream, m->actx);
+      if (b.pooled) cudaFreeAsync(b.ptr, m->stream);
+      else if (m->dealloc) m->dealloc(b.ptr, b.bytes, (void*)m->stream, m->actx);
       else cudaFree(b.ptr);
     }
     m->bufs.clear();
   }
-  if (m->h_ctrl) cudaFreeHost(m->h_ctrl);
-  if (m->h_trace) cudaFreeHost(m->h_trace);
-  if (m->h_scalar) cudaFreeHost(m->h_scalar);
-  if (m->h_params) cudaFreeHost(m->h_params);
+  if (m->h_block) mc::pinned_free(m->h_block, m->h_block_bytes);
+  m->h_block = nullptr;
   for (cudaEvent_t& e : m->ev) {
     if (e) cudaEventDestroy(e);
     e = nullptr;
@@ -253,21 +358,31 @@ int reserve(mc_model* m) {
   m->d_tini = (uint64_t*)q;
   m->d_tmin = (uint64_t*)q + 1;
 
-  if (cudaMallocHost((void**)&m->h_ctrl, sizeof(Ctrl) * kSlots) != cudaSuccess ||
-      cudaMallocHost((void**)&m->h_trace, 16 * L2) != cudaSuccess ||
-      cudaMallocHost((void**)&m->h_scalar, 32) != cudaSuccess ||
-      cudaMallocHost((void**)&m->h_params, np * 4) != cudaSuccess) {
-    cudaGetLastError();
+  // host staging: one pinned block, carved (from the process-wide pool)
+  const size_t o_trace = align_up(sizeof(Ctrl) * kSlots, 64);
+  const size_t o_scalar = o_trace + align_up(16 * L2, 64);
+  const size_t o_params = o_scalar + 64;
+  m->h_block_bytes = o_params + np * 4;
+  m->h_block = (uint8_t*)mc::pinned_alloc(m->h_block_bytes);
+  if (!m->h_block) {
     release(m);
     return MC_ERR_NOMEM;
   }
-  for (cudaEvent_t& e : m->ev) MC_CUDA(m, cudaEventCreate(&e));
+  m->h_ctrl = (Ctrl*)m->h_block;
+  m->h_trace = (uint64_t*)(m->h_block + o_trace);
+  m->h_scalar = (uint64_t*)(m->h_block + o_scalar);
+  m->h_params = (uint32_t*)(m->h_block + o_params);
+  if (m->opt.timing) {
+    const int rc_ = make_events(m);
+    if (rc_) return rc_;
+  }
   std::copy(m->N.begin(), m->N.end(), m->h_params);
   std::copy(m->cost.begin(), m->cost.end(), m->h_params + (size_t)m->a * m->b);
   std::copy(m->speed.begin(), m->speed.end(), m->h_params + 2ull * m->a * m->b);
+  // stream-ordered before every query's kernels; the pinned staging is not
+  // written again, so the host need not wait for the copy
   MC_CUDA(m, cudaMemcpyAsync(m->d_params, m->h_params, np * 4, cudaMemcpyHostToDevice, m->stream));
   m->stats.h2d_bytes += np * 4;
-  MC_CUDA(m, cudaStreamSynchronize(m->stream));
 
   Params& p = m->params;
   p.a = m->a;
@@ -329,6 +444,10 @@ int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, 
   A.bar_lines = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(A.ctrl) + 256);
   A.timeout_ns = m->opt.barrier_timeout_ns ? m->opt.barrier_timeout_ns : 60ull * 1000000000ull;
   MC_CUDA(m, cudaMemsetAsync(A.ctrl, 0, kCtrlStride, m->stream));
+  if (m->opt.timing) {
+    const int rc_ = make_events(m);
+    if (rc_) return rc_;
+  }
   if (m->opt.timing) MC_CUDA(m, cudaEventRecord(m->ev[2 * slot], m->stream));
   MC_CUDA(m, mc::launch_explore(m->key_words, m->tile, m->rule, m->grid, m->threads, A, m->stream));
   if (m->opt.timing) {
@@ -690,6 +809,12 @@ int mc_min_time(mc_model* m, mc_min_result* out, mc_trace** trace) {
         if (p == 0) MC_TRY(enqueue_pass(m, 0, m->d_tini, 0, prune, ee, true, nullptr, 0));
         else MC_TRY(enqueue_pass(m, 0, nullptr, 0, prune, ee, true, nullptr, p % kSlots, (p - 1) % kSlots));
       }
+      // the trace buffer then holds the last failing check's trace (a check
+      // that holds or does not run leaves it alone): read it with the group
+      if (trace) {
+        MC_CUDA(m, cudaMemcpyAsync(m->h_trace, m->d_trace, 16 * L2, cudaMemcpyDeviceToHost, m->stream));
+        m->stats.d2h_bytes += 16 * L2;
+      }
       MC_TRY(sync(m));
       for (int q = first; q < p && !held; ++q) {
         const int slot = q % kSlots;
@@ -707,11 +832,6 @@ int mc_min_time(mc_model* m, mc_min_result* out, mc_trace** trace) {
       return MC_ERR_CUDA;
     }
     final_slot = last;
-    if (trace) {
-      MC_CUDA(m, cudaMemcpyAsync(m->h_trace, m->d_trace, 16 * L2, cudaMemcpyDeviceToHost, m->stream));
-      m->stats.d2h_bytes += 16 * L2;
-      MC_TRY(sync(m));
-    }
   } else {
     MC_CUDA(m, cudaMemcpyAsync(m->h_scalar, m->d_tini, 8, cudaMemcpyDeviceToHost, m->stream));
     m->stats.d2h_bytes += 8;

@@ -22,6 +22,7 @@
 
 #include "mc.h"
 #include "mc_device.cuh"
+#include "mc_host.h"
 #include "mc_internal.h"
 #include "mc_pe.h"
 
@@ -586,8 +587,10 @@ struct mc_pe_model {
   mc::Ctrl* d_ctrl = nullptr;
   uint32_t* d_bar = nullptr;
   uint64_t *d_levels = nullptr, *d_off = nullptr, *d_trace = nullptr, *d_tmin = nullptr;
-  mc::Ctrl* h_ctrl = nullptr;    // pinned [3]
-  uint64_t* h_trace = nullptr;   // pinned [(max_level + 2) * 2]
+  uint8_t* h_block = nullptr;    // pinned host staging (pooled), carved into:
+  size_t h_block_bytes = 0;
+  mc::Ctrl* h_ctrl = nullptr;    // [3]
+  uint64_t* h_trace = nullptr;   // [(max_level + 2) * 2]
   cudaEvent_t ev[6] = {};
   bool ev_pending[3] = {};
   bool reserved = false;
@@ -628,8 +631,8 @@ void pe_release(mc_pe_model* m) {
     m->bufs.clear();
     if (prev >= 0 && prev != m->device) cudaSetDevice(prev);
   }
-  if (m->h_ctrl) cudaFreeHost(m->h_ctrl);
-  if (m->h_trace) cudaFreeHost(m->h_trace);
+  if (m->h_block) mc::pinned_free(m->h_block, m->h_block_bytes);
+  m->h_block = nullptr;
   for (cudaEvent_t& e : m->ev) {
     if (e) cudaEventDestroy(e);
     e = nullptr;
@@ -703,13 +706,17 @@ int pe_reserve(mc_pe_model* m) {
   m->d_trace = (uint64_t*)q;
   q += 16 * L2;
   m->d_tmin = (uint64_t*)q;
-  if (cudaMallocHost((void**)&m->h_ctrl, sizeof(Ctrl) * 3) != cudaSuccess ||
-      cudaMallocHost((void**)&m->h_trace, 16 * L2) != cudaSuccess) {
-    cudaGetLastError();
+  const size_t o_trace = (sizeof(Ctrl) * 3 + 63) / 64 * 64;
+  m->h_block_bytes = o_trace + 16 * L2;
+  m->h_block = (uint8_t*)mc::pinned_alloc(m->h_block_bytes);
+  if (!m->h_block) {
     pe_release(m);
     return MC_ERR_NOMEM;
   }
-  for (cudaEvent_t& e : m->ev) PE_CUDA(m, cudaEventCreate(&e));
+  m->h_ctrl = (Ctrl*)m->h_block;
+  m->h_trace = (uint64_t*)(m->h_block + o_trace);
+  if (m->opt.timing && !m->ev[0])
+    for (cudaEvent_t& e : m->ev) PE_CUDA(m, cudaEventCreate(&e));
   std::vector<uint32_t> cfg(4 * ab);
   std::copy(m->N.begin(), m->N.end(), cfg.begin());
   std::copy(m->tau.begin(), m->tau.end(), cfg.begin() + ab);
@@ -760,6 +767,8 @@ int pe_enqueue(mc_pe_model* m, uint64_t T, const uint64_t* T_src, int64_t delta,
   A.slots = (lanes + m->lay.tile - 1) / m->lay.tile;
   static_assert(sizeof(Ctrl) <= 256, "control block header");
   PE_CUDA(m, cudaMemsetAsync(m->d_ctrl, 0, 256 + mc::kBarBytes, m->stream));
+  if (m->opt.timing && !m->ev[0])
+    for (cudaEvent_t& e : m->ev) PE_CUDA(m, cudaEventCreate(&e));
   if (m->opt.timing) PE_CUDA(m, cudaEventRecord(m->ev[2 * slot], m->stream));
   void* args[] = {&A};
   PE_CUDA(m, cudaLaunchCooperativeKernel(mc::pe_pick(m->lay.tile), dim3(m->grid), dim3(m->threads), args, 0,

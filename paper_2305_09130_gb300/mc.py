@@ -293,7 +293,7 @@ def mc_model_create(spec, options: Optional[McOptions] = None, allocator: Option
                     stream=None) -> Model:
     """Create a model from a ``workloads.ModelSpec`` (or any object with the
     same fields).  ``allocator``: "torch" (PyTorch caching allocator),
-    "cuda" (the library's cudaMalloc) or None (same as "cuda")."""
+    "cuda" (the library's own stream-ordered pool) or None (same as "cuda")."""
     L = load()
     arrs = (_u32(spec.wg_values), _u32(spec.ts_values), _u32(spec.n_workgroups), _u32(spec.cost),
             _u32(spec.speed))

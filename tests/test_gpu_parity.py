@@ -127,6 +127,21 @@ def test_simulation_matches_oracle(mc, oracle):
                 assert mc.mc_simulate(model, seed, walks) == oracle.simulate(spec, seed, walks)
 
 
+def test_library_allocator_create_query_destroy_cycles(mc, oracle):
+    """The library's own device pool and pooled pinned staging: many models
+    made, queried and destroyed in a row (buffers reused across them), with
+    models on the PyTorch allocator in between, all give the oracle's answers."""
+    exp = oracle.min_time(W.c1(FREE))
+    exp_g = oracle.min_time(W.c1(GREEDY))
+    for k in range(24):
+        spec = W.c1(FREE) if k % 2 == 0 else W.c1(GREEDY)
+        want = exp if k % 2 == 0 else exp_g
+        m = mc.mc_model_create(spec, allocator=None if k % 3 else "torch")
+        r = mc.mc_min_time(m, trace=(k % 4 == 0))
+        assert (r["t_min"], r["i"], r["j"], r["states"]) == (want["t_min"], want["i"], want["j"], want["states"])
+        mc.mc_model_destroy(m)
+
+
 def test_key_width_does_not_change_results(mc):
     spec = W.c1(FREE)
     a = make(mc, spec)
