@@ -750,18 +750,19 @@ def run_c5(args):
 
     # one-query-at-a-time service times on a sample of the same query stream:
     # end to end as a caller of the single-model API sees it (create the
-    # model from host arrays, mc_min_time, read the result, destroy; PyTorch's
-    # caching allocator), and the exploration's device time alone
+    # model from host arrays, mc_min_time, read the result, destroy; the
+    # library's own pooled allocator, its fastest path), and the
+    # exploration's device time alone
     sample = [make_query(10_000_000 + k) for k in range(args.c5_sample)]
     for sp in sample[:3]:  # warm the allocator and the library
-        m = mc.mc_model_create(sp)
+        m = mc.mc_model_create(sp, allocator=None)
         mc.mc_min_time(m, trace=False)
         mc.mc_model_destroy(m)
     service, service_dev, service_states = [], [], []
     for sp in sample:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        m = mc.mc_model_create(sp)
+        m = mc.mc_model_create(sp, allocator=None)
         r = mc.mc_min_time(m, trace=False)
         mc.mc_model_destroy(m)
         service.append(time.perf_counter() - t0)
