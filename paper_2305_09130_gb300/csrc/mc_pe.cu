@@ -371,10 +371,12 @@ __device__ void pe_expand_level(const PeArgs& A, PeStage<TILE>& st, uint64_t T, 
   }
 }
 
-// Register budgets: 64 per thread (4 blocks of 256 per SM) for tiles of 16
-// and 32 lanes, 85 (3 blocks) for the three-successor tiles, which spill at 64.
+// Register budgets: 64 per thread (4 blocks of 256 per SM) for warp-wide
+// tiles (one successor per lane), 85 (3 blocks) for the narrower tiles, whose
+// lanes propose two or three successors and spill at 64 (the Minimum model
+// measured 4% faster at 16 lanes without the spill).
 template <int TILE>
-__global__ void __launch_bounds__(kThreads, TILE >= 16 ? 4 : 3) pe_explore_kernel(const PeArgs A) {
+__global__ void __launch_bounds__(kThreads, TILE >= 32 ? 4 : 3) pe_explore_kernel(const PeArgs A) {
   const PeParams& p = A.p;
   Ctrl* ctrl = A.ctrl;
   const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
