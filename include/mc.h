@@ -431,6 +431,12 @@ int mc_measure_random_access(uint64_t buffer_bytes, uint64_t accesses, int op,
 int mc_check_noalloc(const mc_model_desc* desc, uint64_t T, uint32_t prune, uint32_t early_exit,
                      void* stream, mc_check_result* out);
 
+/* Give the library's cached memory back: the freed device blocks kept in its
+ * stream-ordered pools (up to 1 GiB per device) and the pinned host blocks
+ * kept for reuse (up to 64 MiB).  Models in use keep theirs.  Safe at any
+ * time, also without a device.  Returns MC_OK. */
+int mc_release_cached(void);
+
 /* Static name of an error code. */
 const char* mc_strerror(int code);
 

@@ -90,6 +90,22 @@ cudaMemPool_t device_pool(int dev) {
   return g_pools[dev];
 }
 
+void release_cached() {
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    for (cudaMemPool_t pool : g_pools)
+      if (pool) cudaMemPoolTrimTo(pool, 0);
+  }
+  std::multimap<size_t, void*> blocks;
+  {
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    blocks.swap(g_pinned_free);
+    g_pinned_cached = 0;
+  }
+  for (auto& b : blocks) cudaFreeHost(b.second);
+  cudaGetLastError();
+}
+
 void pinned_free(void* p, size_t bytes) {
   const size_t c = pinned_class(bytes);
   {
@@ -997,6 +1013,11 @@ uint32_t mc_trace_key_words(const mc_trace* t) { return t ? t->words : 0; }
 const uint64_t* mc_trace_states(const mc_trace* t) { return t && !t->keys.empty() ? t->keys.data() : nullptr; }
 
 void mc_trace_free(mc_trace* t) { delete t; }
+
+int mc_release_cached(void) {
+  mc::release_cached();
+  return MC_OK;
+}
 
 const char* mc_strerror(int code) {
   switch (code) {

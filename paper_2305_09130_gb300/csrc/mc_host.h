@@ -15,4 +15,7 @@ void pinned_free(void* p, size_t bytes);
 // The library's stream-ordered device pool of a device.
 cudaMemPool_t device_pool(int device);
 
+// Trim every device pool and free the cached pinned blocks.
+void release_cached();
+
 }  // namespace mc

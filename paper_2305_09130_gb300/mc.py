@@ -237,6 +237,7 @@ def load(build: bool = True):
             "mc_trace_states": (C.POINTER(C.c_uint64), [P]),
             "mc_trace_free": (None, [P]),
             "mc_strerror": (C.c_char_p, [C.c_int]),
+            "mc_release_cached": (C.c_int, []),
             "mc_last_error": (C.c_char_p, [P]),
         }
         for name, (res, args) in sig.items():
@@ -245,6 +246,13 @@ def load(build: bool = True):
             f.argtypes = args
         _lib = L
         return L
+
+
+def mc_release_cached():
+    """Give back the library's cached device blocks and pinned host blocks."""
+    rc = load(build=False).mc_release_cached()
+    if rc != MC_OK:
+        raise MCError(rc, "mc_release_cached")
 
 
 def mc_strerror(code: int) -> str:

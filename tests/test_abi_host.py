@@ -102,6 +102,11 @@ def test_invalid_descriptions(lib):
     assert e.value.code == mc.MC_ERR_INVAL
 
 
+def test_release_cached_is_safe_without_a_device(lib):
+    mc.mc_release_cached()
+    mc.mc_release_cached()
+
+
 def test_strerror(lib):
     assert mc.mc_strerror(mc.MC_ERR_TABLE_FULL).startswith("visited set full")
     assert mc.mc_strerror(-99) == "unknown error"
