@@ -790,6 +790,8 @@ def run_c5(args):
         specs = [make_query(qid + k) for k in range(n)]
         qid += n
         got = {}
+        sampler = ClockSampler(local)
+        sampler.start()
         t0 = time.perf_counter()
         for k in range(n):
             while time.perf_counter() - t0 < arrivals[k]:
@@ -802,6 +804,7 @@ def run_c5(args):
                 got[r["ticket"]] = r
             if time.perf_counter() - t0 > arrivals[-1] + 600:
                 raise SystemExit(f"served run at {rate}/s did not finish: {mc.mc_server_status(srv)}")
+        clocks = sampler.stop()
         res = list(got.values())
         assert all(r["status"] == 0 for r in res)
         lat = [1000.0 * (r["done_s"] - r["submit_s"]) for r in res]
@@ -829,6 +832,7 @@ def run_c5(args):
             "sequential_device_only": {
                 "throughput_qps": n / (clock_dev - arrivals[0]) if clock_dev > arrivals[0] else None,
                 "latency_ms_p50": percentile(seq_lat_dev, 50), "latency_ms_p99": percentile(seq_lat_dev, 99)},
+            "clocks": clocks,
         })
     status = mc.mc_server_status(srv)
     mc.mc_server_destroy(srv)
@@ -849,7 +853,7 @@ def run_c5(args):
                            "times each query end to end through the single-model C-ABI (create, "
                            "mc_min_time, destroy), as the served latency is measured from submit to "
                            "result; 'sequential_device_only' counts the exploration's device time alone"},
-        "sweep": sweep, "device_loop_launches": status["launches"],
+        "sweep": sweep, "device_loop_launches": status["launches"], "clocks": top["clocks"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
