@@ -252,6 +252,10 @@ void* dev_alloc(mc_model* m, size_t bytes) {
     } else {
       cudaGetLastError();
       p = nullptr;
+      if (!pool && cudaMalloc(&p, bytes) != cudaSuccess) {  // no pool on this device: plain allocation
+        cudaGetLastError();
+        p = nullptr;
+      }
     }
   }
   if (p) m->bufs.push_back({p, bytes, pooled});
