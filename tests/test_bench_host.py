@@ -1,0 +1,30 @@
+"""Host-side pieces of bench.py (no GPU): the DRAM-traffic lookup that fills
+roofline.traffic from the committed ncu summary."""
+import bench
+
+
+def _write(tmp_path, body):
+    p = tmp_path / "traffic.txt"
+    p.write_text(body)
+    return str(p)
+
+
+def test_traffic_is_read_per_load_factor(tmp_path, monkeypatch):
+    h = bench.kernel_source_hash()
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", _write(tmp_path, f"""# comment: 1
+kernel_source_sha256_16: {h}
+dram_bytes_per_launch_lf10: 100
+dram_bytes_per_launch_lf15: 200
+"""))
+    assert bench.ncu_traffic_per_launch(10) == 100.0
+    assert bench.ncu_traffic_per_launch(15) == 200.0
+    assert bench.ncu_traffic_per_launch(25) is None  # no capture at that load factor
+
+
+def test_traffic_is_null_for_other_kernel_sources(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", _write(tmp_path, """kernel_source_sha256_16: 0000000000000000
+dram_bytes_per_launch_lf10: 100
+"""))
+    assert bench.ncu_traffic_per_launch(10) is None
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "missing.txt"))
+    assert bench.ncu_traffic_per_launch(10) is None

@@ -191,10 +191,10 @@ def test_c3_literal_greedy_u128(mc, oracle):
     assert got["t_min"] == CF.tmin(spec)[0]
 
 
-@pytest.mark.parametrize("load_factor_pct", [25, 15])
+@pytest.mark.parametrize("load_factor_pct", [25, 15, 10])
 def test_c2_star_full(mc, load_factor_pct):
-    """C2 at G=80 at full size; load factor 15% is the visited-set size the
-    benchmark's inline tuner picks (the bench's launch configuration)."""
+    """C2 at G=80 at full size; load factors of 10% and 15% are the visited-set
+    sizes the benchmark's inline tuner picks (the bench's launch configuration)."""
     spec = W.c2_star()
     g = golden()["c2_star"]
     model = make(mc, spec, load_factor_pct=load_factor_pct)
