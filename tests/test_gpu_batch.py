@@ -112,6 +112,36 @@ def test_batch_equals_single_model_queries(mc):
         mc.mc_model_destroy(m)
 
 
+def test_batch_full_c4_in_the_bench_configuration(mc):
+    """All 256 C4 instances in one launch with the options the benchmark's
+    tuner picks (one block per SM, load factor 25%), run twice through the
+    captured graph: every answer equals the single-model entry point's and the
+    closed-form minimal time."""
+    specs = W.c4_instances(256)
+    t_mins = [CF.tmin(s)[0] for s in specs]
+    queries = [("min_time", None) if s.meta["query"] else ("check", round(t * s.meta["t_frac_milli"] / 1000))
+               for s, t in zip(specs, t_mins)]
+    b = mc.mc_batch_create(specs, mc.mc_options_default(blocks_per_sm=1, load_factor_pct=25))
+    first = mc.mc_batch_run(b, queries)
+    again = mc.mc_batch_run(b, queries)
+    assert [(r["status"], r["time"], r["states"], r["key"]) for r in first] == \
+           [(r["status"], r["time"], r["states"], r["key"]) for r in again]
+    for spec, q, r, t_min in zip(specs, queries, first, t_mins):
+        assert r["status"] == 0
+        m = mc.mc_model_create(spec.with_key_bits(128))
+        if q[0] == "min_time":
+            s = mc.mc_min_time(m, trace=False)
+            assert r["time"] == s["t_min"] == t_min
+            assert (r["i"], r["j"], r["states"], r["checks"], r["key"]) == \
+                   (s["i"], s["j"], s["states"], s["checks"], s["witness_key"])
+        else:
+            s = mc.mc_check(m, q[1], trace=False)
+            assert r["holds"] == s["holds"] == (q[1] < t_min)
+            assert (r["states"], r["levels"]) == (s["states"], s["levels"])
+        mc.mc_model_destroy(m)
+    assert mc.mc_batch_get_stats(b)["graph_launches"] == 2
+
+
 def test_batch_errors_are_per_instance(mc):
     specs = [W.c1(W.FREE), W.tiny(W.GREEDY)]
     b = mc.mc_batch_create(specs, mc.mc_options_default(table_log2=3, max_probes=1))
