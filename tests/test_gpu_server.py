@@ -74,6 +74,34 @@ def test_served_results_equal_alone_and_in_mix(mc):
     mc.mc_server_destroy(srv)
 
 
+def test_c5_shaped_queries_in_the_benchmark_server(mc):
+    """Min-time queries drawn as the served benchmark draws them (G=4096,
+    P=8, a new seed each, 128-bit keys), on a server with its slot count:
+    submitted together they share the device loop, and each answer equals the
+    single-model entry point's; one of them alone takes the latency path with
+    the same answer."""
+    specs = [W.c3(G=4096, rule=W.GREEDY, seed=2305091305 * 1000003 + 20_000_000 + k, key_bits=128)
+             for k in range(16)]
+    srv = mc.mc_server_create(slots=512, pool_bytes=8 << 30)
+    tickets = {mc.mc_server_submit(srv, s, "min_time"): k for k, s in enumerate(specs)}
+    got = collect(mc, srv, len(specs))
+    assert sum(r["path"] == "loop" for r in got.values()) >= len(specs) - 2
+    for t, k in tickets.items():
+        r = got[t]
+        exp = single(mc, specs[k], "min_time", None)
+        for key in KEYS:
+            if exp[key] is not None:
+                assert r[key] == exp[key], (k, key, r, exp)
+    mc.mc_server_destroy(srv)
+    alone = mc.mc_server_create(slots=512, pool_bytes=8 << 30)
+    t = mc.mc_server_submit(alone, specs[5], "min_time")
+    r = collect(mc, alone, 1)[t]
+    assert r["path"] == "alone"
+    exp = single(mc, specs[5], "min_time", None)
+    assert {k: r[k] for k in KEYS if exp[k] is not None} == {k: exp[k] for k in KEYS if exp[k] is not None}
+    mc.mc_server_destroy(alone)
+
+
 def test_requests_join_a_running_device_loop(mc):
     # a long GREEDY search is running when small queries arrive: they are
     # admitted into the same device loop and finish first
