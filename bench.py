@@ -176,10 +176,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_launch(load_factor_pct: int):
+def ncu_traffic_per_launch(load_factor_pct: int, probe_scheme: str):
     """dram bytes per exploration launch from the committed ncu summary, or
     None when the summary is missing, was taken on another kernel source, or
-    holds no capture at this visited-set load factor."""
+    holds no capture at this visited-set load factor and probe scheme
+    ("split" or "one_call")."""
     try:
         fields = {}
         with open(TRAFFIC_FILE) as f:
@@ -189,7 +190,7 @@ def ncu_traffic_per_launch(load_factor_pct: int):
                     fields[k.strip()] = v.strip()
         if fields.get("kernel_source_sha256_16") != kernel_source_hash():
             return None
-        return float(fields[f"dram_bytes_per_launch_lf{int(load_factor_pct)}"])
+        return float(fields[f"dram_bytes_per_launch_lf{int(load_factor_pct)}_{probe_scheme}"])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -259,13 +260,25 @@ def run_ours(args):
     dist_init(world, True)
     spec = WORKLOADS[args.workload][0]()
     workload = WORKLOADS[args.workload][1] or WORKLOAD
-    # visited-set load factor from the autotuner (outside the timed region;
-    # every candidate must return the same answer); launch shape at the
+    # visited-set load factor (C2 at G=80) and probe scheme from the
+    # autotuner (outside the timed region; every candidate must return the
+    # same answer) unless fixed on the command line; launch shape at the
     # occupancy maximum, which the tuner also picks for this kernel
     from paper_2305_09130_gb300 import autotune as AT
 
+    space, fixed = {}, {}
+    if args.load_factor:
+        fixed["load_factor_pct"] = args.load_factor
+    elif args.workload == "c2_star":
+        space["load_factor_pct"] = [10, 15]
+    if args.probe_scheme == "tune":
+        space["probe_scheme"] = [mc.PROBE["split"], mc.PROBE["one_call"]]
+    else:
+        fixed["probe_scheme"] = mc.PROBE[args.probe_scheme]
+
     def lf_measure(c):
-        m = mc.mc_model_create(spec, mc.mc_options_default(search=args.mode, prune=args.prune, timing=1, **c),
+        m = mc.mc_model_create(spec, mc.mc_options_default(search=args.mode, prune=args.prune, timing=1,
+                                                           **fixed, **c),
                                allocator="torch")
         run = (lambda: mc.mc_count_states(m)) if args.query == "count" else (lambda: mc.mc_min_time(m, trace=False))
         run()
@@ -276,13 +289,14 @@ def run_ours(args):
             best = min(best, mc.mc_get_stats(m)["explore_ms"])
         mc.mc_model_destroy(m)
         return best, ans
-    tuned = AT.tune(lf_measure, {"load_factor_pct": [10, 15, 25]}, reps=1) if args.workload == "c2_star" else \
-        {"options": {}}
-    opts = mc.mc_options_default(search=args.mode, prune=args.prune, timing=1, **tuned["options"])
+    tuned = AT.tune(lf_measure, space, reps=1) if space else {"options": {}}
+    chosen = {**fixed, **tuned["options"]}
+    opts = mc.mc_options_default(search=args.mode, prune=args.prune, timing=1, **chosen)
     stream = torch.cuda.Stream(device)
     model = mc.mc_model_create(spec, opts, allocator="torch", stream=stream)
     mc.mc_reserve(model)
     layout = mc.mc_model_layout(model)
+    scheme = "split" if layout["probe_scheme"] == mc.PROBE["split"] else "one_call"
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > 129 MB of L2
 
     def flush_l2(k):
@@ -338,7 +352,7 @@ def run_ours(args):
     launches = st["explore_launches"]
     achieved = bps * st["states"] / (st["explore_ms"] / 1000.0) / 1e9
     peak, peak_kind = measured_hbm_peak()
-    traffic = (ncu_traffic_per_launch(opts.load_factor_pct)
+    traffic = (ncu_traffic_per_launch(opts.load_factor_pct, scheme)
                if (args.workload, args.query) == ("c2_star", "min_time") else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
@@ -346,7 +360,7 @@ def run_ours(args):
                 "bytes_per_state": bps, "states_per_launch": st["states"] / max(launches, 1),
                 "avg_launch_ms": st["explore_ms"] / max(launches, 1),
                 "kernel": f"explore_kernel<u{64 * layout['key_words']}, tile {1 << (spec.P - 1).bit_length()}, "
-                          f"{'FREE' if spec.rule == W.FREE else 'GREEDY'}>",
+                          f"{'FREE' if spec.rule == W.FREE else 'GREEDY'}, {scheme} insert>",
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                                if peak_kind == "measured" else "fallback 6.8 TB/s"}
     gpu_launches = st["explore_launches"] + st["other_launches"]
@@ -372,7 +386,7 @@ def run_ours(args):
     # makes the calls: create (H2D of the model arrays through pinned
     # staging), query, read results, destroy; the library's own allocator and
     # no kernel timing
-    e2e_opts = mc.mc_options_default(search=args.mode, prune=args.prune, **tuned["options"])
+    e2e_opts = mc.mc_options_default(search=args.mode, prune=args.prune, **chosen)
     e2e_s = []
     h2d = d2h = 0
     for k in range(args.steps):
@@ -403,7 +417,9 @@ def run_ours(args):
                              f"(iterative threshold lowering from the simulated T_ini)"
                              if args.query == "min_time" else "mc_count_states (every reachable state)"),
                    "l2": "flushed between steps (256 MiB write, untimed)",
-                   "autotuned": tuned["options"],
+                   "autotuned": tuned["options"], "autotune_ms": tuned.get("timings", {}),
+                   "options_fixed": fixed,
+                   "probe_scheme": scheme,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "states_per_step": states_local / args.steps,
                    "checks_per_step": r["checks"]},
@@ -870,6 +886,10 @@ def main(argv=None):
     p.add_argument("--prune", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-random-roofline", action="store_true")
+    p.add_argument("--load-factor", type=int, default=0,
+                   help="visited-set load factor in percent (0: the autotuner picks it for c2_star)")
+    p.add_argument("--probe-scheme", choices=["tune", "auto", "split", "one_call"], default="tune",
+                   help="visited-set insert of the exploration kernel (tune: the autotuner picks it)")
     p.add_argument("--rates", default="10,30,100,300,1000", help="c5 arrival rates (queries/s)")
     p.add_argument("--slots", type=int, default=512, help="c5 requests on the device at once")
     p.add_argument("--c5-seconds", type=float, default=10.0, help="c5 arrivals per rate span")

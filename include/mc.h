@@ -76,6 +76,20 @@ typedef enum {
   MC_SEARCH_BISECT = 2  /* bisection between 0 and T_ini (Fig. 1)            */
 } mc_search;
 
+/* How the exploration kernel inserts a successor into the visited set
+ * (mc_options.probe_scheme).  Both fetch the successor's first 32-byte bucket
+ * into shared memory first; the results are identical, only the speed
+ * differs. */
+typedef enum {
+  MC_PROBE_AUTO = 0,     /* SPLIT with 64-bit keys, ONE_CALL with 128-bit     */
+  MC_PROBE_SPLIT = 1,    /* pick the slot from the fetched bucket, issue the
+                            CAS of every proposal of the round, then resolve
+                            (a lost slot or a full bucket falls back to the
+                            general insert from the same bucket)              */
+  MC_PROBE_ONE_CALL = 2  /* the general insert (scan, CAS, next bucket) from
+                            the fetched bucket, one proposal at a time        */
+} mc_probe_scheme;
+
 typedef struct mc_model mc_model;
 typedef struct mc_trace mc_trace;
 
@@ -125,7 +139,11 @@ typedef struct {
                                    warp tile that expands one state: 4 or 8
                                    (up to 3 successors per lane), 16 (up to
                                    2) or 32 (1); 0 = the smallest that fits */
-  uint32_t reserved[5];
+  uint32_t probe_scheme;        /* mc_probe_scheme of the single-model
+                                   explorer (mc_check, mc_min_time,
+                                   mc_count_states); batches and the PE-level
+                                   model keep their own                      */
+  uint32_t reserved[4];
 } mc_options;
 
 /* Result of mc_check (Section 4, Step 2: Phi = G(FIN -> time > T)). */
@@ -173,6 +191,9 @@ typedef struct {
   uint64_t max_width;    /* bound on one level's width                     */
   uint64_t state_bound;  /* bound on all reachable states (saturates)      */
   uint64_t device_bytes; /* device memory the model needs                  */
+  uint32_t probe_scheme; /* the insert its explorations use: MC_PROBE_SPLIT
+                            or MC_PROBE_ONE_CALL (AUTO resolved)           */
+  uint32_t reserved;
 } mc_layout;
 
 /* Counters accumulated over the model's queries (reset by mc_reset_stats). */
@@ -211,7 +232,8 @@ void mc_model_destroy(mc_model* m);
 
 /* Replace the options of later queries.  Options that size buffers or the
  * launch (load_factor_pct, table_log2, log_capacity, threads_per_block,
- * blocks_per_sm) only act before the buffers exist.  Errors: INVAL. */
+ * blocks_per_sm, probe_scheme) only act before the buffers exist.  Errors:
+ * INVAL. */
 int mc_set_options(mc_model* m, const mc_options* opt);
 
 /* CUDA stream (a cudaStream_t, NULL = legacy default stream) for every later

@@ -1,7 +1,10 @@
 """Autotuner for the explorer's launch and table parameters, with a JSON cache.
 
 The knobs are the runtime options of ``mc_options``: threads per block,
-blocks per SM (the persistent grid) and the visited-set load factor; for the
+blocks per SM (the persistent grid), the visited-set load factor and the
+probe scheme of the insert (split: pick a slot from the fetched bucket and
+issue every CAS of the round before resolving any; one call: the general
+insert per proposal); for batches the grid and the load factor; for the
 processing-element level model, the lanes that expand one state (a quarter,
 half or whole warp) and the grid.  A
 candidate is timed on the real query through the C-ABI (CUDA events recorded
@@ -26,6 +29,7 @@ DEFAULT_SPACE = {
     "threads_per_block": [128, 256],
     "blocks_per_sm": [0, 2, 3],
     "load_factor_pct": [25, 50],
+    "probe_scheme": [1, 2],  # mc_probe_scheme: split, one call
 }
 KNOBS = tuple(DEFAULT_SPACE)
 
@@ -132,7 +136,8 @@ def tune_batch(specs, queries, space=None, reps: int = 2, cache: Optional[dict] 
     from . import mc
 
     mc.load()
-    space = {k: v for k, v in (space or DEFAULT_SPACE).items() if k != "threads_per_block"}
+    # the lockstep kernel has one block size and one probe scheme
+    space = {k: v for k, v in (space or DEFAULT_SPACE).items() if k not in ("threads_per_block", "probe_scheme")}
     lay = mc.mc_model_layout(mc.mc_model_create(specs[0].with_key_bits(128), allocator=None))
     sig = signature(lay, specs[0], "batch", len(specs))
     cache = load_cache(path) if cache is None else cache

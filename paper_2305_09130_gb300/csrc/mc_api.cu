@@ -175,6 +175,7 @@ struct mc_model {
   bool reserved = false;
   int device = -1;
   int grid = 0, threads = 0;
+  bool split = true;  // probe scheme of the exploration kernel (resolved at reserve)
   cudaStream_t stream = nullptr;
   mc_alloc_fn alloc = nullptr;
   mc_free_fn dealloc = nullptr;
@@ -294,7 +295,15 @@ bool valid_options(const mc_options* o) {
                                o->threads_per_block % 32))
     return false;
   if (o->table_log2 && (o->table_log2 < 3 || o->table_log2 > 40)) return false;
+  if (o->probe_scheme > MC_PROBE_ONE_CALL) return false;
   return true;
+}
+
+// the probe scheme of the exploration kernel: AUTO follows the key width
+// (the split insert measured faster with 64-bit keys, the one-call insert
+// with 128-bit keys)
+bool resolve_split(uint32_t scheme, uint32_t key_words) {
+  return scheme == MC_PROBE_AUTO ? key_words == 1 : scheme == MC_PROBE_SPLIT;
 }
 
 // sizes of the frontier log and the visited set
@@ -344,8 +353,9 @@ int reserve(mc_model* m) {
     return MC_ERR_CUDA;
   }
   m->threads = m->opt.threads_per_block ? (int)m->opt.threads_per_block : (int)mc::kThreads;
+  m->split = resolve_split(m->opt.probe_scheme, m->key_words);
   int bps = 0;
-  if (mc::explore_kernel_occupancy(m->key_words, m->tile, m->rule, m->threads, &bps) || bps < 1) {
+  if (mc::explore_kernel_occupancy(m->key_words, m->tile, m->rule, m->split, m->threads, &bps) || bps < 1) {
     m->last_err = "occupancy query failed";
     cudaGetLastError();
     return MC_ERR_CUDA;
@@ -469,7 +479,7 @@ int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, 
     if (rc_) return rc_;
   }
   if (m->opt.timing) MC_CUDA(m, cudaEventRecord(m->ev[2 * slot], m->stream));
-  MC_CUDA(m, mc::launch_explore(m->key_words, m->tile, m->rule, m->grid, m->threads, A, m->stream));
+  MC_CUDA(m, mc::launch_explore(m->key_words, m->tile, m->rule, m->split, m->grid, m->threads, A, m->stream));
   if (m->opt.timing) {
     MC_CUDA(m, cudaEventRecord(m->ev[2 * slot + 1], m->stream));
     m->ev_pending[slot] = true;
@@ -680,6 +690,7 @@ int mc_set_options(mc_model* m, const mc_options* o) {
     m->opt.log_capacity = keep.log_capacity;
     m->opt.threads_per_block = keep.threads_per_block;
     m->opt.blocks_per_sm = keep.blocks_per_sm;
+    m->opt.probe_scheme = keep.probe_scheme;  // the grid was sized for its kernel
   }
   return MC_OK;
 }
@@ -724,6 +735,7 @@ int mc_model_layout(const mc_model* m, mc_layout* out) {
   out->table_slots = m->table_slots;
   out->log_capacity = m->log_cap;
   out->device_bytes = m->device_bytes;
+  out->probe_scheme = resolve_split(m->opt.probe_scheme, m->key_words) ? MC_PROBE_SPLIT : MC_PROBE_ONE_CALL;
   return MC_OK;
 }
 

@@ -109,9 +109,11 @@ struct ExploreArgs {
                           // time) - 1, or not at all if prev held, failed or was skipped
 };
 
-// Launch helpers implemented in mc_kernels.cu.
-int explore_kernel_occupancy(int key_words, int tile, int rule, int threads, int* blocks_per_sm);
-cudaError_t launch_explore(int key_words, int tile, int rule, int grid, int threads,
+// Launch helpers implemented in mc_kernels.cu.  `split` is the probe scheme:
+// true picks a slot from the fetched bucket and issues the CAS before the
+// result is looked at; false takes the general insert from the fetched bucket.
+int explore_kernel_occupancy(int key_words, int tile, int rule, bool split, int threads, int* blocks_per_sm);
+cudaError_t launch_explore(int key_words, int tile, int rule, bool split, int grid, int threads,
                            const ExploreArgs& args, cudaStream_t stream);
 cudaError_t launch_simulate(const Params& p, uint64_t seed, uint32_t walks, uint64_t* t_out,
                             cudaStream_t stream);

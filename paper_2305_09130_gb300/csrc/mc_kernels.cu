@@ -74,8 +74,9 @@ __device__ __forceinline__ void copy_out(const ExploreArgs& A, const K* keys, co
 // frontier log, and a winner that is terminal (FIN, Listing 4) with
 // time <= T updates the level's minimum packed (time, i, j) -- the property
 // G(FIN -> time > T) of Step 2.  The keys of the next round are loaded
-// before the current round's probes.
-template <class K, int TILE, int RULE>
+// before the current round's probes.  SPLIT selects the probe scheme (see
+// the insert below).
+template <class K, int TILE, int RULE, bool SPLIT>
 __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st, uint64_t T,
                                              uint32_t L, uint64_t offL, uint64_t W, uint64_t offN,
                                              const K (&first)[kDepth], bool have_first) {
@@ -153,13 +154,14 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
       }
     }
     cp_async_wait_all();
-    // 64-bit keys: pick a slot for every proposal from the fetched bucket,
-    // issue all of their CAS, and only then look at the results, with the
-    // general insert (rereading the bucket) when the slot went to another
-    // key or the bucket is full.  128-bit keys take the general insert from
+    // SPLIT: pick a slot for every proposal from the fetched bucket, issue
+    // all of their CAS, and only then look at the results, with the general
+    // insert (rereading the bucket) when the slot went to another key or the
+    // bucket is full.  Otherwise each proposal takes the general insert from
     // the fetched bucket directly.  (Measured: the split form is 8% faster
-    // on C2 at G=80 and 2-3% slower per level with 128-bit keys.)
-    constexpr bool kSplit = sizeof(K) == 8;
+    // on C2 at G=80 with 64-bit keys and 2-3% slower per level with 128-bit
+    // keys, which is why the default follows the key width.)
+    constexpr bool kSplit = SPLIT;
     uint32_t pick[D];
     K cur[D], old[D];
 #pragma unroll
@@ -240,7 +242,7 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
 }
 
 // ------------------------------------------------------------------ the exploration pass
-template <class K, int TILE, int RULE>
+template <class K, int TILE, int RULE, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 4) explore_kernel(const ExploreArgs A) {
   const Params& p = A.p;
   Ctrl* ctrl = A.ctrl;
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 4) explore_kernel(const ExploreArgs 
     if (L >= p.max_level) break;  // the deepest level holds only terminals
     const uint64_t offN = off_last + W;
     if (gtid == 0) A.off[L + 1] = offN;
-    expand_level<K, TILE, RULE>(A, stage, T, L, off_last, W, offN, first, have_first);
+    expand_level<K, TILE, RULE, SPLIT>(A, stage, T, L, off_last, W, offN, first, have_first);
     // level L+1's width word doubles as the barrier: it ends with the width
     // and the number of blocks that saw an error or (with early exit) a
     // violating terminal
@@ -554,39 +556,42 @@ __global__ void replay_walk_kernel(const Params p, uint64_t seed, uint64_t w, in
 }
 
 // ------------------------------------------------------------------ dispatch tables
-template <class K, int RULE>
+template <class K, int RULE, bool SPLIT>
 const void* pick_tile(int tile) {
   switch (tile) {
-    case 1: return (const void*)explore_kernel<K, 1, RULE>;
-    case 2: return (const void*)explore_kernel<K, 2, RULE>;
-    case 4: return (const void*)explore_kernel<K, 4, RULE>;
-    case 8: return (const void*)explore_kernel<K, 8, RULE>;
-    case 16: return (const void*)explore_kernel<K, 16, RULE>;
+    case 1: return (const void*)explore_kernel<K, 1, RULE, SPLIT>;
+    case 2: return (const void*)explore_kernel<K, 2, RULE, SPLIT>;
+    case 4: return (const void*)explore_kernel<K, 4, RULE, SPLIT>;
+    case 8: return (const void*)explore_kernel<K, 8, RULE, SPLIT>;
+    case 16: return (const void*)explore_kernel<K, 16, RULE, SPLIT>;
   }
   return nullptr;
 }
 
-const void* pick_kernel(int key_words, int tile, int rule) {
-  if (key_words == 1) return rule == MC_FREE ? pick_tile<uint64_t, MC_FREE>(tile)
-                                             : pick_tile<uint64_t, MC_GREEDY>(tile);
-  if (key_words == 2) return rule == MC_FREE ? pick_tile<u128, MC_FREE>(tile)
-                                             : pick_tile<u128, MC_GREEDY>(tile);
+template <class K, bool SPLIT>
+const void* pick_rule(int tile, int rule) {
+  return rule == MC_FREE ? pick_tile<K, MC_FREE, SPLIT>(tile) : pick_tile<K, MC_GREEDY, SPLIT>(tile);
+}
+
+const void* pick_kernel(int key_words, int tile, int rule, bool split) {
+  if (key_words == 1) return split ? pick_rule<uint64_t, true>(tile, rule) : pick_rule<uint64_t, false>(tile, rule);
+  if (key_words == 2) return split ? pick_rule<u128, true>(tile, rule) : pick_rule<u128, false>(tile, rule);
   return nullptr;
 }
 
 }  // namespace
 
-int explore_kernel_occupancy(int key_words, int tile, int rule, int threads, int* blocks_per_sm) {
-  const void* f = pick_kernel(key_words, tile, rule);
+int explore_kernel_occupancy(int key_words, int tile, int rule, bool split, int threads, int* blocks_per_sm) {
+  const void* f = pick_kernel(key_words, tile, rule, split);
   if (!f) return -1;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, 0) == cudaSuccess
              ? 0
              : -1;
 }
 
-cudaError_t launch_explore(int key_words, int tile, int rule, int grid, int threads,
+cudaError_t launch_explore(int key_words, int tile, int rule, bool split, int grid, int threads,
                            const ExploreArgs& args, cudaStream_t stream) {
-  const void* f = pick_kernel(key_words, tile, rule);
+  const void* f = pick_kernel(key_words, tile, rule, split);
   if (!f) return cudaErrorInvalidValue;
   void* params[] = {const_cast<ExploreArgs*>(&args)};
   return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(threads), params, 0, stream);

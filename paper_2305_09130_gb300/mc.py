@@ -27,6 +27,7 @@ MC_ERR_CUDA = -6
 MC_ERR_OVERFLOW = -7
 MC_FREE, MC_GREEDY = 0, 1
 SEARCH = {"single": 0, "lower": 1, "bisect": 2}
+PROBE = {"auto": 0, "split": 1, "one_call": 2}  # mc_probe_scheme
 NO_LIMIT = (1 << 64) - 1
 
 U32P = C.POINTER(C.c_uint32)
@@ -46,7 +47,7 @@ class McOptions(C.Structure):
                 ("max_probes", C.c_uint32), ("log_capacity", C.c_uint64),
                 ("barrier_timeout_ns", C.c_uint64), ("debug_barrier_extra", C.c_uint32),
                 ("timing", C.c_uint32), ("lanes_per_state", C.c_uint32),
-                ("reserved", C.c_uint32 * 5)]
+                ("probe_scheme", C.c_uint32), ("reserved", C.c_uint32 * 4)]
 
 
 class McCheckResult(C.Structure):
@@ -71,7 +72,7 @@ class McLayout(C.Structure):
                 ("max_level", C.c_uint32), ("n_shift", C.c_uint32 * 16),
                 ("table_slots", C.c_uint64), ("log_capacity", C.c_uint64),
                 ("max_width", C.c_uint64), ("state_bound", C.c_uint64),
-                ("device_bytes", C.c_uint64)]
+                ("device_bytes", C.c_uint64), ("probe_scheme", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class McSwarmResult(C.Structure):
@@ -259,12 +260,19 @@ def mc_strerror(code: int) -> str:
     return load(build=False).mc_strerror(code).decode() if _lib else f"error {code}"
 
 
+_OPTION_FIELDS = frozenset(f[0] for f in McOptions._fields_ if f[0] != "reserved")
+
+
 def mc_options_default(**overrides) -> McOptions:
     o = McOptions()
     load().mc_options_default(C.byref(o))
     for k, v in overrides.items():
+        if k not in _OPTION_FIELDS:  # ctypes would keep an unknown name as a plain attribute
+            raise TypeError(f"unknown mc_options field {k!r}")
         if k == "search" and isinstance(v, str):
             v = SEARCH[v]
+        if k == "probe_scheme" and isinstance(v, str):
+            v = PROBE[v]
         setattr(o, k, int(v))
     return o
 
@@ -364,7 +372,7 @@ def mc_reserve(model: Model):
 def mc_model_layout(model: Model) -> dict:
     lay = McLayout()
     model._check(load().mc_model_layout(model.handle, C.byref(lay)), "mc_model_layout")
-    out = {k: getattr(lay, k) for k, _t in McLayout._fields_ if k != "n_shift"}
+    out = {k: getattr(lay, k) for k, _t in McLayout._fields_ if k not in ("n_shift", "reserved")}
     out["n_shift"] = list(lay.n_shift[: lay.P])
     model._layout = out
     return out

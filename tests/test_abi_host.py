@@ -100,6 +100,26 @@ def test_invalid_descriptions(lib):
     with pytest.raises(mc.MCError) as e:
         mc.mc_model_create(ok, mc.mc_options_default(load_factor_pct=95), allocator=None)
     assert e.value.code == mc.MC_ERR_INVAL
+    with pytest.raises(mc.MCError) as e:
+        mc.mc_model_create(ok, mc.mc_options_default(probe_scheme=3), allocator=None)
+    assert e.value.code == mc.MC_ERR_INVAL
+
+
+def test_probe_schemes_are_accepted_by_name_and_number(lib):
+    for name, code in (("auto", 0), ("split", 1), ("one_call", 2)):
+        o = mc.mc_options_default(probe_scheme=name)
+        assert o.probe_scheme == code == mc.PROBE[name]
+        mc.mc_model_create(W.c1(), o, allocator=None)
+    # AUTO resolves by key width: split for 64-bit keys, one call for 128-bit
+    assert layout(W.c1())["probe_scheme"] == mc.PROBE["split"]
+    assert layout(W.c1().with_key_bits(128))["probe_scheme"] == mc.PROBE["one_call"]
+    assert layout(W.c1(), probe_scheme="one_call")["probe_scheme"] == mc.PROBE["one_call"]
+    assert layout(W.c1().with_key_bits(128), probe_scheme="split")["probe_scheme"] == mc.PROBE["split"]
+
+
+def test_unknown_option_names_are_rejected(lib):
+    with pytest.raises(TypeError):
+        mc.mc_options_default(load_factor=10)  # the field is load_factor_pct
 
 
 def test_release_cached_is_safe_without_a_device(lib):

@@ -308,3 +308,38 @@ def test_lowering_chained_over_several_groups(mc, oracle, P, b, rule):
         st = mc.mc_get_stats(model)
         assert st["explore_launches"] >= exp["checks"]
         mc.mc_reset_stats(model)
+
+
+# ---------------------------------------------------------------- probe schemes
+
+@pytest.mark.parametrize("scheme", ["split", "one_call"])
+def test_probe_schemes_match_oracle(mc, oracle, scheme):
+    """Both inserts (mc_options.probe_scheme), forced on 64- and 128-bit keys,
+    give the oracle's counts, widths, checks and minima."""
+    for spec in sweep_models()[::3]:
+        model = make(mc, spec, probe_scheme=scheme)
+        mc.mc_reserve(model)  # the scheme is fixed once the buffers exist
+        assert mc.mc_model_layout(model)["probe_scheme"] == mc.PROBE[scheme]
+        assert mc.mc_count_states(model) == oracle.count(spec)
+        assert mc.mc_last_widths(model) == CF.widths(spec)
+        t_min = oracle.min_time(spec)["t_min"]
+        for T in (t_min - 1, t_min, 3 * t_min):
+            for prune, ee in ((True, True), (False, False)):
+                assert gpu_check(mc, model, T, prune, ee) == oracle.check(spec, T, prune=prune, early_exit=ee)
+        assert mc.mc_model_layout(model)["probe_scheme"] == mc.PROBE[scheme]
+        assert gpu_min(mc, model, "single", True) == oracle.min_time(spec, search="single", prune=True)
+
+
+@pytest.mark.parametrize("scheme", ["split", "one_call"])
+def test_probe_schemes_at_full_size(mc, scheme):
+    """C2 at G=80 (64-bit keys) and C3 literal under GREEDY (128-bit keys) with
+    each insert forced: the full counts, every level's width and the minimum."""
+    g = golden()
+    for spec, exp in ((W.c2_star(), g["c2_star"]), (W.c3(rule=GREEDY), g["c3_greedy"])):
+        model = make(mc, spec, probe_scheme=scheme, load_factor_pct=10)
+        mc.mc_reserve(model)
+        assert mc.mc_count_states(model) == exp["count"] == CF.count(spec)
+        assert mc.mc_last_widths(model) == CF.widths(spec)
+        got = gpu_min(mc, model, "single", True)
+        want = exp["min_time"]["single/prune1"]
+        assert got == {k: want[k] for k in got}
