@@ -124,7 +124,17 @@ void pinned_free(void* p, size_t bytes) {
 namespace {
 
 constexpr int kSlots = 4;  // per-pass result slots (device header + pinned copy)
-constexpr size_t kCtrlStride = 256 + mc::kBarBytes;  // one slot: header, then its barrier lines
+// Device control block, in this order:
+//   barrier lines  kSlots x kBarBytes (one device-wide barrier per slot)
+//   headers        kSlots x Ctrl      (one pass result per slot)
+//   scalars        kScalarBytes       (T_ini, T_min, spare)
+//   trace          16 x (max_level + 2)
+//   levels         16 x (max_level + 2), then off 8 x (max_level + 2)
+// The headers, scalars and trace are contiguous and mirrored in pinned host
+// memory with the same layout, so one copy reads a whole query's results
+// back, and the barrier lines and headers are cleared by one memset.
+constexpr size_t kScalarBytes = 64;
+static_assert(sizeof(Ctrl) % 16 == 0, "headers keep 16-byte alignment");
 
 struct Buf {
   void* ptr = nullptr;
@@ -191,9 +201,10 @@ struct mc_model {
   uint64_t *d_tini = nullptr, *d_tmin = nullptr;
   uint8_t* h_block = nullptr;   // pinned host staging (from the pool), carved into:
   size_t h_block_bytes = 0;
-  Ctrl* h_ctrl = nullptr;       // [kSlots]
+  Ctrl* h_ctrl = nullptr;       // [kSlots]  } the device's headers, scalars and trace,
+  uint64_t* h_scalar = nullptr; // [8]       } contiguous, read back by one copy
   uint64_t* h_trace = nullptr;  // [(max_level + 2) * 2]
-  uint64_t* h_scalar = nullptr; // [4]
+  size_t mirror_bytes = 0;
   uint32_t* h_params = nullptr; // staging of N, cost, speed
   cudaEvent_t ev[2 * kSlots] = {};
   bool ev_pending[kSlots] = {};
@@ -329,7 +340,7 @@ int size_buffers(mc_model* m) {
   if (m->max_width >= (1ull << 31) && slots > (1ull << 31)) return MC_ERR_OVERFLOW;
   m->table_slots = slots;
   const uint64_t key_bytes = 8ull * m->key_words;
-  const uint64_t ctrl_bytes = kCtrlStride * kSlots + 8ull * (m->max_level + 2) * 5 + 64;
+  const uint64_t ctrl_bytes = (mc::kBarBytes + sizeof(Ctrl)) * kSlots + kScalarBytes + 8ull * (m->max_level + 2) * 5;
   uint64_t total = mul_sat(slots, key_bytes);
   total = add_sat(total, mul_sat(m->log_cap, key_bytes + 4));
   total = add_sat(total, ctrl_bytes + 4ull * (2ull * m->a * m->b + m->P));
@@ -370,28 +381,29 @@ int reserve(mc_model* m) {
   m->d_log_keys = dev_alloc(m, m->log_cap * key_bytes);
   m->d_log_par = (uint32_t*)dev_alloc(m, m->log_cap * 4);
   const size_t L2 = m->max_level + 2;
-  const size_t ctrl_bytes = kCtrlStride * kSlots + 16 * L2 + 8 * L2 + 16 * L2 + 64;
+  const size_t mirror_bytes = sizeof(Ctrl) * kSlots + kScalarBytes + 16 * L2;  // headers, scalars, trace
+  const size_t ctrl_bytes = mc::kBarBytes * kSlots + mirror_bytes + 16 * L2 + 8 * L2;
   m->d_ctrl_block = (uint8_t*)dev_alloc(m, ctrl_bytes);
   if (!m->d_params || !m->d_table || !m->d_log_keys || !m->d_log_par || !m->d_ctrl_block) {
     release(m);
     return MC_ERR_NOMEM;
   }
-  uint8_t* q = m->d_ctrl_block;
-  m->d_ctrl = (Ctrl*)q;  // per slot: [Ctrl header, 256 B][barrier lines]
-  q += kCtrlStride * kSlots;
+  uint8_t* q = m->d_ctrl_block + mc::kBarBytes * kSlots;  // after the barrier lines
+  m->d_ctrl = (Ctrl*)q;
+  q += sizeof(Ctrl) * kSlots;
+  m->d_tini = (uint64_t*)q;
+  m->d_tmin = (uint64_t*)q + 1;
+  q += kScalarBytes;
+  m->d_trace = (uint64_t*)q;
+  q += 16 * L2;
   m->d_levels = (uint64_t*)q;
   q += 16 * L2;
   m->d_off = (uint64_t*)q;
-  q += 8 * L2;
-  m->d_trace = (uint64_t*)q;
-  q += 16 * L2;
-  m->d_tini = (uint64_t*)q;
-  m->d_tmin = (uint64_t*)q + 1;
+  m->mirror_bytes = mirror_bytes;
 
-  // host staging: one pinned block, carved (from the process-wide pool)
-  const size_t o_trace = align_up(sizeof(Ctrl) * kSlots, 64);
-  const size_t o_scalar = o_trace + align_up(16 * L2, 64);
-  const size_t o_params = o_scalar + 64;
+  // host staging: one pinned block (from the process-wide pool): the mirror
+  // of headers, scalars and trace, then the model arrays
+  const size_t o_params = align_up(mirror_bytes, 64);
   m->h_block_bytes = o_params + np * 4;
   m->h_block = (uint8_t*)mc::pinned_alloc(m->h_block_bytes);
   if (!m->h_block) {
@@ -399,8 +411,8 @@ int reserve(mc_model* m) {
     return MC_ERR_NOMEM;
   }
   m->h_ctrl = (Ctrl*)m->h_block;
-  m->h_trace = (uint64_t*)(m->h_block + o_trace);
-  m->h_scalar = (uint64_t*)(m->h_block + o_scalar);
+  m->h_scalar = (uint64_t*)(m->h_block + sizeof(Ctrl) * kSlots);
+  m->h_trace = (uint64_t*)(m->h_block + sizeof(Ctrl) * kSlots + kScalarBytes);
   m->h_params = (uint32_t*)(m->h_block + o_params);
   if (m->opt.timing) {
     const int rc_ = make_events(m);
@@ -438,13 +450,32 @@ int reserve(mc_model* m) {
   return MC_OK;
 }
 
-Ctrl* ctrl_at(mc_model* m, int slot) {
-  return reinterpret_cast<Ctrl*>(reinterpret_cast<uint8_t*>(m->d_ctrl) + kCtrlStride * slot);
+Ctrl* ctrl_at(mc_model* m, int slot) { return m->d_ctrl + slot; }
+
+uint32_t* bar_lines_at(mc_model* m, int slot) {
+  return reinterpret_cast<uint32_t*>(m->d_ctrl_block + mc::kBarBytes * slot);
 }
 
-// Enqueue one exploration pass; its Ctrl header lands in h_ctrl[slot].  With
-// `prev`, the pass takes its threshold from that slot's counterexample (see
-// ExploreArgs::prev).
+// One memset: every slot's barrier lines and the headers of slots 0 ..
+// n_headers - 1 (with n_headers == kSlots + 1 also the scalars, T_min = 0).
+int clear_ctrl(mc_model* m, int n_headers) {
+  const size_t n = mc::kBarBytes * kSlots +
+                   (n_headers > kSlots ? sizeof(Ctrl) * kSlots + kScalarBytes : sizeof(Ctrl) * n_headers);
+  MC_CUDA(m, cudaMemsetAsync(m->d_ctrl_block, 0, n, m->stream));
+  return MC_OK;
+}
+
+// One copy: every header, the scalars and the trace buffer into the mirror.
+int fetch_ctrl(mc_model* m) {
+  MC_CUDA(m, cudaMemcpyAsync(m->h_ctrl, m->d_ctrl, m->mirror_bytes, cudaMemcpyDeviceToHost, m->stream));
+  m->stats.d2h_bytes += m->mirror_bytes;
+  return MC_OK;
+}
+
+// Enqueue one exploration pass into `slot`, whose header and barrier lines
+// the caller has cleared (clear_ctrl); fetch_ctrl reads the header back.
+// With `prev`, the pass takes its threshold from that slot's counterexample
+// (see ExploreArgs::prev).
 int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, bool prune,
                  bool early_exit, bool witness, uint64_t* tmin_out, int slot, int prev = -1) {
   ExploreArgs A{};
@@ -471,9 +502,8 @@ int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, 
   A.T_delta = delta;
   A.tmin_out = tmin_out;
   A.barrier_extra = m->opt.debug_barrier_extra;
-  A.bar_lines = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(A.ctrl) + 256);
+  A.bar_lines = bar_lines_at(m, slot);
   A.timeout_ns = m->opt.barrier_timeout_ns ? m->opt.barrier_timeout_ns : 60ull * 1000000000ull;
-  MC_CUDA(m, cudaMemsetAsync(A.ctrl, 0, kCtrlStride, m->stream));
   if (m->opt.timing) {
     const int rc_ = make_events(m);
     if (rc_) return rc_;
@@ -484,9 +514,6 @@ int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, 
     MC_CUDA(m, cudaEventRecord(m->ev[2 * slot + 1], m->stream));
     m->ev_pending[slot] = true;
   }
-  MC_CUDA(m, cudaMemcpyAsync(&m->h_ctrl[slot], A.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost,
-                             m->stream));
-  m->stats.d2h_bytes += sizeof(Ctrl);
   m->stats.explore_launches += 1;
   return MC_OK;
 }
@@ -744,12 +771,9 @@ int mc_check(mc_model* m, uint64_t T, mc_check_result* out, mc_trace** cex) {
   if (cex) *cex = nullptr;
   DeviceGuard g(m->device);
   MC_TRY(reserve(m));
+  MC_TRY(clear_ctrl(m, 1));
   MC_TRY(enqueue_pass(m, T, nullptr, 0, m->opt.prune, m->opt.early_exit, true, nullptr, 0));
-  const size_t L2 = m->max_level + 2;
-  if (cex) {
-    MC_CUDA(m, cudaMemcpyAsync(m->h_trace, m->d_trace, 16 * L2, cudaMemcpyDeviceToHost, m->stream));
-    m->stats.d2h_bytes += 16 * L2;
-  }
+  MC_TRY(fetch_ctrl(m));
   MC_TRY(sync(m));
   MC_TRY(pass_error(m, 0));
   fill_check(m, m->h_ctrl[0], out);
@@ -761,7 +785,9 @@ int mc_count_states(mc_model* m, uint64_t* out) {
   if (!m || !out) return MC_ERR_INVAL;
   DeviceGuard g(m->device);
   MC_TRY(reserve(m));
+  MC_TRY(clear_ctrl(m, 1));
   MC_TRY(enqueue_pass(m, UINT64_MAX, nullptr, 0, false, false, false, nullptr, 0));
+  MC_TRY(fetch_ctrl(m));
   MC_TRY(sync(m));
   MC_TRY(pass_error(m, 0));
   *out = m->h_ctrl[0].states;
@@ -787,27 +813,22 @@ int mc_min_time(mc_model* m, mc_min_result* out, mc_trace** trace) {
   DeviceGuard g(m->device);
   MC_TRY(reserve(m));
   const bool prune = m->opt.prune, ee = m->opt.early_exit;
-  const size_t L2 = m->max_level + 2;
+  // one memset for every slot and the scalars (T_min = 0), then T_ini
+  MC_TRY(clear_ctrl(m, kSlots + 1));
   MC_TRY(run_simulation(m, m->opt.sim_seed, m->opt.sim_walks, m->d_tini));
-  int final_slot = -1;
+  Ctrl c{};  // header of the check whose counterexample is the answer
 
   if (m->opt.search == MC_SEARCH_SINGLE) {
     // one pass with a device-side min-reduction over terminal times, then
     // the certificate checks at T_min - 1 (must hold) and T_min (fails);
     // thresholds stay on the device, so the host waits once
-    MC_CUDA(m, cudaMemsetAsync(m->d_tmin, 0, 8, m->stream));
     MC_TRY(enqueue_pass(m, UINT64_MAX, prune ? m->d_tini : nullptr, 0, prune, false, false,
                         m->d_tmin, 0));
     int slot = 1;
     if (m->opt.refine) MC_TRY(enqueue_pass(m, 0, m->d_tmin, -1, prune, ee, false, nullptr, slot++));
     MC_TRY(enqueue_pass(m, 0, m->d_tmin, 0, prune, ee, true, nullptr, slot));
-    final_slot = slot;
-    MC_CUDA(m, cudaMemcpyAsync(m->h_scalar, m->d_tini, 8, cudaMemcpyDeviceToHost, m->stream));
-    m->stats.d2h_bytes += 8;
-    if (trace) {
-      MC_CUDA(m, cudaMemcpyAsync(m->h_trace, m->d_trace, 16 * L2, cudaMemcpyDeviceToHost, m->stream));
-      m->stats.d2h_bytes += 16 * L2;
-    }
+    const int final_slot = slot;
+    MC_TRY(fetch_ctrl(m));
     MC_TRY(sync(m));
     out->t_ini = m->h_scalar[0];
     for (int s = 0; s <= final_slot; ++s) {
@@ -823,39 +844,41 @@ int mc_min_time(mc_model* m, mc_min_result* out, mc_trace** trace) {
       m->last_err = "certificate checks disagree with the minimum";
       return MC_ERR_CUDA;
     }
+    c = m->h_ctrl[final_slot];
   } else if (m->opt.search == MC_SEARCH_LOWER) {
     // Step 3: check at T_ini, then one below each counterexample, until the
     // property holds.  The checks are chained on the device (each takes its
     // threshold from its predecessor's counterexample, and one after a check
-    // that held does not run) and enqueued in groups of three over four
-    // result slots, so the last failing check's header survives the next
-    // group; the host waits once per group.
+    // that held does not run) in groups of three in slots 0..2; the host
+    // waits once per group.  A group only follows one whose three checks all
+    // failed: the last of them is copied into slot 3 and is the next group's
+    // predecessor (and the answer if that group's first check holds).
     constexpr int kGroup = 3;
-    MC_CUDA(m, cudaMemcpyAsync(m->h_scalar, m->d_tini, 8, cudaMemcpyDeviceToHost, m->stream));
-    m->stats.d2h_bytes += 8;
-    int p = 0, last = -1;
+    static_assert(kGroup < kSlots, "slot kGroup keeps the predecessor");
+    int last = -1;
     bool held = false;
-    while (!held) {
-      const int first = p;
-      for (int k = 0; k < kGroup; ++k, ++p) {
-        if (p == 0) MC_TRY(enqueue_pass(m, 0, m->d_tini, 0, prune, ee, true, nullptr, 0));
-        else MC_TRY(enqueue_pass(m, 0, nullptr, 0, prune, ee, true, nullptr, p % kSlots, (p - 1) % kSlots));
+    for (int group = 0; !held; ++group) {
+      if (group > 0) {
+        MC_CUDA(m, cudaMemcpyAsync(ctrl_at(m, kGroup), ctrl_at(m, kGroup - 1), sizeof(Ctrl),
+                                   cudaMemcpyDeviceToDevice, m->stream));
+        MC_TRY(clear_ctrl(m, kGroup));
+        last = kGroup;
       }
-      // the trace buffer then holds the last failing check's trace (a check
-      // that holds or does not run leaves it alone): read it with the group
-      if (trace) {
-        MC_CUDA(m, cudaMemcpyAsync(m->h_trace, m->d_trace, 16 * L2, cudaMemcpyDeviceToHost, m->stream));
-        m->stats.d2h_bytes += 16 * L2;
+      for (int k = 0; k < kGroup; ++k) {
+        if (group == 0 && k == 0) MC_TRY(enqueue_pass(m, 0, m->d_tini, 0, prune, ee, true, nullptr, 0));
+        else MC_TRY(enqueue_pass(m, 0, nullptr, 0, prune, ee, true, nullptr, k, k == 0 ? kGroup : k - 1));
       }
+      // the trace buffer holds the last failing check's trace (a check that
+      // holds or does not run leaves it alone); the fetch reads it too
+      MC_TRY(fetch_ctrl(m));
       MC_TRY(sync(m));
-      for (int q = first; q < p && !held; ++q) {
-        const int slot = q % kSlots;
-        if (m->h_ctrl[slot].skipped) break;
-        MC_TRY(pass_error(m, slot));
-        out->states += m->h_ctrl[slot].states;
+      for (int k = 0; k < kGroup && !held; ++k) {
+        if (m->h_ctrl[k].skipped) break;
+        MC_TRY(pass_error(m, k));
+        out->states += m->h_ctrl[k].states;
         out->checks += 1;
-        if (m->h_ctrl[slot].stop_level == 0) held = true;
-        else last = slot;
+        if (m->h_ctrl[k].stop_level == 0) held = true;
+        else last = k;
       }
     }
     out->t_ini = m->h_scalar[0];
@@ -863,55 +886,50 @@ int mc_min_time(mc_model* m, mc_min_result* out, mc_trace** trace) {
       m->last_err = "search ended without a counterexample";
       return MC_ERR_CUDA;
     }
-    final_slot = last;
+    c = m->h_ctrl[last];
   } else {
-    MC_CUDA(m, cudaMemcpyAsync(m->h_scalar, m->d_tini, 8, cudaMemcpyDeviceToHost, m->stream));
-    m->stats.d2h_bytes += 8;
+    MC_TRY(fetch_ctrl(m));
     MC_TRY(sync(m));
     out->t_ini = m->h_scalar[0];
-    // run one check, keep its header in `slot`
-    auto check = [&](uint64_t T, int slot) -> int {
-      MC_TRY(enqueue_pass(m, T, nullptr, 0, prune, ee, true, nullptr, slot));
+    // run one check in slot 0 (the host keeps the last failing header)
+    auto check = [&](uint64_t T) -> int {
+      MC_TRY(clear_ctrl(m, 1));
+      MC_TRY(enqueue_pass(m, T, nullptr, 0, prune, ee, true, nullptr, 0));
+      MC_TRY(fetch_ctrl(m));
       MC_TRY(sync(m));
-      MC_TRY(pass_error(m, slot));
-      out->states += m->h_ctrl[slot].states;
+      MC_TRY(pass_error(m, 0));
+      out->states += m->h_ctrl[0].states;
       out->checks += 1;
       return MC_OK;
     };
-    int last = -1;  // slot of the last failing check
+    bool have = false;  // c holds a failing check's header
     {
       // bisection (Fig. 1) between 0 (no terminal has time 0) and T_ini;
       // a counterexample at mid lowers hi to its own time
       uint64_t lo = 0, hi = out->t_ini;
       while (hi - lo > 1) {
         const uint64_t mid = lo + (hi - lo) / 2;
-        const int slot = last == 0 ? 1 : 0;
-        MC_TRY(check(mid, slot));
-        if (m->h_ctrl[slot].stop_level == 0) {
+        MC_TRY(check(mid));
+        if (m->h_ctrl[0].stop_level == 0) {
           lo = mid;
         } else {
-          hi = mc::pack_time(m->h_ctrl[slot].wpack);
-          last = slot;
+          hi = mc::pack_time(m->h_ctrl[0].wpack);
+          c = m->h_ctrl[0];
+          have = true;
         }
       }
-      if (last < 0 || mc::pack_time(m->h_ctrl[last].wpack) != hi) {
-        const int slot = last == 0 ? 1 : 0;
-        MC_TRY(check(hi, slot));
-        last = slot;
+      if (!have || mc::pack_time(c.wpack) != hi) {
+        MC_TRY(check(hi));
+        c = m->h_ctrl[0];
+        have = true;
       }
     }
-    if (last < 0 || m->h_ctrl[last].stop_level == 0) {
+    // the trace buffer (read by every fetch) holds the last failing check's trace
+    if (!have || c.stop_level == 0) {
       m->last_err = "search ended without a counterexample";
       return MC_ERR_CUDA;
     }
-    final_slot = last;
-    if (trace) {
-      MC_CUDA(m, cudaMemcpyAsync(m->h_trace, m->d_trace, 16 * L2, cudaMemcpyDeviceToHost, m->stream));
-      m->stats.d2h_bytes += 16 * L2;
-      MC_TRY(sync(m));
-    }
   }
-  const Ctrl& c = m->h_ctrl[final_slot];
   out->t_min = mc::pack_time(c.wpack);
   out->wg_index = mc::pack_i(c.wpack);
   out->ts_index = mc::pack_j(c.wpack);
