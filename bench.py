@@ -47,6 +47,9 @@ WORKLOADS = {
     "c3_star": (lambda: W.c3_star(),
                 "c3_star: G=36, P=8, WG 2^0..2^9, TS 2^0..2^5, FREE, cost U{1..16} (splitmix64 seed "
                 "2305091303), 128-bit keys; 1,072,924,481 reachable states"),
+    "c2": (lambda: W.c2(rule=W.GREEDY),
+           "c2: G=1024, P=4, WG 2^0..2^8, TS 2^0..2^4, GREEDY, cost ceil(WG/TS)*4+WG+2*TS, speeds U{1..3} "
+           "(splitmix64 seed 2305091302), 64-bit keys (deep, narrow levels)"),
     "c3": (lambda: W.c3(rule=W.GREEDY),
            "c3: G=4096, P=8, WG 2^0..2^9, TS 2^0..2^5, GREEDY, cost U{1..16} (splitmix64 seed "
            "2305091303), 128-bit keys"),
@@ -271,6 +274,8 @@ def run_ours(args):
         fixed["load_factor_pct"] = args.load_factor
     elif args.workload == "c2_star":
         space["load_factor_pct"] = [10, 15]
+    if args.no_log_tags:
+        fixed["no_log_tags"] = 1
     if args.probe_scheme == "tune":
         space["probe_scheme"] = [mc.PROBE["split"], mc.PROBE["one_call"]]
     else:
@@ -890,6 +895,8 @@ def main(argv=None):
                    help="visited-set load factor in percent (0: the autotuner picks it for c2_star)")
     p.add_argument("--probe-scheme", choices=["tune", "auto", "split", "one_call"], default="tune",
                    help="visited-set insert of the exploration kernel (tune: the autotuner picks it)")
+    p.add_argument("--no-log-tags", action="store_true",
+                   help="untagged frontier log: blocks write their entries before they arrive at a level")
     p.add_argument("--rates", default="10,30,100,300,1000", help="c5 arrival rates (queries/s)")
     p.add_argument("--slots", type=int, default=512, help="c5 requests on the device at once")
     p.add_argument("--c5-seconds", type=float, default=10.0, help="c5 arrivals per rate span")

@@ -143,7 +143,11 @@ typedef struct {
                                    explorer (mc_check, mc_min_time,
                                    mc_count_states); batches and the PE-level
                                    model keep their own                      */
-  uint32_t reserved[4];
+  uint32_t no_log_tags;         /* 1: never tag the frontier log (every block
+                                   writes its entries before it arrives at the
+                                   level barrier); 0: tag it where the keys
+                                   have room (mc_layout.log_tag_bits)        */
+  uint32_t reserved[3];
 } mc_options;
 
 /* Result of mc_check (Section 4, Step 2: Phi = G(FIN -> time > T)). */
@@ -193,7 +197,11 @@ typedef struct {
   uint64_t device_bytes; /* device memory the model needs                  */
   uint32_t probe_scheme; /* the insert its explorations use: MC_PROBE_SPLIT
                             or MC_PROBE_ONE_CALL (AUTO resolved)           */
-  uint32_t reserved;
+  uint32_t log_tag_bits; /* spare top key bits that tag each pass's
+                            frontier-log entries, so a block can arrive at a
+                            level's barrier before writing its last entries
+                            (64-bit keys with >= 8 spare bits, at most 16;
+                            0: untagged)                                   */
 } mc_layout;
 
 /* Counters accumulated over the model's queries (reset by mc_reset_stats). */
@@ -232,8 +240,8 @@ void mc_model_destroy(mc_model* m);
 
 /* Replace the options of later queries.  Options that size buffers or the
  * launch (load_factor_pct, table_log2, log_capacity, threads_per_block,
- * blocks_per_sm, probe_scheme) only act before the buffers exist.  Errors:
- * INVAL. */
+ * blocks_per_sm, probe_scheme, no_log_tags) only act before the buffers
+ * exist.  Errors: INVAL. */
 int mc_set_options(mc_model* m, const mc_options* opt);
 
 /* CUDA stream (a cudaStream_t, NULL = legacy default stream) for every later

@@ -186,6 +186,8 @@ struct mc_model {
   int device = -1;
   int grid = 0, threads = 0;
   bool split = true;  // probe scheme of the exploration kernel (resolved at reserve)
+  uint32_t tag_bits = 0;  // spare top key bits tagging the frontier log (0: untagged)
+  uint32_t tag = 0;       // the last pass's tag
   cudaStream_t stream = nullptr;
   mc_alloc_fn alloc = nullptr;
   mc_free_fn dealloc = nullptr;
@@ -307,7 +309,14 @@ bool valid_options(const mc_options* o) {
     return false;
   if (o->table_log2 && (o->table_log2 < 3 || o->table_log2 > 40)) return false;
   if (o->probe_scheme > MC_PROBE_ONE_CALL) return false;
+  if (o->no_log_tags > 1) return false;
   return true;
+}
+
+// spare top bits of 64-bit keys that tag the frontier log (8 to 16), or 0
+uint32_t log_tag_bits(const mc_model* m) {
+  const uint32_t spare = m->key_words == 1 && !m->opt.no_log_tags ? 64 - m->used_bits : 0;
+  return spare >= 8 ? std::min<uint32_t>(spare, 16) : 0;
 }
 
 // the probe scheme of the exploration kernel: AUTO follows the key width
@@ -400,6 +409,11 @@ int reserve(mc_model* m) {
   q += 16 * L2;
   m->d_off = (uint64_t*)q;
   m->mirror_bytes = mirror_bytes;
+  // tagged frontier log for 64-bit keys with 8 or more spare top bits: the
+  // log starts cleared, so no entry of freed memory carries a tag
+  m->tag_bits = log_tag_bits(m);
+  m->tag = 0;
+  if (m->tag_bits) MC_CUDA(m, cudaMemsetAsync(m->d_log_keys, 0, m->log_cap * key_bytes, m->stream));
 
   // host staging: one pinned block (from the process-wide pool): the mirror
   // of headers, scalars and trace, then the model arrays
@@ -504,6 +518,14 @@ int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, 
   A.barrier_extra = m->opt.debug_barrier_extra;
   A.bar_lines = bar_lines_at(m, slot);
   A.timeout_ns = m->opt.barrier_timeout_ns ? m->opt.barrier_timeout_ns : 60ull * 1000000000ull;
+  if (m->tag_bits) {  // a new tag per pass; the log is cleared when the tags wrap
+    if (++m->tag >= (1u << m->tag_bits)) {
+      MC_CUDA(m, cudaMemsetAsync(m->d_log_keys, 0, m->log_cap * 8ull * m->key_words, m->stream));
+      m->tag = 1;
+    }
+    A.tag_mask = ~0ull << (64 - m->tag_bits);
+    A.tag = (uint64_t)m->tag << (64 - m->tag_bits);
+  }
   if (m->opt.timing) {
     const int rc_ = make_events(m);
     if (rc_) return rc_;
@@ -718,6 +740,7 @@ int mc_set_options(mc_model* m, const mc_options* o) {
     m->opt.threads_per_block = keep.threads_per_block;
     m->opt.blocks_per_sm = keep.blocks_per_sm;
     m->opt.probe_scheme = keep.probe_scheme;  // the grid was sized for its kernel
+    m->opt.no_log_tags = keep.no_log_tags;    // the log was cleared (or not) for it
   }
   return MC_OK;
 }
@@ -763,6 +786,7 @@ int mc_model_layout(const mc_model* m, mc_layout* out) {
   out->log_capacity = m->log_cap;
   out->device_bytes = m->device_bytes;
   out->probe_scheme = resolve_split(m->opt.probe_scheme, m->key_words) ? MC_PROBE_SPLIT : MC_PROBE_ONE_CALL;
+  out->log_tag_bits = log_tag_bits(m);
   return MC_OK;
 }
 

@@ -398,15 +398,45 @@ __device__ __forceinline__ uint64_t level_reserve(uint64_t* word, uint32_t n) {
   return atomicAdd(reinterpret_cast<unsigned long long*>(word), (unsigned long long)n) & kLevelWidthMask;
 }
 
+__device__ __forceinline__ uint64_t atom_add_release_u64(uint64_t* p, uint64_t v) {
+  uint64_t old;
+  asm volatile("atom.release.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+
+// Thread 0 only: the arrival of this block (with its stop vote from `flags`,
+// which is cleared) plus `n` frontier-log entries reserved in the same
+// atomic; returns the offset of the first.  A block that arrives this way
+// writes those entries after its arrival, so readers of the next level check
+// each entry's tag (see the exploration kernel) instead of relying on the
+// barrier for them.  Wait with level_wait.
+__device__ __forceinline__ uint64_t level_arrive_reserve(uint64_t* word, uint32_t* flags, uint32_t stop_mask,
+                                                         uint32_t n) {
+  const bool stop = (*flags & stop_mask) != 0;
+  *flags = 0;
+  return atom_add_release_u64(word, (1ull << kLevelArriveShift) | (stop ? 1ull << kLevelStopShift : 0ull) | n) &
+         kLevelWidthMask;
+}
+
+// The waiting half of level_sync for blocks that arrived with
+// level_arrive_reserve: every thread of the block calls it.
+__device__ __forceinline__ bool level_wait(const Barrier& B, uint64_t* word, uint64_t* value);
+
 __device__ __forceinline__ bool level_sync(const Barrier& B, uint64_t* word, uint32_t* flags,
                                            uint32_t stop_mask, uint64_t* value) {
-  __shared__ uint32_t s_ok;
-  __shared__ unsigned long long s_v;
   __syncthreads();
   if (threadIdx.x == 0) {
     const bool stop = (*flags & stop_mask) != 0;
     *flags = 0;
     red_add_release_u64(word, (1ull << kLevelArriveShift) | (stop ? 1ull << kLevelStopShift : 0ull));
+  }
+  return level_wait(B, word, value);
+}
+
+__device__ __forceinline__ bool level_wait(const Barrier& B, uint64_t* word, uint64_t* value) {
+  __shared__ uint32_t s_ok;
+  __shared__ unsigned long long s_v;
+  if (threadIdx.x == 0) {
     const uint64_t target = (uint64_t)gridDim.x + B.extra;
     uint32_t* abort_flag = B.lines + kBarAbort * 32;
     const uint64_t t0 = globaltimer();

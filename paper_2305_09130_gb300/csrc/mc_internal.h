@@ -107,6 +107,8 @@ struct ExploreArgs {
   uint64_t timeout_ns;
   const Ctrl* prev;       // lowering chained on the device: run at (prev's counterexample
                           // time) - 1, or not at all if prev held, failed or was skipped
+  uint64_t tag;           // tagged frontier log: this pass's tag in the key's spare top
+  uint64_t tag_mask;      // bits, and those bits (0: untagged; see the exploration kernel)
 };
 
 // Launch helpers implemented in mc_kernels.cu.  `split` is the probe scheme:

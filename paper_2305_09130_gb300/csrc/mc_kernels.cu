@@ -12,6 +12,18 @@
 //   control block  per-level widths, log offsets, minima of packed
 //                  (time, i, j) over violating terminals, the trace buffer.
 //
+// Tagged frontier log (64-bit keys with at least 8 spare top bits): every
+// pass stores its log keys with its own tag in those bits, and at the end of
+// a level a block arrives at the barrier and reserves the log space for its
+// warps' remaining winners in one atomic, then writes them.  Readers of the
+// next level therefore check the tag of every entry they load and, if the
+// entry is not yet this pass's, load it again (bounded by the barrier
+// timeout).  A position is written once per pass, so a matching tag means
+// the entry is the one this pass wrote.  The host clears the log when a
+// model reserves its buffers and whenever the tag counter wraps.  Without
+// spare bits the blocks reserve first, write, and arrive with a release
+// reduction, so the barrier alone orders the entries.
+//
 // Why a per-pass table that is never cleared between levels: every
 // transition raises sum(n) by one (the WG/TS selects sit at levels 1 and 2
 // and are written directly), so a state can only be generated again within
@@ -54,13 +66,36 @@ __device__ __forceinline__ void copy_out(const ExploreArgs& A, const K* keys, co
   for (uint32_t x = lane; x < n; x += 32) {
     const uint64_t at = at0 + x;
     if (at < A.log_cap) {
-      KeyOps<K>::store(A.log_keys, at, keys[x]);
+      KeyOps<K>::store(A.log_keys, at, keys[x] | (K)A.tag);
       A.log_par[at] = par[x];
     } else {
       set_error(A.ctrl, MC_ERR_FRONTIER);
       atomicOr(flags, kFlagError);
     }
   }
+}
+
+// The key of log entry `pos` of this pass from a first load `key`: in a
+// tagged log, loaded again until it carries this pass's tag, then stripped.
+// False (and MC_ERR_TIMEOUT) when it does not appear within the barrier
+// timeout.
+template <class K>
+__device__ __forceinline__ bool log_entry(const ExploreArgs& A, uint64_t pos, K& key) {
+  if (!A.tag_mask) return true;
+  const K mask = (K)A.tag_mask, tag = (K)A.tag;
+  if ((key & mask) != tag) {
+    const uint64_t t0 = globaltimer();
+    do {
+      __nanosleep(64);
+      key = KeyOps<K>::load(A.log_keys, pos);
+      if ((key & mask) != tag && globaltimer() - t0 > A.timeout_ns) {
+        set_error(A.ctrl, MC_ERR_TIMEOUT);
+        return false;
+      }
+    } while ((key & mask) != tag);
+  }
+  key &= ~mask;
+  return true;
 }
 
 // A tile of TILE >= P lanes handles kDepth states per round; lane c proposes,
@@ -79,7 +114,7 @@ __device__ __forceinline__ void copy_out(const ExploreArgs& A, const K* keys, co
 template <class K, int TILE, int RULE, bool SPLIT>
 __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st, uint64_t T,
                                              uint32_t L, uint64_t offL, uint64_t W, uint64_t offN,
-                                             const K (&first)[kDepth], bool have_first) {
+                                             const K (&first)[kDepth], bool have_first, uint32_t stop_mask) {
   constexpr int S = KeyOps<K>::kSlots;
   constexpr uint32_t D = kDepth;
   __shared__ __align__(16) K probe[kThreads][D][S];
@@ -117,9 +152,13 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
 #pragma unroll
     for (uint32_t d = 0; d < D; ++d) {
       const uint64_t s = base + d * kTilesPerWarp + my;
-      const bool valid = s < W;
-      const K key = key_next[d];
+      bool valid = s < W;
+      K key = key_next[d];
       if (s + stride < W) key_next[d] = KeyOps<K>::load(A.log_keys, offL + s + stride);
+      if (valid && !log_entry<K>(A, offL + s, key)) {
+        valid = false;
+        atomicOr(&st.flags, kFlagError);
+      }
       uint32_t i = 0, j = 0, r = 0;
       uint64_t t_c = 0, clk = 0;
       if (valid) {
@@ -224,14 +263,16 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
       fill = 0;
     }
   }
-  // end of level: one reservation per block for the warps' remainders
+  // end of level: one reservation per block for the warps' remainders; in a
+  // tagged log the same atomic is the block's arrival at the level barrier
   if (lane == 0) st.fill[warp] = fill;
   __syncthreads();
   const uint32_t nw = blockDim.x >> 5;
   if (threadIdx.x == 0) {
     uint32_t total = 0;
     for (uint32_t w = 0; w < nw; ++w) total += st.fill[w];
-    st.base = total ? level_reserve(lvl_next, total) : 0ull;
+    if (A.tag_mask) st.base = level_arrive_reserve(lvl_next, &st.flags, stop_mask, total);
+    else st.base = total ? level_reserve(lvl_next, total) : 0ull;
   }
   __syncthreads();
   if (fill) {
@@ -302,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, 4) explore_kernel(const ExploreArgs 
         key = ((K)(i + 1) << p.wg_shift) | ((K)(j + 1) << p.ts_shift);
         par = i;
       }
-      KeyOps<K>::store(A.log_keys, x, key);
+      KeyOps<K>::store(A.log_keys, x, key | (K)A.tag);
       A.log_par[x] = par;
     }
     if (threadIdx.x == 0) stage.flags = 0;
@@ -333,13 +374,14 @@ __global__ void __launch_bounds__(kThreads, 4) explore_kernel(const ExploreArgs 
     if (L >= p.max_level) break;  // the deepest level holds only terminals
     const uint64_t offN = off_last + W;
     if (gtid == 0) A.off[L + 1] = offN;
-    expand_level<K, TILE, RULE, SPLIT>(A, stage, T, L, off_last, W, offN, first, have_first);
+    const uint32_t stop_mask = kFlagError | (A.early_exit ? kFlagViolation : 0u);
+    expand_level<K, TILE, RULE, SPLIT>(A, stage, T, L, off_last, W, offN, first, have_first, stop_mask);
     // level L+1's width word doubles as the barrier: it ends with the width
     // and the number of blocks that saw an error or (with early exit) a
-    // violating terminal
+    // violating terminal (a tagged log's blocks arrived in expand_level)
     uint64_t word = 0;
-    if (!level_sync(bar, A.levels + 2 * (L + 1), &stage.flags,
-                    kFlagError | (A.early_exit ? kFlagViolation : 0u), &word))
+    if (!(A.tag_mask ? level_wait(bar, A.levels + 2 * (L + 1), &word)
+                     : level_sync(bar, A.levels + 2 * (L + 1), &stage.flags, stop_mask, &word)))
       return;
 #pragma unroll
     for (uint32_t d = 0; d < kDepth; ++d) {
@@ -348,6 +390,10 @@ __global__ void __launch_bounds__(kThreads, 4) explore_kernel(const ExploreArgs 
     }
     have_first = true;
     const uint64_t Wn = word & kLevelWidthMask;
+    if (offN + Wn > A.log_cap) {  // the same decision in every block (one final word)
+      set_error(ctrl, MC_ERR_FRONTIER);
+      break;
+    }
     if ((word >> kLevelStopShift) & 0xFFFFu) {  // an error, or level L+1 holds a violating terminal
       if (ld_relaxed_u32(&ctrl->err)) break;
       last = L + 1;
@@ -409,7 +455,8 @@ __global__ void __launch_bounds__(kThreads, 4) explore_kernel(const ExploreArgs 
   const uint32_t cfg_t = ti * p.b + tj;
   const uint32_t n_t = __ldg(p.N + cfg_t);
   for (uint64_t x = gtid; x < Ww; x += nthreads) {
-    const K key = KeyOps<K>::load(A.log_keys, offW + x);
+    K key = KeyOps<K>::load(A.log_keys, offW + x);
+    if (!log_entry<K>(A, offW + x, key)) break;
     if (field(key, p.wg_shift, p.wg_mask) - 1 != ti || field(key, p.ts_shift, p.ts_mask) - 1 != tj)
       continue;
     if (sum_n(key, p) != n_t || key_time(key, p, cfg_t) != tt) continue;
@@ -424,7 +471,8 @@ __global__ void __launch_bounds__(kThreads, 4) explore_kernel(const ExploreArgs 
   if (sizeof(K) == 16) {
     const uint64_t whi = ld_relaxed_u64(&ctrl->wkey_hi);
     for (uint64_t x = gtid; x < Ww; x += nthreads) {
-      const K key = KeyOps<K>::load(A.log_keys, offW + x);
+      K key = KeyOps<K>::load(A.log_keys, offW + x);
+      if (!log_entry<K>(A, offW + x, key)) break;
       if (KeyOps<K>::hi(key) != whi) continue;
       if (field(key, p.wg_shift, p.wg_mask) - 1 != ti || field(key, p.ts_shift, p.ts_mask) - 1 != tj)
         continue;
@@ -440,7 +488,8 @@ __global__ void __launch_bounds__(kThreads, 4) explore_kernel(const ExploreArgs 
     const uint64_t wlo = ld_relaxed_u64(&ctrl->wkey_lo);
     const uint64_t whi = sizeof(K) == 16 ? ld_relaxed_u64(&ctrl->wkey_hi) : 0;
     for (uint64_t x = gtid; x < Ww; x += nthreads) {
-      const K key = KeyOps<K>::load(A.log_keys, offW + x);
+      K key = KeyOps<K>::load(A.log_keys, offW + x);
+      if (!log_entry<K>(A, offW + x, key)) break;
       if (KeyOps<K>::lo(key) == wlo && KeyOps<K>::hi(key) == whi) ctrl->widx = x;
     }
   }
@@ -455,7 +504,8 @@ __global__ void __launch_bounds__(kThreads, 4) explore_kernel(const ExploreArgs 
     uint32_t l = wl;
     for (;;) {
       const uint64_t at = ld_relaxed_u64(&A.off[l]) + idx;
-      const K key = KeyOps<K>::load(A.log_keys, at);
+      K key = KeyOps<K>::load(A.log_keys, at);
+      if (!log_entry<K>(A, at, key)) return;
       A.trace[2 * l] = KeyOps<K>::lo(key);
       A.trace[2 * l + 1] = KeyOps<K>::hi(key);
       if (l == 0) break;

@@ -47,7 +47,7 @@ class McOptions(C.Structure):
                 ("max_probes", C.c_uint32), ("log_capacity", C.c_uint64),
                 ("barrier_timeout_ns", C.c_uint64), ("debug_barrier_extra", C.c_uint32),
                 ("timing", C.c_uint32), ("lanes_per_state", C.c_uint32),
-                ("probe_scheme", C.c_uint32), ("reserved", C.c_uint32 * 4)]
+                ("probe_scheme", C.c_uint32), ("no_log_tags", C.c_uint32), ("reserved", C.c_uint32 * 3)]
 
 
 class McCheckResult(C.Structure):
@@ -72,7 +72,7 @@ class McLayout(C.Structure):
                 ("max_level", C.c_uint32), ("n_shift", C.c_uint32 * 16),
                 ("table_slots", C.c_uint64), ("log_capacity", C.c_uint64),
                 ("max_width", C.c_uint64), ("state_bound", C.c_uint64),
-                ("device_bytes", C.c_uint64), ("probe_scheme", C.c_uint32), ("reserved", C.c_uint32)]
+                ("device_bytes", C.c_uint64), ("probe_scheme", C.c_uint32), ("log_tag_bits", C.c_uint32)]
 
 
 class McSwarmResult(C.Structure):

@@ -117,6 +117,22 @@ def test_probe_schemes_are_accepted_by_name_and_number(lib):
     assert layout(W.c1().with_key_bits(128), probe_scheme="split")["probe_scheme"] == mc.PROBE["split"]
 
 
+def test_frontier_log_tags_use_spare_key_bits(lib):
+    # 64-bit keys with at least 8 spare top bits tag their log entries (up to 16 bits)
+    assert layout(W.c1())["log_tag_bits"] == 16                    # 19 bits used
+    assert layout(W.c2_star())["log_tag_bits"] == 16               # 35 bits used
+    assert layout(W.c2(rule=W.GREEDY))["log_tag_bits"] == 13       # 51 bits used
+    assert layout(W.c1().with_key_bits(128))["log_tag_bits"] == 0  # 128-bit keys: untagged
+    # a=b=1, P=6, N=256: 1 + 1 + 6 x 9 = 56 bits, 8 spare; N=512: 62 bits, too few
+    wrap8 = W.ModelSpec("wrap8", 6, [1], [1], [256], [3], [1] * 6, W.GREEDY)
+    assert layout(wrap8)["used_bits"] == 56 and layout(wrap8)["log_tag_bits"] == 8
+    few = W.ModelSpec("few", 6, [1], [1], [512], [3], [1] * 6, W.GREEDY)
+    assert layout(few)["used_bits"] == 62 and layout(few)["log_tag_bits"] == 0
+    assert layout(W.c1(), no_log_tags=1)["log_tag_bits"] == 0
+    with pytest.raises(mc.MCError):
+        mc.mc_model_create(W.c1(), mc.mc_options_default(no_log_tags=2), allocator=None)
+
+
 def test_unknown_option_names_are_rejected(lib):
     with pytest.raises(TypeError):
         mc.mc_options_default(load_factor=10)  # the field is load_factor_pct

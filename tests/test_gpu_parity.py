@@ -343,3 +343,37 @@ def test_probe_schemes_at_full_size(mc, scheme):
         got = gpu_min(mc, model, "single", True)
         want = exp["min_time"]["single/prune1"]
         assert got == {k: want[k] for k in got}
+
+
+# ---------------------------------------------------------------- tagged frontier log
+
+def test_tagged_log_survives_tag_wrap(mc, oracle):
+    """8 spare key bits: the log's tag counter wraps every 255 passes (the
+    host clears the log then); 600 checks on one model all agree with the
+    oracle, and so does a min-time query after them."""
+    spec = W.ModelSpec("wrap8", 6, [1], [1], [256], [3], [1] * 6, GREEDY)
+    model = make(mc, spec)
+    assert mc.mc_model_layout(model)["log_tag_bits"] == 8
+    exp_min = oracle.min_time(spec)
+    t_min = exp_min["t_min"]
+    exp = {T: oracle.check(spec, T) for T in (t_min - 1, t_min)}
+    for k in range(600):
+        T = t_min - 1 + (k & 1)
+        assert gpu_check(mc, model, T, trace=(k % 50 == 0)) == exp[T], k
+    assert gpu_min(mc, model, "single", True) == exp_min
+
+
+def test_tagged_and_untagged_logs_agree(mc, oracle):
+    """The same models with a tagged log and with mc_options.no_log_tags:
+    identical counts, widths, checks and minima."""
+    for spec in (W.c1(FREE), W.c1(GREEDY), W.c2(rule=GREEDY)):
+        a, b = make(mc, spec), make(mc, spec, no_log_tags=1)
+        mc.mc_reserve(b)  # fixed once the buffers exist
+        assert mc.mc_model_layout(a)["log_tag_bits"] > 0 and mc.mc_model_layout(b)["log_tag_bits"] == 0
+        assert mc.mc_count_states(a) == mc.mc_count_states(b) == oracle.count(spec)
+        assert mc.mc_last_widths(a) == mc.mc_last_widths(b)
+        for T in thresholds(oracle, spec):
+            assert gpu_check(mc, a, T) == gpu_check(mc, b, T) == oracle.check(spec, T), T
+        assert mc.mc_model_layout(b)["log_tag_bits"] == 0
+        assert gpu_min(mc, a, "lower", True) == gpu_min(mc, b, "lower", True) == \
+            oracle.min_time(spec, search="lower", prune=True)
