@@ -197,11 +197,12 @@ typedef struct {
   uint64_t device_bytes; /* device memory the model needs                  */
   uint32_t probe_scheme; /* the insert its explorations use: MC_PROBE_SPLIT
                             or MC_PROBE_ONE_CALL (AUTO resolved)           */
-  uint32_t log_tag_bits; /* spare top key bits that tag each pass's
-                            frontier-log entries, so a block can arrive at a
-                            level's barrier before writing its last entries
-                            (64-bit keys with >= 8 spare bits, at most 16;
-                            0: untagged)                                   */
+  uint32_t log_tag_bits; /* bits per 64-bit word of a frontier-log entry
+                            that tag it with its pass, so a block can arrive
+                            at a level's barrier before writing its last
+                            entries: 8 to 16 where the key leaves that many
+                            spare (a 128-bit key is stored as two words of
+                            64 - log_tag_bits payload bits), else 0        */
 } mc_layout;
 
 /* Counters accumulated over the model's queries (reset by mc_reset_stats). */

@@ -313,9 +313,11 @@ bool valid_options(const mc_options* o) {
   return true;
 }
 
-// spare top bits of 64-bit keys that tag the frontier log (8 to 16), or 0
+// spare top bits per 64-bit word of a key that tag the frontier log (8 to
+// 16), or 0: a 128-bit key is stored as two words of 64 - t payload bits
 uint32_t log_tag_bits(const mc_model* m) {
-  const uint32_t spare = m->key_words == 1 && !m->opt.no_log_tags ? 64 - m->used_bits : 0;
+  if (m->opt.no_log_tags) return 0;
+  const uint32_t spare = m->key_words == 1 ? 64 - m->used_bits : (128 - m->used_bits) / 2;
   return spare >= 8 ? std::min<uint32_t>(spare, 16) : 0;
 }
 
@@ -523,8 +525,8 @@ int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, 
       MC_CUDA(m, cudaMemsetAsync(m->d_log_keys, 0, m->log_cap * 8ull * m->key_words, m->stream));
       m->tag = 1;
     }
-    A.tag_mask = ~0ull << (64 - m->tag_bits);
-    A.tag = (uint64_t)m->tag << (64 - m->tag_bits);
+    A.tag_bits = m->tag_bits;
+    A.tag = m->tag;
   }
   if (m->opt.timing) {
     const int rc_ = make_events(m);

@@ -107,8 +107,9 @@ struct ExploreArgs {
   uint64_t timeout_ns;
   const Ctrl* prev;       // lowering chained on the device: run at (prev's counterexample
                           // time) - 1, or not at all if prev held, failed or was skipped
-  uint64_t tag;           // tagged frontier log: this pass's tag in the key's spare top
-  uint64_t tag_mask;      // bits, and those bits (0: untagged; see the exploration kernel)
+  uint64_t tag;           // tagged frontier log: this pass's tag (< 2^tag_bits) and the
+  uint32_t tag_bits;      // bits it takes in each 64-bit word of a key (0: untagged; see
+  uint32_t pad2;          // the exploration kernel)
 };
 
 // Launch helpers implemented in mc_kernels.cu.  `split` is the probe scheme:

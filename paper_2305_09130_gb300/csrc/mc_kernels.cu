@@ -12,17 +12,19 @@
 //   control block  per-level widths, log offsets, minima of packed
 //                  (time, i, j) over violating terminals, the trace buffer.
 //
-// Tagged frontier log (64-bit keys with at least 8 spare top bits): every
-// pass stores its log keys with its own tag in those bits, and at the end of
+// Tagged frontier log (keys with at least 8 spare top bits per 64-bit word):
+// every pass stores its log keys with its own tag in the top bits of each
+// word (a 128-bit key is split into two halves of 64 - tag_bits bits), and at the end of
 // a level a block arrives at the barrier and reserves the log space for its
 // warps' remaining winners in one atomic, then writes them.  Readers of the
 // next level therefore check the tag of every entry they load and, if the
 // entry is not yet this pass's, load it again (bounded by the barrier
 // timeout).  A position is written once per pass, so a matching tag means
-// the entry is the one this pass wrote.  The host clears the log when a
-// model reserves its buffers and whenever the tag counter wraps.  Without
-// spare bits the blocks reserve first, write, and arrive with a release
-// reduction, so the barrier alone orders the entries.
+// the entry is the one this pass wrote; each 8-byte word is written and read
+// whole, so a 16-byte entry whose two tags match is whole too.  The host
+// clears the log when a model reserves its buffers and whenever the tag
+// counter wraps.  Without spare bits the blocks reserve first, write, and
+// arrive with a release reduction, so the barrier alone orders the entries.
 //
 // Why a per-pass table that is never cleared between levels: every
 // transition raises sum(n) by one (the WG/TS selects sit at levels 1 and 2
@@ -41,6 +43,40 @@ namespace mc {
 namespace {
 
 using namespace mc::dev;
+
+// How a key is stored in a tagged frontier log (see the top of this file).
+template <class K>
+struct LogTag;
+
+template <>
+struct LogTag<uint64_t> {  // payload in the low 64 - tb bits, the tag above
+  __device__ static uint64_t pack(uint64_t k, uint32_t tb, uint64_t tag) { return tb ? k | (tag << (64 - tb)) : k; }
+  __device__ static bool unpack(uint64_t& k, uint32_t tb, uint64_t tag) {
+    if ((k >> (64 - tb)) != tag) return false;
+    k &= ~0ull >> tb;
+    return true;
+  }
+};
+
+template <>
+struct LogTag<u128> {  // each 64-bit word: 64 - tb payload bits, then the tag
+  __device__ static u128 pack(u128 k, uint32_t tb, uint64_t tag) {
+    if (!tb) return k;
+    const uint32_t pb = 64 - tb;
+    const uint64_t m = ~0ull >> tb;
+    const uint64_t lo = ((uint64_t)k & m) | (tag << pb);
+    const uint64_t hi = ((uint64_t)(k >> pb) & m) | (tag << pb);
+    return ((u128)hi << 64) | lo;
+  }
+  __device__ static bool unpack(u128& k, uint32_t tb, uint64_t tag) {
+    const uint32_t pb = 64 - tb;
+    const uint64_t lo = (uint64_t)k, hi = (uint64_t)(k >> 64);
+    if ((lo >> pb) != tag || (hi >> pb) != tag) return false;
+    const uint64_t m = ~0ull >> tb;
+    k = ((u128)(hi & m) << pb) | (lo & m);
+    return true;
+  }
+};
 
 // ------------------------------------------------------------------ expansion of one level
 // Winners are staged per warp in shared memory.  A warp whose buffer is
@@ -66,7 +102,7 @@ __device__ __forceinline__ void copy_out(const ExploreArgs& A, const K* keys, co
   for (uint32_t x = lane; x < n; x += 32) {
     const uint64_t at = at0 + x;
     if (at < A.log_cap) {
-      KeyOps<K>::store(A.log_keys, at, keys[x] | (K)A.tag);
+      KeyOps<K>::store(A.log_keys, at, LogTag<K>::pack(keys[x], A.tag_bits, A.tag));
       A.log_par[at] = par[x];
     } else {
       set_error(A.ctrl, MC_ERR_FRONTIER);
@@ -81,21 +117,17 @@ __device__ __forceinline__ void copy_out(const ExploreArgs& A, const K* keys, co
 // timeout.
 template <class K>
 __device__ __forceinline__ bool log_entry(const ExploreArgs& A, uint64_t pos, K& key) {
-  if (!A.tag_mask) return true;
-  const K mask = (K)A.tag_mask, tag = (K)A.tag;
-  if ((key & mask) != tag) {
-    const uint64_t t0 = globaltimer();
-    do {
-      __nanosleep(64);
-      key = KeyOps<K>::load(A.log_keys, pos);
-      if ((key & mask) != tag && globaltimer() - t0 > A.timeout_ns) {
-        set_error(A.ctrl, MC_ERR_TIMEOUT);
-        return false;
-      }
-    } while ((key & mask) != tag);
+  if (!A.tag_bits || LogTag<K>::unpack(key, A.tag_bits, A.tag)) return true;
+  const uint64_t t0 = globaltimer();
+  for (;;) {
+    __nanosleep(64);
+    key = KeyOps<K>::load(A.log_keys, pos);
+    if (LogTag<K>::unpack(key, A.tag_bits, A.tag)) return true;
+    if (globaltimer() - t0 > A.timeout_ns) {
+      set_error(A.ctrl, MC_ERR_TIMEOUT);
+      return false;
+    }
   }
-  key &= ~mask;
-  return true;
 }
 
 // A tile of TILE >= P lanes handles kDepth states per round; lane c proposes,
@@ -271,7 +303,7 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
   if (threadIdx.x == 0) {
     uint32_t total = 0;
     for (uint32_t w = 0; w < nw; ++w) total += st.fill[w];
-    if (A.tag_mask) st.base = level_arrive_reserve(lvl_next, &st.flags, stop_mask, total);
+    if (A.tag_bits) st.base = level_arrive_reserve(lvl_next, &st.flags, stop_mask, total);
     else st.base = total ? level_reserve(lvl_next, total) : 0ull;
   }
   __syncthreads();
@@ -343,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, 4) explore_kernel(const ExploreArgs 
         key = ((K)(i + 1) << p.wg_shift) | ((K)(j + 1) << p.ts_shift);
         par = i;
       }
-      KeyOps<K>::store(A.log_keys, x, key | (K)A.tag);
+      KeyOps<K>::store(A.log_keys, x, LogTag<K>::pack(key, A.tag_bits, A.tag));
       A.log_par[x] = par;
     }
     if (threadIdx.x == 0) stage.flags = 0;
@@ -380,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, 4) explore_kernel(const ExploreArgs 
     // and the number of blocks that saw an error or (with early exit) a
     // violating terminal (a tagged log's blocks arrived in expand_level)
     uint64_t word = 0;
-    if (!(A.tag_mask ? level_wait(bar, A.levels + 2 * (L + 1), &word)
+    if (!(A.tag_bits ? level_wait(bar, A.levels + 2 * (L + 1), &word)
                      : level_sync(bar, A.levels + 2 * (L + 1), &stage.flags, stop_mask, &word)))
       return;
 #pragma unroll

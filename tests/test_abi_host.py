@@ -122,7 +122,13 @@ def test_frontier_log_tags_use_spare_key_bits(lib):
     assert layout(W.c1())["log_tag_bits"] == 16                    # 19 bits used
     assert layout(W.c2_star())["log_tag_bits"] == 16               # 35 bits used
     assert layout(W.c2(rule=W.GREEDY))["log_tag_bits"] == 13       # 51 bits used
-    assert layout(W.c1().with_key_bits(128))["log_tag_bits"] == 0  # 128-bit keys: untagged
+    # 128-bit keys: two words of 64 - t payload bits, t <= (128 - used) / 2
+    assert layout(W.c1().with_key_bits(128))["log_tag_bits"] == 16  # 19 bits used
+    assert layout(W.c3(rule=W.GREEDY))["log_tag_bits"] == 8         # 111 bits used
+    wrap8w = W.ModelSpec("wrap8w", 10, [1], [1], [1024], [3], [1] * 10, W.GREEDY)
+    assert layout(wrap8w)["used_bits"] == 112 and layout(wrap8w)["log_tag_bits"] == 8
+    few128 = W.ModelSpec("few128", 10, [1, 2, 4], [1], [1024] * 3, [3] * 3, [1] * 10, W.GREEDY)
+    assert layout(few128)["used_bits"] == 113 and layout(few128)["log_tag_bits"] == 0
     # a=b=1, P=6, N=256: 1 + 1 + 6 x 9 = 56 bits, 8 spare; N=512: 62 bits, too few
     wrap8 = W.ModelSpec("wrap8", 6, [1], [1], [256], [3], [1] * 6, W.GREEDY)
     assert layout(wrap8)["used_bits"] == 56 and layout(wrap8)["log_tag_bits"] == 8

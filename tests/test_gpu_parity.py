@@ -347,11 +347,14 @@ def test_probe_schemes_at_full_size(mc, scheme):
 
 # ---------------------------------------------------------------- tagged frontier log
 
-def test_tagged_log_survives_tag_wrap(mc, oracle):
-    """8 spare key bits: the log's tag counter wraps every 255 passes (the
-    host clears the log then); 600 checks on one model all agree with the
-    oracle, and so does a min-time query after them."""
-    spec = W.ModelSpec("wrap8", 6, [1], [1], [256], [3], [1] * 6, GREEDY)
+@pytest.mark.parametrize("spec", [W.ModelSpec("wrap8", 6, [1], [1], [256], [3], [1] * 6, GREEDY),
+                                  W.ModelSpec("wrap8w", 10, [1], [1], [1024], [3], [1] * 10, GREEDY)],
+                         ids=["u64", "u128"])
+def test_tagged_log_survives_tag_wrap(mc, oracle, spec):
+    """8 tag bits (56 of 64 key bits used; 112 of 128, two 56-bit words):
+    the log's tag counter wraps every 255 passes (the host clears the log
+    then); 600 checks on one model all agree with the oracle, and so does a
+    min-time query after them."""
     model = make(mc, spec)
     assert mc.mc_model_layout(model)["log_tag_bits"] == 8
     exp_min = oracle.min_time(spec)
@@ -366,7 +369,8 @@ def test_tagged_log_survives_tag_wrap(mc, oracle):
 def test_tagged_and_untagged_logs_agree(mc, oracle):
     """The same models with a tagged log and with mc_options.no_log_tags:
     identical counts, widths, checks and minima."""
-    for spec in (W.c1(FREE), W.c1(GREEDY), W.c2(rule=GREEDY)):
+    for spec in (W.c1(FREE), W.c1(GREEDY), W.c2(rule=GREEDY), W.c1(FREE).with_key_bits(128),
+                 W.c1(GREEDY).with_key_bits(128)):
         a, b = make(mc, spec), make(mc, spec, no_log_tags=1)
         mc.mc_reserve(b)  # fixed once the buffers exist
         assert mc.mc_model_layout(a)["log_tag_bits"] > 0 and mc.mc_model_layout(b)["log_tag_bits"] == 0
@@ -377,3 +381,20 @@ def test_tagged_and_untagged_logs_agree(mc, oracle):
         assert mc.mc_model_layout(b)["log_tag_bits"] == 0
         assert gpu_min(mc, a, "lower", True) == gpu_min(mc, b, "lower", True) == \
             oracle.min_time(spec, search="lower", prune=True)
+
+
+def test_tagged_log_on_c3_literal(mc, oracle):
+    """C3 literal (GREEDY, 111 of 128 key bits, 8 tag bits per word, 4,099
+    levels): tagged and untagged logs give the golden count, every level's
+    width and the minimum."""
+    spec = W.c3(rule=GREEDY)
+    g = golden()["c3_greedy"]
+    exp = g["min_time"]["single/prune1"]
+    for opts in ({}, {"no_log_tags": 1}):
+        model = make(mc, spec, **opts)
+        mc.mc_reserve(model)
+        assert mc.mc_model_layout(model)["log_tag_bits"] == (0 if opts else 8)
+        assert mc.mc_count_states(model) == g["count"] == CF.count(spec)
+        assert mc.mc_last_widths(model) == CF.widths(spec)
+        got = gpu_min(mc, model, "single", True)
+        assert got == {k: exp[k] for k in got}
