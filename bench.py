@@ -1,22 +1,29 @@
 #!/usr/bin/env python
 """Benchmark of the explorer: unique states/s and time-to-optimal-config.
 
-One step = one ``mc_min_time`` query of the medium workload (C2 at G=80:
-P=4 compute units, WG in 2^0..2^8, TS in 2^0..2^4, FREE dispatch, formula
-cost, per-unit speeds U{1..3} from splitmix64 seed 2305091302; 10,385,335
-reachable states) with iterative threshold lowering and no pruning -- each
-check explores like an exhaustive verifier and stops at its first
-counterexample level, and the last check (T_min - 1, which holds) explores
-every reachable state.  A step covers every stage of the path: the WG/TS
-selects, level expansion, visited-set inserts, the property on terminals,
-the min-reduction and threshold refinement, and the witness trace.
+One step = one ``mc_min_time`` query of the large workload (C3 at G=36:
+P=8 compute units, WG in 2^0..2^9, TS in 2^0..2^5, FREE dispatch, cost
+U{1..16} per (WG, TS) from splitmix64 seed 2305091303, 128-bit packed
+states; 1,072,924,481 reachable states, closed form) with iterative
+threshold lowering and no pruning -- each check explores like an exhaustive
+verifier and stops at its first counterexample level, and the last check
+(T_min - 1, which holds) explores every reachable state.  A step covers
+every stage of the path: the WG/TS selects, level expansion, visited-set
+inserts, the property on terminals, the min-reduction and threshold
+refinement, and the witness trace.
 
 Output: one JSON line (rank 0).  ``value`` = unique states explored per
 second of device time with the model resident in HBM; ``e2e`` = the same
 metric through the public C-ABI calls from host buffers (create, query,
 destroy); ``roofline`` = the exploration kernel's algorithmic bytes per
-launch over its event-timed duration against the measured HBM copy peak;
-``cpu_baseline`` = the CPU oracle on a bounded sample of the same workload.
+launch over its event-timed duration against the measured HBM copy peak,
+beside its probe rate against the random 32-byte read+CAS rate measured in
+the same run; ``cpu_baseline`` = the CPU oracle on a bounded sample of the
+same workload.  The default run adds ``secondary`` (the medium workload C2
+at G=80, 64-bit keys), ``batched`` (256 uneven instances in one batch
+against the same queries one at a time) and ``served`` (Poisson arrivals of
+large-model queries at two rates, against the same arrivals served one at a
+time through the single-model calls).
 
 ``--impl reference`` times the CPU oracle instead (the method's plain CPU
 restatement) on bounded samples of the same workload.
@@ -33,6 +40,7 @@ import subprocess
 import sys
 import tempfile
 import time
+from dataclasses import dataclass, field
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -41,31 +49,57 @@ if ROOT not in sys.path:
 from paper_2305_09130_gb300 import pe_workloads as PW  # noqa: E402
 from paper_2305_09130_gb300 import workloads as W  # noqa: E402
 
+
+@dataclass
+class Workload:
+    make: object                 # () -> ModelSpec
+    desc: str
+    dtype: str                   # key width the path computes in
+    expect: tuple = None         # (T_min, WG, TS) of mc_min_time, from the closed form / the oracle
+    cpu_T: int = None            # CPU baseline: oracle check(T) with pruning (None: check(T_min - 1) unpruned)
+    ref_T: int = None            # reference arm: oracle check(T) with pruning per step
+    tune: dict = field(default_factory=dict)   # autotuner space (option -> candidates)
+    traffic: str = None          # committed ncu DRAM-traffic summary for roofline.traffic
+
+
 WORKLOADS = {
-    # name: (spec factory, description)
-    "c2_star": (lambda: W.c2_star(), None),
-    "c3_star": (lambda: W.c3_star(),
-                "c3_star: G=36, P=8, WG 2^0..2^9, TS 2^0..2^5, FREE, cost U{1..16} (splitmix64 seed "
-                "2305091303), 128-bit keys; 1,072,924,481 reachable states"),
-    "c2": (lambda: W.c2(rule=W.GREEDY),
-           "c2: G=1024, P=4, WG 2^0..2^8, TS 2^0..2^4, GREEDY, cost ceil(WG/TS)*4+WG+2*TS, speeds U{1..3} "
-           "(splitmix64 seed 2305091302), 64-bit keys (deep, narrow levels)"),
-    "c3": (lambda: W.c3(rule=W.GREEDY),
-           "c3: G=4096, P=8, WG 2^0..2^9, TS 2^0..2^5, GREEDY, cost U{1..16} (splitmix64 seed "
-           "2305091303), 128-bit keys"),
-    "c3_star_g24": (lambda: W.c3(G=24, rule=W.FREE, key_bits=128),
-                    "c3 at G=24: P=8, WG 2^0..2^9, TS 2^0..2^5, FREE, cost U{1..16} (seed 2305091303), "
-                    "128-bit keys (a reduced C3* for profiling)"),
+    "c3_star": Workload(
+        lambda: W.c3_star(),
+        "c3_star: G=36, P=8, WG 2^0..2^9, TS 2^0..2^5, FREE dispatch, cost U{1..16} per (WG, TS) "
+        "(splitmix64 seed 2305091303), speed 1, 128-bit packed states; 1,072,924,481 reachable states "
+        "(closed form), widest level 193,344,684",
+        "u128", expect=(1, 512, 2), cpu_T=30, ref_T=16,
+        tune={"probe_scheme": ["split", "one_call"], "load_factor_pct": [25, 40]},
+        traffic="explore_kernel_c3star_traffic.txt"),
+    "c2_star": Workload(
+        lambda: W.c2_star(),
+        "c2_star: G=80, P=4, WG 2^0..2^8, TS 2^0..2^4, FREE dispatch, cost ceil(WG/TS)*4+WG+2*TS, "
+        "speeds U{1..3} (splitmix64 seed 2305091302), 64-bit packed states; 10,385,335 reachable states",
+        "u64", expect=(96, 8, 4), cpu_T=None, ref_T=300,
+        tune={"probe_scheme": ["split", "one_call"], "load_factor_pct": [10, 15]},
+        traffic="explore_kernel_c2star_traffic.txt"),
+    "c2": Workload(
+        lambda: W.c2(rule=W.GREEDY),
+        "c2: G=1024, P=4, WG 2^0..2^8, TS 2^0..2^4, GREEDY, cost ceil(WG/TS)*4+WG+2*TS, speeds U{1..3} "
+        "(splitmix64 seed 2305091302), 64-bit keys (deep, narrow levels)", "u64",
+        tune={"probe_scheme": ["split", "one_call"]}),
+    "c3": Workload(
+        lambda: W.c3(rule=W.GREEDY),
+        "c3: G=4096, P=8, WG 2^0..2^9, TS 2^0..2^5, GREEDY, cost U{1..16} (splitmix64 seed "
+        "2305091303), 128-bit keys", "u128", tune={"probe_scheme": ["split", "one_call"]}),
+    "c3_star_g24": Workload(
+        lambda: W.c3(G=24, rule=W.FREE, key_bits=128),
+        "c3 at G=24: P=8, WG 2^0..2^9, TS 2^0..2^5, FREE, cost U{1..16} (seed 2305091303), "
+        "128-bit keys (a reduced C3* for profiling: 63,885,179 states)", "u128",
+        tune={"probe_scheme": ["split", "one_call"]}),
 }
+DEFAULT_WORKLOAD = "c3_star"
 METRIC = "unique states/sec"
 UNIT = "states/s"
-WORKLOAD = ("c2_star: G=80, P=4, WG 2^0..2^8, TS 2^0..2^4, FREE dispatch, cost ceil(WG/TS)*4+WG+2*TS, "
-            "speeds U{1..3} (splitmix64 seed 2305091302); 10,385,335 reachable states")
-REFERENCE_SAMPLE_T = 300     # pruned check of the same model: ~0.74M states
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SRCS = [os.path.join(ROOT, "paper_2305_09130_gb300", "csrc", f)
                for f in ("mc_kernels.cu", "mc_device.cuh", "mc_internal.h")]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "explore_kernel_c2star_traffic.txt")
+PROFILES = os.path.join(ROOT, "profiles")
 
 
 # ---------------------------------------------------------------- distributed helpers
@@ -179,37 +213,59 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_launch(load_factor_pct: int, probe_scheme: str):
-    """dram bytes per exploration launch from the committed ncu summary, or
+def read_traffic_file(path: str) -> dict:
+    fields = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+    return fields
+
+
+def ncu_traffic_per_launch(path: str, load_factor_pct: int, probe_scheme: str, states_per_launch: float):
+    """DRAM bytes per exploration launch from a committed ncu summary, or
     None when the summary is missing, was taken on another kernel source, or
     holds no capture at this visited-set load factor and probe scheme
-    ("split" or "one_call")."""
+    ("split" or "one_call").  A summary taken on the benchmarked launches
+    gives ``dram_bytes_per_launch_lf<LF>_<scheme>``; one taken on a smaller
+    case of the same kernel gives ``dram_bytes_per_state_<scheme>``, scaled
+    here by the states one launch processes (the traffic of this DRAM-bound
+    kernel grows with the states it inserts)."""
     try:
-        fields = {}
-        with open(TRAFFIC_FILE) as f:
-            for line in f:
-                if ":" in line and not line.startswith("#"):
-                    k, v = line.split(":", 1)
-                    fields[k.strip()] = v.strip()
+        fields = read_traffic_file(path)
         if fields.get("kernel_source_sha256_16") != kernel_source_hash():
             return None
-        return float(fields[f"dram_bytes_per_launch_lf{int(load_factor_pct)}_{probe_scheme}"])
+        key = f"dram_bytes_per_launch_lf{int(load_factor_pct)}_{probe_scheme}"
+        if key in fields:
+            return float(fields[key])
+        key = f"dram_bytes_per_state_{probe_scheme}"
+        if key in fields:
+            return float(fields[key]) * states_per_launch
+        return None
     except (OSError, KeyError, ValueError):
         return None
 
 
 # ---------------------------------------------------------------- arms
-def cpu_baseline_sample(spec, t_min: int) -> dict:
-    """The oracle as it stands on the holding check check(T_min - 1) of the
-    workload without pruning: a full DFS over every reachable state."""
+def cpu_baseline_sample(spec, wl: Workload, t_min: int) -> dict:
+    """The oracle as it stands on a bounded sample of the workload: a pruned
+    check(T) (the states of time <= T) or, for a workload the oracle finishes
+    in seconds, the holding check check(T_min - 1) without pruning."""
     from oracle import oracle as O
     O.build()
     t0 = time.perf_counter()
-    r = O.check(spec, t_min - 1, prune=False, early_exit=True)
+    if wl.cpu_T is None:
+        r = O.check(spec, t_min - 1, prune=False, early_exit=True)
+        what = f"check(T_min-1={t_min - 1}) without pruning"
+    else:
+        r = O.check(spec, wl.cpu_T, prune=True, early_exit=False)
+        what = f"check(T={wl.cpu_T}) with pruning (every state of time <= {wl.cpu_T})"
     dt = time.perf_counter() - t0
-    return {"value": r["states"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle DFS (std::unordered_set) over check(T_min-1={t_min - 1}) of c2_star "
-                      f"without pruning: {r['states']} states in {dt:.2f} s, single thread"}
+    return {"value": r["states"] / dt, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"oracle DFS (std::unordered_set) over {what} of {spec.name}: {r['states']} states "
+                      f"in {dt:.2f} s, single thread on a host with {os.cpu_count()} cores"}
 
 
 def run_reference(args):
@@ -218,11 +274,13 @@ def run_reference(args):
         return 0
     from oracle import oracle as O
     O.build()
-    spec = W.c2_star()
+    wl = WORKLOADS[args.workload or DEFAULT_WORKLOAD]
+    spec = wl.make()
+    T = wl.ref_T if wl.ref_T is not None else 16
 
     def step():
         t0 = time.perf_counter()
-        r = O.check(spec, REFERENCE_SAMPLE_T, prune=True, early_exit=False)
+        r = O.check(spec, T, prune=True, early_exit=False)
         return r["states"], time.perf_counter() - t0
 
     for _ in range(args.warmup):
@@ -234,15 +292,16 @@ def run_reference(args):
         states += s
         secs += dt
     value = states / secs
-    sample = (f"each step: oracle DFS over check(T={REFERENCE_SAMPLE_T}) of c2_star with pruning, "
-              f"{states // max(args.steps, 1)} states, single thread")
+    sample = (f"each step: oracle DFS over check(T={T}) of {spec.name} with pruning (every state of time "
+              f"<= {T}), {states // max(args.steps, 1)} states, single thread on a host with "
+              f"{os.cpu_count()} cores")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "scaling": "weak", "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
+            "config": {"workload": wl.desc, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
@@ -250,38 +309,38 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
+def measure_single(args, name: str, steps: int, warmup: int, device, stream, local: int,
+                   cpu_baseline: bool, random_roofline: bool) -> dict:
+    """One workload's line: `steps` timed mc_min_time (or mc_count_states)
+    queries on a resident model, the exploration kernel's roofline, the end
+    to end rate through the C-ABI from host buffers, and optionally the CPU
+    oracle on a bounded sample."""
     import torch
 
+    from paper_2305_09130_gb300 import autotune as AT
     from paper_2305_09130_gb300 import mc
 
-    rank, world, local = dist_env()
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
-    torch.cuda.set_device(local)
-    device = torch.device("cuda", local)
-    dist_init(world, True)
-    spec = WORKLOADS[args.workload][0]()
-    workload = WORKLOADS[args.workload][1] or WORKLOAD
-    # visited-set load factor (C2 at G=80) and probe scheme from the
-    # autotuner (outside the timed region; every candidate must return the
-    # same answer) unless fixed on the command line; launch shape at the
-    # occupancy maximum, which the tuner also picks for this kernel
-    from paper_2305_09130_gb300 import autotune as AT
-
+    wl = WORKLOADS[name]
+    spec = wl.make()
+    # visited-set load factor and probe scheme from the autotuner (outside
+    # the timed region; every candidate must return the same answer) unless
+    # fixed on the command line; launch shape at the occupancy maximum
     space, fixed = {}, {}
-    if args.load_factor:
+    for k, cands in wl.tune.items():
+        if k == "load_factor_pct" and args.load_factor:
+            fixed[k] = args.load_factor
+        elif k == "probe_scheme" and args.probe_scheme != "tune":
+            fixed[k] = mc.PROBE[args.probe_scheme]
+        else:
+            space[k] = [mc.PROBE[c] for c in cands] if k == "probe_scheme" else list(cands)
+    if args.load_factor and "load_factor_pct" not in fixed:
         fixed["load_factor_pct"] = args.load_factor
-    elif args.workload == "c2_star":
-        space["load_factor_pct"] = [10, 15]
+    if args.probe_scheme not in ("tune",) and "probe_scheme" not in fixed:
+        fixed["probe_scheme"] = mc.PROBE[args.probe_scheme]
     if args.no_log_tags:
         fixed["no_log_tags"] = 1
-    if args.probe_scheme == "tune":
-        space["probe_scheme"] = [mc.PROBE["split"], mc.PROBE["one_call"]]
-    else:
-        fixed["probe_scheme"] = mc.PROBE[args.probe_scheme]
 
-    def lf_measure(c):
+    def tune_measure(c):
         m = mc.mc_model_create(spec, mc.mc_options_default(search=args.mode, prune=args.prune, timing=1,
                                                            **fixed, **c),
                                allocator="torch")
@@ -293,11 +352,11 @@ def run_ours(args):
             ans = run()
             best = min(best, mc.mc_get_stats(m)["explore_ms"])
         mc.mc_model_destroy(m)
+        torch.cuda.empty_cache()
         return best, ans
-    tuned = AT.tune(lf_measure, space, reps=1) if space else {"options": {}}
+    tuned = AT.tune(tune_measure, space, reps=1) if space else {"options": {}}
     chosen = {**fixed, **tuned["options"]}
     opts = mc.mc_options_default(search=args.mode, prune=args.prune, timing=1, **chosen)
-    stream = torch.cuda.Stream(device)
     model = mc.mc_model_create(spec, opts, allocator="torch", stream=stream)
     mc.mc_reserve(model)
     layout = mc.mc_model_layout(model)
@@ -317,13 +376,12 @@ def run_ours(args):
             return mc.mc_min_time(model, trace=True)
 
     ref = None
-    for w in range(args.warmup):
+    for w in range(warmup):
         flush_l2(w)
         ref = query()
-    if args.workload == "c2_star" and args.query == "min_time":
-        expect = (96, 8, 4)  # T_min and (WG, TS) of this workload, from the oracle
-        if (ref["t_min"], ref["wg"], ref["ts"]) != expect:
-            raise SystemExit(f"wrong result {ref} != {expect}")
+    if wl.expect and args.query == "min_time":
+        if (ref["t_min"], ref["wg"], ref["ts"]) != wl.expect:
+            raise SystemExit(f"wrong result on {name}: {ref} != {wl.expect}")
     if args.query == "count" and spec.rule == W.FREE and ref["states"] != layout["state_bound"]:
         raise SystemExit(f"wrong count {ref['states']} != {layout['state_bound']}")
 
@@ -333,9 +391,9 @@ def run_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+          for _ in range(steps)]
     wall0 = time.perf_counter()
-    for k in range(args.steps):
+    for k in range(steps):
         flush_l2(k)
         ev[k][0].record(stream)
         r = query()
@@ -355,37 +413,55 @@ def run_ours(args):
     # roofline of the exploration kernel (events on the model's stream)
     bps = algorithmic_bytes_per_state(spec.P, layout["key_words"])
     launches = st["explore_launches"]
+    states_per_launch = st["states"] / max(launches, 1)
     achieved = bps * st["states"] / (st["explore_ms"] / 1000.0) / 1e9
     peak, peak_kind = measured_hbm_peak()
-    traffic = (ncu_traffic_per_launch(opts.load_factor_pct, scheme)
-               if (args.workload, args.query) == ("c2_star", "min_time") else None)
+    traffic = (ncu_traffic_per_launch(os.path.join(PROFILES, wl.traffic), layout_lf(opts), scheme,
+                                      states_per_launch)
+               if wl.traffic and args.query == "min_time" else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "algorithmic_bytes_per_launch": bps * st["states"] / max(launches, 1),
-                "bytes_per_state": bps, "states_per_launch": st["states"] / max(launches, 1),
+                "algorithmic_bytes_per_launch": bps * states_per_launch,
+                "bytes_per_state": bps, "states_per_launch": states_per_launch,
                 "avg_launch_ms": st["explore_ms"] / max(launches, 1),
                 "kernel": f"explore_kernel<u{64 * layout['key_words']}, tile {1 << (spec.P - 1).bit_length()}, "
                           f"{'FREE' if spec.rule == W.FREE else 'GREEDY'}, {scheme} insert>",
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                                if peak_kind == "measured" else "fallback 6.8 TB/s"}
+    if wl.traffic:
+        roofline["traffic_source"] = (f"profiles/{wl.traffic}: dram__bytes_read.sum + dram__bytes_write.sum "
+                                      f"per exploration launch from ncu (null when the kernel source changed "
+                                      f"since the capture)")
     gpu_launches = st["explore_launches"] + st["other_launches"]
     # random-access ceilings (outside the timed region): random 32-byte sector
-    # reads over a buffer far larger than L2, and over one the size of this
-    # model's visited set (L2-resident when it fits)
-    if not args.no_random_roofline:
+    # reads and reads followed by a CAS over a buffer far larger than L2, and
+    # reads over one the size of this model's visited set (L2-resident when
+    # it fits)
+    if random_roofline:
         table_bytes = layout["table_slots"] * 8 * layout["key_words"]
         hbm = mc.mc_measure_random_access(64 << 30, 200_000_000, 0)
         hbm_cas = mc.mc_measure_random_access(64 << 30, 200_000_000, 1)
         l2 = mc.mc_measure_random_access(max(table_bytes, 1 << 20), 200_000_000, 0)
-        probes = spec.P * st["states"] / (st["explore_ms"] / 1000.0)
+        explore_s = st["explore_ms"] / 1000.0
+        probes = spec.P * st["states"] / explore_s
+        # P probe reads and about one CAS per unique state: the rate of a
+        # kernel that did nothing else, at the measured random-access rates
+        ceiling = 1.0 / (spec.P / hbm["sectors_per_s"] + 1.0 / hbm_cas["sectors_per_s"])
         roofline["random_access"] = {
             "hbm_64GiB_sector_reads_per_s": hbm["sectors_per_s"],
             "hbm_64GiB_sector_read_cas_per_s": hbm_cas["sectors_per_s"],
             "table_sized_sector_reads_per_s": l2["sectors_per_s"],
             "table_bytes": table_bytes,
             "kernel_probe_reads_per_s": probes,
+            "frac_of_hbm_64GiB": probes / hbm["sectors_per_s"],
             "frac_of_table_sized": probes / l2["sectors_per_s"],
-            "note": "one 32-byte bucket read per generated successor (P per state)"}
+            "states_per_s_ceiling_hbm": ceiling,
+            "kernel_states_per_s": st["states"] / explore_s,
+            "frac_of_states_ceiling_hbm": (st["states"] / explore_s) / ceiling,
+            "note": "P random 32-byte bucket reads per unique state (one per generated successor) and about "
+                    "one CAS; ceiling = 1 / (P / read rate + 1 / read+CAS rate) over 64 GiB"}
+        if traffic:
+            roofline["random_access"]["dram_bytes_per_state"] = traffic / states_per_launch
 
     # end to end through the public C-ABI from host buffers, as a C caller
     # makes the calls: create (H2D of the model arrays through pinned
@@ -394,7 +470,7 @@ def run_ours(args):
     e2e_opts = mc.mc_options_default(search=args.mode, prune=args.prune, **chosen)
     e2e_s = []
     h2d = d2h = 0
-    for k in range(args.steps):
+    for k in range(steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         m2 = mc.mc_model_create(spec, e2e_opts, allocator=None, stream=stream)
@@ -411,13 +487,12 @@ def run_ours(args):
         assert r2["t_min"] == r["t_min"]
     e2e_total = reduce_scalar(sum(e2e_s), "max", device)
     e2e_value = states_all / e2e_total
+    mc.mc_release_cached()
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic (seeded model description; no dataset)",
-        "config": {"workload": workload,
+        "metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": dev_ms_max / steps,
+        "dtype": wl.dtype,
+        "config": {"workload": wl.desc,
                    "query": (f"mc_min_time search={args.mode} prune={int(args.prune)} early_exit=1 "
                              f"(iterative threshold lowering from the simulated T_ini)"
                              if args.query == "min_time" else "mc_count_states (every reachable state)"),
@@ -425,25 +500,69 @@ def run_ours(args):
                    "autotuned": tuned["options"], "autotune_ms": tuned.get("timings", {}),
                    "options_fixed": fixed,
                    "probe_scheme": scheme,
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "states_per_step": states_local / args.steps,
+                   "load_factor_pct": layout_lf(opts),
+                   "visited_set_bytes": layout["table_slots"] * 8 * layout["key_words"],
+                   "frontier_log_bytes": layout["log_capacity"] * (8 * layout["key_words"] + 4),
+                   "states_per_step": states_local / steps,
                    "checks_per_step": r["checks"]},
-        "time_to_optimal_config_ms": dev_ms_max / args.steps,
-        "result": {"t_min": r["t_min"], "wg": r["wg"], "ts": r["ts"], "t_ini": r["t_ini"]},
+        "time_to_optimal_config_ms": dev_ms_max / steps,
+        "result": {"t_min": r["t_min"], "wg": r["wg"], "ts": r["ts"], "t_ini": r["t_ini"],
+                   "expected": list(wl.expect) if wl.expect else None},
         "roofline": roofline,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
-                "d2h_bytes_per_step": d2h // args.steps,
-                "ms_per_step": 1000.0 * e2e_total / args.steps},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // steps,
+                "d2h_bytes_per_step": d2h // steps,
+                "ms_per_step": 1000.0 * e2e_total / steps},
         "gpu_launches": gpu_launches,
         "clocks": clocks,
         "wall_s_timed_region": wall,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "c2_star" \
-            and args.query == "min_time":
-        line["cpu_baseline"] = cpu_baseline_sample(spec, r["t_min"])
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     mc.mc_model_destroy(model)
+    del flush
+    torch.cuda.empty_cache()
+    if cpu_baseline and args.query == "min_time":
+        line["cpu_baseline"] = cpu_baseline_sample(spec, wl, r["t_min"])
+    return line
+
+
+def layout_lf(opts) -> int:
+    return int(opts.load_factor_pct)
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist_init(world, True)
+    stream = torch.cuda.Stream(device)
+    name = args.workload or DEFAULT_WORKLOAD
+    default_run = args.workload is None
+    first = rank == 0 and world == 1
+    line = measure_single(args, name, args.steps, args.warmup, device, stream, local,
+                          cpu_baseline=first and not args.no_cpu_baseline,
+                          random_roofline=not args.no_random_roofline)
+    out = {"metric": METRIC, "value": line["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": line["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": line["dtype"],
+           "data": "synthetic (seeded model description; no dataset)"}
+    out.update({k: v for k, v in line.items() if k not in out})
+    out["config"]["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
+    if default_run and not args.no_extras:
+        # the medium workload beside the headline; then the batched and
+        # served forms against one query at a time
+        sec = measure_single(args, "c2_star", min(args.steps, 20), args.warmup, device, stream, local,
+                             cpu_baseline=False, random_roofline=False)
+        out["secondary"] = {"c2_star": {k: sec[k] for k in ("value", "unit", "ms_per_step", "dtype", "config",
+                                                            "result", "roofline", "e2e", "clocks")}}
+        out["gpu_launches"] += sec["gpu_launches"]
+        if first:
+            out["batched"] = measure_c4(args, device, local, steps=min(args.steps, 10), warmup=args.warmup)
+            out["served"] = measure_c5(args, local, rates=[100.0, 1000.0], queries=args.served_queries)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
     return 0
 
 
@@ -465,7 +584,8 @@ def run_swarm(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    spec = WORKLOADS[args.workload][0]()
+    wl = WORKLOADS[args.workload or DEFAULT_WORKLOAD]
+    spec = wl.make()
     m = mc.mc_model_create(spec, mc.mc_options_default(timing=1))
     t_min = mc.mc_min_time(m, trace=False)["t_min"]
     walks = args.swarm_walks
@@ -479,8 +599,8 @@ def run_swarm(args):
         "value": sum(r["walks"] for r in runs) / (sum(r["total_ms"] for r in runs) / 1000.0),
         "unit": "runs/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
         "ms_per_step": sum(r["total_ms"] for r in runs) / len(runs), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload][1] or WORKLOAD, "walks_per_round": walks,
+        "scaling": "weak", "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
+        "config": {"workload": wl.desc, "walks_per_round": walks,
                    "stop": "after the first round without a run at or below best - 1 (at most 64 rounds)"},
         "t_min_exact": t_min,
         "runs": [{"first_trail_ms": r["first_trail_ms"], "total_ms": r["total_ms"], "rounds": r["rounds"],
@@ -644,21 +764,25 @@ def run_pe(args):
     return 0
 
 
-def run_c4(args):
+C4_DESC = ("c4: 256 instances, G=2^U{6..12}, P in {2,4,8}, WG 2^0..2^8, TS 2^0..2^4, cost U{1..16}, "
+           "speeds U{1..3} (splitmix64 seed 2305091304), GREEDY; half mc_min_time, half mc_check at "
+           "round(U[0.8,1.2] x T_min)")
+C5_DESC = ("c5: min-time queries on G=4096, P=8, WG 2^0..2^9, TS 2^0..2^5, cost U{1..16} (new splitmix64 "
+           "seed per query), GREEDY, 128-bit keys; Poisson arrivals (splitmix64 seed 2305091305)")
+
+
+def measure_c4(args, device, local: int, steps: int, warmup: int) -> dict:
     """Batched queries: 256 uneven models (G = 2^U{6..12}, P in {2,4,8}, WG
     2^0..2^8, TS 2^0..2^4, cost U{1..16}, speeds U{1..3}, GREEDY), half
     min-time and half check at round(U[0.8,1.2] x T_min), answered by one
-    persistent launch, against the same queries one at a time."""
+    mc_batch_run, against the same queries one at a time on the single-model
+    calls."""
     import torch
 
+    from paper_2305_09130_gb300 import autotune as AT
     from paper_2305_09130_gb300 import mc
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    device = torch.device("cuda", local)
-    dist_init(world, True)
     specs = W.c4_instances(256)
-    from paper_2305_09130_gb300 import autotune as AT
     probe = mc.mc_batch_create(specs)
     optima0 = [r["time"] for r in mc.mc_batch_run(probe, [("min_time", None)] * len(specs))]
     mc.mc_batch_destroy(probe)
@@ -674,16 +798,15 @@ def run_c4(args):
     optima = [r["time"] for r in mc.mc_batch_run(batch, [("min_time", None)] * len(specs))]
     queries = [("min_time", None) if sp.meta["query"] else
                ("check", round(t * sp.meta["t_frac_milli"] / 1000)) for sp, t in zip(specs, optima)]
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         ref = mc.mc_batch_run(batch, queries)
     torch.cuda.synchronize()
-    barrier(device)
     sampler = ClockSampler(local)
     sampler.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+          for _ in range(steps)]
     states = 0
-    for k in range(args.steps):
+    for k in range(steps):
         ev[k][0].record(stream)
         res = mc.mc_batch_run(batch, queries)
         ev[k][1].record(stream)
@@ -691,25 +814,24 @@ def run_c4(args):
         assert [r["status"] for r in res] == [0] * len(res)
         assert [(r["time"], r["states"]) for r in res] == [(r["time"], r["states"]) for r in ref]
     torch.cuda.synchronize()
-    barrier(device)
     clocks = sampler.stop()
+    bst = mc.mc_batch_get_stats(batch)
+    mc.mc_batch_destroy(batch)
     batch_ms = [a.elapsed_time(b) for a, b in ev]
     dev_ms = sum(batch_ms)
-    dev_ms_max = reduce_scalar(dev_ms, "max", device)
-    states_all = reduce_scalar(states, "sum", device)
-    value = states_all / (dev_ms_max / 1000.0)
+    value = states / (dev_ms / 1000.0)
 
     # one query at a time on the single-model entry points (models created
     # untimed, with the library's default launch shape -- the batch's tuned
-    # options suit its lockstep steps, not a lone query); latency of query k
-    # when all arrive together = sum of the service times of queries 0..k
+    # options suit its own launch, not a lone query); latency of query k when
+    # all arrive together = sum of the service times of queries 0..k
     seq_opts = mc.mc_options_default(timing=1)
     models = [mc.mc_model_create(sp.with_key_bits(128), seq_opts, stream=stream) for sp in specs]
     for m in models:
         mc.mc_reserve(m)
     service = []
     seq_states = 0
-    for m, (kind, T) in zip(models, queries):
+    for m, (kind, T), rb in zip(models, queries, ref):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         r = mc.mc_min_time(m, trace=False) if kind == "min_time" else mc.mc_check(m, T, trace=False)
@@ -717,108 +839,96 @@ def run_c4(args):
         b.synchronize()
         service.append(a.elapsed_time(b))
         seq_states += r["states"]
+        assert r["states"] == rb["states"]
+    for m in models:
+        mc.mc_model_destroy(m)
     seq_total = sum(service)
     cum, acc = [], 0.0
     for x in service:
         acc += x
         cum.append(acc)
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u128", "data": "synthetic (seeded model descriptions)",
-        "config": {"workload": "c4: 256 instances, G=2^U{6..12}, P in {2,4,8}, WG 2^0..2^8, TS 2^0..2^4, "
-                               "cost U{1..16}, speeds U{1..3} (splitmix64 seed 2305091304), GREEDY; "
-                               "half mc_min_time, half mc_check at round(U[0.8,1.2] x T_min)",
-                   "query": "one mc_batch_run per step (one persistent launch)",
-                   "autotuned_options": tuned["options"], "autotune_ms": tuned["timings"],
-                   "sequential_options": "library defaults (occupancy-maximum grid, load factor 25%)",
-                   "states_per_step": states / args.steps},
-        "batched": {"ms_per_batch": dev_ms_max / args.steps, "states_per_s": value,
-                    "query_latency_ms_p50": percentile(batch_ms, 50),
-                    "query_latency_ms_p99": percentile(batch_ms, 99)},
-        "sequential": {"ms_total": seq_total, "states_per_s": seq_states / (seq_total / 1000.0),
+    return {
+        "workload": C4_DESC,
+        "query": "one mc_batch_run per step",
+        "autotuned_options": tuned["options"], "autotune_ms": tuned["timings"],
+        "steps": steps, "ms_per_batch": dev_ms / steps, "states_per_s": value,
+        "states_per_batch": states / steps, "launches_per_batch": bst["explore_launches"] / max(
+            bst["graph_launches"] + 1, 1),
+        "query_latency_ms_p50": percentile(batch_ms, 50), "query_latency_ms_p99": percentile(batch_ms, 99),
+        "sequential": {"options": "library defaults (single-model explorer, load factor 25%)",
+                       "ms_total": seq_total, "states_per_s": seq_states / (seq_total / 1000.0),
                        "service_ms_p50": percentile(service, 50), "service_ms_p99": percentile(service, 99),
                        "latency_all_arrive_together_ms_p50": percentile(cum, 50),
                        "latency_all_arrive_together_ms_p99": percentile(cum, 99)},
-        "speedup_vs_sequential": seq_total / (dev_ms_max / args.steps),
-        "gpu_launches": args.steps, "clocks": clocks,
+        "speedup_vs_sequential": seq_total / (dev_ms / steps),
+        "clocks": clocks,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
 
 
-def run_c5(args):
+def c5_query(k: int):
+    return W.c3(G=4096, rule=W.GREEDY, seed=2305091305 * 1000003 + k, key_bits=128)
+
+
+def poisson_arrivals(rng, rate: float, n: int):
+    out, t = [], 0.0
+    for _ in range(n):
+        u = (rng.next() >> 11) / float(1 << 53)
+        t += -math.log(1.0 - u) / rate
+        out.append(t)
+    return out
+
+
+def wait_until(t0: float, t: float, poll=None):
+    """Sleep until perf_counter() - t0 >= t (the last 0.3 ms spinning)."""
+    while True:
+        left = t - (time.perf_counter() - t0)
+        if left <= 0:
+            return
+        if poll:
+            poll()
+        if left > 0.0006:
+            time.sleep(min(left - 0.0003, 0.0002 if poll else left - 0.0003))
+
+
+def measure_c5(args, local: int, rates, queries: int) -> dict:
     """Served queries: Poisson arrivals of min-time queries on models drawn as
     the large single query (G=4096, P=8, WG 2^0..2^9, TS 2^0..2^5, cost
-    U{1..16} with a new seed per query, GREEDY, 128-bit keys), at each rate of
-    --rates, answered by the request loop (mc_server_*), against the same
-    arrivals served one query at a time on the single-model entry point."""
+    U{1..16} with a new seed per query, GREEDY, 128-bit keys), at each rate,
+    answered by the request loop (mc_server_*), against the same arrival
+    stream served one query at a time through the single-model calls
+    (mc_model_create, mc_min_time, mc_model_destroy), each started at its
+    arrival or when the previous one finished."""
     import torch
 
     from paper_2305_09130_gb300 import mc
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    rates = [float(x) for x in args.rates.split(",")]
     rng = W.SplitMix64(2305091305)
     free_b, _tot = torch.cuda.mem_get_info()
     pool = int(min(free_b * 0.6, 120 << 30))
     srv = mc.mc_server_create(slots=args.slots, pool_bytes=pool)
-
-    def make_query(k):
-        return W.c3(G=4096, rule=W.GREEDY, seed=2305091305 * 1000003 + k, key_bits=128)
-
-    # one-query-at-a-time service times on a sample of the same query stream:
-    # end to end as a caller of the single-model API sees it (create the
-    # model from host arrays, mc_min_time, read the result, destroy; the
-    # library's own pooled allocator, its fastest path), and the
-    # exploration's device time alone
-    sample = [make_query(10_000_000 + k) for k in range(args.c5_sample)]
-    for sp in sample[:3]:  # warm the allocator and the library
-        m = mc.mc_model_create(sp, allocator=None)
+    opts = mc.mc_options_default()
+    for k in range(3):  # warm the library's allocator and staging
+        m = mc.mc_model_create(c5_query(10_000_000 + k), opts, allocator=None)
         mc.mc_min_time(m, trace=False)
         mc.mc_model_destroy(m)
-    service, service_dev, service_states = [], [], []
-    for sp in sample:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        m = mc.mc_model_create(sp, allocator=None)
-        r = mc.mc_min_time(m, trace=False)
-        mc.mc_model_destroy(m)
-        service.append(time.perf_counter() - t0)
-        service_states.append(r["states"])
-        m = mc.mc_model_create(sp)
-        mc.mc_reserve(m)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record()
-        mc.mc_min_time(m, trace=False)
-        b.record()
-        b.synchronize()
-        service_dev.append(a.elapsed_time(b) / 1000.0)
-        mc.mc_model_destroy(m)
-
     sweep = []
     qid = 0
     for rate in rates:
-        n = int(min(args.c5_queries, max(20, rate * args.c5_seconds)))
-        arrivals, t = [], 0.0
-        for _ in range(n):
-            u = (rng.next() >> 11) / float(1 << 53)
-            t += -math.log(1.0 - u) / rate
-            arrivals.append(t)
-        specs = [make_query(qid + k) for k in range(n)]
+        n = queries if queries else int(min(10000, max(2000, rate * args.c5_seconds)))
+        arrivals = poisson_arrivals(rng, rate, n)
+        specs = [c5_query(qid + k) for k in range(n)]
         qid += n
+        # served
         got = {}
+
+        def poll():
+            for r in mc.mc_server_poll(srv, wait_ms=0):
+                got[r["ticket"]] = r
         sampler = ClockSampler(local)
         sampler.start()
         t0 = time.perf_counter()
         for k in range(n):
-            while time.perf_counter() - t0 < arrivals[k]:
-                for r in mc.mc_server_poll(srv, wait_ms=0):
-                    got[r["ticket"]] = r
-                time.sleep(0.0002)
+            wait_until(t0, arrivals[k], poll)
             mc.mc_server_submit(srv, specs[k], "min_time")
         while len(got) < n:
             for r in mc.mc_server_poll(srv, wait_ms=20):
@@ -826,56 +936,79 @@ def run_c5(args):
             if time.perf_counter() - t0 > arrivals[-1] + 600:
                 raise SystemExit(f"served run at {rate}/s did not finish: {mc.mc_server_status(srv)}")
         clocks = sampler.stop()
-        res = list(got.values())
+        res = [got[t] for t in sorted(got)]
         assert all(r["status"] == 0 for r in res)
         lat = [1000.0 * (r["done_s"] - r["submit_s"]) for r in res]
-        first = min(r["submit_s"] for r in res)
-        last = max(r["done_s"] for r in res)
-        # the same arrivals served FIFO one at a time, service times cycling
-        # through the measured sample (end to end; and device time only)
-        def fifo(times):
-            clock, out = 0.0, []
-            for k, a in enumerate(arrivals):
-                clock = max(clock, a) + times[k % len(times)]
-                out.append(1000.0 * (clock - a))
-            return clock, out
-
-        clock, seq_lat = fifo(service)
-        clock_dev, seq_lat_dev = fifo(service_dev)
+        span = max(r["done_s"] for r in res) - min(r["submit_s"] for r in res)
+        # one at a time, the same arrival stream in real time
+        seq_lat, seq_res = [], []
+        sampler2 = ClockSampler(local)
+        sampler2.start()
+        t0 = time.perf_counter()
+        for k in range(n):
+            wait_until(t0, arrivals[k])
+            m = mc.mc_model_create(specs[k], opts, allocator=None)
+            rr = mc.mc_min_time(m, trace=False)
+            mc.mc_model_destroy(m)
+            seq_lat.append(1000.0 * (time.perf_counter() - t0 - arrivals[k]))
+            seq_res.append(rr)
+        seq_span = time.perf_counter() - t0 - arrivals[0]
+        clocks2 = sampler2.stop()
+        # every served result equals the one-at-a-time result of the same query
+        mism = sum(1 for a, b in zip(res, seq_res)
+                   if (a["time"], a["states"], a["wg"], a["ts"]) != (b["t_min"], b["states"], b["wg"], b["ts"]))
         sweep.append({
             "rate_per_s": rate, "queries": n,
-            "served": {"throughput_qps": n / (last - first), "latency_ms_p50": percentile(lat, 50),
-                       "latency_ms_p99": percentile(lat, 99),
-                       "states_per_s": sum(r["states"] for r in res) / (last - first),
-                       "ran_alone": sum(r["path"] == "alone" for r in res)},
-            "sequential": {"throughput_qps": n / (clock - arrivals[0]) if clock > arrivals[0] else None,
-                           "latency_ms_p50": percentile(seq_lat, 50), "latency_ms_p99": percentile(seq_lat, 99)},
-            "sequential_device_only": {
-                "throughput_qps": n / (clock_dev - arrivals[0]) if clock_dev > arrivals[0] else None,
-                "latency_ms_p50": percentile(seq_lat_dev, 50), "latency_ms_p99": percentile(seq_lat_dev, 99)},
-            "clocks": clocks,
+            "served": {"throughput_qps": n / span, "latency_ms_p50": percentile(lat, 50),
+                       "latency_ms_p99": percentile(lat, 99), "latency_ms_max": max(lat),
+                       "states_per_s": sum(r["states"] for r in res) / span,
+                       "ran_alone": sum(r["path"] == "alone" for r in res), "clocks": clocks},
+            "one_at_a_time": {"throughput_qps": n / seq_span, "latency_ms_p50": percentile(seq_lat, 50),
+                              "latency_ms_p99": percentile(seq_lat, 99), "latency_ms_max": max(seq_lat),
+                              "states_per_s": sum(r["states"] for r in seq_res) / seq_span,
+                              "clocks": clocks2},
+            "results_differ": mism,
         })
     status = mc.mc_server_status(srv)
     mc.mc_server_destroy(srv)
-    top = sweep[-1]
-    line = {
-        "metric": "served queries: throughput with p50/p99 latency", "value": top["served"]["throughput_qps"],
-        "unit": "queries/s", "n_gpus": 1, "steps": len(rates), "warmup": 0,
-        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u128", "data": "synthetic (seeded model per query)",
-        "config": {"workload": "c5: min-time queries on G=4096, P=8, WG 2^0..2^9, TS 2^0..2^5, "
-                               "cost U{1..16} (new splitmix64 seed per query), GREEDY, 128-bit keys; "
-                               "Poisson arrivals", "slots": args.slots, "pool_bytes": pool,
-                   "sequential_service_ms_mean": 1000.0 * sum(service) / len(service),
-                   "sequential_device_ms_mean": 1000.0 * sum(service_dev) / len(service_dev),
-                   "sequential_sample": len(service),
-                   "note": "sequential latencies: the same arrival times served FIFO one at a time, with "
-                           "service times cycling through the measured single-query sample; 'sequential' "
-                           "times each query end to end through the single-model C-ABI (create, "
-                           "mc_min_time, destroy), as the served latency is measured from submit to "
-                           "result; 'sequential_device_only' counts the exploration's device time alone"},
-        "sweep": sweep, "device_loop_launches": status["launches"], "clocks": top["clocks"],
-    }
+    mc.mc_release_cached()
+    return {"workload": C5_DESC, "slots": args.slots, "pool_bytes": pool,
+            "query": "mc_min_time (search SINGLE, library default options) per request",
+            "one_at_a_time": "the same arrival stream replayed in real time; each query starts at its arrival "
+                             "or when the previous one finished and runs mc_model_create, mc_min_time, "
+                             "mc_model_destroy (library allocator); latency from arrival to result",
+            "sweep": sweep, "device_loop_launches": status["launches"]}
+
+
+def run_c4(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    b = measure_c4(args, device, local, steps=args.steps, warmup=args.warmup)
+    line = {"metric": METRIC, "value": b["states_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": b["ms_per_batch"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u128", "data": "synthetic (seeded model descriptions)",
+            "config": {"workload": C4_DESC}, "batched": b, "clocks": b["clocks"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_c5(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    rates = [float(x) for x in args.rates.split(",")]
+    s = measure_c5(args, local, rates, queries=args.c5_queries)
+    top = s["sweep"][-1]
+    line = {"metric": "served queries: throughput with p50/p99 latency", "value": top["served"]["throughput_qps"],
+            "unit": "queries/s", "n_gpus": 1, "steps": len(rates), "warmup": 0, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u128",
+            "data": "synthetic (seeded model per query)", "config": {"workload": C5_DESC}, "served": s,
+            "clocks": top["served"]["clocks"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -884,33 +1017,39 @@ def run_c5(args):
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--mode", choices=["single", "lower", "bisect"], default="lower")
     p.add_argument("--prune", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-random-roofline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="default run: skip the secondary, batched and served objects")
     p.add_argument("--load-factor", type=int, default=0,
-                   help="visited-set load factor in percent (0: the autotuner picks it for c2_star)")
+                   help="visited-set load factor in percent (0: the autotuner picks it)")
     p.add_argument("--probe-scheme", choices=["tune", "auto", "split", "one_call"], default="tune",
                    help="visited-set insert of the exploration kernel (tune: the autotuner picks it)")
     p.add_argument("--no-log-tags", action="store_true",
                    help="untagged frontier log: blocks write their entries before they arrive at a level")
     p.add_argument("--rates", default="10,30,100,300,1000", help="c5 arrival rates (queries/s)")
     p.add_argument("--slots", type=int, default=512, help="c5 requests on the device at once")
-    p.add_argument("--c5-seconds", type=float, default=10.0, help="c5 arrivals per rate span")
-    p.add_argument("--c5-queries", type=int, default=10000, help="c5 queries per rate at most")
-    p.add_argument("--c5-sample", type=int, default=48, help="c5 single-query service sample")
+    p.add_argument("--c5-seconds", type=float, default=100.0,
+                   help="c5: queries per rate = min(10000, max(2000, rate x this)) unless --c5-queries")
+    p.add_argument("--c5-queries", type=int, default=0, help="c5 queries per rate (0: from --c5-seconds)")
+    p.add_argument("--served-queries", type=int, default=2000, help="default run: queries per served rate")
     p.add_argument("--workload", choices=sorted(WORKLOADS) + ["c4", "c5"] + sorted(PE_WORKLOADS),
-                   default="c2_star",
-                   help="profiling aid; the benchmark line is c2_star")
+                   default=None,
+                   help="one workload alone (default: the c3_star line with the c2_star, batched and "
+                        "served objects)")
     p.add_argument("--query", choices=["min_time", "count", "swarm"], default="min_time")
     p.add_argument("--swarm-walks", type=int, default=1 << 20, help="random runs per swarm round")
     args = p.parse_args(argv)
     if args.warmup < 3:
         p.error("--warmup must be >= 3")
     if args.impl == "reference":
+        if args.workload not in (None,) + tuple(WORKLOADS):
+            p.error("--impl reference times the oracle on a single-model workload")
         return run_reference(args)
     if args.workload == "c4":
         return run_c4(args)

@@ -229,10 +229,16 @@ typedef void (*mc_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
  * refine 1, sim_seed 2305091300, sim_walks 1, load_factor_pct 25, the rest 0. */
 void mc_options_default(mc_options* opt);
 
-/* Validate and copy the description; compute the key layout and the
- * closed-form bounds that size the device buffers.  No device memory is
- * touched.  opt may be NULL (defaults).  Errors: INVAL (NULL or zero sizes,
- * P > 16, N/cost/speed of 0, unknown rule or key_bits), OVERFLOW. */
+/* The model of Section 4, Step 1 (the problem statement of the method):
+ * the domains of the tuning parameters that `main` selects from (Listing 3),
+ * the work-groups of each configuration and the time one of them takes on
+ * a compute unit (the abstract kernel of Listing 2 folded into a cost per
+ * (WG, TS) and a speed per unit), and the unit count of the abstract
+ * platform (Section 3.1).  Validate and copy the description; compute the
+ * key layout and the closed-form bounds that size the device buffers.  No
+ * device memory is touched.  opt may be NULL (defaults).  Errors: INVAL
+ * (NULL or zero sizes, P > 16, N/cost/speed of 0, unknown rule or
+ * key_bits), OVERFLOW. */
 int mc_model_create(const mc_model_desc* desc, const mc_options* opt, mc_model** out);
 
 /* Free the model, its device buffers (through the allocator that made them)
@@ -277,7 +283,10 @@ int mc_check(mc_model* m, uint64_t T, mc_check_result* out, mc_trace** cex);
  * mc_check. */
 int mc_min_time(mc_model* m, mc_min_result* out, mc_trace** trace);
 
-/* Count every reachable state (no pruning, no early exit).  Errors: as mc_check. */
+/* The reachable-state count of exhaustive verification (Section 6, Table 1
+ * reports the memory such a search takes): every state reachable from s0
+ * under the model's dispatch rule, explored without pruning and without
+ * early exit.  Errors: as mc_check. */
 int mc_count_states(mc_model* m, uint64_t* out);
 
 /* T_ini: the least terminal time over `walks` random runs (Section 4,

@@ -29,6 +29,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "mc.h"
 #include "mc_internal.h"
@@ -123,25 +124,46 @@ extern "C" int mc_check_noalloc(const mc_model_desc* d, uint64_t T, uint32_t pru
   uint32_t tile = 1;
   while (tile < P) tile <<= 1;
 
-  // closed-form bounds (as mc_model_create) and the scratch they need
+  // Every configuration has at least one state per level 2 .. N_ij + 2
+  // under either rule, so the frontier log holds at least 1 + a +
+  // sum(N_ij + 1) states: a model whose log cannot fit is refused here, in
+  // one pass over the table, before the bounds below (which cost time
+  // proportional to max N) are computed.
+  const uint64_t key_bytes = 8ull * key_words;
+  const uint64_t params_bytes = align256(4 * (2 * ab + P));
+  {
+    uint64_t floor_states = 1 + (uint64_t)a;
+    for (uint64_t k = 0; k < ab; ++k) floor_states += (uint64_t)d->n_workgroups[k] + 1;
+    if (sat_add(params_bytes, sat_mul(floor_states, key_bytes + 4)) > MC_NOALLOC_SCRATCH_BYTES)
+      return MC_ERR_NOMEM;
+  }
+
+  // closed-form bounds (as mc_model_create) and the scratch they need: the
+  // configurations with N_ij >= k for every k from a suffix histogram (max N
+  // is small here: the check above bounds it by the array's size)
   const uint64_t greedy_cap = choose_sat(P, P / 2);
+  std::vector<uint64_t> at_least((size_t)n_max + 2, 0);
+  for (uint64_t c = 0; c < ab; ++c) at_least[d->n_workgroups[c]] += 1;
+  for (int64_t k = (int64_t)n_max - 1; k >= 0; --k) at_least[k] += at_least[k + 1];
   uint64_t total = sat_add(1 + (uint64_t)a, ab), widest = 0;
+  uint64_t per_free = 1;  // C(k+P-1, P-1), updated incrementally (saturating)
   for (uint32_t k = 1; k <= n_max; ++k) {
-    uint64_t cnt = 0;
-    for (uint64_t c = 0; c < ab; ++c) cnt += d->n_workgroups[c] >= k;
-    uint64_t per = choose_sat((uint64_t)k + P - 1, P - 1);
+    if (per_free != UINT64_MAX) {
+      const unsigned __int128 nx = (unsigned __int128)per_free * (k + P - 1) / k;
+      per_free = nx > (unsigned __int128)UINT64_MAX ? UINT64_MAX : (uint64_t)nx;
+    }
+    uint64_t per = per_free;
     if (d->rule == MC_GREEDY && greedy_cap < per) per = greedy_cap;
-    const uint64_t w = sat_mul(per, cnt);
+    const uint64_t w = sat_mul(per, at_least[k]);
     if (w > widest) widest = w;
     total = sat_add(total, w);
+    if (sat_mul(total, key_bytes + 4) > MC_NOALLOC_SCRATCH_BYTES) return MC_ERR_NOMEM;
   }
   const uint64_t per_bucket = key_words == 1 ? 4 : 2;
   const uint64_t want = sat_mul(widest ? widest : 1, 4) + 1;  // load factor 25%
   uint64_t slots = 64;
   while (slots < want && slots < (1ull << 40)) slots <<= 1;
-  const uint64_t key_bytes = 8ull * key_words;
   const uint64_t L2 = max_level + 2;
-  const uint64_t params_bytes = align256(4 * (2 * ab + P));
   const uint64_t ctrl_bytes = align256(256 + mc::kBarBytes + 16 * L2 + 8 * L2 + 16 * L2 + 64);
   const uint64_t table_bytes = align256(sat_mul(slots, key_bytes));
   const uint64_t keys_bytes = align256(sat_mul(total, key_bytes));
@@ -233,9 +255,18 @@ extern "C" int mc_check_noalloc(const mc_model_desc* d, uint64_t T, uint32_t pru
   A.timeout_ns = 60ull * 1000000000ull;
 
   mc::Ctrl h;
-  if (mc::launch_explore(key_words, tile, d->rule, key_words == 1, sms * bps, mc::kThreads, A, stream) != cudaSuccess ||
-      cudaMemcpyAsync(&h, d_ctrl, sizeof(h), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+  if (mc::launch_explore(key_words, tile, d->rule, key_words == 1, sms * bps, mc::kThreads, A, stream) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return MC_ERR_CUDA;
+  }
+  // from here the kernel may be running on the shared array: every return
+  // waits for the stream first, so the next call cannot clear the array
+  // under it
+  if (cudaMemcpyAsync(&h, d_ctrl, sizeof(h), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
       cudaStreamSynchronize(stream) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(stream);
     cudaGetLastError();
     return MC_ERR_CUDA;
   }

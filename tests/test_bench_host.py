@@ -1,5 +1,6 @@
 """Host-side pieces of bench.py (no GPU): the DRAM-traffic lookup that fills
-roofline.traffic from the committed ncu summary."""
+roofline.traffic from a committed ncu summary, and the bench's choice of
+workloads."""
 import bench
 
 
@@ -9,25 +10,54 @@ def _write(tmp_path, body):
     return str(p)
 
 
-def test_traffic_is_read_per_load_factor_and_probe_scheme(tmp_path, monkeypatch):
+def test_traffic_is_read_per_load_factor_and_probe_scheme(tmp_path):
     h = bench.kernel_source_hash()
-    monkeypatch.setattr(bench, "TRAFFIC_FILE", _write(tmp_path, f"""# comment: 1
+    path = _write(tmp_path, f"""# comment: 1
 kernel_source_sha256_16: {h}
 dram_bytes_per_launch_lf10_split: 100
 dram_bytes_per_launch_lf15_split: 200
 dram_bytes_per_launch_lf10_one_call: 300
-"""))
-    assert bench.ncu_traffic_per_launch(10, "split") == 100.0
-    assert bench.ncu_traffic_per_launch(15, "split") == 200.0
-    assert bench.ncu_traffic_per_launch(10, "one_call") == 300.0
-    assert bench.ncu_traffic_per_launch(15, "one_call") is None  # no capture for that pair
-    assert bench.ncu_traffic_per_launch(25, "split") is None
+""")
+    assert bench.ncu_traffic_per_launch(path, 10, "split", 1e6) == 100.0
+    assert bench.ncu_traffic_per_launch(path, 15, "split", 1e6) == 200.0
+    assert bench.ncu_traffic_per_launch(path, 10, "one_call", 1e6) == 300.0
+    assert bench.ncu_traffic_per_launch(path, 15, "one_call", 1e6) is None  # no capture for that pair
+    assert bench.ncu_traffic_per_launch(path, 25, "split", 1e6) is None
 
 
-def test_traffic_is_null_for_other_kernel_sources(tmp_path, monkeypatch):
-    monkeypatch.setattr(bench, "TRAFFIC_FILE", _write(tmp_path, """kernel_source_sha256_16: 0000000000000000
+def test_traffic_per_state_is_scaled_by_the_states_of_a_launch(tmp_path):
+    h = bench.kernel_source_hash()
+    path = _write(tmp_path, f"""kernel_source_sha256_16: {h}
+dram_bytes_per_state_one_call: 512.5
+""")
+    assert bench.ncu_traffic_per_launch(path, 25, "one_call", 2e6) == 512.5 * 2e6
+    assert bench.ncu_traffic_per_launch(path, 25, "split", 2e6) is None
+
+
+def test_traffic_is_null_for_other_kernel_sources(tmp_path):
+    path = _write(tmp_path, """kernel_source_sha256_16: 0000000000000000
 dram_bytes_per_launch_lf10_split: 100
-"""))
-    assert bench.ncu_traffic_per_launch(10, "split") is None
-    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "missing.txt"))
-    assert bench.ncu_traffic_per_launch(10, "split") is None
+""")
+    assert bench.ncu_traffic_per_launch(path, 10, "split", 1.0) is None
+    assert bench.ncu_traffic_per_launch(str(tmp_path / "missing.txt"), 10, "split", 1.0) is None
+
+
+def test_default_line_is_the_large_model_with_its_closed_form_optimum():
+    """The headline is C3 at G=36 (FREE, P=8, 128-bit keys); its expected
+    optimum is the closed form's (T_min = min over configurations of
+    ceil(N/P) * cost with unit speeds)."""
+    import closed_forms as CF
+
+    wl = bench.WORKLOADS[bench.DEFAULT_WORKLOAD]
+    spec = wl.make()
+    assert spec.P == 8 and spec.key_bits == 128 and spec.rule == 0
+    assert CF.count(spec) == 1_072_924_481
+    t, cfgs = CF.tmin(spec)
+    i, j = cfgs[0]
+    assert wl.expect == (t, spec.wg_values[i], spec.ts_values[j])
+    assert wl.dtype == "u128"
+    c2 = bench.WORKLOADS["c2_star"]
+    s2 = c2.make()
+    assert CF.count(s2) == 10_385_335
+    t2, cfg2 = CF.tmin(s2)
+    assert c2.expect == (t2, s2.wg_values[cfg2[0][0]], s2.ts_values[cfg2[0][1]])

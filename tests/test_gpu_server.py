@@ -1,10 +1,12 @@
-"""Served queries (continuous batching): results equal the single-model
-entry points, alone and in a mix (tolerance zero), and requests submitted
-while others run are admitted into the running device loop."""
+"""Served queries (continuous batching): results equal the CPU oracle's and
+the single-model entry points', alone and in a mix (tolerance zero), and
+requests submitted while others run are admitted into the running device
+loop."""
 import time
 
 import pytest
 
+import replay as RP
 from paper_2305_09130_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -28,6 +30,28 @@ def single(mc, spec, kind, T):
     return out
 
 
+def against_oracle(mc, oracle, spec, kind, T, r):
+    """A served result against the oracle under the server's options (the
+    library defaults: pruning, early exit, search SINGLE with the
+    certificate check, one simulated run from the default seed): every count,
+    the threshold decision, the minimal time or counterexample time, its
+    configuration and level, and the witness state's work-group counts."""
+    lay = mc.mc_model_layout(mc.mc_model_create(spec.with_key_bits(128)))
+    assert r["status"] == 0
+    if kind == "min_time":
+        e = oracle.min_time(spec)
+        got = (r["time"], r["t_ini"], r["states"], r["checks"], r["i"], r["j"], r["level"])
+        assert got == (e["t_min"], e["t_ini"], e["states"], e["checks"], e["i"], e["j"], e["level"]), (got, e)
+        assert list(RP.decode(lay, r["key"])[2]) == e["n"]
+    else:
+        e = oracle.check(spec, T)
+        assert (r["holds"], r["states"], r["levels"]) == (e["holds"], e["states"], e["levels"]), (r, e)
+        if not e["holds"]:
+            got = (r["time"], r["i"], r["j"], r["level"])
+            assert got == (e["cex_time"], e["cex_i"], e["cex_j"], e["cex_level"]), (got, e)
+            assert list(RP.decode(lay, r["key"])[2]) == e["cex_n"]
+
+
 def collect(mc, srv, n, timeout_s=120):
     got = {}
     t0 = time.time()
@@ -47,13 +71,14 @@ def mix():
     return specs, queries
 
 
-def test_served_results_equal_alone_and_in_mix(mc):
+def test_served_results_equal_alone_and_in_mix(mc, oracle):
     specs, queries = mix()
     srv = mc.mc_server_create(slots=8, pool_bytes=4 << 30)
     tickets = {mc.mc_server_submit(srv, s, k, T): idx for idx, (s, (k, T)) in enumerate(zip(specs, queries))}
     got = collect(mc, srv, len(specs))
     for t, idx in tickets.items():
         r = got[t]
+        against_oracle(mc, oracle, specs[idx], *queries[idx], r)
         exp = single(mc, specs[idx], *queries[idx])
         for key in KEYS:
             if exp[key] is not None:
@@ -74,7 +99,7 @@ def test_served_results_equal_alone_and_in_mix(mc):
     mc.mc_server_destroy(srv)
 
 
-def test_c5_shaped_queries_in_the_benchmark_server(mc):
+def test_c5_shaped_queries_in_the_benchmark_server(mc, oracle):
     """Min-time queries drawn as the served benchmark draws them (G=4096,
     P=8, a new seed each, 128-bit keys), on a server with its slot count:
     submitted together they share the device loop, and each answer equals the
@@ -88,6 +113,7 @@ def test_c5_shaped_queries_in_the_benchmark_server(mc):
     assert sum(r["path"] == "loop" for r in got.values()) >= len(specs) - 2
     for t, k in tickets.items():
         r = got[t]
+        against_oracle(mc, oracle, specs[k], "min_time", None, r)
         exp = single(mc, specs[k], "min_time", None)
         for key in KEYS:
             if exp[key] is not None:
@@ -97,6 +123,7 @@ def test_c5_shaped_queries_in_the_benchmark_server(mc):
     t = mc.mc_server_submit(alone, specs[5], "min_time")
     r = collect(mc, alone, 1)[t]
     assert r["path"] == "alone"
+    against_oracle(mc, oracle, specs[5], "min_time", None, r)
     exp = single(mc, specs[5], "min_time", None)
     assert {k: r[k] for k in KEYS if exp[k] is not None} == {k: exp[k] for k in KEYS if exp[k] is not None}
     mc.mc_server_destroy(alone)
@@ -132,7 +159,7 @@ def test_server_rejects_models_larger_than_its_pool(mc):
     mc.mc_server_destroy(srv)
 
 
-def test_lone_requests_take_the_latency_path(mc):
+def test_lone_requests_take_the_latency_path(mc, oracle):
     # each request finds the server idle: it runs alone on the single-model
     # explorer, with the answer of the single-model entry point; requests
     # submitted together go through the device loop
@@ -142,6 +169,7 @@ def test_lone_requests_take_the_latency_path(mc):
         t = mc.mc_server_submit(srv, specs[idx], *queries[idx])
         r = collect(mc, srv, 1)[t]
         assert r["path"] == "alone"
+        against_oracle(mc, oracle, specs[idx], *queries[idx], r)
         exp = single(mc, specs[idx], *queries[idx])
         for key in KEYS:
             if exp[key] is not None:

@@ -182,3 +182,74 @@ def test_swarm_runs_are_schedules_and_never_beat_tmin(oracle):
         assert sw["best_time"] >= best and sw["first_time"] >= sw["best_time"]
         # many runs per round reach the optimum of a tiny model
         assert oracle.swarm(spec, 99, 4000, 30)["best_time"] == best
+
+
+# ---------------------------------------------------------------- swarm rounds, worked by hand
+# Models with one compute unit and one work-group per configuration: every
+# random run of configuration i then ends at time cost[i], whatever its
+# dispatch draws, so a swarm's rounds depend only on the configuration each
+# run draws -- splitmix64 output number (w << 32) of the seed, modulo a
+# (Section 4, Step 3's simulation; Section 5 runs many of them).  The draws
+# come from the published generator in the input module; the expected best
+# times, walks and round counts below are worked out from the search rule of
+# Section 5 (round 0 takes the least time of its runs; round r >= 1 takes
+# fresh runs r*W .. (r+1)*W - 1 and keeps one that ends at or below the best
+# time minus one; the search stops after the first round that finds none).
+def _one_unit_model(costs):
+    return W.ModelSpec("swarm_pin", 1, [1 << i for i in range(len(costs))], [1], [1] * len(costs),
+                       list(costs), [1], W.FREE)
+
+
+def _drawn_config(seed, w, a):
+    return W.splitmix64_mix(seed + ((w << 32) + 1) * W.SPLITMIX_GAMMA) % a
+
+
+def _seed_where(pred, a, walks):
+    for seed in range(1, 100000):
+        if pred([_drawn_config(seed, w, a) for w in range(walks)]):
+            return seed
+    raise AssertionError("no seed found")
+
+
+def test_swarm_stops_after_the_round_that_finds_nothing(oracle):
+    # times 10, 20, 30 and 64 runs per round: round 0 draws every
+    # configuration, finds 10 at its first run of configuration 0; round 1
+    # looks for a time <= 9, finds none, and ends the search: two rounds
+    spec = _one_unit_model([10, 20, 30])
+    seed = _seed_where(lambda d: set(d[:64]) == {0, 1, 2}, 3, 64)
+    first0 = [_drawn_config(seed, w, 3) for w in range(64)].index(0)
+    sw = oracle.swarm(spec, seed, 64, 30)
+    assert (sw["rounds"], sw["first_time"], sw["best_time"], sw["best_walk"]) == (2, 10, 10, first0)
+    assert sw["walks"] == 128 and (sw["i"], sw["j"]) == (0, 0)
+
+
+def test_swarm_improves_in_a_later_round_at_best_minus_one(oracle):
+    # times 19 and 20, 4 runs per round, a seed whose round 0 draws only
+    # configuration 1 and whose round 1 (runs 4..7, fresh) draws
+    # configuration 0: round 0 finds 20, round 1 finds 19 = 20 - 1 (a run
+    # ending exactly at best - 1 counts), round 2 finds nothing: three rounds.
+    # A strict bound, runs reused across rounds or a late stop all fail here.
+    spec = _one_unit_model([19, 20])
+    seed = _seed_where(lambda d: d[:4] == [1, 1, 1, 1] and 0 in d[4:8], 2, 8)
+    d = [_drawn_config(seed, w, 2) for w in range(8)]
+    k = d[4:8].index(0)
+    sw = oracle.swarm(spec, seed, 4, 30)
+    assert (sw["rounds"], sw["first_time"], sw["best_time"], sw["best_walk"]) == (3, 20, 19, 4 + k)
+    assert sw["walks"] == 12 and sw["i"] == 0
+    # the round limit ends the search early with the same best
+    sw2 = oracle.swarm(spec, seed, 4, 2)
+    assert (sw2["rounds"], sw2["best_time"], sw2["best_walk"]) == (2, 19, 4 + k)
+    sw1 = oracle.swarm(spec, seed, 4, 1)
+    assert (sw1["rounds"], sw1["best_time"], sw1["best_walk"]) == (1, 20, 0)
+
+
+def test_swarm_keeps_its_first_trail_when_the_next_round_misses(oracle):
+    # times 19 and 20, a seed whose runs 0..7 all draw configuration 1:
+    # round 0 finds 20 at run 0, round 1 (configuration 1 again, 20 > 19)
+    # finds nothing: two rounds and the first trail is the answer, a miss
+    # of the optimum the swarm cannot detect (optimality is not proven)
+    spec = _one_unit_model([19, 20])
+    seed = _seed_where(lambda d: d == [1] * 8, 2, 8)
+    sw = oracle.swarm(spec, seed, 4, 30)
+    assert (sw["rounds"], sw["first_time"], sw["best_time"], sw["best_walk"]) == (2, 20, 20, 0)
+    assert sw["i"] == 1

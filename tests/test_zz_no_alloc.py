@@ -30,9 +30,16 @@ def cases():
             W.random_small(4243, 8, 2, 2, 4, rule=W.GREEDY, key_bits=128)]
 
 
+def optimum(mc, spec):
+    m = mc.mc_model_create(spec)
+    t = mc.mc_min_time(m, trace=False)["t_min"]
+    mc.mc_model_destroy(m)
+    return t
+
+
 @pytest.mark.parametrize("spec", cases(), ids=lambda s: f"{s.name}_r{s.rule}")
 def test_noalloc_matches_mc_check_twice(mc, spec):
-    t_min = mc.mc_min_time(mc.mc_model_create(spec), trace=False)["t_min"]
+    t_min = optimum(mc, spec)
     for T in (t_min - 1, t_min, 3 * t_min, NO_LIMIT):
         for prune, ee in ((True, True), (False, False)):
             exp = reference(mc, spec, T, prune, ee)
@@ -49,3 +56,23 @@ def test_noalloc_rejects_models_beyond_its_scratch(mc):
     # the array is still usable afterwards
     spec = W.c1(W.FREE)
     assert mc.mc_check_noalloc(spec, 80) == reference(mc, spec, 80, True, True)
+
+
+def test_noalloc_allocates_no_device_memory(mc):
+    """The point of the entry point: a batch of calls leaves the device's
+    free memory unchanged (the library's cached pool blocks are given back
+    first, and one warm-up call looks the array's address up)."""
+    import torch
+
+    spec = W.c1(W.GREEDY)
+    t_min = optimum(mc, spec)
+    mc.mc_check_noalloc(spec, t_min)
+    mc.mc_release_cached()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    answers = [mc.mc_check_noalloc(spec, T, prune=p, early_exit=p)
+               for T in (t_min - 1, t_min, NO_LIMIT) for p in (True, False)]
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert [a["holds"] for a in answers] == [True, True, False, False, False, False]
