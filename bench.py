@@ -229,7 +229,7 @@ def ncu_traffic_per_launch(path: str, load_factor_pct: int, probe_scheme: str, s
     holds no capture at this visited-set load factor and probe scheme
     ("split" or "one_call").  A summary taken on the benchmarked launches
     gives ``dram_bytes_per_launch_lf<LF>_<scheme>``; one taken on a smaller
-    case of the same kernel gives ``dram_bytes_per_state_<scheme>``, scaled
+    case of the same kernel gives ``dram_bytes_per_state_lf<LF>_<scheme>``, scaled
     here by the states one launch processes (the traffic of this DRAM-bound
     kernel grows with the states it inserts)."""
     try:
@@ -239,7 +239,7 @@ def ncu_traffic_per_launch(path: str, load_factor_pct: int, probe_scheme: str, s
         key = f"dram_bytes_per_launch_lf{int(load_factor_pct)}_{probe_scheme}"
         if key in fields:
             return float(fields[key])
-        key = f"dram_bytes_per_state_{probe_scheme}"
+        key = f"dram_bytes_per_state_lf{int(load_factor_pct)}_{probe_scheme}"
         if key in fields:
             return float(fields[key]) * states_per_launch
         return None
@@ -339,6 +339,8 @@ def measure_single(args, name: str, steps: int, warmup: int, device, stream, loc
         fixed["probe_scheme"] = mc.PROBE[args.probe_scheme]
     if args.no_log_tags:
         fixed["no_log_tags"] = 1
+    if args.engine != "auto":
+        fixed["engine"] = mc.ENGINE[args.engine]
 
     def tune_measure(c):
         m = mc.mc_model_create(spec, mc.mc_options_default(search=args.mode, prune=args.prune, timing=1,
@@ -424,8 +426,11 @@ def measure_single(args, name: str, steps: int, warmup: int, device, stream, loc
                 "algorithmic_bytes_per_launch": bps * states_per_launch,
                 "bytes_per_state": bps, "states_per_launch": states_per_launch,
                 "avg_launch_ms": st["explore_ms"] / max(launches, 1),
-                "kernel": f"explore_kernel<u{64 * layout['key_words']}, tile {1 << (spec.P - 1).bit_length()}, "
-                          f"{'FREE' if spec.rule == W.FREE else 'GREEDY'}, {scheme} insert>",
+                "kernel": (f"explore_kernel<u{64 * layout['key_words']}, tile {1 << (spec.P - 1).bit_length()}, "
+                           f"{'FREE' if spec.rule == W.FREE else 'GREEDY'}, {scheme} insert>"
+                           if layout["engine"] == mc.ENGINE["level"] else
+                           f"cfg_kernel<u{64 * layout['key_words']}> ({layout['unit_threads']} threads per "
+                           f"configuration)"),
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                                if peak_kind == "measured" else "fallback 6.8 TB/s"}
     if wl.traffic:
@@ -1032,6 +1037,9 @@ def main(argv=None):
                    help="visited-set insert of the exploration kernel (tune: the autotuner picks it)")
     p.add_argument("--no-log-tags", action="store_true",
                    help="untagged frontier log: blocks write their entries before they arrive at a level")
+    p.add_argument("--engine", choices=["auto", "level", "config"], default="auto",
+                   help="single-model explorer: level-synchronous or one block per configuration "
+                        "(auto: by the model's widest configuration level)")
     p.add_argument("--rates", default="10,30,100,300,1000", help="c5 arrival rates (queries/s)")
     p.add_argument("--slots", type=int, default=512, help="c5 requests on the device at once")
     p.add_argument("--c5-seconds", type=float, default=100.0,

@@ -90,6 +90,25 @@ typedef enum {
                             the fetched bucket, one proposal at a time        */
 } mc_probe_scheme;
 
+/* Which kernel explores a pass (mc_options.engine).  Both report identical
+ * results; only the speed differs. */
+typedef enum {
+  MC_ENGINE_AUTO = 0,    /* CONFIG when one configuration's widest level fits
+                            the shared memory of a thread block (closed-form
+                            bound: at most 2048 states with 64-bit keys, 1024
+                            with 128-bit keys), else LEVEL                    */
+  MC_ENGINE_LEVEL = 1,   /* level-synchronous BFS over the whole state space:
+                            one persistent cooperative launch per pass, a
+                            device-wide barrier per level, the visited set in
+                            device memory (any model)                         */
+  MC_ENGINE_CONFIG = 2   /* one thread block per (WG, TS) configuration: the
+                            selects of Listing 3 split the states below level 2
+                            into disjoint subtrees, and a block explores one
+                            subtree with its frontier and visited set in shared
+                            memory and a block-wide barrier per level (models
+                            whose per-configuration levels fit, see AUTO)     */
+} mc_engine;
+
 typedef struct mc_model mc_model;
 typedef struct mc_trace mc_trace;
 
@@ -147,7 +166,12 @@ typedef struct {
                                    writes its entries before it arrives at the
                                    level barrier); 0: tag it where the keys
                                    have room (mc_layout.log_tag_bits)        */
-  uint32_t reserved[3];
+  uint32_t engine;              /* mc_engine of the single-model queries    */
+  uint32_t unit_threads;        /* CONFIG engine: threads of the block that
+                                   explores one configuration, 64..512, a
+                                   multiple of 32; 0 = from the model's
+                                   widest configuration level                */
+  uint32_t reserved[1];
 } mc_options;
 
 /* Result of mc_check (Section 4, Step 2: Phi = G(FIN -> time > T)). */
@@ -203,6 +227,12 @@ typedef struct {
                             entries: 8 to 16 where the key leaves that many
                             spare (a 128-bit key is stored as two words of
                             64 - log_tag_bits payload bits), else 0        */
+  uint32_t engine;       /* MC_ENGINE_LEVEL or MC_ENGINE_CONFIG (AUTO
+                            resolved); with CONFIG, table_slots is the
+                            shared-memory table of one block and the log
+                            holds one segment per configuration           */
+  uint32_t unit_threads; /* CONFIG: threads per block (0 with LEVEL)       */
+  uint64_t unit_width;   /* bound on one configuration's widest level      */
 } mc_layout;
 
 /* Counters accumulated over the model's queries (reset by mc_reset_stats). */

@@ -181,6 +181,15 @@ struct mc_model {
   uint32_t ts_shift = 0, wg_shift = 0, used_bits = 0, max_level = 0, tile = 1;
   uint64_t max_width = 0, state_bound = 0;
   uint64_t log_cap = 0, table_slots = 0, device_bytes = 0;
+  // configuration engine: closed-form widest level of one configuration,
+  // and each configuration's frontier-log segment (its states' bound)
+  uint64_t unit_width = 0, unit_log = 0;
+  std::vector<uint64_t> seg;       // [a*b + 1] segment starts
+  std::vector<uint32_t> order;     // [a*b] configurations, deepest first
+  uint32_t engine = MC_ENGINE_LEVEL;
+  uint32_t cfg_wcap = 0, cfg_tsize = 0;
+  int cfg_threads = 0, cfg_grid = 0;
+  size_t cfg_smem = 0;
   // device state
   bool reserved = false;
   int device = -1;
@@ -201,13 +210,18 @@ struct mc_model {
   Ctrl* d_ctrl = nullptr;
   uint64_t *d_levels = nullptr, *d_off = nullptr, *d_trace = nullptr;
   uint64_t *d_tini = nullptr, *d_tmin = nullptr;
+  uint64_t* d_seg = nullptr;         // configuration engine: segment starts, records, order,
+  mc::CfgRec* d_rec = nullptr;       // and one level-width array per result slot (a skipped
+  uint32_t* d_order = nullptr;       // chained pass must not clear the last pass's widths)
+  uint64_t* d_cfg_levels = nullptr;
+  int last_slot = 0;                 // slot of the last pass that ran
   uint8_t* h_block = nullptr;   // pinned host staging (from the pool), carved into:
   size_t h_block_bytes = 0;
   Ctrl* h_ctrl = nullptr;       // [kSlots]  } the device's headers, scalars and trace,
   uint64_t* h_scalar = nullptr; // [8]       } contiguous, read back by one copy
   uint64_t* h_trace = nullptr;  // [(max_level + 2) * 2]
   size_t mirror_bytes = 0;
-  uint32_t* h_params = nullptr; // staging of N, cost, speed
+  uint32_t* h_params = nullptr; // staging of N, cost, speed (then seg and order)
   cudaEvent_t ev[2 * kSlots] = {};
   bool ev_pending[kSlots] = {};
   mc_stats stats{};
@@ -310,7 +324,22 @@ bool valid_options(const mc_options* o) {
   if (o->table_log2 && (o->table_log2 < 3 || o->table_log2 > 40)) return false;
   if (o->probe_scheme > MC_PROBE_ONE_CALL) return false;
   if (o->no_log_tags > 1) return false;
+  if (o->engine > MC_ENGINE_CONFIG) return false;
+  if (o->unit_threads && (o->unit_threads < 64 || o->unit_threads > mc::kCfgMaxThreads || o->unit_threads % 32))
+    return false;
   return true;
+}
+
+// the configuration engine takes a model whose per-configuration levels fit
+// a block's shared memory and whose log indices fit 32 bits
+bool cfg_eligible(const mc_model* m) {
+  const uint64_t cap = m->key_words == 1 ? mc::kCfgMaxWidth64 : mc::kCfgMaxWidth128;
+  return m->unit_width <= cap && m->unit_log < (1ull << 32) && (uint64_t)m->a * m->b < (1ull << 31);
+}
+
+uint32_t resolve_engine(const mc_model* m) {
+  if (m->opt.engine == MC_ENGINE_AUTO) return cfg_eligible(m) ? MC_ENGINE_CONFIG : MC_ENGINE_LEVEL;
+  return m->opt.engine;
 }
 
 // spare top bits per 64-bit word of a key that tag the frontier log (8 to
@@ -330,6 +359,35 @@ bool resolve_split(uint32_t scheme, uint32_t key_words) {
 
 // sizes of the frontier log and the visited set
 int size_buffers(mc_model* m) {
+  m->engine = resolve_engine(m);
+  if (m->engine == MC_ENGINE_CONFIG) {
+    if (!cfg_eligible(m)) return MC_ERR_INVAL;
+    // a segment of the log per configuration, shared-memory tables per block
+    const uint64_t ab = (uint64_t)m->a * m->b;
+    m->log_cap = m->unit_log;
+    uint32_t w = 32;
+    while (w < m->unit_width) w <<= 1;
+    m->cfg_wcap = w;
+    m->cfg_tsize = 2 * w;  // at most half full
+    m->table_slots = m->cfg_tsize;
+    // enough threads for the widest level's lanes in one round, 64..512
+    if (m->opt.unit_threads) {
+      m->cfg_threads = (int)m->opt.unit_threads;
+    } else {
+      const uint64_t want = m->unit_width * m->tile;
+      int t = 64;
+      while ((uint64_t)t < want && t < (int)mc::kCfgMaxThreads) t <<= 1;
+      m->cfg_threads = t;
+    }
+    const uint64_t key_bytes = 8ull * m->key_words;
+    const uint64_t ctrl_bytes = (mc::kBarBytes + sizeof(Ctrl)) * kSlots + kScalarBytes + 8ull * (m->max_level + 2) * 5;
+    uint64_t total = mul_sat(m->log_cap, key_bytes + 4);
+    total = add_sat(total, ctrl_bytes + 4ull * (2 * ab + m->P));
+    total = add_sat(total, 8 * (ab + 1) + sizeof(mc::CfgRec) * ab + 4 * ab);
+    total = add_sat(total, 16ull * (m->max_level + 2) * kSlots);  // level widths per result slot
+    m->device_bytes = total;
+    return MC_OK;
+  }
   const uint64_t n_init = 1 + (uint64_t)m->a + (uint64_t)m->a * m->b;
   m->log_cap = m->opt.log_capacity ? std::max(m->opt.log_capacity, n_init) : m->state_bound;
   if (m->log_cap == UINT64_MAX) return MC_ERR_NOMEM;
@@ -359,6 +417,27 @@ int size_buffers(mc_model* m) {
   return MC_OK;
 }
 
+// The model's constants every kernel takes (device table pointers unset).
+void fill_params(const mc_model* m, Params& p) {
+  p = Params{};
+  p.a = m->a;
+  p.b = m->b;
+  p.P = m->P;
+  p.rule = m->rule;
+  p.n_bits = m->n_bits;
+  p.ts_shift = m->ts_shift;
+  p.wg_shift = m->wg_shift;
+  p.ts_mask = (1u << m->ts_bits) - 1;
+  p.wg_mask = (1u << m->wg_bits) - 1;
+  p.max_level = m->max_level;
+  p.n_mask = (1ull << m->n_bits) - 1;
+  const uint32_t nf = m->P * m->n_bits;
+  p.swar_ok = nf <= 64;
+  p.swar_mask = nf >= 64 ? ~0ull : ((1ull << nf) - 1);
+  p.swar_mul = 0;
+  for (uint32_t t = 0; t < m->P && t * m->n_bits < 64; ++t) p.swar_mul |= 1ull << (t * m->n_bits);
+}
+
 int reserve(mc_model* m) {
   if (m->reserved) return MC_OK;
   int rc = size_buffers(m);
@@ -368,34 +447,57 @@ int reserve(mc_model* m) {
   m->device = dev;
   int sms = 0;
   MC_CUDA(m, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  int coop = 0;
-  MC_CUDA(m, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  if (!coop) {
-    m->last_err = "device lacks cooperative launch";
-    return MC_ERR_CUDA;
-  }
-  m->threads = m->opt.threads_per_block ? (int)m->opt.threads_per_block : (int)mc::kThreads;
-  m->split = resolve_split(m->opt.probe_scheme, m->key_words);
+  const bool cfg = m->engine == MC_ENGINE_CONFIG;
+  const uint64_t ab = (uint64_t)m->a * m->b;
   int bps = 0;
-  if (mc::explore_kernel_occupancy(m->key_words, m->tile, m->rule, m->split, m->threads, &bps) || bps < 1) {
-    m->last_err = "occupancy query failed";
-    cudaGetLastError();
-    return MC_ERR_CUDA;
+  if (!cfg) {
+    int coop = 0;
+    MC_CUDA(m, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) {
+      m->last_err = "device lacks cooperative launch";
+      return MC_ERR_CUDA;
+    }
+    m->threads = m->opt.threads_per_block ? (int)m->opt.threads_per_block : (int)mc::kThreads;
+    m->split = resolve_split(m->opt.probe_scheme, m->key_words);
+    if (mc::explore_kernel_occupancy(m->key_words, m->tile, m->rule, m->split, m->threads, &bps) || bps < 1) {
+      m->last_err = "occupancy query failed";
+      cudaGetLastError();
+      return MC_ERR_CUDA;
+    }
+    if (m->opt.blocks_per_sm) bps = std::min<int>(bps, (int)m->opt.blocks_per_sm);
+    m->grid = sms * bps;
+  } else {
+    // a block per configuration (threads from size_buffers), shared memory
+    // for two frontiers and two tables; as many blocks as fit, at most one
+    // per configuration
+    m->cfg_smem = mc::cfg_smem_bytes((int)m->key_words, m->cfg_wcap, m->cfg_tsize);
+    if (mc::cfg_occupancy((int)m->key_words, m->cfg_threads, m->cfg_smem, &bps) || bps < 1) {
+      m->last_err = "occupancy query failed (configuration engine)";
+      cudaGetLastError();
+      return MC_ERR_CUDA;
+    }
+    if (m->opt.blocks_per_sm) bps = std::min<int>(bps, (int)m->opt.blocks_per_sm);
+    m->cfg_grid = (int)std::min<uint64_t>(ab, (uint64_t)sms * bps);
   }
-  if (m->opt.blocks_per_sm) bps = std::min<int>(bps, (int)m->opt.blocks_per_sm);
-  m->grid = sms * bps;
 
   const uint64_t key_bytes = 8ull * m->key_words;
   const size_t np = 2ull * m->a * m->b + m->P;
   m->d_params = (uint32_t*)dev_alloc(m, np * 4);
-  m->d_table = dev_alloc(m, m->table_slots * key_bytes);
+  if (!cfg) m->d_table = dev_alloc(m, m->table_slots * key_bytes);
   m->d_log_keys = dev_alloc(m, m->log_cap * key_bytes);
   m->d_log_par = (uint32_t*)dev_alloc(m, m->log_cap * 4);
   const size_t L2 = m->max_level + 2;
   const size_t mirror_bytes = sizeof(Ctrl) * kSlots + kScalarBytes + 16 * L2;  // headers, scalars, trace
   const size_t ctrl_bytes = mc::kBarBytes * kSlots + mirror_bytes + 16 * L2 + 8 * L2;
   m->d_ctrl_block = (uint8_t*)dev_alloc(m, ctrl_bytes);
-  if (!m->d_params || !m->d_table || !m->d_log_keys || !m->d_log_par || !m->d_ctrl_block) {
+  if (cfg) {
+    m->d_seg = (uint64_t*)dev_alloc(m, 8 * (ab + 1));
+    m->d_rec = (mc::CfgRec*)dev_alloc(m, sizeof(mc::CfgRec) * ab);
+    m->d_order = (uint32_t*)dev_alloc(m, 4 * ab);
+    m->d_cfg_levels = (uint64_t*)dev_alloc(m, 16 * L2 * kSlots);
+  }
+  if (!m->d_params || (!cfg && !m->d_table) || !m->d_log_keys || !m->d_log_par || !m->d_ctrl_block ||
+      (cfg && (!m->d_seg || !m->d_rec || !m->d_order || !m->d_cfg_levels))) {
     release(m);
     return MC_ERR_NOMEM;
   }
@@ -413,14 +515,17 @@ int reserve(mc_model* m) {
   m->mirror_bytes = mirror_bytes;
   // tagged frontier log for 64-bit keys with 8 or more spare top bits: the
   // log starts cleared, so no entry of freed memory carries a tag
-  m->tag_bits = log_tag_bits(m);
+  m->tag_bits = cfg ? 0 : log_tag_bits(m);  // the configuration engine's log is read only after its pass
   m->tag = 0;
   if (m->tag_bits) MC_CUDA(m, cudaMemsetAsync(m->d_log_keys, 0, m->log_cap * key_bytes, m->stream));
 
   // host staging: one pinned block (from the process-wide pool): the mirror
-  // of headers, scalars and trace, then the model arrays
+  // of headers, scalars and trace, then the model arrays (and, for the
+  // configuration engine, the segment starts and the order)
   const size_t o_params = align_up(mirror_bytes, 64);
-  m->h_block_bytes = o_params + np * 4;
+  const size_t o_seg = align_up(o_params + np * 4, 8);
+  const size_t o_order = o_seg + (cfg ? 8 * (ab + 1) : 0);
+  m->h_block_bytes = o_order + (cfg ? 4 * ab : 0);
   m->h_block = (uint8_t*)mc::pinned_alloc(m->h_block_bytes);
   if (!m->h_block) {
     release(m);
@@ -441,24 +546,18 @@ int reserve(mc_model* m) {
   // written again, so the host need not wait for the copy
   MC_CUDA(m, cudaMemcpyAsync(m->d_params, m->h_params, np * 4, cudaMemcpyHostToDevice, m->stream));
   m->stats.h2d_bytes += np * 4;
+  if (cfg) {
+    uint64_t* h_seg = (uint64_t*)(m->h_block + o_seg);
+    uint32_t* h_order = (uint32_t*)(m->h_block + o_order);
+    std::copy(m->seg.begin(), m->seg.end(), h_seg);
+    std::copy(m->order.begin(), m->order.end(), h_order);
+    MC_CUDA(m, cudaMemcpyAsync(m->d_seg, h_seg, 8 * (ab + 1), cudaMemcpyHostToDevice, m->stream));
+    MC_CUDA(m, cudaMemcpyAsync(m->d_order, h_order, 4 * ab, cudaMemcpyHostToDevice, m->stream));
+    m->stats.h2d_bytes += 12 * ab + 8;
+  }
 
   Params& p = m->params;
-  p.a = m->a;
-  p.b = m->b;
-  p.P = m->P;
-  p.rule = m->rule;
-  p.n_bits = m->n_bits;
-  p.ts_shift = m->ts_shift;
-  p.wg_shift = m->wg_shift;
-  p.ts_mask = (1u << m->ts_bits) - 1;
-  p.wg_mask = (1u << m->wg_bits) - 1;
-  p.max_level = m->max_level;
-  p.n_mask = (1ull << m->n_bits) - 1;
-  const uint32_t nf = m->P * m->n_bits;
-  p.swar_ok = nf <= 64;
-  p.swar_mask = nf >= 64 ? ~0ull : ((1ull << nf) - 1);
-  p.swar_mul = 0;
-  for (uint32_t t = 0; t < m->P && t * m->n_bits < 64; ++t) p.swar_mul |= 1ull << (t * m->n_bits);
+  fill_params(m, p);
   p.N = m->d_params;
   p.cost = m->d_params + (size_t)m->a * m->b;
   p.speed = m->d_params + 2ull * m->a * m->b;
@@ -492,8 +591,55 @@ int fetch_ctrl(mc_model* m) {
 // the caller has cleared (clear_ctrl); fetch_ctrl reads the header back.
 // With `prev`, the pass takes its threshold from that slot's counterexample
 // (see ExploreArgs::prev).
+uint64_t* cfg_levels_at(mc_model* m, int slot) { return m->d_cfg_levels + 2ull * (m->max_level + 2) * slot; }
+
+// The configuration engine's pass: the level widths start at zero, the
+// header's unit counters and stop word are cleared with it (clear_ctrl).
+int enqueue_cfg_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, bool prune,
+                     bool early_exit, bool witness, uint64_t* tmin_out, int slot, int prev) {
+  mc::CfgLaunch L{};
+  mc::CfgPass& Q = L.one;
+  Q.p = m->params;
+  Q.T = T;
+  Q.T_src = T_src;
+  Q.T_delta = delta;
+  Q.prev = prev >= 0 ? ctrl_at(m, prev) : nullptr;
+  Q.prune = prune;
+  Q.early_exit = early_exit;
+  Q.want_witness = witness;
+  Q.group = m->tile;
+  Q.log_keys = m->d_log_keys;
+  Q.log_par = m->d_log_par;
+  Q.seg = m->d_seg;
+  Q.levels = cfg_levels_at(m, slot);
+  Q.rec = m->d_rec;
+  Q.ctrl = ctrl_at(m, slot);
+  Q.trace = m->d_trace;
+  Q.tmin_out = tmin_out;
+  Q.order = m->d_order;
+  L.n_units = (uint64_t)m->a * m->b;
+  L.next = &Q.ctrl->units_next;
+  L.wcap = m->cfg_wcap;
+  L.tsize = m->cfg_tsize;
+  MC_CUDA(m, cudaMemsetAsync(Q.levels, 0, 16ull * (m->max_level + 2), m->stream));
+  if (m->opt.timing) {
+    const int rc_ = make_events(m);
+    if (rc_) return rc_;
+    MC_CUDA(m, cudaEventRecord(m->ev[2 * slot], m->stream));
+  }
+  MC_CUDA(m, mc::launch_cfg((int)m->key_words, m->cfg_grid, m->cfg_threads, m->cfg_smem, L, m->stream));
+  if (m->opt.timing) {
+    MC_CUDA(m, cudaEventRecord(m->ev[2 * slot + 1], m->stream));
+    m->ev_pending[slot] = true;
+  }
+  m->stats.explore_launches += 1;
+  return MC_OK;
+}
+
 int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, bool prune,
                  bool early_exit, bool witness, uint64_t* tmin_out, int slot, int prev = -1) {
+  if (m->engine == MC_ENGINE_CONFIG)
+    return enqueue_cfg_pass(m, T, T_src, delta, prune, early_exit, witness, tmin_out, slot, prev);
   ExploreArgs A{};
   A.p = m->params;
   A.table = m->d_table;
@@ -557,6 +703,7 @@ int sync(mc_model* m) {
 int pass_error(mc_model* m, int slot) {
   const Ctrl& c = m->h_ctrl[slot];
   m->last_levels = c.levels;
+  m->last_slot = slot;
   m->stats.states += c.states;
   m->stats.device_steps += c.levels;
   return c.err ? (int)c.err : MC_OK;  // the kernel stores the negative MC_ERR_* code
@@ -613,6 +760,22 @@ int run_simulation(mc_model* m, uint64_t seed, uint32_t walks, uint64_t* dst) {
   } while (0)
 
 }  // namespace
+
+namespace mc {
+
+int cfg_model_info(mc_model* m, CfgModelInfo* out) {
+  if (!m || !out) return MC_ERR_INVAL;
+  fill_params(m, out->p);
+  out->group = m->tile;
+  out->key_words = m->key_words;
+  out->unit_width = m->unit_width;
+  out->unit_log = m->unit_log;
+  out->seg = m->seg.data();
+  out->eligible = cfg_eligible(m);
+  return MC_OK;
+}
+
+}  // namespace mc
 
 extern "C" {
 
@@ -721,6 +884,31 @@ int mc_model_create(const mc_model_desc* d, const mc_options* opt, mc_model** ou
   }
   m->max_width = widest;
   m->state_bound = total;
+  // the configuration engine's bounds: the widest level of one
+  // configuration is w(n_max) (w grows with k), and configuration c's
+  // states number at most sum_{k <= N_c} w(k); its frontier-log segment
+  // has that size.  Configurations are taken deepest first.
+  {
+    std::vector<uint64_t> upto(n_max + 1);  // sum_{k' <= k} w(k')
+    uint64_t pf = 1, acc = 0;
+    for (uint32_t k = 0; k <= n_max; ++k) {
+      if (k > 0 && pf != UINT64_MAX) {
+        const unsigned __int128 nx = (unsigned __int128)pf * (k + m->P - 1) / k;
+        pf = nx > (unsigned __int128)UINT64_MAX ? UINT64_MAX : (uint64_t)nx;
+      }
+      const uint64_t w = m->rule == MC_GREEDY ? std::min(pf, greedy_cap) : pf;
+      acc = add_sat(acc, w);
+      upto[k] = acc;
+      if (k == n_max) m->unit_width = w;
+    }
+    m->seg.assign(ab + 1, 0);
+    for (size_t k = 0; k < ab; ++k) m->seg[k + 1] = add_sat(m->seg[k], upto[m->N[k]]);
+    m->unit_log = m->seg[ab];
+    m->order.resize(ab);
+    for (size_t k = 0; k < ab; ++k) m->order[k] = (uint32_t)k;
+    std::stable_sort(m->order.begin(), m->order.end(),
+                     [m](uint32_t x, uint32_t y) { return m->N[x] > m->N[y]; });
+  }
   *out = m;
   return MC_OK;
 }
@@ -743,6 +931,8 @@ int mc_set_options(mc_model* m, const mc_options* o) {
     m->opt.blocks_per_sm = keep.blocks_per_sm;
     m->opt.probe_scheme = keep.probe_scheme;  // the grid was sized for its kernel
     m->opt.no_log_tags = keep.no_log_tags;    // the log was cleared (or not) for it
+    m->opt.engine = keep.engine;              // the buffers were made for one engine
+    m->opt.unit_threads = keep.unit_threads;
   }
   return MC_OK;
 }
@@ -788,7 +978,10 @@ int mc_model_layout(const mc_model* m, mc_layout* out) {
   out->log_capacity = m->log_cap;
   out->device_bytes = m->device_bytes;
   out->probe_scheme = resolve_split(m->opt.probe_scheme, m->key_words) ? MC_PROBE_SPLIT : MC_PROBE_ONE_CALL;
-  out->log_tag_bits = log_tag_bits(m);
+  out->engine = m->engine;
+  out->log_tag_bits = m->engine == MC_ENGINE_CONFIG ? 0 : log_tag_bits(m);
+  out->unit_width = m->unit_width;
+  out->unit_threads = m->engine == MC_ENGINE_CONFIG ? (uint32_t)m->cfg_threads : 0;
   return MC_OK;
 }
 
@@ -1043,7 +1236,8 @@ int mc_last_widths(mc_model* m, uint64_t* out, uint32_t cap, uint32_t* n) {
   DeviceGuard g(m->device);
   const uint32_t k = std::min(cap, *n);
   std::vector<uint64_t> rec(2ull * k);
-  MC_CUDA(m, cudaMemcpyAsync(rec.data(), m->d_levels, 16ull * k, cudaMemcpyDeviceToHost, m->stream));
+  const uint64_t* src = m->engine == MC_ENGINE_CONFIG ? cfg_levels_at(m, m->last_slot) : m->d_levels;
+  MC_CUDA(m, cudaMemcpyAsync(rec.data(), src, 16ull * k, cudaMemcpyDeviceToHost, m->stream));
   m->stats.d2h_bytes += 16ull * k;
   MC_TRY(sync(m));
   // the low 32 bits of a level's word are its width (the kernel's level

@@ -34,6 +34,7 @@
 #include <string>
 #include <vector>
 
+#include "mc_cfg_jobs.h"
 #include "mc_device.cuh"
 
 namespace mc {
@@ -711,6 +712,15 @@ struct mc_batch {
   cudaEvent_t ev[2] = {};
   mc_stats stats{};
   std::string last_err;
+  // configuration engine (every instance one block per configuration)
+  uint32_t engine = MC_ENGINE_LEVEL;
+  std::vector<mc::CfgModelPrep> cm;
+  mc::CfgRun run;
+  uint8_t* h_run = nullptr;           // pinned mirror of the run block
+  int cfg_grid = 0, cfg_threads = 0;
+  uint32_t cfg_wcap = 32;
+  size_t cfg_smem = 0;
+  std::vector<uint32_t> trace_len;    // per instance, from the last run
 };
 
 namespace {
@@ -761,6 +771,8 @@ void brelease(mc_batch* b) {
   if (b->h_inst) cudaFreeHost(b->h_inst);
   if (b->h_state) cudaFreeHost(b->h_state);
   if (b->h_ctrl2) cudaFreeHost(b->h_ctrl2);
+  if (b->h_run) cudaFreeHost(b->h_run);
+  b->h_run = nullptr;
   b->graph = nullptr;
   b->graph_tried = false;
   b->cap_stream = nullptr;
@@ -775,8 +787,10 @@ int describe_instance(const mc_model_desc& d_in, const mc_options& o, mc::BInst&
                       std::vector<uint32_t>& pr, uint64_t& region_bytes) {
   mc_model_desc d = d_in;
   d.key_bits = 128;  // every instance uses 128-bit keys
+  mc_options lo = o;
+  lo.engine = MC_ENGINE_LEVEL;  // the lockstep engine's layout and buffers
   mc_model* m = nullptr;
-  int rc = mc_model_create(&d, &o, &m);
+  int rc = mc_model_create(&d, &lo, &m);
   if (rc) return rc;
   rc = mc_model_layout(m, &L);
   mc_model_destroy(m);
@@ -836,8 +850,60 @@ void place_instance(mc::BInst& I, const mc_layout& L, uint8_t* q, size_t n_param
   I.log_par = (uint32_t*)q;
 }
 
+// The configuration engine's batch: one pool holding every instance's region
+// and the run block; the instances' tables and segment starts uploaded once.
+int breserve_cfg(mc_batch* b) {
+  MCB_CUDA(b, cudaGetDevice(&b->device));
+  int sms = 0, bps = 0;
+  MCB_CUDA(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+  uint64_t units = 0;
+  b->cfg_threads = 64;
+  b->cfg_wcap = 32;
+  for (const mc::CfgModelPrep& M : b->cm) {
+    units += M.ab;
+    b->cfg_threads = std::max<int>(b->cfg_threads, (int)M.threads);
+    b->cfg_wcap = std::max(b->cfg_wcap, M.wcap);
+  }
+  if (b->opt.unit_threads) b->cfg_threads = (int)b->opt.unit_threads;
+  b->cfg_smem = mc::cfg_smem_bytes(2, b->cfg_wcap, 2 * b->cfg_wcap);
+  if (mc::cfg_occupancy(2, b->cfg_threads, b->cfg_smem, &bps) || bps < 1) {
+    b->last_err = "occupancy query failed (configuration engine)";
+    cudaGetLastError();
+    return MC_ERR_CUDA;
+  }
+  if (b->opt.blocks_per_sm) bps = std::min<int>(bps, (int)b->opt.blocks_per_sm);
+  b->cfg_grid = (int)std::min<uint64_t>((uint64_t)sms * bps, std::max<uint64_t>(units * 2, 1));
+  b->d_pool = (uint8_t*)balloc(b, b->pool_bytes);
+  if (!b->d_pool) {
+    brelease(b);
+    return MC_ERR_NOMEM;
+  }
+  const uint64_t run_bytes = mc::CfgRun::block_bytes(b->n, units);
+  const uint64_t run_off = b->pool_bytes - run_bytes;
+  if (cudaMallocHost((void**)&b->h_run, run_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    brelease(b);
+    return MC_ERR_NOMEM;
+  }
+  b->run.layout(b->n, units, b->d_pool + run_off, b->h_run);
+  for (cudaEvent_t& e : b->ev) MCB_CUDA(b, cudaEventCreate(&e));
+  MCB_CUDA(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  for (uint32_t i = 0; i < b->n; ++i) {
+    mc::CfgModelPrep& M = b->cm[i];
+    mc::cfg_place(M, b->d_pool + b->pool_off[i]);
+    MCB_CUDA(b, cudaMemcpyAsync(M.base, M.params.data(), 4 * M.params.size(), cudaMemcpyHostToDevice, b->stream));
+    MCB_CUDA(b, cudaMemcpyAsync(M.d_seg, M.seg.data(), 8 * M.seg.size(), cudaMemcpyHostToDevice, b->stream));
+    b->stats.h2d_bytes += 4 * M.params.size() + 8 * M.seg.size();
+  }
+  MCB_CUDA(b, cudaStreamSynchronize(b->stream));
+  b->trace_len.assign(b->n, 0);
+  b->reserved = true;
+  return MC_OK;
+}
+
 int breserve(mc_batch* b) {
   if (b->reserved) return MC_OK;
+  if (b->engine == MC_ENGINE_CONFIG) return breserve_cfg(b);
   MCB_CUDA(b, cudaGetDevice(&b->device));
   int sms = 0, coop = 0, bps = 0;
   MCB_CUDA(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
@@ -883,6 +949,62 @@ int breserve(mc_batch* b) {
 
 }  // namespace
 
+namespace {
+
+// One batch run on the configuration engine: the run's descriptors go to
+// the pinned mirror, then the captured sequence (upload, clear, simulate,
+// both pass launches, read-back) is replayed; where capture is refused the
+// sequence is enqueued directly.
+int batch_run_cfg(mc_batch* b, const mc_query* queries, mc_batch_result* results) {
+  std::vector<mc::CfgModelPrep*> ms(b->n);
+  for (uint32_t i = 0; i < b->n; ++i) ms[i] = &b->cm[i];
+  b->run.prepare(ms, queries, b->opt);
+  b->run.threads = b->cfg_threads;  // the launch shape of the reservation
+  b->run.wcap = b->cfg_wcap;
+  b->run.tsize = 2 * b->cfg_wcap;
+  cudaEvent_t e0 = b->opt.timing ? b->ev[0] : nullptr, e1 = b->opt.timing ? b->ev[1] : nullptr;
+  if (!b->graph_tried) {
+    b->graph_tried = true;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const cudaError_t e1c = b->run.enqueue(b->cap_stream, b->cfg_grid, b->cfg_grid, b->cfg_smem, e0, e1, true);
+      const cudaError_t e2c = cudaStreamEndCapture(b->cap_stream, &g);
+      if (e1c == cudaSuccess && e2c == cudaSuccess && g && cudaGraphInstantiate(&b->graph, g, 0) != cudaSuccess)
+        b->graph = nullptr;
+      if (e1c != cudaSuccess || e2c != cudaSuccess) b->graph = nullptr;
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();  // a refused capture is not an error of the run
+  }
+  if (b->graph) {
+    MCB_CUDA(b, cudaGraphLaunch(b->graph, b->stream));
+    b->stats.graph_launches += 1;
+  } else {
+    MCB_CUDA(b, b->run.enqueue(b->stream, b->cfg_grid, b->cfg_grid, b->cfg_smem, e0, e1, false));
+  }
+  MCB_CUDA(b, cudaStreamSynchronize(b->stream));
+  b->stats.h2d_bytes += b->run.upload_bytes;
+  b->stats.d2h_bytes += b->run.result_bytes;
+  b->stats.explore_launches += 2;
+  b->stats.other_launches += 2;
+  if (b->opt.timing) {
+    float ms = 0.f;
+    MCB_CUDA(b, cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+    b->stats.explore_ms += ms;
+  }
+  uint32_t deepest = 0;
+  for (uint32_t i = 0; i < b->n; ++i) {
+    uint64_t states = 0;
+    b->run.result(b->cm[i], i, queries[i], results[i], &b->trace_len[i], &states);
+    b->stats.states += states;
+    deepest = std::max(deepest, results[i].levels);
+  }
+  b->stats.device_steps += deepest;
+  return MC_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int mc_batch_create(const mc_model_desc* descs, uint32_t n, const mc_options* opt, mc_batch** out) {
@@ -895,6 +1017,46 @@ int mc_batch_create(const mc_model_desc* descs, uint32_t n, const mc_options* op
   if (!b) return MC_ERR_NOMEM;
   b->n = n;
   b->opt = o;
+  if (o.engine != MC_ENGINE_LEVEL) {
+    // the configuration engine when it takes every instance
+    b->cm.resize(n);
+    bool all = true;
+    uint64_t off = 0, units = 0;
+    b->pool_off.resize(n);
+    b->wg.resize(n);
+    b->ts.resize(n);
+    for (uint32_t i = 0; i < n && all; ++i) {
+      const int rc = mc::cfg_prepare(descs[i], o, b->cm[i]);
+      if (rc == MC_ERR_INVAL && o.engine == MC_ENGINE_AUTO) {
+        mc_model_desc d = descs[i];  // a malformed description stays an error
+        mc_model* m = nullptr;
+        const int rc2 = mc_model_create(&d, &o, &m);
+        mc_model_destroy(m);
+        if (rc2) {
+          delete b;
+          return rc2;
+        }
+        all = false;
+        break;
+      }
+      if (rc) {
+        delete b;
+        return rc;
+      }
+      b->pool_off[i] = off;
+      off += b->cm[i].region;
+      units += b->cm[i].ab;
+      b->wg[i] = b->cm[i].wg;
+      b->ts[i] = b->cm[i].ts;
+    }
+    if (all) {
+      b->engine = MC_ENGINE_CONFIG;
+      b->pool_bytes = off + mc::CfgRun::block_bytes(n, units);
+      *out = b;
+      return MC_OK;
+    }
+    b->cm.clear();
+  }
   b->inst.resize(n);
   b->lay.resize(n);
   b->params.resize(n);
@@ -955,6 +1117,11 @@ int mc_batch_run(mc_batch* b, const mc_query* queries, mc_batch_result* results)
   if (b->device >= 0 && prev != b->device) cudaSetDevice(b->device);
   int rc = breserve(b);
   if (rc) return rc;
+  if (b->engine == MC_ENGINE_CONFIG) {
+    rc = batch_run_cfg(b, queries, results);
+    if (b->device >= 0 && prev >= 0 && prev != b->device) cudaSetDevice(prev);
+    return rc;
+  }
   for (uint32_t i = 0; i < b->n; ++i) {
     b->inst[i].kind = queries[i].kind;
     b->inst[i].T_query = queries[i].T;
@@ -1060,6 +1227,15 @@ int mc_batch_run(mc_batch* b, const mc_query* queries, mc_batch_result* results)
 
 int mc_batch_trace(mc_batch* b, uint32_t i, uint64_t* keys, uint32_t cap, uint32_t* len) {
   if (!b || !len || i >= b->n || (!keys && cap)) return MC_ERR_INVAL;
+  if (b->engine == MC_ENGINE_CONFIG) {
+    *len = b->reserved ? b->trace_len[i] : 0;
+    if (!b->reserved || *len == 0 || cap == 0) return MC_OK;
+    const uint32_t k = std::min(cap, *len);
+    MCB_CUDA(b, cudaMemcpyAsync(keys, b->cm[i].d_trace, 16ull * k, cudaMemcpyDeviceToHost, b->stream));
+    MCB_CUDA(b, cudaStreamSynchronize(b->stream));
+    b->stats.d2h_bytes += 16ull * k;
+    return MC_OK;
+  }
   const mc::BState& s = b->h_state[i];
   *len = s.trace_len;
   if (!b->reserved || s.trace_len == 0 || cap == 0) return MC_OK;

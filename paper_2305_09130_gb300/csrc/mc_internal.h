@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include "mc.h"
+
 // A counterexample or witness path returned through the C-ABI (mc_trace is
 // opaque in mc.h): `words` u64 per state, states s0 .. the last one.
 struct mc_trace {
@@ -65,7 +67,8 @@ struct Params {
 struct Ctrl {
   uint32_t err;           // first error code of the pass (0 = none)
   uint32_t skipped;       // 1: a chained pass that did not run (its predecessor held or failed)
-  uint32_t pad0[2];
+  uint32_t units_next;    // configuration engine: next configuration to take
+  uint32_t units_done;    // configuration engine: configurations finished
   uint32_t levels;        // last explored level + 1
   uint32_t stop_level;    // first level holding a violating terminal (0 = none)
   uint32_t witness_level; // level the witness was taken from (0 = none)
@@ -78,6 +81,9 @@ struct Ctrl {
   uint64_t wpack;         // packed (time, i, j) of the first violating level
   uint64_t T;             // threshold the pass used
   uint64_t probes;        // successors generated (PE-level explorer only)
+  uint32_t stop_c;        // configuration engine, early exit: ~(least level known to hold a
+                          // violating terminal), 0 while none is known
+  uint32_t pad1[3];
 };
 
 // Everything one exploration pass needs.
@@ -124,6 +130,107 @@ cudaError_t launch_swarm(const Params& p, uint64_t seed, uint64_t w0, uint32_t w
                          unsigned long long* best, int grid, cudaStream_t stream);
 cudaError_t launch_replay_walk(const Params& p, uint64_t seed, uint64_t w, int key_words,
                                uint64_t* trace, uint32_t* len, cudaStream_t stream);
+
+// ---------------------------------------------------------------------------
+// Configuration engine (mc_cfg.cu).  The WG and TS selects (levels 1 and 2)
+// split the state space into disjoint subtrees, one per configuration (i, j):
+// every later state carries its (i, j).  A thread block explores one
+// subtree level by level with its frontier and visited set in shared
+// memory, so a level costs one block-wide barrier instead of a device-wide
+// one.  Counts, the first violating level, the minimum and the witness are
+// combined per level and per configuration, so a pass reports exactly what
+// the level-synchronous kernel reports.
+constexpr uint32_t kCfgMaxThreads = 512;
+constexpr uint64_t kCfgMaxWidth64 = 2048;   // widest level of one configuration, 64-bit keys
+constexpr uint64_t kCfgMaxWidth128 = 1024;  // 128-bit keys
+
+// One configuration's outcome in one pass.
+struct CfgRec {
+  uint64_t vpack;         // min packed (time, i, j) of its violating terminals, kNone if none
+  uint64_t wkey_lo;       // the smallest key among its violating terminals of that time
+  uint64_t wkey_hi;
+  uint32_t widx;          // log index of that key (passes that keep the log)
+  uint32_t deepest;       // deepest level it reached with a nonempty width
+};
+
+// One pass over every configuration of one model.
+struct CfgPass {
+  Params p;
+  uint64_t T;             // threshold, unless T_src or prev is set
+  const uint64_t* T_src;  // device threshold source (T = *T_src + T_delta)
+  int64_t T_delta;
+  const Ctrl* prev;       // chained lowering: run at prev's counterexample time - 1,
+                          // or not at all if prev held, failed or was skipped
+  uint32_t prune;
+  uint32_t early_exit;
+  uint32_t want_witness;  // keep the log and find the witness and its trace
+  uint32_t group;         // lanes per state: next power of two >= P
+  void* log_keys;         // [seg[a*b]] keys, written only with want_witness
+  uint32_t* log_par;      // parent log index of each entry
+  const uint64_t* seg;    // [a*b + 1] first log entry of each configuration's segment
+  uint64_t* levels;       // [max_level + 2] x {width, unused}, zeroed before the pass
+  CfgRec* rec;            // [a*b]
+  Ctrl* ctrl;             // header; units_next, units_done and stop_c start at 0
+  uint64_t* trace;        // [(max_level + 1) * 2]
+  uint64_t* tmin_out;     // if set: receives the least violating terminal time
+  const uint32_t* order;  // [a*b] configurations in the order blocks take them (deepest first)
+};
+
+// A launch: one pass (`one`), or many passes of many models (`passes`, with
+// `units` listing (pass index << 32 | configuration) in the order blocks
+// take them).  `next` counts the units handed out.
+struct CfgLaunch {
+  CfgPass one;
+  const CfgPass* passes;
+  const uint64_t* units;
+  uint64_t n_units;
+  const uint32_t* n_units_dev;  // if set: the unit count, read on the device
+  uint32_t* next;
+  uint32_t wcap;          // frontier capacity per level (states), a power of two
+  uint32_t tsize;         // shared visited-set slots per level, a power of two
+};
+
+size_t cfg_smem_bytes(int key_words, uint32_t wcap, uint32_t tsize);
+int cfg_occupancy(int key_words, int threads, size_t smem, int* blocks_per_sm);
+cudaError_t launch_cfg(int key_words, int grid, int threads, size_t smem, const CfgLaunch& L,
+                       cudaStream_t stream);
+
+// Runs of many models on the configuration engine (batches, served jobs):
+// before the passes, one launch clears every model's pass headers and level
+// widths and sets its T_ini word; a second draws the T_ini simulations.
+struct CfgClear {         // one model's words to clear
+  uint64_t* levels;       // its passes' level-width arrays, contiguous
+  uint64_t level_words;
+  Ctrl* ctrl;             // its pass headers, contiguous
+  uint32_t n_ctrl;
+  uint32_t pad;
+  uint64_t* scal;         // {T_ini = kNone, T_min = 0}
+};
+struct CfgSim {           // one min-time model's simulation (Section 4, Step 3)
+  Params p;
+  uint64_t* tini;
+  uint64_t seed;
+  uint32_t walks;
+  uint32_t pad;
+};
+cudaError_t launch_cfg_clear(const CfgClear* clears, const uint32_t* n_dev, uint32_t n_max, cudaStream_t stream);
+cudaError_t launch_cfg_sim(const CfgSim* sims, const uint32_t* n_dev, uint32_t n_max, uint32_t walks_max,
+                           cudaStream_t stream);
+
+// What the configuration engine needs of a model made by mc_model_create
+// (host only): its constants (device pointers unset), the lanes per state,
+// the closed-form widest level of one configuration, and the frontier-log
+// segment starts of its configurations ([a*b + 1], owned by the model).
+struct CfgModelInfo {
+  Params p;
+  uint32_t group;
+  uint32_t key_words;
+  uint64_t unit_width;
+  uint64_t unit_log;
+  const uint64_t* seg;
+  bool eligible;
+};
+int cfg_model_info(mc_model* m, CfgModelInfo* out);
 
 }  // namespace mc
 

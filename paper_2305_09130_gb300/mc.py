@@ -28,6 +28,7 @@ MC_ERR_OVERFLOW = -7
 MC_FREE, MC_GREEDY = 0, 1
 SEARCH = {"single": 0, "lower": 1, "bisect": 2}
 PROBE = {"auto": 0, "split": 1, "one_call": 2}  # mc_probe_scheme
+ENGINE = {"auto": 0, "level": 1, "config": 2}  # mc_engine
 NO_LIMIT = (1 << 64) - 1
 
 U32P = C.POINTER(C.c_uint32)
@@ -47,7 +48,8 @@ class McOptions(C.Structure):
                 ("max_probes", C.c_uint32), ("log_capacity", C.c_uint64),
                 ("barrier_timeout_ns", C.c_uint64), ("debug_barrier_extra", C.c_uint32),
                 ("timing", C.c_uint32), ("lanes_per_state", C.c_uint32),
-                ("probe_scheme", C.c_uint32), ("no_log_tags", C.c_uint32), ("reserved", C.c_uint32 * 3)]
+                ("probe_scheme", C.c_uint32), ("no_log_tags", C.c_uint32), ("engine", C.c_uint32),
+                ("unit_threads", C.c_uint32), ("reserved", C.c_uint32 * 1)]
 
 
 class McCheckResult(C.Structure):
@@ -72,7 +74,8 @@ class McLayout(C.Structure):
                 ("max_level", C.c_uint32), ("n_shift", C.c_uint32 * 16),
                 ("table_slots", C.c_uint64), ("log_capacity", C.c_uint64),
                 ("max_width", C.c_uint64), ("state_bound", C.c_uint64),
-                ("device_bytes", C.c_uint64), ("probe_scheme", C.c_uint32), ("log_tag_bits", C.c_uint32)]
+                ("device_bytes", C.c_uint64), ("probe_scheme", C.c_uint32), ("log_tag_bits", C.c_uint32),
+                ("engine", C.c_uint32), ("unit_threads", C.c_uint32), ("unit_width", C.c_uint64)]
 
 
 class McSwarmResult(C.Structure):
@@ -273,6 +276,8 @@ def mc_options_default(**overrides) -> McOptions:
             v = SEARCH[v]
         if k == "probe_scheme" and isinstance(v, str):
             v = PROBE[v]
+        if k == "engine" and isinstance(v, str):
+            v = ENGINE[v]
         setattr(o, k, int(v))
     return o
 

@@ -118,25 +118,62 @@ def test_probe_schemes_are_accepted_by_name_and_number(lib):
 
 
 def test_frontier_log_tags_use_spare_key_bits(lib):
-    # 64-bit keys with at least 8 spare top bits tag their log entries (up to 16 bits)
-    assert layout(W.c1())["log_tag_bits"] == 16                    # 19 bits used
-    assert layout(W.c2_star())["log_tag_bits"] == 16               # 35 bits used
-    assert layout(W.c2(rule=W.GREEDY))["log_tag_bits"] == 13       # 51 bits used
+    # the level-synchronous engine: 64-bit keys with at least 8 spare top bits
+    # tag their log entries (up to 16 bits)
+    lv = {"engine": "level"}
+    assert layout(W.c1(), **lv)["log_tag_bits"] == 16                    # 19 bits used
+    assert layout(W.c2_star())["log_tag_bits"] == 16                     # 35 bits used
+    assert layout(W.c2(rule=W.GREEDY), **lv)["log_tag_bits"] == 13       # 51 bits used
     # 128-bit keys: two words of 64 - t payload bits, t <= (128 - used) / 2
-    assert layout(W.c1().with_key_bits(128))["log_tag_bits"] == 16  # 19 bits used
-    assert layout(W.c3(rule=W.GREEDY))["log_tag_bits"] == 8         # 111 bits used
+    assert layout(W.c1().with_key_bits(128), **lv)["log_tag_bits"] == 16  # 19 bits used
+    assert layout(W.c3(rule=W.GREEDY), **lv)["log_tag_bits"] == 8         # 111 bits used
     wrap8w = W.ModelSpec("wrap8w", 10, [1], [1], [1024], [3], [1] * 10, W.GREEDY)
-    assert layout(wrap8w)["used_bits"] == 112 and layout(wrap8w)["log_tag_bits"] == 8
+    assert layout(wrap8w, **lv)["used_bits"] == 112 and layout(wrap8w, **lv)["log_tag_bits"] == 8
     few128 = W.ModelSpec("few128", 10, [1, 2, 4], [1], [1024] * 3, [3] * 3, [1] * 10, W.GREEDY)
-    assert layout(few128)["used_bits"] == 113 and layout(few128)["log_tag_bits"] == 0
+    assert layout(few128, **lv)["used_bits"] == 113 and layout(few128, **lv)["log_tag_bits"] == 0
     # a=b=1, P=6, N=256: 1 + 1 + 6 x 9 = 56 bits, 8 spare; N=512: 62 bits, too few
     wrap8 = W.ModelSpec("wrap8", 6, [1], [1], [256], [3], [1] * 6, W.GREEDY)
-    assert layout(wrap8)["used_bits"] == 56 and layout(wrap8)["log_tag_bits"] == 8
+    assert layout(wrap8, **lv)["used_bits"] == 56 and layout(wrap8, **lv)["log_tag_bits"] == 8
     few = W.ModelSpec("few", 6, [1], [1], [512], [3], [1] * 6, W.GREEDY)
-    assert layout(few)["used_bits"] == 62 and layout(few)["log_tag_bits"] == 0
-    assert layout(W.c1(), no_log_tags=1)["log_tag_bits"] == 0
+    assert layout(few, **lv)["used_bits"] == 62 and layout(few, **lv)["log_tag_bits"] == 0
+    assert layout(W.c1(), no_log_tags=1, **lv)["log_tag_bits"] == 0
+    # the configuration engine reads its log only after the pass: untagged
+    assert layout(W.c1())["engine"] == mc.ENGINE["config"] and layout(W.c1())["log_tag_bits"] == 0
     with pytest.raises(mc.MCError):
         mc.mc_model_create(W.c1(), mc.mc_options_default(no_log_tags=2), allocator=None)
+
+
+def test_engine_follows_the_width_of_one_configuration(lib):
+    """AUTO takes the configuration engine when one configuration's widest
+    level (closed form: C(N+P-1, P-1) under FREE, at most C(P, P/2) under
+    GREEDY) fits a block's shared memory: 2048 states with 64-bit keys, 1024
+    with 128-bit keys.  Its log holds one segment per configuration, as long
+    as that configuration's states can be."""
+    from math import comb
+
+    c1 = layout(W.c1())  # FREE, P=2, N <= 64: the widest level of a configuration holds 65 states
+    assert (c1["engine"], c1["unit_width"]) == (mc.ENGINE["config"], 65)
+    assert c1["log_capacity"] == CF.count(W.c1()) - 1 - 5  # FREE: exact, without levels 0 and 1
+    assert c1["unit_threads"] == 256  # 65 states x 2 lanes in one round
+    c3 = layout(W.c3(rule=W.GREEDY))  # GREEDY, P=8
+    assert (c3["engine"], c3["unit_width"], c3["unit_threads"]) == (mc.ENGINE["config"], comb(8, 4), 512)
+    assert c3["log_capacity"] >= CF.count(W.c3(rule=W.GREEDY)) - 1 - 10
+    assert layout(W.c2_star())["engine"] == mc.ENGINE["level"]  # C(83, 3) states per level
+    assert layout(W.c3_star())["engine"] == mc.ENGINE["level"]
+    assert layout(W.c1(), engine="level")["engine"] == mc.ENGINE["level"]
+    assert layout(W.c3(rule=W.GREEDY), unit_threads=128)["unit_threads"] == 128
+    # 128-bit keys halve the width the engine takes
+    wide = W.ModelSpec("w", 2, [1], [1], [1500], [1], [1, 1])  # FREE, P=2: 1501 states per level
+    assert layout(wide)["engine"] == mc.ENGINE["config"]
+    assert layout(wide.with_key_bits(128))["engine"] == mc.ENGINE["level"]
+    # forcing the configuration engine on a model it cannot take is refused
+    m = mc.mc_model_create(W.c2_star(), mc.mc_options_default(engine="config"), allocator=None)
+    with pytest.raises(mc.MCError) as e:
+        mc.mc_reserve(m)
+    assert e.value.code == mc.MC_ERR_INVAL
+    for bad in ({"engine": 3}, {"unit_threads": 48}, {"unit_threads": 1024}):
+        with pytest.raises(mc.MCError):
+            mc.mc_model_create(W.c1(), mc.mc_options_default(**bad), allocator=None)
 
 
 def test_unknown_option_names_are_rejected(lib):

@@ -28,10 +28,11 @@ dram_bytes_per_launch_lf10_one_call: 300
 def test_traffic_per_state_is_scaled_by_the_states_of_a_launch(tmp_path):
     h = bench.kernel_source_hash()
     path = _write(tmp_path, f"""kernel_source_sha256_16: {h}
-dram_bytes_per_state_one_call: 512.5
+dram_bytes_per_state_lf25_one_call: 512.5
 """)
     assert bench.ncu_traffic_per_launch(path, 25, "one_call", 2e6) == 512.5 * 2e6
     assert bench.ncu_traffic_per_launch(path, 25, "split", 2e6) is None
+    assert bench.ncu_traffic_per_launch(path, 40, "one_call", 2e6) is None
 
 
 def test_traffic_is_null_for_other_kernel_sources(tmp_path):

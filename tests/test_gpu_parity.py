@@ -59,6 +59,9 @@ def gpu_min(mc, model, search, prune, seed=2305091300, walks=1, refine=True):
             "i": r["i"], "j": r["j"], "level": r["level"], "n": n}
 
 
+ENGINES = ["level", "config"]
+
+
 def thresholds(oracle, spec):
     t_min = oracle.min_time(spec)["t_min"]
     return sorted({0, 1, t_min - 1, t_min, t_min + 1, 2 * t_min, 5 * t_min, NO_LIMIT})
@@ -66,10 +69,11 @@ def thresholds(oracle, spec):
 
 # ---------------------------------------------------------------- small exact parity
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("name,rule", [("tiny", FREE), ("tiny", GREEDY), ("c1", FREE), ("c1", GREEDY)])
-def test_checks_match_oracle(mc, oracle, name, rule):
+def test_checks_match_oracle(mc, oracle, name, rule, engine):
     spec = W.NAMED[name](rule)
-    model = make(mc, spec)
+    model = make(mc, spec, engine=engine)
     assert mc.mc_count_states(model) == oracle.count(spec) == CF.count(spec)
     assert mc.mc_last_widths(model) == CF.widths(spec)
     for T in thresholds(oracle, spec):
@@ -80,10 +84,11 @@ def test_checks_match_oracle(mc, oracle, name, rule):
                 assert got == exp, (T, prune, ee)
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("name,rule", [("tiny", FREE), ("tiny", GREEDY), ("c1", FREE), ("c1", GREEDY)])
-def test_min_time_matches_oracle(mc, oracle, name, rule):
+def test_min_time_matches_oracle(mc, oracle, name, rule, engine):
     spec = W.NAMED[name](rule)
-    model = make(mc, spec)
+    model = make(mc, spec, engine=engine)
     for search in ("single", "lower", "bisect"):
         for prune in (False, True):
             got = gpu_min(mc, model, search, prune)
@@ -105,9 +110,11 @@ def sweep_models():
     return out
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("spec", sweep_models(), ids=lambda s: f"P{s.P}_r{s.rule}_k{s.key_bits}_{s.meta['seed']}")
-def test_random_models_match_oracle(mc, oracle, spec):
-    model = make(mc, spec)
+def test_random_models_match_oracle(mc, oracle, spec, engine):
+    model = make(mc, spec, engine=engine)
+    assert mc.mc_model_layout(model)["engine"] == mc.ENGINE[engine]
     assert mc.mc_model_layout(model)["key_bits"] == (spec.key_bits or 64)
     assert mc.mc_count_states(model) == oracle.count(spec) == CF.count(spec)
     assert mc.mc_last_widths(model) == CF.widths(spec)
@@ -164,10 +171,11 @@ def golden():
         return json.load(f)
 
 
-def test_c2_literal_greedy(mc, oracle):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_c2_literal_greedy(mc, oracle, engine):
     spec = W.c2(rule=GREEDY)
     g = golden()["c2_greedy"]
-    model = make(mc, spec)
+    model = make(mc, spec, engine=engine)
     assert mc.mc_count_states(model) == g["count"] == CF.count(spec)
     assert mc.mc_last_widths(model) == CF.widths(spec)
     for key, exp in g["min_time"].items():
@@ -179,10 +187,11 @@ def test_c2_literal_greedy(mc, oracle):
         assert gpu_check(mc, model, T) == oracle.check(spec, T)
 
 
-def test_c3_literal_greedy_u128(mc, oracle):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_c3_literal_greedy_u128(mc, oracle, engine):
     spec = W.c3(rule=GREEDY)
     g = golden()["c3_greedy"]
-    model = make(mc, spec)
+    model = make(mc, spec, engine=engine)
     assert mc.mc_model_layout(model)["key_words"] == 2
     assert mc.mc_count_states(model) == g["count"] == CF.count(spec)
     got = gpu_min(mc, model, "single", True)
@@ -229,7 +238,8 @@ def test_c3_star_full(mc):
 
 # ---------------------------------------------------------------- edge cases and errors
 
-def test_degenerate_models(mc, oracle):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_degenerate_models(mc, oracle, engine):
     cases = [
         W.ModelSpec("one", 1, [1], [1], [1], [1], [1]),
         W.ModelSpec("one_g", 1, [1], [1], [1], [1], [1], GREEDY),
@@ -239,29 +249,37 @@ def test_degenerate_models(mc, oracle):
                     [1 + (k % 3) for k in range(1200)], [1 + (k % 5) for k in range(1200)], [1, 2]),
     ]
     for spec in cases:
-        model = make(mc, spec)
+        if engine == "config" and mc.mc_model_layout(make(mc, spec))["engine"] != mc.ENGINE["config"]:
+            # p16g: one configuration's GREEDY level can hold C(16, 8) states,
+            # beyond a block's shared memory; forcing the engine is refused
+            with pytest.raises(mc.MCError) as e:
+                mc.mc_reserve(make(mc, spec, engine=engine))
+            assert e.value.code == mc.MC_ERR_INVAL and spec.name == "p16g"
+            continue
+        model = make(mc, spec, engine=engine)
         assert mc.mc_count_states(model) == oracle.count(spec) == CF.count(spec), spec.name
         for T in (0, 1, 3, NO_LIMIT):
             assert gpu_check(mc, model, T) == oracle.check(spec, T), (spec.name, T)
         assert gpu_min(mc, model, "single", True) == oracle.min_time(spec), spec.name
 
 
-def test_threshold_zero_keeps_only_selects(mc):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_threshold_zero_keeps_only_selects(mc, engine):
     spec = W.c1(FREE)
-    model = make(mc, spec)
+    model = make(mc, spec, engine=engine)
     r = gpu_check(mc, model, 0, prune=True, early_exit=True)
     assert r == {"holds": True, "states": 1 + spec.a + spec.a * spec.b, "levels": 3}
 
 
 def test_table_full_is_reported(mc):
-    model = make(mc, W.c1(FREE), table_log2=3, max_probes=2)
+    model = make(mc, W.c1(FREE), table_log2=3, max_probes=2, engine="level")
     with pytest.raises(mc.MCError) as e:
         mc.mc_count_states(model)
     assert e.value.code == mc.MC_ERR_TABLE_FULL
 
 
 def test_frontier_overflow_is_reported(mc):
-    model = make(mc, W.c1(FREE), log_capacity=100)
+    model = make(mc, W.c1(FREE), log_capacity=100, engine="level")
     with pytest.raises(mc.MCError) as e:
         mc.mc_count_states(model)
     assert e.value.code == mc.MC_ERR_FRONTIER
@@ -270,7 +288,7 @@ def test_frontier_overflow_is_reported(mc):
 def test_barrier_timeout_is_reported_and_context_survives(mc):
     # every device-wide wait expects one arrival that never comes: each block
     # gives up after 0.2 s of %globaltimer and the pass returns MC_ERR_TIMEOUT
-    model = make(mc, W.c1(FREE), debug_barrier_extra=1, barrier_timeout_ns=200_000_000)
+    model = make(mc, W.c1(FREE), debug_barrier_extra=1, barrier_timeout_ns=200_000_000, engine="level")
     with pytest.raises(mc.MCError) as e:
         mc.mc_count_states(model)
     assert e.value.code == mc.MC_ERR_TIMEOUT
@@ -294,14 +312,15 @@ def staircase(P, b, rule):
     return W.ModelSpec(f"staircase_P{P}", P, [1], W.pow2_range(0, b - 1), n, cost, [1] * P, rule)
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("P,b", [(1, 12), (2, 10), (3, 9)])
 @pytest.mark.parametrize("rule", [FREE, GREEDY])
-def test_lowering_chained_over_several_groups(mc, oracle, P, b, rule):
+def test_lowering_chained_over_several_groups(mc, oracle, P, b, rule, engine):
     # the device chains the lowering checks in groups of three over four
     # result slots; up to eight checks here cross two group boundaries, and a
     # group's remaining checks are skipped once one holds
     spec = staircase(P, b, rule)
-    model = make(mc, spec)
+    model = make(mc, spec, engine=engine)
     for prune in (True, False):
         exp = oracle.min_time(spec, search="lower", prune=prune)
         assert gpu_min(mc, model, "lower", prune) == exp
@@ -317,7 +336,7 @@ def test_probe_schemes_match_oracle(mc, oracle, scheme):
     """Both inserts (mc_options.probe_scheme), forced on 64- and 128-bit keys,
     give the oracle's counts, widths, checks and minima."""
     for spec in sweep_models()[::3]:
-        model = make(mc, spec, probe_scheme=scheme)
+        model = make(mc, spec, probe_scheme=scheme, engine="level")
         mc.mc_reserve(model)  # the scheme is fixed once the buffers exist
         assert mc.mc_model_layout(model)["probe_scheme"] == mc.PROBE[scheme]
         assert mc.mc_count_states(model) == oracle.count(spec)
@@ -336,7 +355,7 @@ def test_probe_schemes_at_full_size(mc, scheme):
     each insert forced: the full counts, every level's width and the minimum."""
     g = golden()
     for spec, exp in ((W.c2_star(), g["c2_star"]), (W.c3(rule=GREEDY), g["c3_greedy"])):
-        model = make(mc, spec, probe_scheme=scheme, load_factor_pct=10)
+        model = make(mc, spec, probe_scheme=scheme, load_factor_pct=10, engine="level")
         mc.mc_reserve(model)
         assert mc.mc_count_states(model) == exp["count"] == CF.count(spec)
         assert mc.mc_last_widths(model) == CF.widths(spec)
@@ -355,7 +374,7 @@ def test_tagged_log_survives_tag_wrap(mc, oracle, spec):
     the log's tag counter wraps every 255 passes (the host clears the log
     then); 600 checks on one model all agree with the oracle, and so does a
     min-time query after them."""
-    model = make(mc, spec)
+    model = make(mc, spec, engine="level")
     assert mc.mc_model_layout(model)["log_tag_bits"] == 8
     exp_min = oracle.min_time(spec)
     t_min = exp_min["t_min"]
@@ -371,7 +390,7 @@ def test_tagged_and_untagged_logs_agree(mc, oracle):
     identical counts, widths, checks and minima."""
     for spec in (W.c1(FREE), W.c1(GREEDY), W.c2(rule=GREEDY), W.c1(FREE).with_key_bits(128),
                  W.c1(GREEDY).with_key_bits(128)):
-        a, b = make(mc, spec), make(mc, spec, no_log_tags=1)
+        a, b = make(mc, spec, engine="level"), make(mc, spec, no_log_tags=1, engine="level")
         mc.mc_reserve(b)  # fixed once the buffers exist
         assert mc.mc_model_layout(a)["log_tag_bits"] > 0 and mc.mc_model_layout(b)["log_tag_bits"] == 0
         assert mc.mc_count_states(a) == mc.mc_count_states(b) == oracle.count(spec)
@@ -391,7 +410,7 @@ def test_tagged_log_on_c3_literal(mc, oracle):
     g = golden()["c3_greedy"]
     exp = g["min_time"]["single/prune1"]
     for opts in ({}, {"no_log_tags": 1}):
-        model = make(mc, spec, **opts)
+        model = make(mc, spec, engine="level", **opts)
         mc.mc_reserve(model)
         assert mc.mc_model_layout(model)["log_tag_bits"] == (0 if opts else 8)
         assert mc.mc_count_states(model) == g["count"] == CF.count(spec)
