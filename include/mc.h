@@ -449,7 +449,8 @@ typedef struct {
   double submit_s;       /* host steady-clock seconds: submitted,          */
   double admit_s;        /*   posted to the device (or started alone),     */
   double done_s;         /*   result harvested                             */
-  uint32_t path;         /* 0: the device loop, 1: alone (solo_states)     */
+  uint32_t path;         /* 0: the lockstep device loop, 1: alone
+                            (solo_states), 2: a configuration-engine job  */
   uint32_t reserved;
 } mc_server_result;
 

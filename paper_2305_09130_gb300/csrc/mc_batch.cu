@@ -1323,7 +1323,30 @@ struct Request {
   std::vector<uint32_t> params, wg, ts;
   uint64_t bytes = 0;
   double t_submit = 0;
+  bool cfg = false;         // runs in a configuration-engine job
+  mc::CfgModelPrep cm;      // its layout there (tables travel with the job)
 };
+
+// A configuration-engine job: requests admitted together, answered by one
+// run on the job's own stream; jobs on different streams overlap on the
+// device.
+struct CfgJob {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  uint8_t* d_block = nullptr;
+  uint8_t* h_block = nullptr;
+  mc::CfgRun run;
+  std::vector<Request> reqs;
+  std::vector<uint64_t> offs;
+  std::vector<mc_query> qs;
+  bool busy = false;
+  double t_admit = 0;
+};
+
+constexpr uint32_t kJobs = 8;             // job streams
+constexpr uint32_t kJobModels = 256;      // requests per job at most
+constexpr uint64_t kJobUnits = 1u << 16;  // configurations per job at most
+constexpr uint64_t kJobTables = 8ull << 20;  // bytes of model tables per job
 
 struct SlotInfo {
   bool busy = false;
@@ -1362,6 +1385,10 @@ struct mc_server {
   std::deque<mc_server_result> done;
   uint64_t next_ticket = 1;
   uint32_t next_seq = 1;
+  std::vector<CfgJob> jobs;
+  std::map<uint64_t, int> cfg_grid;  // (threads << 32 | frontier capacity) -> blocks of a launch
+  int sms = 0;
+  uint32_t jobs_running = 0;
   std::thread pump;
   std::atomic<bool> shutdown{false};
   int fatal = 0;
@@ -1542,6 +1569,113 @@ bool run_alone(mc_server* S, Request& req, mc_server_result& res) {
   return true;
 }
 
+// Blocks of a configuration-engine launch for a job's launch shape (the
+// occupancy maximum, cached per shape).
+int job_grid(mc_server* S, uint32_t threads, uint32_t wcap, size_t* smem) {
+  *smem = mc::cfg_smem_bytes(2, wcap, 2 * wcap);
+  const uint64_t key = ((uint64_t)threads << 32) | wcap;
+  auto it = S->cfg_grid.find(key);
+  if (it != S->cfg_grid.end()) return it->second;
+  int bps = 0;
+  if (mc::cfg_occupancy(2, (int)threads, *smem, &bps) || bps < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (S->opt.blocks_per_sm) bps = std::min<int>(bps, (int)S->opt.blocks_per_sm);
+  const int g = S->sms * bps;
+  S->cfg_grid[key] = g;
+  return g;
+}
+
+// Harvest finished jobs (caller holds S->mu).  Returns true on progress.
+bool harvest_jobs(mc_server* S) {
+  bool progress = false;
+  for (CfgJob& j : S->jobs) {
+    if (!j.busy) continue;
+    const cudaError_t q = cudaEventQuery(j.done);
+    if (q == cudaErrorNotReady) continue;
+    const double t = now_s();
+    for (size_t k = 0; k < j.reqs.size(); ++k) {
+      Request& req = j.reqs[k];
+      mc_server_result res;
+      std::memset(&res, 0, sizeof(res));
+      res.ticket = req.ticket;
+      if (q == cudaSuccess) {
+        j.run.result(req.cm, (uint32_t)k, j.qs[k], res.result, nullptr, nullptr);
+      } else {
+        res.result.status = MC_ERR_CUDA;
+        res.result.kind = req.q.kind;
+      }
+      res.submit_s = req.t_submit;
+      res.admit_s = j.t_admit;
+      res.done_s = t;
+      res.path = 2;
+      S->done.push_back(res);
+      S->pool.release(j.offs[k], req.bytes);
+    }
+    if (q != cudaSuccess) {
+      S->fatal = MC_ERR_CUDA;
+      S->last_err = cudaGetErrorString(q);
+      cudaGetLastError();
+    }
+    j.reqs.clear();
+    j.offs.clear();
+    j.qs.clear();
+    j.busy = false;
+    S->jobs_running -= 1;
+    progress = true;
+  }
+  return progress;
+}
+
+// Admit queued configuration-engine requests (from the front of the queue,
+// in arrival order) into free jobs while the pool has room for their
+// regions; each job is launched at once.  Caller holds S->mu.
+bool admit_jobs(mc_server* S) {
+  bool progress = false;
+  for (CfgJob& j : S->jobs) {
+    if (S->queue.empty() || !S->queue.front().cfg || S->fatal) break;
+    if (j.busy) continue;
+    j.run.tables_used = 0;
+    uint64_t units = 0;
+    while (!S->queue.empty() && S->queue.front().cfg && j.reqs.size() < kJobModels) {
+      Request& req = S->queue.front();
+      if (units + req.cm.ab > kJobUnits && !j.reqs.empty()) break;
+      uint64_t off = 0;
+      if (!S->pool.alloc(req.bytes, &off)) break;
+      if (!j.run.place_tables(req.cm)) {
+        S->pool.release(off, req.bytes);
+        break;
+      }
+      mc::cfg_place_state(req.cm, S->d_pool + off);
+      units += req.cm.ab;
+      j.offs.push_back(off);
+      j.qs.push_back(req.q);
+      j.reqs.push_back(std::move(req));
+      S->queue.pop_front();
+    }
+    if (j.reqs.empty()) break;  // the front request waits for pool room
+    std::vector<mc::CfgModelPrep*> ms(j.reqs.size());
+    for (size_t k = 0; k < j.reqs.size(); ++k) ms[k] = &j.reqs[k].cm;
+    j.run.prepare(ms, j.qs.data(), S->opt);
+    size_t smem = 0;
+    const int grid = job_grid(S, j.run.threads, j.run.wcap, &smem);
+    const int ga = (int)std::min<uint64_t>((uint64_t)grid, std::max<uint64_t>(j.run.n_units_a, 1));
+    const int gb = (int)std::min<uint64_t>((uint64_t)grid, std::max<uint64_t>(j.run.n_units_b, 1));
+    j.t_admit = now_s();
+    if (!grid || j.run.enqueue(j.stream, ga, gb, smem, nullptr, nullptr, false) != cudaSuccess ||
+        cudaEventRecord(j.done, j.stream) != cudaSuccess) {
+      S->fatal = MC_ERR_CUDA;
+      S->last_err = cudaGetErrorString(cudaGetLastError());
+    }
+    j.busy = true;
+    S->jobs_running += 1;
+    S->launches += 1;
+    progress = true;
+  }
+  return progress;
+}
+
 // Requests waiting on an idle server that still take the latency path one
 // after another (FIFO); a longer queue goes to the device loop, where the
 // requests share its steps.
@@ -1552,10 +1686,16 @@ void pump_loop(mc_server* S) {
   const uint32_t n = S->cfg.slots;
   while (!S->shutdown.load()) {
     bool progress = false;
+    {  // configuration-engine jobs: harvest finished ones, launch new ones
+      std::lock_guard<std::mutex> g(S->mu);
+      progress |= harvest_jobs(S);
+      progress |= admit_jobs(S);
+    }
+    if (progress) S->cv_done.notify_all();
     {  // latency path for a lone request on an idle server
       std::unique_lock<std::mutex> g(S->mu);
       bool idle = !S->fatal && !S->kernel_running && !S->queue.empty() && S->queue.size() <= kSoloQueue &&
-                  S->queue.front().lay.state_bound <= S->solo_states;
+                  !S->queue.front().cfg && S->queue.front().lay.state_bound <= S->solo_states;
       for (uint32_t i = 0; i < n && idle; ++i) idle = !S->slots[i].busy;
       if (idle) {
         Request req = std::move(S->queue.front());
@@ -1586,7 +1726,7 @@ void pump_loop(mc_server* S) {
       }
       // admit queued requests in arrival order while a slot and pool room are free
       uint32_t scan = 0;
-      while (!S->queue.empty() && !S->fatal) {
+      while (!S->queue.empty() && !S->fatal && !S->queue.front().cfg) {
         while (scan < n && S->slots[scan].busy) ++scan;
         if (scan == n) break;
         Request& req = S->queue.front();
@@ -1640,6 +1780,9 @@ void pump_loop(mc_server* S) {
         mc::OutboxEntry none{};
         for (uint32_t i = 0; i < n; ++i)
           if (S->slots[i].busy) finish_slot(S, i, none, S->fatal);
+        for (CfgJob& j : S->jobs)
+          if (j.busy) cudaStreamSynchronize(j.stream);
+        harvest_jobs(S);
         while (!S->queue.empty()) {
           mc_server_result res;
           std::memset(&res, 0, sizeof(res));
@@ -1657,6 +1800,7 @@ void pump_loop(mc_server* S) {
       }
     }
     if (progress) S->cv_done.notify_all();
+    else if (S->jobs_running) std::this_thread::sleep_for(std::chrono::microseconds(2));  // a job is due soon
     else std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
 }
@@ -1664,6 +1808,14 @@ void pump_loop(mc_server* S) {
 void server_free(mc_server* S) {
   if (S->h_stop) __atomic_store_n(S->h_stop, 1u, __ATOMIC_RELEASE);
   if (S->stream) cudaStreamSynchronize(S->stream);
+  for (CfgJob& j : S->jobs) {
+    if (j.stream) cudaStreamSynchronize(j.stream);
+    if (j.d_block) cudaFree(j.d_block);
+    if (j.h_block) cudaFreeHost(j.h_block);
+    if (j.done) cudaEventDestroy(j.done);
+    if (j.stream) cudaStreamDestroy(j.stream);
+  }
+  S->jobs.clear();
   if (S->d_pool) cudaFree(S->d_pool);
   if (S->d_inst) cudaFree(S->d_inst);
   if (S->d_state) cudaFree(S->d_state);
@@ -1706,6 +1858,21 @@ int mc_server_create(const mc_server_config* cfg, const mc_options* opt, mc_serv
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, S->device) != cudaSuccess || !coop)
     return bad(MC_ERR_CUDA);
+  S->sms = sms;
+  if (S->opt.engine != MC_ENGINE_LEVEL) {
+    // configuration-engine jobs: a stream, an event, a run block and its
+    // pinned mirror each
+    S->jobs.resize(kJobs);
+    const uint64_t jb = mc::CfgRun::block_bytes(kJobModels, kJobUnits, kJobTables);
+    for (CfgJob& j : S->jobs) {
+      if (cudaStreamCreateWithFlags(&j.stream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&j.done, cudaEventDisableTiming) != cudaSuccess)
+        return bad(MC_ERR_CUDA);
+      if (cudaMalloc((void**)&j.d_block, jb) != cudaSuccess || cudaMallocHost((void**)&j.h_block, jb) != cudaSuccess)
+        return bad(MC_ERR_NOMEM);
+      j.run.layout(kJobModels, kJobUnits, j.d_block, j.h_block, kJobTables);
+    }
+  }
   S->threads = (int)mc::kThreads;
   if (mc::batch_kernel_occupancy(S->threads, &bps) || bps < 1) return bad(MC_ERR_CUDA);
   // the served loop's steps are short and latency-bound: one block per SM
@@ -1749,8 +1916,22 @@ int mc_server_submit(mc_server* S, const mc_model_desc* desc, const mc_query* q,
   Request req;
   req.t_submit = now_s();
   req.q = *q;
-  int rc = describe_instance(*desc, S->opt, req.inst, req.lay, req.params, req.bytes);
-  if (rc) return rc;
+  int rc = MC_ERR_INVAL;
+  if (S->opt.engine != MC_ENGINE_LEVEL) {
+    // the configuration engine when it takes the model and it fits a job
+    rc = mc::cfg_prepare(*desc, S->opt, req.cm);
+    if (rc == MC_OK && (req.cm.ab > kJobUnits || mc::cfg_tables_bytes(req.cm) > kJobTables)) rc = MC_ERR_INVAL;
+    if (rc == MC_OK) {
+      req.cfg = true;
+      req.bytes = req.cm.region - mc::cfg_tables_bytes(req.cm);
+    } else if (rc != MC_ERR_INVAL || S->opt.engine == MC_ENGINE_CONFIG) {
+      return rc;
+    }
+  }
+  if (!req.cfg) {
+    rc = describe_instance(*desc, S->opt, req.inst, req.lay, req.params, req.bytes);
+    if (rc) return rc;
+  }
   if (req.bytes > S->cfg.pool_bytes) return MC_ERR_NOMEM;
   if (desc->wg_values) req.wg.assign(desc->wg_values, desc->wg_values + desc->n_wg);
   if (desc->ts_values) req.ts.assign(desc->ts_values, desc->ts_values + desc->n_ts);
@@ -1783,6 +1964,7 @@ int mc_server_status(mc_server* S, uint32_t* queued, uint32_t* running, uint64_t
   if (running) {
     uint32_t r = 0;
     for (const SlotInfo& sl : S->slots) r += sl.busy;
+    for (const CfgJob& j : S->jobs) r += (uint32_t)j.reqs.size();
     *running = r;
   }
   if (launches) *launches = S->launches;

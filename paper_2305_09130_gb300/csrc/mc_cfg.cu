@@ -502,9 +502,19 @@ size_t cfg_smem_bytes(int key_words, uint32_t wcap, uint32_t tsize) {
   return (size_t)8 * key_words * (2ull * wcap + 2ull * tsize);
 }
 
+// The kernels' dynamic shared memory limit is a property of the function,
+// shared by every model: it is raised once to the device's opt-in maximum
+// (a model's own size would lower it under a larger one reserved earlier).
 int cfg_occupancy(int key_words, int threads, size_t smem, int* blocks_per_sm) {
   const void* f = key_words == 1 ? (const void*)cfg_kernel<uint64_t> : (const void*)cfg_kernel<u128>;
-  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return -1;
+  const int static_bytes = (int)sizeof(CfgShared);
+  if ((int)smem > optin - static_bytes) return -1;
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - static_bytes) != cudaSuccess)
+    return -1;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, smem) == cudaSuccess ? 0 : -1;
 }
 

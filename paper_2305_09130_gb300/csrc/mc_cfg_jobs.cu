@@ -102,14 +102,48 @@ void cfg_place(CfgModelPrep& M, uint8_t* q) {
   M.d_par = (uint32_t*)q;
 }
 
-// ---------------------------------------------------------------- a run
-uint64_t CfgRun::block_bytes(uint32_t n, uint64_t units) {
-  return al256(sizeof(CfgPass) * 3ull * n) + al256(sizeof(CfgClear) * (uint64_t)n) +
-         al256(sizeof(CfgSim) * (uint64_t)n) + al256(8 * 3 * units) + 256 +  // upload part
-         al256(sizeof(Ctrl) * 3ull * n) + al256(16ull * n);                   // result part
+uint64_t cfg_tables_bytes(const CfgModelPrep& M) {
+  return al256(4ull * M.params.size()) + al256(8ull * (M.ab + 1));
 }
 
-void CfgRun::layout(uint32_t n_max, uint64_t units_max, uint8_t* dev, uint8_t* host) {
+void cfg_place_state(CfgModelPrep& M, uint8_t* q) {
+  const uint64_t ab = M.ab;
+  M.base = q;
+  M.d_rec = (CfgRec*)q;
+  q += al256(3ull * sizeof(CfgRec) * ab);
+  M.d_levels = (uint64_t*)q;
+  q += al256(48ull * M.L2);
+  M.d_trace = (uint64_t*)q;
+  q += al256(16ull * M.L2);
+  M.d_keys = q;
+  q += al256(16 * M.unit_log);
+  M.d_par = (uint32_t*)q;
+}
+
+// ---------------------------------------------------------------- a run
+uint64_t CfgRun::block_bytes(uint32_t n, uint64_t units, uint64_t tables_bytes) {
+  return al256(sizeof(CfgPass) * 3ull * n) + al256(sizeof(CfgClear) * (uint64_t)n) +
+         al256(sizeof(CfgSim) * (uint64_t)n) + al256(8 * 3 * units) + 256 + al256(tables_bytes) +  // upload
+         al256(sizeof(Ctrl) * 3ull * n) + al256(16ull * n);                                        // result
+}
+
+bool CfgRun::place_tables(CfgModelPrep& M) {
+  const uint64_t need = cfg_tables_bytes(M);
+  if (tables_used + need > tables_cap) return false;
+  uint8_t* h = h_tables + tables_used;
+  uint8_t* d = d_tables + tables_used;
+  std::memcpy(h, M.params.data(), 4 * M.params.size());
+  const uint64_t o_seg = al256(4ull * M.params.size());
+  std::memcpy(h + o_seg, M.seg.data(), 8 * M.seg.size());
+  M.p.N = (const uint32_t*)d;
+  M.p.cost = (const uint32_t*)d + M.ab;
+  M.p.speed = (const uint32_t*)d + 2ull * M.ab;
+  M.d_seg = (uint64_t*)(d + o_seg);
+  tables_used += need;
+  return true;
+}
+
+void CfgRun::layout(uint32_t n_max, uint64_t units_max, uint8_t* dev, uint8_t* host, uint64_t tables_bytes) {
   cap_n = n_max;
   cap_units = units_max;
   uint64_t o = 0;
@@ -123,6 +157,9 @@ void CfgRun::layout(uint32_t n_max, uint64_t units_max, uint8_t* dev, uint8_t* h
   const uint64_t o_sim = take(sizeof(CfgSim) * (uint64_t)n_max);
   const uint64_t o_units = take(8 * 3 * units_max);  // pass A: units_max, pass B: 2 x units_max
   const uint64_t o_cnt = take(256);
+  const uint64_t o_tab = take(tables_bytes);
+  tables_cap = al256(tables_bytes);
+  tables_used = 0;
   upload_bytes = o;
   const uint64_t o_ctrl = take(sizeof(Ctrl) * 3ull * n_max);
   const uint64_t o_scal = take(16ull * n_max);
@@ -144,6 +181,8 @@ void CfgRun::layout(uint32_t n_max, uint64_t units_max, uint8_t* dev, uint8_t* h
   h_cnt = (uint32_t*)(host + o_cnt);
   h_ctrl = (Ctrl*)(host + o_ctrl);
   h_scal = (uint64_t*)(host + o_scal);
+  d_tables = dev + o_tab;
+  h_tables = host + o_tab;
 }
 
 void CfgRun::prepare(const std::vector<CfgModelPrep*>& models, const mc_query* queries, const mc_options& opt) {
@@ -246,7 +285,8 @@ void CfgRun::prepare(const std::vector<CfgModelPrep*>& models, const mc_query* q
 cudaError_t CfgRun::enqueue(cudaStream_t st, int grid_a, int grid_b, size_t smem, cudaEvent_t ev0,
                             cudaEvent_t ev1, bool capturing) {
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(d_block, h_block, upload_bytes, cudaMemcpyHostToDevice, st))) return e;
+  const uint64_t up = tables_cap ? (uint64_t)(h_tables - h_block) + tables_used : upload_bytes;
+  if ((e = cudaMemcpyAsync(d_block, h_block, up, cudaMemcpyHostToDevice, st))) return e;
   if ((e = launch_cfg_clear(d_clear, d_cnt + 4, cap_n, st))) return e;
   if ((e = launch_cfg_sim(d_sim, d_cnt + 5, cap_n, walks_max, st))) return e;
   if (ev0 && (e = capturing ? cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal) : cudaEventRecord(ev0, st)))

@@ -36,6 +36,10 @@ int cfg_prepare(const mc_model_desc& d, const mc_options& o, CfgModelPrep& M);
 // Point the model at its region (M.region bytes, 256-byte aligned); the
 // caller uploads M.params and M.seg to M.base and M.d_seg.
 void cfg_place(CfgModelPrep& M, uint8_t* base);
+// The same without the tables: the region holds M.region - cfg_tables_bytes(M)
+// bytes, and the tables travel in a run's upload (CfgRun::place_tables).
+uint64_t cfg_tables_bytes(const CfgModelPrep& M);
+void cfg_place_state(CfgModelPrep& M, uint8_t* base);
 
 // One run's descriptors and results: a device block and its pinned mirror,
 // [passes][clears][sims][units][counters] uploaded, [headers][T_ini, T_min]
@@ -57,8 +61,14 @@ struct CfgRun {
   uint64_t n_units_a = 0, n_units_b = 0;
   bool refine = true, any_min = false;
 
-  static uint64_t block_bytes(uint32_t n_max, uint64_t units_max);
-  void layout(uint32_t n_max, uint64_t units_max, uint8_t* dev, uint8_t* host);
+  uint64_t tables_cap = 0, tables_used = 0;     // model tables carried by the upload
+  uint8_t *d_tables = nullptr, *h_tables = nullptr;
+
+  static uint64_t block_bytes(uint32_t n_max, uint64_t units_max, uint64_t tables_bytes = 0);
+  void layout(uint32_t n_max, uint64_t units_max, uint8_t* dev, uint8_t* host, uint64_t tables_bytes = 0);
+  // Copy M's tables and segment starts into the upload and point M at them
+  // (false when they do not fit); reset with tables_used = 0 per run.
+  bool place_tables(CfgModelPrep& M);
   // Fill the pinned descriptors for queries[k] on *models[k].
   void prepare(const std::vector<CfgModelPrep*>& models, const mc_query* queries, const mc_options& opt);
   // Upload, clear, simulate, both pass launches, read back (events around

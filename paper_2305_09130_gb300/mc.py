@@ -664,7 +664,7 @@ def mc_server_poll(server: Server, cap: int = 1024, wait_ms: int = 0) -> list:
         r = buf[k]
         d = _batch_result(r.result)
         d.update(ticket=r.ticket, submit_s=r.submit_s, admit_s=r.admit_s, done_s=r.done_s,
-                 path="alone" if r.path == 1 else "loop")
+                 path={0: "loop", 1: "alone", 2: "config"}.get(r.path, "loop"))
         out.append(d)
     return out
 

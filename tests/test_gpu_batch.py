@@ -1,4 +1,5 @@
-"""Batched exploration (one persistent launch for many models) against the
+"""Batched exploration (many models per run: the lockstep engine's one
+persistent launch, or the configuration engine's four launches) against the
 CPU oracle, the closed forms and the single-model entry points.
 
 Integer results, tolerance zero: per instance the decision, counts, levels,
@@ -13,6 +14,14 @@ from paper_2305_09130_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 NO_LIMIT = (1 << 64) - 1
+ENGINES = ["level", "config"]
+
+
+def engine_launches(mc, b, engine, runs):
+    """The engine that ran: one exploration launch per run on the lockstep
+    engine, two (first passes; certificate and final passes) on the
+    configuration engine."""
+    assert mc.mc_batch_get_stats(b)["explore_launches"] == runs * (2 if engine == "config" else 1)
 
 
 def layout128(mc, spec):
@@ -63,12 +72,13 @@ def check_against_oracle(mc, oracle, spec, query, r):
         assert got == exp
 
 
-def test_batch_matches_oracle(mc, oracle):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_batch_matches_oracle(mc, oracle, engine):
     specs = mixed_specs()
     t_mins = [oracle.min_time(s)["t_min"] for s in specs]
     queries = make_queries(specs, t_mins)
     assert {k for k, _ in queries} == {"check", "min_time"}
-    b = mc.mc_batch_create(specs)
+    b = mc.mc_batch_create(specs, mc.mc_options_default(engine=engine))
     for _run in range(2):  # the pool is reused; results must not depend on its contents
         res = mc.mc_batch_run(b, queries)
         for k, (spec, q, r) in enumerate(zip(specs, queries, res)):
@@ -85,15 +95,18 @@ def test_batch_matches_oracle(mc, oracle):
     for spec, q, r in zip(specs, flipped, mc.mc_batch_run(b, flipped)):
         check_against_oracle(mc, oracle, spec, q, r)
     assert mc.mc_batch_get_stats(b)["graph_launches"] == 3
+    engine_launches(mc, b, engine, 3)
 
 
-def test_batch_equals_single_model_queries(mc):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_batch_equals_single_model_queries(mc, engine):
     specs = W.c4_instances(96)
     t_mins = [CF.tmin(s)[0] for s in specs]
     queries = [("min_time", None) if s.meta["query"] else ("check", round(t * s.meta["t_frac_milli"] / 1000))
                for s, t in zip(specs, t_mins)]
-    b = mc.mc_batch_create(specs)
+    b = mc.mc_batch_create(specs, mc.mc_options_default(engine=engine))
     res = mc.mc_batch_run(b, queries)
+    engine_launches(mc, b, engine, 1)
     for spec, q, r, t_min in zip(specs, queries, res, t_mins):
         assert r["status"] == 0
         m = mc.mc_model_create(spec.with_key_bits(128))
@@ -112,16 +125,17 @@ def test_batch_equals_single_model_queries(mc):
         mc.mc_model_destroy(m)
 
 
-def test_batch_full_c4_in_the_bench_configuration(mc):
-    """All 256 C4 instances in one launch with the options the benchmark's
-    tuner picks (one block per SM, load factor 25%), run twice through the
+@pytest.mark.parametrize("engine", ENGINES)
+def test_batch_full_c4_in_the_bench_configuration(mc, engine):
+    """All 256 C4 instances in one batch with options the benchmark's tuner
+    may pick (one block per SM, load factor 25%), run twice through the
     captured graph: every answer equals the single-model entry point's and the
     closed-form minimal time."""
     specs = W.c4_instances(256)
     t_mins = [CF.tmin(s)[0] for s in specs]
     queries = [("min_time", None) if s.meta["query"] else ("check", round(t * s.meta["t_frac_milli"] / 1000))
                for s, t in zip(specs, t_mins)]
-    b = mc.mc_batch_create(specs, mc.mc_options_default(blocks_per_sm=1, load_factor_pct=25))
+    b = mc.mc_batch_create(specs, mc.mc_options_default(blocks_per_sm=1, load_factor_pct=25, engine=engine))
     first = mc.mc_batch_run(b, queries)
     again = mc.mc_batch_run(b, queries)
     assert [(r["status"], r["time"], r["states"], r["key"]) for r in first] == \
@@ -140,18 +154,38 @@ def test_batch_full_c4_in_the_bench_configuration(mc):
             assert (r["states"], r["levels"]) == (s["states"], s["levels"])
         mc.mc_model_destroy(m)
     assert mc.mc_batch_get_stats(b)["graph_launches"] == 2
+    engine_launches(mc, b, engine, 2)
+
+
+def test_batch_with_a_model_the_configuration_engine_cannot_take(mc, oracle):
+    """AUTO takes the lockstep engine for the whole batch when one instance's
+    configuration levels are too wide (C2 at G=80 under FREE); forcing the
+    configuration engine is refused."""
+    specs = [W.c1(W.GREEDY), W.c2_star()]
+    b = mc.mc_batch_create(specs)
+    res = mc.mc_batch_run(b, [("check", 80), ("check", 95)])
+    engine_launches(mc, b, "level", 1)
+    for spec, T, r in zip(specs, (80, 95), res):
+        e = oracle.check(spec, T)
+        assert (r["holds"], r["states"], r["levels"], r["time"]) == (e["holds"], e["states"], e["levels"],
+                                                                     e.get("cex_time", 0))
+    assert not res[0]["holds"] and res[1]["holds"]
+    with pytest.raises(mc.MCError) as err:
+        mc.mc_batch_create(specs, mc.mc_options_default(engine="config"))
+    assert err.value.code == mc.MC_ERR_INVAL
 
 
 def test_batch_errors_are_per_instance(mc):
     specs = [W.c1(W.FREE), W.tiny(W.GREEDY)]
-    b = mc.mc_batch_create(specs, mc.mc_options_default(table_log2=3, max_probes=1))
+    b = mc.mc_batch_create(specs, mc.mc_options_default(table_log2=3, max_probes=1, engine="level"))
     res = mc.mc_batch_run(b, [("check", NO_LIMIT), ("min_time", None)])
     assert [r["status"] for r in res] == [mc.MC_ERR_TABLE_FULL, mc.MC_ERR_TABLE_FULL]
 
 
 def test_batch_barrier_timeout(mc):
     b = mc.mc_batch_create([W.c1(W.FREE)], mc.mc_options_default(debug_barrier_extra=1,
-                                                                    barrier_timeout_ns=200_000_000))
+                                                                    barrier_timeout_ns=200_000_000,
+                                                                    engine="level"))
     with pytest.raises(mc.MCError) as e:
         mc.mc_batch_run(b, [("min_time", None)])
     assert e.value.code == mc.MC_ERR_TIMEOUT

@@ -417,3 +417,20 @@ def test_tagged_log_on_c3_literal(mc, oracle):
         assert mc.mc_last_widths(model) == CF.widths(spec)
         got = gpu_min(mc, model, "single", True)
         assert got == {k: exp[k] for k in got}
+
+
+def test_models_with_different_shared_memory_interleave(mc, oracle):
+    """The configuration kernel's shared-memory limit is a property of the
+    function, not of a model: a model whose configuration levels need more
+    than 48 KB of shared memory still runs after a smaller model was reserved
+    (FREE, P=2, 1000 work-groups: 1001 states per level, 64-bit keys)."""
+    big = W.ModelSpec("big_smem", 2, [1, 2], [1], [1000, 500], [1, 2], [1, 2])
+    small = W.c1(FREE)
+    a = make(mc, big, engine="config")
+    mc.mc_reserve(a)
+    b = make(mc, small, engine="config")
+    mc.mc_reserve(b)
+    assert mc.mc_model_layout(a)["unit_width"] == 1001
+    assert mc.mc_count_states(a) == oracle.count(big) == CF.count(big)
+    assert mc.mc_count_states(b) == 8763
+    assert gpu_min(mc, a, "single", True) == oracle.min_time(big)

@@ -1,7 +1,8 @@
 """Served queries (continuous batching): results equal the CPU oracle's and
 the single-model entry points', alone and in a mix (tolerance zero), and
-requests submitted while others run are admitted into the running device
-loop."""
+requests submitted while others run are admitted at once: into jobs of the
+configuration engine that overlap on the device, or (lockstep engine) into
+the running device loop."""
 import time
 
 import pytest
@@ -84,10 +85,13 @@ def test_served_results_equal_alone_and_in_mix(mc, oracle):
             if exp[key] is not None:
                 assert r[key] == exp[key], (idx, key, r, exp)
         assert r["submit_s"] <= r["admit_s"] <= r["done_s"]
-    # the same query alone on a fresh server gives the same answer, on the
-    # device loop and on the latency path for a lone request
-    for solo, path in ((1, "loop"), (0, "alone")):
-        alone = mc.mc_server_create(slots=1, pool_bytes=1 << 30, solo_states=solo)
+    assert all(r["path"] == "config" for r in got.values())
+    # the same query alone on a fresh server gives the same answer: in a job
+    # of its own, and with the lockstep engine on the device loop and on the
+    # latency path for a lone request
+    for engine, solo, path in (("auto", 0, "config"), ("level", 1, "loop"), ("level", 0, "alone")):
+        alone = mc.mc_server_create(slots=1, pool_bytes=1 << 30, solo_states=solo,
+                                    options=mc.mc_options_default(engine=engine))
         for idx in (0, 3, 9):
             t = mc.mc_server_submit(alone, specs[idx], *queries[idx])
             r = collect(mc, alone, 1)[t]
@@ -102,15 +106,15 @@ def test_served_results_equal_alone_and_in_mix(mc, oracle):
 def test_c5_shaped_queries_in_the_benchmark_server(mc, oracle):
     """Min-time queries drawn as the served benchmark draws them (G=4096,
     P=8, a new seed each, 128-bit keys), on a server with its slot count:
-    submitted together they share the device loop, and each answer equals the
-    single-model entry point's; one of them alone takes the latency path with
-    the same answer."""
+    submitted together they run in configuration-engine jobs that overlap on
+    the device, and each answer equals the oracle's and the single-model
+    entry point's; one of them alone gives the same answer."""
     specs = [W.c3(G=4096, rule=W.GREEDY, seed=2305091305 * 1000003 + 20_000_000 + k, key_bits=128)
              for k in range(16)]
     srv = mc.mc_server_create(slots=512, pool_bytes=8 << 30)
     tickets = {mc.mc_server_submit(srv, s, "min_time"): k for k, s in enumerate(specs)}
     got = collect(mc, srv, len(specs))
-    assert sum(r["path"] == "loop" for r in got.values()) >= len(specs) - 2
+    assert all(r["path"] == "config" for r in got.values())
     for t, k in tickets.items():
         r = got[t]
         against_oracle(mc, oracle, specs[k], "min_time", None, r)
@@ -122,30 +126,32 @@ def test_c5_shaped_queries_in_the_benchmark_server(mc, oracle):
     alone = mc.mc_server_create(slots=512, pool_bytes=8 << 30)
     t = mc.mc_server_submit(alone, specs[5], "min_time")
     r = collect(mc, alone, 1)[t]
-    assert r["path"] == "alone"
+    assert r["path"] == "config"
     against_oracle(mc, oracle, specs[5], "min_time", None, r)
     exp = single(mc, specs[5], "min_time", None)
     assert {k: r[k] for k in KEYS if exp[k] is not None} == {k: exp[k] for k in KEYS if exp[k] is not None}
     mc.mc_server_destroy(alone)
 
 
-def test_requests_join_a_running_device_loop(mc):
+@pytest.mark.parametrize("engine,path,wait_s", [("auto", "config", 0.002), ("level", "loop", 0.01)])
+def test_requests_join_while_others_run(mc, engine, path, wait_s):
     # a long GREEDY search is running when small queries arrive: they are
-    # admitted into the same device loop and finish first
+    # admitted at once (jobs of their own on other streams, or the running
+    # lockstep device loop) and finish first
     long_spec = W.c3(rule=W.GREEDY)
-    srv = mc.mc_server_create(slots=16, pool_bytes=8 << 30, options=mc.mc_options_default(prune=0),
+    srv = mc.mc_server_create(slots=16, pool_bytes=8 << 30, options=mc.mc_options_default(prune=0, engine=engine),
                               solo_states=1)
     t_long = mc.mc_server_submit(srv, long_spec, "min_time")
-    time.sleep(0.01)
+    time.sleep(wait_s)
     small = [mc.mc_server_submit(srv, W.c1(W.FREE), "check", 80) for _ in range(6)]
     got = collect(mc, srv, 7)
     L = got[t_long]
-    assert L["status"] == 0
+    assert L["status"] == 0 and L["path"] == path
     for t in small:
         r = got[t]
         assert r["status"] == 0 and not r["holds"] and r["time"] == 80
         assert r["admit_s"] < L["done_s"] and r["done_s"] < L["done_s"]
-        assert r["path"] == "loop"
+        assert r["path"] == path
     st = mc.mc_server_status(srv)
     assert st["launches"] >= 1 and st["fatal"] == 0
     mc.mc_server_destroy(srv)
@@ -160,10 +166,11 @@ def test_server_rejects_models_larger_than_its_pool(mc):
 
 
 def test_lone_requests_take_the_latency_path(mc, oracle):
-    # each request finds the server idle: it runs alone on the single-model
-    # explorer, with the answer of the single-model entry point; requests
-    # submitted together go through the device loop
-    srv = mc.mc_server_create(slots=8, pool_bytes=2 << 30)
+    # lockstep engine: each request finds the server idle, so it runs alone
+    # on the single-model explorer, with the answer of the single-model entry
+    # point; a request above the latency path's bound goes through the
+    # device loop
+    srv = mc.mc_server_create(slots=8, pool_bytes=2 << 30, options=mc.mc_options_default(engine="level"))
     specs, queries = mix()
     for idx in (0, 1, 4, 5):
         t = mc.mc_server_submit(srv, specs[idx], *queries[idx])
@@ -174,7 +181,8 @@ def test_lone_requests_take_the_latency_path(mc, oracle):
         for key in KEYS:
             if exp[key] is not None:
                 assert r[key] == exp[key], (idx, key)
-    big = mc.mc_server_create(slots=8, pool_bytes=2 << 30, solo_states=1 << 12)
+    big = mc.mc_server_create(slots=8, pool_bytes=2 << 30, solo_states=1 << 12,
+                              options=mc.mc_options_default(engine="level"))
     t = mc.mc_server_submit(big, specs[3], *queries[3])  # c2 literal: bound above 2^12
     assert collect(mc, big, 1)[t]["path"] == "loop"
     mc.mc_server_destroy(big)
