@@ -69,14 +69,14 @@ WORKLOADS = {
         "(splitmix64 seed 2305091303), speed 1, 128-bit packed states; 1,072,924,481 reachable states "
         "(closed form), widest level 193,344,684",
         "u128", expect=(1, 512, 2), cpu_T=30, ref_T=16,
-        tune={"probe_scheme": ["split", "one_call"], "load_factor_pct": [25, 40]},
+        tune={"probe_scheme": ["split", "one_call"], "stage_chunk": [64, 128]},
         traffic="explore_kernel_c3star_traffic.txt"),
     "c2_star": Workload(
         lambda: W.c2_star(),
         "c2_star: G=80, P=4, WG 2^0..2^8, TS 2^0..2^4, FREE dispatch, cost ceil(WG/TS)*4+WG+2*TS, "
         "speeds U{1..3} (splitmix64 seed 2305091302), 64-bit packed states; 10,385,335 reachable states",
         "u64", expect=(96, 8, 4), cpu_T=None, ref_T=300,
-        tune={"probe_scheme": ["split", "one_call"], "load_factor_pct": [10, 15]},
+        tune={"probe_scheme": ["split", "one_call"], "load_factor_pct": [10, 15], "stage_chunk": [64, 128]},
         traffic="explore_kernel_c2star_traffic.txt"),
     "c2": Workload(
         lambda: W.c2(rule=W.GREEDY),
@@ -793,7 +793,7 @@ def measure_c4(args, device, local: int, steps: int, warmup: int) -> dict:
     mc.mc_batch_destroy(probe)
     queries0 = [("min_time", None) if sp.meta["query"] else
                 ("check", round(t * sp.meta["t_frac_milli"] / 1000)) for sp, t in zip(specs, optima0)]
-    tuned = AT.tune_batch(specs, queries0, space={"blocks_per_sm": [0, 1, 2], "load_factor_pct": [25, 50]},
+    tuned = AT.tune_batch(specs, queries0, space=[AT.BATCH_LEVEL_SPACE, AT.BATCH_CONFIG_SPACE],
                           reps=1, cache={}, path=os.path.join(tempfile.gettempdir(), "mc_autotune_c4.json"))
     opts = mc.mc_options_default(timing=1, **tuned["options"])
     stream = torch.cuda.Stream(device)

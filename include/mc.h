@@ -154,10 +154,12 @@ typedef struct {
                                    MC_ERR_TIMEOUT.  Keep 0.                 */
   uint32_t timing;              /* 1: time every exploration kernel with CUDA
                                    events on the model's stream (mc_get_stats) */
-  uint32_t lanes_per_state;     /* PE-level model (mc_pe.h) only: lanes of the
-                                   warp tile that expands one state: 4 or 8
-                                   (up to 3 successors per lane), 16 (up to
-                                   2) or 32 (1); 0 = the smallest that fits */
+  uint32_t lanes_per_state;     /* lanes of the warp tile that expands one
+                                   state.  Cost-table model: a power of two
+                                   from P (rounded up) to 16, one unit per
+                                   lane; PE-level model (mc_pe.h): 4 or 8 (up
+                                   to 3 successors per lane), 16 (up to 2) or
+                                   32 (1).  0 = the smallest that fits      */
   uint32_t probe_scheme;        /* mc_probe_scheme of the single-model
                                    explorer (mc_check, mc_min_time,
                                    mc_count_states); batches and the PE-level
@@ -171,7 +173,10 @@ typedef struct {
                                    explores one configuration, 64..512, a
                                    multiple of 32; 0 = from the model's
                                    widest configuration level                */
-  uint32_t reserved[1];
+  uint32_t stage_chunk;         /* LEVEL engine: winners a warp stages in
+                                   shared memory before it reserves frontier-
+                                   log space and copies them out: 64, 96 or
+                                   128; 0 = 128                              */
 } mc_options;
 
 /* Result of mc_check (Section 4, Step 2: Phi = G(FIN -> time > T)). */
@@ -277,8 +282,8 @@ void mc_model_destroy(mc_model* m);
 
 /* Replace the options of later queries.  Options that size buffers or the
  * launch (load_factor_pct, table_log2, log_capacity, threads_per_block,
- * blocks_per_sm, probe_scheme, no_log_tags) only act before the buffers
- * exist.  Errors: INVAL. */
+ * blocks_per_sm, probe_scheme, no_log_tags, engine, unit_threads,
+ * lanes_per_state) only act before the buffers exist.  Errors: INVAL. */
 int mc_set_options(mc_model* m, const mc_options* opt);
 
 /* CUDA stream (a cudaStream_t, NULL = legacy default stream) for every later

@@ -1,12 +1,21 @@
 """Autotuner for the explorer's launch and table parameters, with a JSON cache.
 
-The knobs are the runtime options of ``mc_options``: threads per block,
-blocks per SM (the persistent grid), the visited-set load factor and the
-probe scheme of the insert (split: pick a slot from the fetched bucket and
-issue every CAS of the round before resolving any; one call: the general
-insert per proposal); for batches the grid and the load factor; for the
-processing-element level model, the lanes that expand one state (a quarter,
-half or whole warp) and the grid.  A
+The knobs are the runtime options of ``mc_options``, searched per engine:
+
+* the level-synchronous engine: threads per block, blocks per SM (the
+  persistent grid), the visited-set load factor, the probe scheme of the
+  insert (split: pick a slot from the fetched bucket and issue every CAS of
+  the round before resolving any; one call: the general insert per
+  proposal), the frontier chunk a warp stages before it copies its winners
+  out, and the lanes per state;
+* the configuration engine (one block per configuration): threads per block
+  and lanes per state;
+* batches: the engine, and per engine the grid and load factor, or the
+  threads per block and lanes per state;
+* the processing-element level model: the lanes that expand one state (a
+  quarter, half or whole warp) and the grid.
+
+A
 candidate is timed on the real query through the C-ABI (CUDA events recorded
 by the library around its kernels), every candidate must return the same
 answer as the default options (a tuning run never trades correctness), and
@@ -31,7 +40,22 @@ DEFAULT_SPACE = {
     "load_factor_pct": [25, 50],
     "probe_scheme": [1, 2],  # mc_probe_scheme: split, one call
 }
-KNOBS = tuple(DEFAULT_SPACE)
+KNOBS = tuple(DEFAULT_SPACE) + ("engine", "stage_chunk", "unit_threads", "lanes_per_state")
+# per engine (mc_engine: 1 level-synchronous, 2 one block per configuration)
+LEVEL_SPACE = {
+    "engine": [1],
+    "blocks_per_sm": [0, 2],
+    "load_factor_pct": [25, 50],
+    "probe_scheme": [1, 2],
+    "stage_chunk": [64, 128],
+}
+CONFIG_SPACE = {
+    "engine": [2],
+    "unit_threads": [0, 128, 256, 512],
+    "lanes_per_state": [0, 16],
+}
+BATCH_LEVEL_SPACE = {"engine": [1], "blocks_per_sm": [0, 1, 2], "load_factor_pct": [25, 50]}
+BATCH_CONFIG_SPACE = {"engine": [2], "unit_threads": [0, 256, 512], "lanes_per_state": [0, 8]}
 
 
 def cache_path() -> str:
@@ -62,8 +86,19 @@ def signature(layout: dict, spec, query: str, batch: int = 1) -> str:
             f"|b{len(spec.ts_values)}|L{layout['max_level']}|S2^{int(math.log2(bound))}|n{batch}")
 
 
-def candidates(space: Optional[Dict[str, Sequence[int]]] = None) -> List[dict]:
+def candidates(space=None) -> List[dict]:
+    """Every combination of a space's values; a list of spaces gives the
+    union of their candidates (one space per engine)."""
     space = space or DEFAULT_SPACE
+    if isinstance(space, (list, tuple)):
+        out, seen = [], set()
+        for sp in space:
+            for c in candidates(sp):
+                key = json.dumps(c, sort_keys=True)
+                if key not in seen:
+                    seen.add(key)
+                    out.append(c)
+        return out
     names = [k for k in KNOBS if k in space] + sorted(k for k in space if k not in KNOBS)
     return [dict(zip(names, vals)) for vals in itertools.product(*(space[k] for k in names))]
 
@@ -82,7 +117,11 @@ def tune(measure: Callable[[dict], tuple], space=None, reps: int = 3) -> dict:
         key = json.dumps(c, sort_keys=True)
         best = math.inf
         for _ in range(reps):
-            ms, ans = measure(c)
+            try:
+                ms, ans = measure(c)
+            except RuntimeError:  # options the library refuses for this model
+                best = math.inf
+                break
             if reference is None:
                 reference = ans
             if ans != reference:
@@ -109,6 +148,8 @@ def tune_query(spec, query: str = "min_time", T: Optional[int] = None, space=Non
     lay = mc.mc_model_layout(mc.mc_model_create(spec, allocator=None))
     sig = signature(lay, spec, query)
     cache = load_cache(path) if cache is None else cache
+    if space is None:  # both engines where the configuration engine takes the model
+        space = [LEVEL_SPACE] + ([CONFIG_SPACE] if lay["engine"] == mc.ENGINE["config"] else [])
 
     def measure(c):
         m = mc.mc_model_create(spec, mc.mc_options_default(timing=1, **c))
@@ -136,8 +177,12 @@ def tune_batch(specs, queries, space=None, reps: int = 2, cache: Optional[dict] 
     from . import mc
 
     mc.load()
-    # the lockstep kernel has one block size and one probe scheme
-    space = {k: v for k, v in (space or DEFAULT_SPACE).items() if k not in ("threads_per_block", "probe_scheme")}
+    # the lockstep kernel has one block size and one probe scheme; the
+    # configuration engine is tried where it takes every instance
+    if space is None:
+        space = [BATCH_LEVEL_SPACE, BATCH_CONFIG_SPACE]
+    elif isinstance(space, dict):
+        space = {k: v for k, v in space.items() if k not in ("threads_per_block", "probe_scheme")}
     lay = mc.mc_model_layout(mc.mc_model_create(specs[0].with_key_bits(128), allocator=None))
     sig = signature(lay, specs[0], "batch", len(specs))
     cache = load_cache(path) if cache is None else cache

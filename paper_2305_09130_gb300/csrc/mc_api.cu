@@ -188,7 +188,7 @@ struct mc_model {
   std::vector<uint32_t> order;     // [a*b] configurations, deepest first
   uint32_t engine = MC_ENGINE_LEVEL;
   uint32_t cfg_wcap = 0, cfg_tsize = 0;
-  int cfg_threads = 0, cfg_grid = 0;
+  int cfg_threads = 0, cfg_grid = 0, cfg_grid_max = 0;
   size_t cfg_smem = 0;
   // device state
   bool reserved = false;
@@ -215,6 +215,11 @@ struct mc_model {
   uint32_t* d_order = nullptr;       // chained pass must not clear the last pass's widths)
   uint64_t* d_cfg_levels = nullptr;
   int last_slot = 0;                 // slot of the last pass that ran
+  // min-time's certificate and counterexample checks in one launch: their
+  // pass descriptors (slots 1 and 2, T_min read on the device) and the units
+  // [(check, configuration) deepest first; with and without the certificate]
+  mc::CfgPass* d_pair_pass = nullptr;
+  uint64_t* d_pair_units = nullptr;
   uint8_t* h_block = nullptr;   // pinned host staging (from the pool), carved into:
   size_t h_block_bytes = 0;
   Ctrl* h_ctrl = nullptr;       // [kSlots]  } the device's headers, scalars and trace,
@@ -325,9 +330,24 @@ bool valid_options(const mc_options* o) {
   if (o->probe_scheme > MC_PROBE_ONE_CALL) return false;
   if (o->no_log_tags > 1) return false;
   if (o->engine > MC_ENGINE_CONFIG) return false;
+  if (o->stage_chunk && (o->stage_chunk < 64 || o->stage_chunk > mc::kWarpCap || o->stage_chunk % 32)) return false;
   if (o->unit_threads && (o->unit_threads < 64 || o->unit_threads > mc::kCfgMaxThreads || o->unit_threads % 32))
     return false;
   return true;
+}
+
+// Lanes per state: the options' lanes_per_state (a power of two from P
+// rounded up to 16), else P rounded up to a power of two.
+int resolve_tile(mc_model* m) {
+  uint32_t t = 1;
+  while (t < m->P) t <<= 1;
+  const uint32_t want = m->opt.lanes_per_state;
+  if (want) {
+    if (want < t || want > 16 || (want & (want - 1))) return MC_ERR_INVAL;
+    t = want;
+  }
+  m->tile = t;
+  return MC_OK;
 }
 
 // the configuration engine takes a model whose per-configuration levels fit
@@ -359,6 +379,7 @@ bool resolve_split(uint32_t scheme, uint32_t key_words) {
 
 // sizes of the frontier log and the visited set
 int size_buffers(mc_model* m) {
+  if (resolve_tile(m)) return MC_ERR_INVAL;
   m->engine = resolve_engine(m);
   if (m->engine == MC_ENGINE_CONFIG) {
     if (!cfg_eligible(m)) return MC_ERR_INVAL;
@@ -383,7 +404,7 @@ int size_buffers(mc_model* m) {
     const uint64_t ctrl_bytes = (mc::kBarBytes + sizeof(Ctrl)) * kSlots + kScalarBytes + 8ull * (m->max_level + 2) * 5;
     uint64_t total = mul_sat(m->log_cap, key_bytes + 4);
     total = add_sat(total, ctrl_bytes + 4ull * (2 * ab + m->P));
-    total = add_sat(total, 8 * (ab + 1) + sizeof(mc::CfgRec) * ab + 4 * ab);
+    total = add_sat(total, 8 * (ab + 1) + 2 * sizeof(mc::CfgRec) * ab + 4 * ab + 24 * ab + 8 * sizeof(mc::CfgPass));
     total = add_sat(total, 16ull * (m->max_level + 2) * kSlots);  // level widths per result slot
     m->device_bytes = total;
     return MC_OK;
@@ -416,6 +437,9 @@ int size_buffers(mc_model* m) {
   m->device_bytes = total;
   return MC_OK;
 }
+
+Ctrl* ctrl_at(mc_model* m, int slot) { return m->d_ctrl + slot; }
+uint64_t* cfg_levels_at(mc_model* m, int slot) { return m->d_cfg_levels + 2ull * (m->max_level + 2) * slot; }
 
 // The model's constants every kernel takes (device table pointers unset).
 void fill_params(const mc_model* m, Params& p) {
@@ -477,6 +501,7 @@ int reserve(mc_model* m) {
       return MC_ERR_CUDA;
     }
     if (m->opt.blocks_per_sm) bps = std::min<int>(bps, (int)m->opt.blocks_per_sm);
+    m->cfg_grid_max = sms * bps;
     m->cfg_grid = (int)std::min<uint64_t>(ab, (uint64_t)sms * bps);
   }
 
@@ -492,12 +517,15 @@ int reserve(mc_model* m) {
   m->d_ctrl_block = (uint8_t*)dev_alloc(m, ctrl_bytes);
   if (cfg) {
     m->d_seg = (uint64_t*)dev_alloc(m, 8 * (ab + 1));
-    m->d_rec = (mc::CfgRec*)dev_alloc(m, sizeof(mc::CfgRec) * ab);
+    m->d_rec = (mc::CfgRec*)dev_alloc(m, 2 * sizeof(mc::CfgRec) * ab);  // two passes at once
     m->d_order = (uint32_t*)dev_alloc(m, 4 * ab);
     m->d_cfg_levels = (uint64_t*)dev_alloc(m, 16 * L2 * kSlots);
+    m->d_pair_pass = (mc::CfgPass*)dev_alloc(m, 8 * sizeof(mc::CfgPass));
+    m->d_pair_units = (uint64_t*)dev_alloc(m, 8 * 3 * ab);
   }
   if (!m->d_params || (!cfg && !m->d_table) || !m->d_log_keys || !m->d_log_par || !m->d_ctrl_block ||
-      (cfg && (!m->d_seg || !m->d_rec || !m->d_order || !m->d_cfg_levels))) {
+      (cfg && (!m->d_seg || !m->d_rec || !m->d_order || !m->d_cfg_levels || !m->d_pair_pass ||
+               !m->d_pair_units))) {
     release(m);
     return MC_ERR_NOMEM;
   }
@@ -525,7 +553,9 @@ int reserve(mc_model* m) {
   const size_t o_params = align_up(mirror_bytes, 64);
   const size_t o_seg = align_up(o_params + np * 4, 8);
   const size_t o_order = o_seg + (cfg ? 8 * (ab + 1) : 0);
-  m->h_block_bytes = o_order + (cfg ? 4 * ab : 0);
+  const size_t o_pair = align_up(o_order + (cfg ? 4 * ab : 0), 64);
+  const size_t o_pair_units = o_pair + (cfg ? 8 * sizeof(mc::CfgPass) : 0);
+  m->h_block_bytes = o_pair_units + (cfg ? 8 * 3 * ab : 0);
   m->h_block = (uint8_t*)mc::pinned_alloc(m->h_block_bytes);
   if (!m->h_block) {
     release(m);
@@ -561,11 +591,43 @@ int reserve(mc_model* m) {
   p.N = m->d_params;
   p.cost = m->d_params + (size_t)m->a * m->b;
   p.speed = m->d_params + 2ull * m->a * m->b;
+  if (cfg) {
+    // the certificate check (T_min - 1) and the counterexample check (T_min)
+    // of a single-pass min-time query, launched together
+    mc::CfgPass* hp = (mc::CfgPass*)(m->h_block + o_pair);
+    for (int k = 0; k < 8; ++k) {  // (prune, early exit) x (certificate, counterexample)
+      mc::CfgPass& Q = hp[k];
+      std::memset(&Q, 0, sizeof(Q));
+      Q.prune = (k >> 2) & 1;
+      Q.early_exit = (k >> 1) & 1;
+      Q.p = p;
+      const int c = k & 1;  // 0: certificate at T_min - 1, 1: counterexample at T_min
+      Q.T_src = m->d_tmin;
+      Q.T_delta = c == 0 ? -1 : 0;
+      Q.group = m->tile;
+      Q.log_keys = m->d_log_keys;
+      Q.log_par = m->d_log_par;
+      Q.seg = m->d_seg;
+      Q.levels = cfg_levels_at(m, 1 + c);
+      Q.rec = m->d_rec + ab * c;  // the min pass's records are not read after its pass
+      Q.ctrl = ctrl_at(m, 1 + c);
+      Q.trace = m->d_trace;
+      Q.want_witness = c == 1;
+    }
+    uint64_t* hu = (uint64_t*)(m->h_block + o_pair_units);
+    for (uint64_t x = 0; x < ab; ++x) {
+      hu[2 * x] = m->order[x];                        // certificate
+      hu[2 * x + 1] = (1ull << 32) | m->order[x];     // counterexample
+      hu[2 * ab + x] = (1ull << 32) | m->order[x];    // counterexample alone
+    }
+    MC_CUDA(m, cudaMemcpyAsync(m->d_pair_pass, hp, 8 * sizeof(mc::CfgPass), cudaMemcpyHostToDevice, m->stream));
+    MC_CUDA(m, cudaMemcpyAsync(m->d_pair_units, hu, 8 * 3 * ab, cudaMemcpyHostToDevice, m->stream));
+    m->stats.h2d_bytes += 8 * sizeof(mc::CfgPass) + 24 * ab;
+  }
   m->reserved = true;
   return MC_OK;
 }
 
-Ctrl* ctrl_at(mc_model* m, int slot) { return m->d_ctrl + slot; }
 
 uint32_t* bar_lines_at(mc_model* m, int slot) {
   return reinterpret_cast<uint32_t*>(m->d_ctrl_block + mc::kBarBytes * slot);
@@ -591,7 +653,6 @@ int fetch_ctrl(mc_model* m) {
 // the caller has cleared (clear_ctrl); fetch_ctrl reads the header back.
 // With `prev`, the pass takes its threshold from that slot's counterexample
 // (see ExploreArgs::prev).
-uint64_t* cfg_levels_at(mc_model* m, int slot) { return m->d_cfg_levels + 2ull * (m->max_level + 2) * slot; }
 
 // The configuration engine's pass: the level widths start at zero, the
 // header's unit counters and stop word are cleared with it (clear_ctrl).
@@ -636,6 +697,34 @@ int enqueue_cfg_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t del
   return MC_OK;
 }
 
+// Configuration engine, min-time: the certificate check at T_min - 1 (slot
+// 1, unless refine is off) and the counterexample check at T_min (slot 2)
+// in one launch; T_min is read on the device from the min pass.
+int enqueue_cfg_pair(mc_model* m, bool prune, bool early_exit, bool refine) {
+  const uint64_t ab = (uint64_t)m->a * m->b;
+  MC_CUDA(m, cudaMemsetAsync(cfg_levels_at(m, 1), 0, 2 * 16ull * (m->max_level + 2), m->stream));
+  mc::CfgLaunch L{};
+  L.passes = m->d_pair_pass + 2 * ((prune ? 2 : 0) + (early_exit ? 1 : 0));  // descriptors per option pair
+  L.units = refine ? m->d_pair_units : m->d_pair_units + 2 * ab;
+  L.n_units = refine ? 2 * ab : ab;
+  L.next = &ctrl_at(m, 2)->units_next;  // the launch's unit counter (the header starts at zero)
+  L.wcap = m->cfg_wcap;
+  L.tsize = m->cfg_tsize;
+  if (m->opt.timing) {
+    const int rc_ = make_events(m);
+    if (rc_) return rc_;
+    MC_CUDA(m, cudaEventRecord(m->ev[2], m->stream));
+  }
+  const int grid = (int)std::min<uint64_t>((uint64_t)m->cfg_grid_max, L.n_units);
+  MC_CUDA(m, mc::launch_cfg((int)m->key_words, grid, m->cfg_threads, m->cfg_smem, L, m->stream));
+  if (m->opt.timing) {
+    MC_CUDA(m, cudaEventRecord(m->ev[3], m->stream));
+    m->ev_pending[1] = true;
+  }
+  m->stats.explore_launches += 1;
+  return MC_OK;
+}
+
 int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, bool prune,
                  bool early_exit, bool witness, uint64_t* tmin_out, int slot, int prev = -1) {
   if (m->engine == MC_ENGINE_CONFIG)
@@ -664,6 +753,7 @@ int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, 
   A.T_delta = delta;
   A.tmin_out = tmin_out;
   A.barrier_extra = m->opt.debug_barrier_extra;
+  A.stage_chunk = m->opt.stage_chunk ? m->opt.stage_chunk : mc::kWarpCap;
   A.bar_lines = bar_lines_at(m, slot);
   A.timeout_ns = m->opt.barrier_timeout_ns ? m->opt.barrier_timeout_ns : 60ull * 1000000000ull;
   if (m->tag_bits) {  // a new tag per pass; the log is cleared when the tags wrap
@@ -855,8 +945,10 @@ int mc_model_create(const mc_model_desc* d, const mc_options* opt, mc_model** ou
   }
   m->key_words = m->key_bits / 64;
   m->max_level = n_max + 2;
-  m->tile = 1;
-  while (m->tile < m->P) m->tile <<= 1;
+  if (resolve_tile(m)) {
+    delete m;
+    return MC_ERR_INVAL;
+  }
 
   // closed-form bounds on the widths of the levels (sizing only):
   //   FREE:   C(k+P-1, P-1) states of sum(n) = k per configuration;
@@ -933,6 +1025,7 @@ int mc_set_options(mc_model* m, const mc_options* o) {
     m->opt.no_log_tags = keep.no_log_tags;    // the log was cleared (or not) for it
     m->opt.engine = keep.engine;              // the buffers were made for one engine
     m->opt.unit_threads = keep.unit_threads;
+    m->opt.lanes_per_state = keep.lanes_per_state;  // the grid was sized for its tile
   }
   return MC_OK;
 }
@@ -1044,13 +1137,22 @@ int mc_min_time(mc_model* m, mc_min_result* out, mc_trace** trace) {
     MC_TRY(enqueue_pass(m, UINT64_MAX, prune ? m->d_tini : nullptr, 0, prune, false, false,
                         m->d_tmin, 0));
     int slot = 1;
-    if (m->opt.refine) MC_TRY(enqueue_pass(m, 0, m->d_tmin, -1, prune, ee, false, nullptr, slot++));
-    MC_TRY(enqueue_pass(m, 0, m->d_tmin, 0, prune, ee, true, nullptr, slot));
+    if (m->engine == MC_ENGINE_CONFIG) {
+      // both checks in one launch: the certificate in slot 1 (with refine),
+      // the counterexample in slot 2
+      MC_TRY(enqueue_cfg_pair(m, prune, ee, m->opt.refine != 0));
+      slot = 2;
+    } else {
+      if (m->opt.refine) MC_TRY(enqueue_pass(m, 0, m->d_tmin, -1, prune, ee, false, nullptr, slot++));
+      MC_TRY(enqueue_pass(m, 0, m->d_tmin, 0, prune, ee, true, nullptr, slot));
+    }
     const int final_slot = slot;
     MC_TRY(fetch_ctrl(m));
     MC_TRY(sync(m));
     out->t_ini = m->h_scalar[0];
+    const int cert_slot = m->opt.refine ? 1 : -1;
     for (int s = 0; s <= final_slot; ++s) {
+      if (s != 0 && s != cert_slot && s != final_slot) continue;  // no certificate check
       MC_TRY(pass_error(m, s));
       out->states += m->h_ctrl[s].states;
       out->checks += 1;
@@ -1059,7 +1161,7 @@ int mc_min_time(mc_model* m, mc_min_result* out, mc_trace** trace) {
       m->last_err = "no terminal below T_ini";
       return MC_ERR_CUDA;
     }
-    if ((m->opt.refine && m->h_ctrl[1].stop_level != 0) || m->h_ctrl[final_slot].stop_level == 0) {
+    if ((m->opt.refine && m->h_ctrl[cert_slot].stop_level != 0) || m->h_ctrl[final_slot].stop_level == 0) {
       m->last_err = "certificate checks disagree with the minimum";
       return MC_ERR_CUDA;
     }

@@ -108,7 +108,7 @@ struct ExploreArgs {
   int64_t T_delta;
   uint64_t* tmin_out;     // if set: receives pack_time(best_pack) at the end
   uint32_t barrier_extra; // extra arrivals a barrier waits for (test hook)
-  uint32_t pad;
+  uint32_t stage_chunk;   // winners a warp stages before a flush (64..kWarpCap)
   uint32_t* bar_lines;    // the device-wide barrier's lines (zeroed per pass)
   uint64_t timeout_ns;
   const Ctrl* prev;       // lowering chained on the device: run at (prev's counterexample

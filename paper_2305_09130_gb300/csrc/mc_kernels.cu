@@ -283,8 +283,9 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
         }
       }
     }
-    // each round adds at most 32 * D winners to the warp's buffer
-    if (fill > kWarpCap - 32 * D) {
+    // each round adds at most 32 * D winners to the warp's buffer, which
+    // is flushed once it holds more than stage_chunk - 32 * D of them
+    if (fill > A.stage_chunk - 32 * D) {
       __syncwarp();
       unsigned long long b = 0;
       if (lane == 0)

@@ -252,6 +252,7 @@ extern "C" int mc_check_noalloc(const mc_model_desc* d, uint64_t T, uint32_t pru
   A.trace = d_trace;
   A.T = T;
   A.bar_lines = d_bar;
+  A.stage_chunk = mc::kWarpCap;
   A.timeout_ns = 60ull * 1000000000ull;
 
   mc::Ctrl h;

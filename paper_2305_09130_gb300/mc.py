@@ -49,7 +49,7 @@ class McOptions(C.Structure):
                 ("barrier_timeout_ns", C.c_uint64), ("debug_barrier_extra", C.c_uint32),
                 ("timing", C.c_uint32), ("lanes_per_state", C.c_uint32),
                 ("probe_scheme", C.c_uint32), ("no_log_tags", C.c_uint32), ("engine", C.c_uint32),
-                ("unit_threads", C.c_uint32), ("reserved", C.c_uint32 * 1)]
+                ("unit_threads", C.c_uint32), ("stage_chunk", C.c_uint32)]
 
 
 class McCheckResult(C.Structure):

@@ -171,9 +171,24 @@ def test_engine_follows_the_width_of_one_configuration(lib):
     with pytest.raises(mc.MCError) as e:
         mc.mc_reserve(m)
     assert e.value.code == mc.MC_ERR_INVAL
-    for bad in ({"engine": 3}, {"unit_threads": 48}, {"unit_threads": 1024}):
+    for bad in ({"engine": 3}, {"unit_threads": 48}, {"unit_threads": 1024}, {"stage_chunk": 32},
+                {"stage_chunk": 160}, {"stage_chunk": 100}):
         with pytest.raises(mc.MCError):
             mc.mc_model_create(W.c1(), mc.mc_options_default(**bad), allocator=None)
+
+
+def test_lanes_per_state_of_the_cost_table_model(lib):
+    """A power of two from P (rounded up) to 16; the configuration engine's
+    threads follow the tile (one round of the widest level)."""
+    c3 = W.c3(rule=W.GREEDY)  # P = 8
+    for lanes in (0, 8, 16):
+        assert layout(c3, lanes_per_state=lanes)["engine"] == mc.ENGINE["config"]
+    assert layout(c3, lanes_per_state=16)["unit_threads"] == 512
+    assert layout(W.c1(), lanes_per_state=4)["unit_threads"] == 512  # 65 states x 4 lanes in one round
+    for bad in (4, 12, 32):  # below P, not a power of two, above 16
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_model_create(c3, mc.mc_options_default(lanes_per_state=bad), allocator=None)
+        assert e.value.code == mc.MC_ERR_INVAL
 
 
 def test_unknown_option_names_are_rejected(lib):

@@ -63,3 +63,50 @@ def test_tuned_options_reproduce_results(mc, tmp_path):
 def test_candidates_cover_knobs_outside_the_default_space():
     c = AT.candidates({"lanes_per_state": [8, 16], "blocks_per_sm": [0, 1]})
     assert sorted((x["lanes_per_state"], x["blocks_per_sm"]) for x in c) == [(8, 0), (8, 1), (16, 0), (16, 1)]
+
+
+def test_candidates_of_several_spaces_are_their_union():
+    c = AT.candidates([{"engine": [1], "blocks_per_sm": [0, 2]}, {"engine": [2], "unit_threads": [0, 256]},
+                       {"engine": [1], "blocks_per_sm": [2]}])
+    assert c == [{"engine": 1, "blocks_per_sm": 0}, {"engine": 1, "blocks_per_sm": 2},
+                 {"engine": 2, "unit_threads": 0}, {"engine": 2, "unit_threads": 256}]
+    # the named knobs of both engines
+    level = AT.candidates(AT.LEVEL_SPACE)
+    assert {"probe_scheme", "stage_chunk", "load_factor_pct", "blocks_per_sm"} <= set(level[0])
+    config = AT.candidates(AT.CONFIG_SPACE)
+    assert {"unit_threads", "lanes_per_state"} <= set(config[0])
+
+
+def test_candidates_the_library_refuses_are_skipped():
+    space = {"lanes_per_state": [0, 2, 4]}
+
+    def measure(c):
+        if c["lanes_per_state"] == 2:
+            raise RuntimeError("lanes below P")
+        return 1.0 + c["lanes_per_state"], "answer"
+
+    out = AT.tune(measure, space, reps=1)
+    assert out["options"] == {"lanes_per_state": 0} and len(out["timings"]) == 2
+
+
+@pytest.mark.gpu
+def test_tuning_covers_both_engines_and_their_knobs(mc, tmp_path):
+    """The single-model tuner searches both engines (C1 fits the configuration
+    engine) and the batch tuner both batch engines; every candidate it keeps
+    gave the default's answer."""
+    path = str(tmp_path / "tune.json")
+    spec = W.c1(W.GREEDY)
+    space = [dict(AT.LEVEL_SPACE, load_factor_pct=[25], blocks_per_sm=[0]),
+             dict(AT.CONFIG_SPACE, unit_threads=[0, 256])]
+    out = AT.tune_query(spec, "min_time", space=space, reps=1, path=path)
+    keys = [json.loads(k) for k in out["timings"]]
+    assert {k["engine"] for k in keys} == {1, 2}
+    assert {k.get("stage_chunk") for k in keys if k["engine"] == 1} == {64, 128}
+    assert {k.get("lanes_per_state") for k in keys if k["engine"] == 2} == {0, 16}
+    assert len(keys) == 4 + 4  # probe scheme x chunk, threads x lanes
+    m = mc.mc_model_create(spec, AT.options_for(spec, "min_time", path=path))
+    assert mc.mc_min_time(m, trace=False)["t_min"] == 80
+    specs = W.c4_instances(12)
+    queries = [("min_time", None)] * 12
+    b = AT.tune_batch(specs, queries, reps=1, cache={}, path=str(tmp_path / "b.json"))
+    assert {json.loads(k)["engine"] for k in b["timings"]} == {1, 2}

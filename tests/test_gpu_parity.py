@@ -434,3 +434,20 @@ def test_models_with_different_shared_memory_interleave(mc, oracle):
     assert mc.mc_count_states(a) == oracle.count(big) == CF.count(big)
     assert mc.mc_count_states(b) == 8763
     assert gpu_min(mc, a, "single", True) == oracle.min_time(big)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_lanes_per_state_and_stage_chunk_match_oracle(mc, oracle, engine):
+    """The tuner's knobs change the speed, never the answer: every tile width
+    from P (rounded up) to 16 lanes per state on both engines, and the
+    staging chunk of the level-synchronous kernel."""
+    for spec in sweep_models()[::4]:
+        t = 1 << (spec.P - 1).bit_length()
+        for lanes in sorted({t, min(16, 2 * t), 16}):
+            if lanes < spec.P:
+                continue
+            for chunk in ((64, 96, 128) if engine == "level" else (0,)):
+                model = make(mc, spec, engine=engine, lanes_per_state=lanes, stage_chunk=chunk)
+                assert mc.mc_count_states(model) == oracle.count(spec), (spec.name, lanes, chunk)
+                assert mc.mc_last_widths(model) == CF.widths(spec)
+                assert gpu_min(mc, model, "single", True) == oracle.min_time(spec), (spec.name, lanes, chunk)
