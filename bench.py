@@ -806,6 +806,7 @@ def measure_c4(args, device, local: int, steps: int, warmup: int) -> dict:
     for _ in range(warmup):
         ref = mc.mc_batch_run(batch, queries)
     torch.cuda.synchronize()
+    st0 = mc.mc_batch_get_stats(batch)
     sampler = ClockSampler(local)
     sampler.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -857,8 +858,10 @@ def measure_c4(args, device, local: int, steps: int, warmup: int) -> dict:
         "query": "one mc_batch_run per step",
         "autotuned_options": tuned["options"], "autotune_ms": tuned["timings"],
         "steps": steps, "ms_per_batch": dev_ms / steps, "states_per_s": value,
-        "states_per_batch": states / steps, "launches_per_batch": bst["explore_launches"] / max(
-            bst["graph_launches"] + 1, 1),
+        "states_per_batch": states / steps,
+        "kernels_per_batch": ((bst["explore_launches"] + bst["other_launches"])
+                              - (st0["explore_launches"] + st0["other_launches"])) / steps,
+        "graph_replays_per_batch": (bst["graph_launches"] - st0["graph_launches"]) / steps,
         "query_latency_ms_p50": percentile(batch_ms, 50), "query_latency_ms_p99": percentile(batch_ms, 99),
         "sequential": {"options": "library defaults (single-model explorer, load factor 25%)",
                        "ms_total": seq_total, "states_per_s": seq_states / (seq_total / 1000.0),
