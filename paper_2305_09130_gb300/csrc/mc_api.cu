@@ -460,6 +460,10 @@ void fill_params(const mc_model* m, Params& p) {
   p.swar_mask = nf >= 64 ? ~0ull : ((1ull << nf) - 1);
   p.swar_mul = 0;
   for (uint32_t t = 0; t < m->P && t * m->n_bits < 64; ++t) p.swar_mul |= 1ull << (t * m->n_bits);
+  uint64_t s_max = 0, clk_max = 0;
+  for (uint32_t c = 0; c < m->P; ++c) s_max = std::max<uint64_t>(s_max, m->speed[c]);
+  for (size_t k = 0; k < m->N.size(); ++k) clk_max = std::max<uint64_t>(clk_max, (uint64_t)m->N[k] * m->cost[k] * s_max);
+  p.clk32 = clk_max < (1ull << 32);
 }
 
 int reserve(mc_model* m) {

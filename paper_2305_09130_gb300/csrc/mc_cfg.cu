@@ -117,13 +117,13 @@ constexpr uint32_t kNoLevel = 0xFFFFFFFFu;
 // Maximum (and, for GREEDY, minimum) of a value over the aligned group of
 // g lanes that holds one state: butterfly steps below g, unrolled, the two
 // reductions interleaved (g is uniform across the block).
-template <bool MIN>
-__device__ __forceinline__ void group_minmax(uint64_t& mx, uint64_t& mn, uint32_t g) {
+template <bool MIN, class C>
+__device__ __forceinline__ void group_minmax(C& mx, C& mn, uint32_t g) {
 #pragma unroll
   for (uint32_t o = 1; o < 32; o <<= 1) {
     if (o < g) {
-      const uint64_t a = __shfl_xor_sync(0xffffffffu, mx, o);
-      uint64_t b = 0;
+      const C a = __shfl_xor_sync(0xffffffffu, mx, o);
+      C b = 0;
       if (MIN) b = __shfl_xor_sync(0xffffffffu, mn, o);
       mx = a > mx ? a : mx;
       if (MIN) mn = b < mn ? b : mn;
@@ -131,8 +131,10 @@ __device__ __forceinline__ void group_minmax(uint64_t& mx, uint64_t& mn, uint32_
   }
 }
 
-// Explore configuration `cfg` of pass Q at threshold T.
-template <class K>
+// Explore configuration `cfg` of pass Q at threshold T.  Clocks are kept in
+// C: 32 bits when every clock of the model fits (one shuffle per reduction
+// step instead of two), else 64.
+template <class K, class C>
 __device__ void explore_unit(const CfgPass& Q, uint32_t cfg, uint64_t T, K* front0, K* front1, K* tab0,
                              K* tab1, uint32_t wcap, uint32_t tsize, CfgShared& S) {
   // the pass's fields in registers (Q lives in shared memory, which the
@@ -156,7 +158,9 @@ __device__ void explore_unit(const CfgPass& Q, uint32_t cfg, uint64_t T, K* fron
   const uint32_t i = cfg / b, j = cfg % b;
   const uint32_t N = __ldg(Np + cfg);
   const bool unit_ok = c < P;
-  const uint64_t t_c = unit_ok ? (uint64_t)__ldg(costp + cfg) * __ldg(speedp + c) : 0;
+  const C t_c = unit_ok ? (C)((uint64_t)__ldg(costp + cfg) * __ldg(speedp + c)) : (C)0;
+  const C Tc = T < (uint64_t)(C)~(C)0 ? (C)T : (C)~(C)0;  // T, saturated at the clock type's maximum
+  constexpr C kNoneC = (C)~(C)0;
   const uint32_t c_shift = (P - 1 - (unit_ok ? c : 0)) * n_bits;
   const K one_c = (K)1 << c_shift;
   const bool log_on = Q.want_witness != 0;
@@ -181,11 +185,13 @@ __device__ void explore_unit(const CfgPass& Q, uint32_t cfg, uint64_t T, K* fron
     K* tnx = (L & 1u) ? tab0 : tab1;  // receives level L+1
     K* tcl = (L & 1u) ? tab1 : tab0;  // held level L: cleared for level L+2
     uint32_t* cnx = &S.cnt[(L + 1) % 3];
+    // the least level known to violate, for the cut at the next level: the
+    // load is issued here and its value stored after the level's rounds, so
+    // its latency overlaps them
+    uint32_t sc = 0;
     if (tid == 0) {
       S.cnt[(L + 2) % 3] = 0;
-      // the least level known to violate, for the cut at the next level
-      uint32_t sc = early ? ld_relaxed_u32(&ctrl->stop_c) : 0u;
-      S.cut[(L + 1) & 1u] = sc ? ~sc : kNoLevel;
+      if (early) sc = ld_relaxed_u32(&ctrl->stop_c);
     }
     if (L > 2)
       for (uint32_t x = tid; x < tsize; x += nthr) tcl[x] = (K)0;
@@ -195,9 +201,9 @@ __device__ void explore_unit(const CfgPass& Q, uint32_t cfg, uint64_t T, K* fron
       const uint32_t s = base + my;
       const bool valid = s < W;
       const K key = valid ? cur[s] : (K)0;
-      uint64_t clk = 0;
-      if (valid && unit_ok) clk = (uint64_t)field(key, c_shift, n_mask) * t_c;
-      uint64_t mx = clk, mn = (valid && unit_ok) ? clk : kNone;
+      C clk = 0;
+      if (valid && unit_ok) clk = (C)field(key, c_shift, n_mask) * t_c;
+      C mx = clk, mn = (valid && unit_ok) ? clk : kNoneC;
       bool ok = valid && unit_ok;
       if (greedy) {
         group_minmax<true>(mx, mn, g);
@@ -205,9 +211,9 @@ __device__ void explore_unit(const CfgPass& Q, uint32_t cfg, uint64_t T, K* fron
       } else {
         group_minmax<false>(mx, mn, g);
       }
-      const uint64_t nclk = clk + t_c;
-      const uint64_t st = nclk > mx ? nclk : mx;  // model time of the successor
-      if (prune && st > T) ok = false;
+      const C nclk = clk + t_c;
+      const C st = nclk > mx ? nclk : mx;  // model time of the successor
+      if (prune && st > Tc) ok = false;
       const K succ = key + one_c;
       int won = 0;
       if (ok) {
@@ -235,10 +241,11 @@ __device__ void explore_unit(const CfgPass& Q, uint32_t cfg, uint64_t T, K* fron
             }
           }
           // Step 2: a terminal winner with time <= T violates G(FIN -> time > T)
-          if (to_terminal && st <= T) atomicMin(&S.vmin, (unsigned long long)st);
+          if (to_terminal && (uint64_t)st <= T) atomicMin(&S.vmin, (unsigned long long)st);
         }
       }
     }
+    if (tid == 0) S.cut[(L + 1) & 1u] = sc ? ~sc : kNoLevel;
     __syncthreads();
     const uint32_t Wn = S.cnt[(L + 1) % 3];
     if (S.err) return;
@@ -423,7 +430,8 @@ __global__ void __launch_bounds__(kCfgMaxThreads) cfg_kernel(const __grid_consta
     __syncthreads();
     const uint64_t T = S.T;
     if (!S.skip) {
-      explore_unit<K>(Q, cfg, T, front0, front1, tab0, tab1, A.wcap, A.tsize, S);
+      if (Q.p.clk32) explore_unit<K, uint32_t>(Q, cfg, T, front0, front1, tab0, tab1, A.wcap, A.tsize, S);
+      else explore_unit<K, uint64_t>(Q, cfg, T, front0, front1, tab0, tab1, A.wcap, A.tsize, S);
       __syncthreads();
       if (tid == 0 && S.err) set_error(Q.ctrl, (int)S.err);
     }

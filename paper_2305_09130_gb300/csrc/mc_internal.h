@@ -57,7 +57,7 @@ struct Params {
   uint64_t swar_mask;     // low P*n_bits bits (when P*n_bits <= 64)
   uint64_t swar_mul;      // sum_t 2^(t*n_bits): the product's top field sums the n fields
   uint32_t swar_ok;       // 1 when P*n_bits <= 64
-  uint32_t pad;
+  uint32_t clk32;         // 1 when every clock (N * cost * speed) fits 32 bits
   const uint32_t* N;      // device [a*b]
   const uint32_t* cost;   // device [a*b]
   const uint32_t* speed;  // device [P]
