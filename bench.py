@@ -341,6 +341,11 @@ def measure_single(args, name: str, steps: int, warmup: int, device, stream, loc
         fixed["no_log_tags"] = 1
     if args.engine != "auto":
         fixed["engine"] = mc.ENGINE[args.engine]
+    if args.stage_chunk:
+        space.pop("stage_chunk", None)
+        fixed["stage_chunk"] = args.stage_chunk
+    if args.unit_threads:
+        fixed["unit_threads"] = args.unit_threads
 
     def tune_measure(c):
         m = mc.mc_model_create(spec, mc.mc_options_default(search=args.mode, prune=args.prune, timing=1,
@@ -793,8 +798,14 @@ def measure_c4(args, device, local: int, steps: int, warmup: int) -> dict:
     mc.mc_batch_destroy(probe)
     queries0 = [("min_time", None) if sp.meta["query"] else
                 ("check", round(t * sp.meta["t_frac_milli"] / 1000)) for sp, t in zip(specs, optima0)]
-    tuned = AT.tune_batch(specs, queries0, space=[AT.BATCH_LEVEL_SPACE, AT.BATCH_CONFIG_SPACE],
-                          reps=1, cache={}, path=os.path.join(tempfile.gettempdir(), "mc_autotune_c4.json"))
+    if args.engine != "auto":  # fixed on the command line: no tuning
+        fixed = {"engine": mc.ENGINE[args.engine]}
+        if args.unit_threads:
+            fixed["unit_threads"] = args.unit_threads
+        tuned = {"options": fixed, "timings": {}}
+    else:
+        tuned = AT.tune_batch(specs, queries0, space=[AT.BATCH_LEVEL_SPACE, AT.BATCH_CONFIG_SPACE],
+                              reps=1, cache={}, path=os.path.join(tempfile.gettempdir(), "mc_autotune_c4.json"))
     opts = mc.mc_options_default(timing=1, **tuned["options"])
     stream = torch.cuda.Stream(device)
     batch = mc.mc_batch_create(specs, opts, stream=stream)
@@ -1043,6 +1054,10 @@ def main(argv=None):
     p.add_argument("--engine", choices=["auto", "level", "config"], default="auto",
                    help="single-model explorer: level-synchronous or one block per configuration "
                         "(auto: by the model's widest configuration level)")
+    p.add_argument("--stage-chunk", type=int, default=0,
+                   help="level engine: winners staged per warp before a flush (0: the autotuner picks it)")
+    p.add_argument("--unit-threads", type=int, default=0,
+                   help="configuration engine: threads per block (0: from the model, or the tuner's pick)")
     p.add_argument("--rates", default="10,30,100,300,1000", help="c5 arrival rates (queries/s)")
     p.add_argument("--slots", type=int, default=512, help="c5 requests on the device at once")
     p.add_argument("--c5-seconds", type=float, default=100.0,
