@@ -519,7 +519,9 @@ int cfg_occupancy(int key_words, int threads, size_t smem, int* blocks_per_sm) {
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return -1;
-  const int static_bytes = (int)sizeof(CfgShared);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, f) != cudaSuccess) return -1;
+  const int static_bytes = (int)fa.sharedSizeBytes;
   if ((int)smem > optin - static_bytes) return -1;
   if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - static_bytes) != cudaSuccess)
     return -1;
