@@ -69,14 +69,15 @@ WORKLOADS = {
         "(splitmix64 seed 2305091303), speed 1, 128-bit packed states; 1,072,924,481 reachable states "
         "(closed form), widest level 193,344,684",
         "u128", expect=(1, 512, 2), cpu_T=30, ref_T=16,
-        tune={"probe_scheme": ["split", "one_call"], "stage_chunk": [64, 128]},
+        tune={"probe_scheme": ["split", "one_call", "cas_first"], "stage_chunk": [128, 192]},
         traffic="explore_kernel_c3star_traffic.txt"),
     "c2_star": Workload(
         lambda: W.c2_star(),
         "c2_star: G=80, P=4, WG 2^0..2^8, TS 2^0..2^4, FREE dispatch, cost ceil(WG/TS)*4+WG+2*TS, "
         "speeds U{1..3} (splitmix64 seed 2305091302), 64-bit packed states; 10,385,335 reachable states",
         "u64", expect=(96, 8, 4), cpu_T=None, ref_T=300,
-        tune={"probe_scheme": ["split", "one_call"], "load_factor_pct": [10, 15], "stage_chunk": [64, 128]},
+        tune={"probe_scheme": ["split", "one_call", "cas_first"], "load_factor_pct": [10, 15],
+              "stage_chunk": [128, 192]},
         traffic="explore_kernel_c2star_traffic.txt"),
     "c2": Workload(
         lambda: W.c2(rule=W.GREEDY),
@@ -367,7 +368,7 @@ def measure_single(args, name: str, steps: int, warmup: int, device, stream, loc
     model = mc.mc_model_create(spec, opts, allocator="torch", stream=stream)
     mc.mc_reserve(model)
     layout = mc.mc_model_layout(model)
-    scheme = "split" if layout["probe_scheme"] == mc.PROBE["split"] else "one_call"
+    scheme = {v: k for k, v in mc.PROBE.items()}[layout["probe_scheme"]]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > 129 MB of L2
 
     def flush_l2(k):
@@ -1047,7 +1048,7 @@ def main(argv=None):
                    help="default run: skip the secondary, batched and served objects")
     p.add_argument("--load-factor", type=int, default=0,
                    help="visited-set load factor in percent (0: the autotuner picks it)")
-    p.add_argument("--probe-scheme", choices=["tune", "auto", "split", "one_call"], default="tune",
+    p.add_argument("--probe-scheme", choices=["tune", "auto", "split", "one_call", "cas_first"], default="tune",
                    help="visited-set insert of the exploration kernel (tune: the autotuner picks it)")
     p.add_argument("--no-log-tags", action="store_true",
                    help="untagged frontier log: blocks write their entries before they arrive at a level")

@@ -77,17 +77,25 @@ typedef enum {
 } mc_search;
 
 /* How the exploration kernel inserts a successor into the visited set
- * (mc_options.probe_scheme).  Both fetch the successor's first 32-byte bucket
- * into shared memory first; the results are identical, only the speed
- * differs. */
+ * (mc_options.probe_scheme).  SPLIT and ONE_CALL fetch the successor's first
+ * 32-byte bucket into shared memory first; CAS_FIRST starts with the
+ * compare-and-swap.  The results are identical, only the speed differs. */
 typedef enum {
-  MC_PROBE_AUTO = 0,     /* SPLIT with 64-bit keys, ONE_CALL with 128-bit     */
+  MC_PROBE_AUTO = 0,     /* SPLIT with 64-bit keys, CAS_FIRST with 128-bit    */
   MC_PROBE_SPLIT = 1,    /* pick the slot from the fetched bucket, issue the
                             CAS of every proposal of the round, then resolve
                             (a lost slot or a full bucket falls back to the
                             general insert from the same bucket)              */
-  MC_PROBE_ONE_CALL = 2  /* the general insert (scan, CAS, next bucket) from
+  MC_PROBE_ONE_CALL = 2, /* the general insert (scan, CAS, next bucket) from
                             the fetched bucket, one proposal at a time        */
+  MC_PROBE_CAS_FIRST = 3 /* compare-and-swap from empty on the first slot of
+                            the first bucket, no fetch: an empty slot is a
+                            win and the key itself a duplicate in one round
+                            trip; anything else falls back to the general
+                            insert.  Every expanded state empties its own
+                            first slot (compare-and-swap from its key), so
+                            the table holds about two levels' keys and most
+                            first slots are empty when probed              */
 } mc_probe_scheme;
 
 /* Which kernel explores a pass (mc_options.engine).  Both report identical
@@ -175,8 +183,8 @@ typedef struct {
                                    widest configuration level                */
   uint32_t stage_chunk;         /* LEVEL engine: winners a warp stages in
                                    shared memory before it reserves frontier-
-                                   log space and copies them out: 64, 96 or
-                                   128; 0 = 128                              */
+                                   log space and copies them out: 64 to 192,
+                                   a multiple of 32; 0 = 128                 */
 } mc_options;
 
 /* Result of mc_check (Section 4, Step 2: Phi = G(FIN -> time > T)). */
@@ -224,8 +232,9 @@ typedef struct {
   uint64_t max_width;    /* bound on one level's width                     */
   uint64_t state_bound;  /* bound on all reachable states (saturates)      */
   uint64_t device_bytes; /* device memory the model needs                  */
-  uint32_t probe_scheme; /* the insert its explorations use: MC_PROBE_SPLIT
-                            or MC_PROBE_ONE_CALL (AUTO resolved)           */
+  uint32_t probe_scheme; /* the insert its explorations use: MC_PROBE_SPLIT,
+                            MC_PROBE_ONE_CALL or MC_PROBE_CAS_FIRST (AUTO
+                            resolved)                                      */
   uint32_t log_tag_bits; /* bits per 64-bit word of a frontier-log entry
                             that tag it with its pass, so a block can arrive
                             at a level's barrier before writing its last

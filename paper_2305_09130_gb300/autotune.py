@@ -46,8 +46,8 @@ LEVEL_SPACE = {
     "engine": [1],
     "blocks_per_sm": [0, 2],
     "load_factor_pct": [25, 50],
-    "probe_scheme": [1, 2],
-    "stage_chunk": [64, 128],
+    "probe_scheme": [1, 2, 3],  # split, one call, CAS first
+    "stage_chunk": [64, 128, 192],
 }
 CONFIG_SPACE = {
     "engine": [2],

@@ -194,7 +194,7 @@ struct mc_model {
   bool reserved = false;
   int device = -1;
   int grid = 0, threads = 0;
-  bool split = true;  // probe scheme of the exploration kernel (resolved at reserve)
+  int scheme = MC_PROBE_SPLIT;  // probe scheme of the exploration kernel (resolved at reserve)
   uint32_t tag_bits = 0;  // spare top key bits tagging the frontier log (0: untagged)
   uint32_t tag = 0;       // the last pass's tag
   cudaStream_t stream = nullptr;
@@ -327,10 +327,10 @@ bool valid_options(const mc_options* o) {
                                o->threads_per_block % 32))
     return false;
   if (o->table_log2 && (o->table_log2 < 3 || o->table_log2 > 40)) return false;
-  if (o->probe_scheme > MC_PROBE_ONE_CALL) return false;
+  if (o->probe_scheme > MC_PROBE_CAS_FIRST) return false;
   if (o->no_log_tags > 1) return false;
   if (o->engine > MC_ENGINE_CONFIG) return false;
-  if (o->stage_chunk && (o->stage_chunk < 64 || o->stage_chunk > mc::kWarpCap || o->stage_chunk % 32)) return false;
+  if (o->stage_chunk && (o->stage_chunk < 64 || o->stage_chunk > mc::kStageCap || o->stage_chunk % 32)) return false;
   if (o->unit_threads && (o->unit_threads < 64 || o->unit_threads > mc::kCfgMaxThreads || o->unit_threads % 32))
     return false;
   return true;
@@ -371,10 +371,12 @@ uint32_t log_tag_bits(const mc_model* m) {
 }
 
 // the probe scheme of the exploration kernel: AUTO follows the key width
-// (the split insert measured faster with 64-bit keys, the one-call insert
-// with 128-bit keys)
-bool resolve_split(uint32_t scheme, uint32_t key_words) {
-  return scheme == MC_PROBE_AUTO ? key_words == 1 : scheme == MC_PROBE_SPLIT;
+// (measured: with 64-bit keys the split insert is fastest on C2 at G=80,
+// whose table stays in L2; with 128-bit keys the CAS-first insert is 25%
+// faster than the others on C3 at G=36 and G=24, whose probes go to DRAM)
+int resolve_scheme(uint32_t scheme, uint32_t key_words) {
+  if (scheme == MC_PROBE_AUTO) return key_words == 1 ? MC_PROBE_SPLIT : MC_PROBE_CAS_FIRST;
+  return (int)scheme;
 }
 
 // sizes of the frontier log and the visited set
@@ -486,8 +488,8 @@ int reserve(mc_model* m) {
       return MC_ERR_CUDA;
     }
     m->threads = m->opt.threads_per_block ? (int)m->opt.threads_per_block : (int)mc::kThreads;
-    m->split = resolve_split(m->opt.probe_scheme, m->key_words);
-    if (mc::explore_kernel_occupancy(m->key_words, m->tile, m->rule, m->split, m->threads, &bps) || bps < 1) {
+    m->scheme = resolve_scheme(m->opt.probe_scheme, m->key_words);
+    if (mc::explore_kernel_occupancy(m->key_words, m->tile, m->rule, m->scheme, m->threads, &bps) || bps < 1) {
       m->last_err = "occupancy query failed";
       cudaGetLastError();
       return MC_ERR_CUDA;
@@ -773,7 +775,7 @@ int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, 
     if (rc_) return rc_;
   }
   if (m->opt.timing) MC_CUDA(m, cudaEventRecord(m->ev[2 * slot], m->stream));
-  MC_CUDA(m, mc::launch_explore(m->key_words, m->tile, m->rule, m->split, m->grid, m->threads, A, m->stream));
+  MC_CUDA(m, mc::launch_explore(m->key_words, m->tile, m->rule, m->scheme, m->grid, m->threads, A, m->stream));
   if (m->opt.timing) {
     MC_CUDA(m, cudaEventRecord(m->ev[2 * slot + 1], m->stream));
     m->ev_pending[slot] = true;
@@ -1074,7 +1076,7 @@ int mc_model_layout(const mc_model* m, mc_layout* out) {
   out->table_slots = m->table_slots;
   out->log_capacity = m->log_cap;
   out->device_bytes = m->device_bytes;
-  out->probe_scheme = resolve_split(m->opt.probe_scheme, m->key_words) ? MC_PROBE_SPLIT : MC_PROBE_ONE_CALL;
+  out->probe_scheme = (uint32_t)resolve_scheme(m->opt.probe_scheme, m->key_words);
   out->engine = m->engine;
   out->log_tag_bits = m->engine == MC_ENGINE_CONFIG ? 0 : log_tag_bits(m);
   out->unit_width = m->unit_width;

@@ -23,7 +23,8 @@ constexpr uint64_t kNone = ~0ull;          // "no value" for packed minima
 constexpr int kPackIdxBits = 12;           // i and j fields of a packed (time, i, j)
 constexpr uint32_t kNoParent = 0xFFFFFFFFu;
 constexpr uint32_t kThreads = 256;         // exploration kernel block size (maximum)
-constexpr uint32_t kWarpCap = 128;         // winners staged per warp before a flush
+constexpr uint32_t kWarpCap = 128;         // winners staged per warp before a flush (default chunk)
+constexpr uint32_t kStageCap = 192;        // exploration kernel: staging capacity per warp (largest chunk)
 #ifndef MC_PROBE_DEPTH
 #define MC_PROBE_DEPTH 1
 #endif
@@ -108,7 +109,7 @@ struct ExploreArgs {
   int64_t T_delta;
   uint64_t* tmin_out;     // if set: receives pack_time(best_pack) at the end
   uint32_t barrier_extra; // extra arrivals a barrier waits for (test hook)
-  uint32_t stage_chunk;   // winners a warp stages before a flush (64..kWarpCap)
+  uint32_t stage_chunk;   // winners a warp stages before a flush (64..kStageCap)
   uint32_t* bar_lines;    // the device-wide barrier's lines (zeroed per pass)
   uint64_t timeout_ns;
   const Ctrl* prev;       // lowering chained on the device: run at (prev's counterexample
@@ -118,11 +119,10 @@ struct ExploreArgs {
   uint32_t pad2;          // the exploration kernel)
 };
 
-// Launch helpers implemented in mc_kernels.cu.  `split` is the probe scheme:
-// true picks a slot from the fetched bucket and issues the CAS before the
-// result is looked at; false takes the general insert from the fetched bucket.
-int explore_kernel_occupancy(int key_words, int tile, int rule, bool split, int threads, int* blocks_per_sm);
-cudaError_t launch_explore(int key_words, int tile, int rule, bool split, int grid, int threads,
+// Launch helpers implemented in mc_kernels.cu.  `scheme` is the probe scheme,
+// resolved (MC_PROBE_SPLIT, MC_PROBE_ONE_CALL or MC_PROBE_CAS_FIRST).
+int explore_kernel_occupancy(int key_words, int tile, int rule, int scheme, int threads, int* blocks_per_sm);
+cudaError_t launch_explore(int key_words, int tile, int rule, int scheme, int grid, int threads,
                            const ExploreArgs& args, cudaStream_t stream);
 cudaError_t launch_simulate(const Params& p, uint64_t seed, uint32_t walks, uint64_t* t_out,
                             cudaStream_t stream);
@@ -188,7 +188,19 @@ struct CfgLaunch {
   uint32_t* next;
   uint32_t wcap;          // frontier capacity per level (states), a power of two
   uint32_t tsize;         // shared visited-set slots per level, a power of two
+  // Warp units: configurations of models whose widest level fits one warp
+  // (width bound x lanes per state <= 32) are explored by a single warp with
+  // the level in registers.  The last `warp_blocks` blocks of the grid serve
+  // them, each warp taking units from `wunits` (same encoding as `units`; a
+  // single pass's configurations in `one.order` when null).
+  const uint64_t* wunits;
+  uint64_t n_wunits;
+  const uint32_t* n_wunits_dev;
+  uint32_t* wnext;
+  uint32_t warp_blocks;
+  uint32_t pad;
 };
+constexpr uint32_t kWarpUnitLanes = 32;  // widest level x lanes per state a warp unit takes
 
 size_t cfg_smem_bytes(int key_words, uint32_t wcap, uint32_t tsize);
 int cfg_occupancy(int key_words, int threads, size_t smem, int* blocks_per_sm);

@@ -34,7 +34,10 @@
 // Keys of one level never leave the table during that level, so two threads
 // inserting the same key walk the same probe sequence and meet at the same
 // slot.  The table only has to hold one level (sized from the widest level),
-// and nothing is cleared between levels.
+// and nothing is cleared between levels.  (The CAS-first probe scheme
+// empties a key's first slot when its state is expanded, one level after it
+// was inserted: the table then holds about two levels' keys, and a first
+// probe meets an empty slot far more often; the rule above is unchanged.)
 #include <cstdint>
 
 #include "mc_device.cuh"
@@ -86,8 +89,8 @@ struct LogTag<u128> {  // each 64-bit word: 64 - tb payload bits, then the tag
 // synchronisation happens, so warps run their rounds independently.
 template <class K>
 struct Stage {
-  K keys[kThreads / 32][kWarpCap];
-  uint32_t par[kThreads / 32][kWarpCap];
+  K keys[kThreads / 32][kStageCap];
+  uint32_t par[kThreads / 32][kStageCap];
   uint32_t fill[kThreads / 32];
   unsigned long long base;
   uint32_t flags;  // this level: kFlagError | kFlagViolation
@@ -133,17 +136,18 @@ __device__ __forceinline__ bool log_entry(const ExploreArgs& A, uint64_t pos, K&
 // A tile of TILE >= P lanes handles kDepth states per round; lane c proposes,
 // for each of them, the successor in which unit c takes the next work-group
 // (Listings 4-5): FREE allows every unit, GREEDY only the units with the
-// smallest clock.  The first visited-set bucket of every proposal is fetched
-// with cp.async into this thread's slice of shared memory, all kDepth at
-// once, so the probes are in flight together without holding registers;
-// then each is resolved (a hit is a duplicate; otherwise CAS into the first
-// free slot).  Winners are staged and appended to the next level of the
-// frontier log, and a winner that is terminal (FIN, Listing 4) with
-// time <= T updates the level's minimum packed (time, i, j) -- the property
-// G(FIN -> time > T) of Step 2.  The keys of the next round are loaded
-// before the current round's probes.  SPLIT selects the probe scheme (see
-// the insert below).
-template <class K, int TILE, int RULE, bool SPLIT>
+// smallest clock.  With the split and one-call schemes the first
+// visited-set bucket of every proposal is fetched with cp.async into this
+// thread's slice of shared memory, all kDepth at once, so the probes are in
+// flight together without holding registers; then each is resolved (a hit
+// is a duplicate; otherwise CAS into the first free slot).  The CAS-first
+// scheme skips the fetch (see the insert below).  Winners are staged and
+// appended to the next level of the frontier log, and a winner that is
+// terminal (FIN, Listing 4) with time <= T updates the level's minimum
+// packed (time, i, j) -- the property G(FIN -> time > T) of Step 2.  The
+// keys of the next round are loaded before the current round's probes.
+// SCHEME is the probe scheme (mc_probe_scheme, resolved).
+template <class K, int TILE, int RULE, int SCHEME>
 __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st, uint64_t T,
                                              uint32_t L, uint64_t offL, uint64_t W, uint64_t offN,
                                              const K (&first)[kDepth], bool have_first, uint32_t stop_mask) {
@@ -193,6 +197,12 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
       }
       uint32_t i = 0, j = 0, r = 0;
       uint64_t t_c = 0, clk = 0;
+      // CAS-first: this state's key (inserted during the previous level)
+      // leaves its first slot, so the slot is empty for the next level's
+      // keys; the compare-and-swap only removes this very key, never a key
+      // of the level being built, and its result is not waited for
+      if (SCHEME == MC_PROBE_CAS_FIRST && valid && c == 0)
+        (void)slot_cas(table + (key_hash(key) & A.bucket_mask) * S, key, (K)0);
       if (valid) {
         i = field(key, p.wg_shift, p.wg_mask) - 1;
         j = field(key, p.ts_shift, p.ts_mask) - 1;
@@ -217,44 +227,54 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
       ij[d] = (i << 16) | j;
       succ[d] = key + ((K)1 << c_shift);
       bkt[d] = key_hash(succ[d]) & A.bucket_mask;
-      if (ok) {
+      if (ok && SCHEME != MC_PROBE_CAS_FIRST) {
         const K* src = table + bkt[d] * S;
         cp_async16(&probe[threadIdx.x][d][0], src);
         cp_async16(reinterpret_cast<char*>(&probe[threadIdx.x][d][0]) + 16,
                    reinterpret_cast<const char*>(src) + 16);
       }
     }
-    cp_async_wait_all();
-    // SPLIT: pick a slot for every proposal from the fetched bucket, issue
+    if (SCHEME != MC_PROBE_CAS_FIRST) cp_async_wait_all();
+    // Split: pick a slot for every proposal from the fetched bucket, issue
     // all of their CAS, and only then look at the results, with the general
     // insert (rereading the bucket) when the slot went to another key or the
-    // bucket is full.  Otherwise each proposal takes the general insert from
+    // bucket is full.  One call: each proposal takes the general insert from
     // the fetched bucket directly.  (Measured: the split form is 8% faster
     // on C2 at G=80 with 64-bit keys and 2-3% slower per level with 128-bit
-    // keys, which is why the default follows the key width.)
-    constexpr bool kSplit = SPLIT;
+    // keys, which is why the default follows the key width.)  CAS-first: the
+    // CAS from empty on the first slot of the first bucket, unfetched.  If
+    // it succeeds the key was nowhere in its probe sequence (a key placed
+    // further along means the slots before it held keys of this level when
+    // it was placed, and those stay for the whole level); if it returns the
+    // key, a duplicate; anything else takes the general insert, which
+    // rereads the bucket.
+    constexpr bool kPicked = SCHEME == MC_PROBE_SPLIT || SCHEME == MC_PROBE_CAS_FIRST;
     uint32_t pick[D];
     K cur[D], old[D];
 #pragma unroll
     for (uint32_t d = 0; d < D; ++d) {
       pick[d] = allowed[d] ? kPickFull : kPickDup;
-      if (kSplit && allowed[d])
+      if (SCHEME == MC_PROBE_SPLIT && allowed[d])
         pick[d] = bucket_pick<K>(probe[threadIdx.x][d], succ[d], k_cur + 1, level_of, cur[d]);
+      if (SCHEME == MC_PROBE_CAS_FIRST && allowed[d]) {
+        pick[d] = 0;
+        cur[d] = (K)0;
+      }
     }
 #pragma unroll
     for (uint32_t d = 0; d < D; ++d)
-      if (kSplit && pick[d] < (uint32_t)S) old[d] = slot_cas(table + bkt[d] * S + pick[d], cur[d], succ[d]);
+      if (kPicked && pick[d] < (uint32_t)S) old[d] = slot_cas(table + bkt[d] * S + pick[d], cur[d], succ[d]);
 #pragma unroll
     for (uint32_t d = 0; d < D; ++d) {
       const uint64_t s = base + d * kTilesPerWarp + my;
       int won = 0;
-      if (kSplit && pick[d] < (uint32_t)S) {
+      if (kPicked && pick[d] < (uint32_t)S) {
         if (old[d] == cur[d]) won = 1;
         else if (old[d] != succ[d]) pick[d] = kPickFull;  // the slot went to another key
       }
       if (pick[d] == kPickFull) {
         const int rc = visited_insert<K>(table, A.bucket_mask, A.max_probes, succ[d], k_cur + 1, p, bkt[d],
-                                         kSplit ? nullptr : probe[threadIdx.x][d]);
+                                         kPicked ? nullptr : probe[threadIdx.x][d]);
         if (rc < 0) {
           set_error(A.ctrl, MC_ERR_TABLE_FULL);
           atomicOr(&st.flags, kFlagError);
@@ -316,7 +336,7 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
 }
 
 // ------------------------------------------------------------------ the exploration pass
-template <class K, int TILE, int RULE, bool SPLIT>
+template <class K, int TILE, int RULE, int SCHEME>
 __global__ void __launch_bounds__(kThreads, 4) explore_kernel(const ExploreArgs A) {
   const Params& p = A.p;
   Ctrl* ctrl = A.ctrl;
@@ -408,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 4) explore_kernel(const ExploreArgs 
     const uint64_t offN = off_last + W;
     if (gtid == 0) A.off[L + 1] = offN;
     const uint32_t stop_mask = kFlagError | (A.early_exit ? kFlagViolation : 0u);
-    expand_level<K, TILE, RULE, SPLIT>(A, stage, T, L, off_last, W, offN, first, have_first, stop_mask);
+    expand_level<K, TILE, RULE, SCHEME>(A, stage, T, L, off_last, W, offN, first, have_first, stop_mask);
     // level L+1's width word doubles as the barrier: it ends with the width
     // and the number of blocks that saw an error or (with early exit) a
     // violating terminal (a tagged log's blocks arrived in expand_level)
@@ -639,42 +659,52 @@ __global__ void replay_walk_kernel(const Params p, uint64_t seed, uint64_t w, in
 }
 
 // ------------------------------------------------------------------ dispatch tables
-template <class K, int RULE, bool SPLIT>
+template <class K, int RULE, int SCHEME>
 const void* pick_tile(int tile) {
   switch (tile) {
-    case 1: return (const void*)explore_kernel<K, 1, RULE, SPLIT>;
-    case 2: return (const void*)explore_kernel<K, 2, RULE, SPLIT>;
-    case 4: return (const void*)explore_kernel<K, 4, RULE, SPLIT>;
-    case 8: return (const void*)explore_kernel<K, 8, RULE, SPLIT>;
-    case 16: return (const void*)explore_kernel<K, 16, RULE, SPLIT>;
+    case 1: return (const void*)explore_kernel<K, 1, RULE, SCHEME>;
+    case 2: return (const void*)explore_kernel<K, 2, RULE, SCHEME>;
+    case 4: return (const void*)explore_kernel<K, 4, RULE, SCHEME>;
+    case 8: return (const void*)explore_kernel<K, 8, RULE, SCHEME>;
+    case 16: return (const void*)explore_kernel<K, 16, RULE, SCHEME>;
   }
   return nullptr;
 }
 
-template <class K, bool SPLIT>
+template <class K, int SCHEME>
 const void* pick_rule(int tile, int rule) {
-  return rule == MC_FREE ? pick_tile<K, MC_FREE, SPLIT>(tile) : pick_tile<K, MC_GREEDY, SPLIT>(tile);
+  return rule == MC_FREE ? pick_tile<K, MC_FREE, SCHEME>(tile) : pick_tile<K, MC_GREEDY, SCHEME>(tile);
 }
 
-const void* pick_kernel(int key_words, int tile, int rule, bool split) {
-  if (key_words == 1) return split ? pick_rule<uint64_t, true>(tile, rule) : pick_rule<uint64_t, false>(tile, rule);
-  if (key_words == 2) return split ? pick_rule<u128, true>(tile, rule) : pick_rule<u128, false>(tile, rule);
+template <class K>
+const void* pick_scheme(int tile, int rule, int scheme) {
+  switch (scheme) {
+    case MC_PROBE_SPLIT: return pick_rule<K, MC_PROBE_SPLIT>(tile, rule);
+    case MC_PROBE_ONE_CALL: return pick_rule<K, MC_PROBE_ONE_CALL>(tile, rule);
+    case MC_PROBE_CAS_FIRST: return pick_rule<K, MC_PROBE_CAS_FIRST>(tile, rule);
+  }
+  return nullptr;
+}
+
+const void* pick_kernel(int key_words, int tile, int rule, int scheme) {
+  if (key_words == 1) return pick_scheme<uint64_t>(tile, rule, scheme);
+  if (key_words == 2) return pick_scheme<u128>(tile, rule, scheme);
   return nullptr;
 }
 
 }  // namespace
 
-int explore_kernel_occupancy(int key_words, int tile, int rule, bool split, int threads, int* blocks_per_sm) {
-  const void* f = pick_kernel(key_words, tile, rule, split);
+int explore_kernel_occupancy(int key_words, int tile, int rule, int scheme, int threads, int* blocks_per_sm) {
+  const void* f = pick_kernel(key_words, tile, rule, scheme);
   if (!f) return -1;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, 0) == cudaSuccess
              ? 0
              : -1;
 }
 
-cudaError_t launch_explore(int key_words, int tile, int rule, bool split, int grid, int threads,
+cudaError_t launch_explore(int key_words, int tile, int rule, int scheme, int grid, int threads,
                            const ExploreArgs& args, cudaStream_t stream) {
-  const void* f = pick_kernel(key_words, tile, rule, split);
+  const void* f = pick_kernel(key_words, tile, rule, scheme);
   if (!f) return cudaErrorInvalidValue;
   void* params[] = {const_cast<ExploreArgs*>(&args)};
   return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(threads), params, 0, stream);

@@ -185,7 +185,8 @@ extern "C" int mc_check_noalloc(const mc_model_desc* d, uint64_t T, uint32_t pru
   int sms = 0, coop = 0, bps = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop ||
-      mc::explore_kernel_occupancy(key_words, tile, d->rule, key_words == 1, mc::kThreads, &bps) || bps < 1) {
+      mc::explore_kernel_occupancy(key_words, tile, d->rule, key_words == 1 ? MC_PROBE_SPLIT : MC_PROBE_CAS_FIRST,
+                                   mc::kThreads, &bps) || bps < 1) {
     cudaGetLastError();
     return MC_ERR_CUDA;
   }
@@ -256,7 +257,8 @@ extern "C" int mc_check_noalloc(const mc_model_desc* d, uint64_t T, uint32_t pru
   A.timeout_ns = 60ull * 1000000000ull;
 
   mc::Ctrl h;
-  if (mc::launch_explore(key_words, tile, d->rule, key_words == 1, sms * bps, mc::kThreads, A, stream) !=
+  if (mc::launch_explore(key_words, tile, d->rule, key_words == 1 ? MC_PROBE_SPLIT : MC_PROBE_CAS_FIRST, sms * bps,
+                         mc::kThreads, A, stream) !=
       cudaSuccess) {
     cudaGetLastError();
     return MC_ERR_CUDA;

@@ -101,20 +101,22 @@ def test_invalid_descriptions(lib):
         mc.mc_model_create(ok, mc.mc_options_default(load_factor_pct=95), allocator=None)
     assert e.value.code == mc.MC_ERR_INVAL
     with pytest.raises(mc.MCError) as e:
-        mc.mc_model_create(ok, mc.mc_options_default(probe_scheme=3), allocator=None)
+        mc.mc_model_create(ok, mc.mc_options_default(probe_scheme=4), allocator=None)
     assert e.value.code == mc.MC_ERR_INVAL
 
 
 def test_probe_schemes_are_accepted_by_name_and_number(lib):
-    for name, code in (("auto", 0), ("split", 1), ("one_call", 2)):
+    for name, code in (("auto", 0), ("split", 1), ("one_call", 2), ("cas_first", 3)):
         o = mc.mc_options_default(probe_scheme=name)
         assert o.probe_scheme == code == mc.PROBE[name]
         mc.mc_model_create(W.c1(), o, allocator=None)
-    # AUTO resolves by key width: split for 64-bit keys, one call for 128-bit
+    # AUTO resolves by key width: split for 64-bit keys, CAS first for 128-bit
     assert layout(W.c1())["probe_scheme"] == mc.PROBE["split"]
-    assert layout(W.c1().with_key_bits(128))["probe_scheme"] == mc.PROBE["one_call"]
+    assert layout(W.c1().with_key_bits(128))["probe_scheme"] == mc.PROBE["cas_first"]
     assert layout(W.c1(), probe_scheme="one_call")["probe_scheme"] == mc.PROBE["one_call"]
     assert layout(W.c1().with_key_bits(128), probe_scheme="split")["probe_scheme"] == mc.PROBE["split"]
+    for spec in (W.c1(), W.c1().with_key_bits(128)):
+        assert layout(spec, probe_scheme="cas_first")["probe_scheme"] == mc.PROBE["cas_first"]
 
 
 def test_frontier_log_tags_use_spare_key_bits(lib):
@@ -172,7 +174,7 @@ def test_engine_follows_the_width_of_one_configuration(lib):
         mc.mc_reserve(m)
     assert e.value.code == mc.MC_ERR_INVAL
     for bad in ({"engine": 3}, {"unit_threads": 48}, {"unit_threads": 1024}, {"stage_chunk": 32},
-                {"stage_chunk": 160}, {"stage_chunk": 100}):
+                {"stage_chunk": 224}, {"stage_chunk": 100}):
         with pytest.raises(mc.MCError):
             mc.mc_model_create(W.c1(), mc.mc_options_default(**bad), allocator=None)
 

@@ -331,12 +331,16 @@ def test_lowering_chained_over_several_groups(mc, oracle, P, b, rule, engine):
 
 # ---------------------------------------------------------------- probe schemes
 
-@pytest.mark.parametrize("scheme", ["split", "one_call"])
-def test_probe_schemes_match_oracle(mc, oracle, scheme):
-    """Both inserts (mc_options.probe_scheme), forced on 64- and 128-bit keys,
-    give the oracle's counts, widths, checks and minima."""
+@pytest.mark.parametrize("load_factor", [25, 90])
+@pytest.mark.parametrize("scheme", ["split", "one_call", "cas_first"])
+def test_probe_schemes_match_oracle(mc, oracle, scheme, load_factor):
+    """Every insert (mc_options.probe_scheme), forced on 64- and 128-bit keys,
+    gives the oracle's counts, widths, checks and minima; at a 90% load
+    factor most first slots are taken, so the CAS-first insert's fallback
+    (another key, or a key of an earlier level, in the first slot) runs
+    often."""
     for spec in sweep_models()[::3]:
-        model = make(mc, spec, probe_scheme=scheme, engine="level")
+        model = make(mc, spec, probe_scheme=scheme, engine="level", load_factor_pct=load_factor)
         mc.mc_reserve(model)  # the scheme is fixed once the buffers exist
         assert mc.mc_model_layout(model)["probe_scheme"] == mc.PROBE[scheme]
         assert mc.mc_count_states(model) == oracle.count(spec)
@@ -349,7 +353,7 @@ def test_probe_schemes_match_oracle(mc, oracle, scheme):
         assert gpu_min(mc, model, "single", True) == oracle.min_time(spec, search="single", prune=True)
 
 
-@pytest.mark.parametrize("scheme", ["split", "one_call"])
+@pytest.mark.parametrize("scheme", ["split", "one_call", "cas_first"])
 def test_probe_schemes_at_full_size(mc, scheme):
     """C2 at G=80 (64-bit keys) and C3 literal under GREEDY (128-bit keys) with
     each insert forced: the full counts, every level's width and the minimum."""
@@ -446,7 +450,7 @@ def test_lanes_per_state_and_stage_chunk_match_oracle(mc, oracle, engine):
         for lanes in sorted({t, min(16, 2 * t), 16}):
             if lanes < spec.P:
                 continue
-            for chunk in ((64, 96, 128) if engine == "level" else (0,)):
+            for chunk in ((64, 96, 128, 192) if engine == "level" else (0,)):
                 model = make(mc, spec, engine=engine, lanes_per_state=lanes, stage_chunk=chunk)
                 assert mc.mc_count_states(model) == oracle.count(spec), (spec.name, lanes, chunk)
                 assert mc.mc_last_widths(model) == CF.widths(spec)
