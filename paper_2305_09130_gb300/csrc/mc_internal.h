@@ -188,19 +188,7 @@ struct CfgLaunch {
   uint32_t* next;
   uint32_t wcap;          // frontier capacity per level (states), a power of two
   uint32_t tsize;         // shared visited-set slots per level, a power of two
-  // Warp units: configurations of models whose widest level fits one warp
-  // (width bound x lanes per state <= 32) are explored by a single warp with
-  // the level in registers.  The last `warp_blocks` blocks of the grid serve
-  // them, each warp taking units from `wunits` (same encoding as `units`; a
-  // single pass's configurations in `one.order` when null).
-  const uint64_t* wunits;
-  uint64_t n_wunits;
-  const uint32_t* n_wunits_dev;
-  uint32_t* wnext;
-  uint32_t warp_blocks;
-  uint32_t pad;
 };
-constexpr uint32_t kWarpUnitLanes = 32;  // widest level x lanes per state a warp unit takes
 
 size_t cfg_smem_bytes(int key_words, uint32_t wcap, uint32_t tsize);
 int cfg_occupancy(int key_words, int threads, size_t smem, int* blocks_per_sm);
