@@ -69,14 +69,14 @@ WORKLOADS = {
         "(splitmix64 seed 2305091303), speed 1, 128-bit packed states; 1,072,924,481 reachable states "
         "(closed form), widest level 193,344,684",
         "u128", expect=(1, 512, 2), cpu_T=30, ref_T=16,
-        tune={"probe_scheme": ["split", "one_call", "cas_first"], "stage_chunk": [128, 192]},
+        tune={"probe_scheme": ["split", "one_call", "cas_first", "cas_clear"], "stage_chunk": [128, 192]},
         traffic="explore_kernel_c3star_traffic.txt"),
     "c2_star": Workload(
         lambda: W.c2_star(),
         "c2_star: G=80, P=4, WG 2^0..2^8, TS 2^0..2^4, FREE dispatch, cost ceil(WG/TS)*4+WG+2*TS, "
         "speeds U{1..3} (splitmix64 seed 2305091302), 64-bit packed states; 10,385,335 reachable states",
         "u64", expect=(96, 8, 4), cpu_T=None, ref_T=300,
-        tune={"probe_scheme": ["split", "one_call", "cas_first"], "load_factor_pct": [10, 15],
+        tune={"probe_scheme": ["split", "one_call", "cas_first", "cas_clear"], "load_factor_pct": [10, 15],
               "stage_chunk": [128, 192]},
         traffic="explore_kernel_c2star_traffic.txt"),
     "c2": Workload(
@@ -99,7 +99,7 @@ METRIC = "unique states/sec"
 UNIT = "states/s"
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SRCS = [os.path.join(ROOT, "paper_2305_09130_gb300", "csrc", f)
-               for f in ("mc_kernels.cu", "mc_device.cuh", "mc_internal.h")]
+               for f in ("mc_explore.cuh", "mc_device.cuh", "mc_internal.h")]
 PROFILES = os.path.join(ROOT, "profiles")
 
 
@@ -1048,7 +1048,7 @@ def main(argv=None):
                    help="default run: skip the secondary, batched and served objects")
     p.add_argument("--load-factor", type=int, default=0,
                    help="visited-set load factor in percent (0: the autotuner picks it)")
-    p.add_argument("--probe-scheme", choices=["tune", "auto", "split", "one_call", "cas_first"], default="tune",
+    p.add_argument("--probe-scheme", choices=["tune", "auto", "split", "one_call", "cas_first", "cas_clear"], default="tune",
                    help="visited-set insert of the exploration kernel (tune: the autotuner picks it)")
     p.add_argument("--no-log-tags", action="store_true",
                    help="untagged frontier log: blocks write their entries before they arrive at a level")

@@ -81,21 +81,27 @@ typedef enum {
  * 32-byte bucket into shared memory first; CAS_FIRST starts with the
  * compare-and-swap.  The results are identical, only the speed differs. */
 typedef enum {
-  MC_PROBE_AUTO = 0,     /* SPLIT with 64-bit keys, CAS_FIRST with 128-bit    */
+  MC_PROBE_AUTO = 0,     /* SPLIT with 64-bit keys, CAS_FIRST with 128-bit
+                            (the fastest on C2 at G=80, whose table stays in
+                            L2, and on C3 at G=36, whose probes go to DRAM) */
   MC_PROBE_SPLIT = 1,    /* pick the slot from the fetched bucket, issue the
                             CAS of every proposal of the round, then resolve
                             (a lost slot or a full bucket falls back to the
                             general insert from the same bucket)              */
   MC_PROBE_ONE_CALL = 2, /* the general insert (scan, CAS, next bucket) from
                             the fetched bucket, one proposal at a time        */
-  MC_PROBE_CAS_FIRST = 3 /* compare-and-swap from empty on the first slot of
-                            the first bucket, no fetch: an empty slot is a
-                            win and the key itself a duplicate in one round
-                            trip; anything else falls back to the general
-                            insert.  Every expanded state empties its own
-                            first slot (compare-and-swap from its key), so
-                            the table holds about two levels' keys and most
-                            first slots are empty when probed              */
+  MC_PROBE_CAS_FIRST = 3, /* compare-and-swap from empty on the first slot
+                            of the first bucket, no fetch: an empty slot is
+                            a win and the key itself a duplicate in one
+                            round trip; anything else (another key, or a
+                            key of an earlier level) falls back to the
+                            general insert                                 */
+  MC_PROBE_CAS_CLEAR = 4 /* CAS_FIRST, and every expanded state empties its
+                            own first slot (compare-and-swap from its key),
+                            so the table holds about two levels' keys and
+                            most first slots are empty when probed: faster
+                            in deep searches over tables that stay in L2,
+                            slower where the extra atomic goes to DRAM    */
 } mc_probe_scheme;
 
 /* Which kernel explores a pass (mc_options.engine).  Both report identical
@@ -232,9 +238,8 @@ typedef struct {
   uint64_t max_width;    /* bound on one level's width                     */
   uint64_t state_bound;  /* bound on all reachable states (saturates)      */
   uint64_t device_bytes; /* device memory the model needs                  */
-  uint32_t probe_scheme; /* the insert its explorations use: MC_PROBE_SPLIT,
-                            MC_PROBE_ONE_CALL or MC_PROBE_CAS_FIRST (AUTO
-                            resolved)                                      */
+  uint32_t probe_scheme; /* the insert its explorations use (mc_probe_scheme,
+                            AUTO resolved)                                 */
   uint32_t log_tag_bits; /* bits per 64-bit word of a frontier-log entry
                             that tag it with its pass, so a block can arrive
                             at a level's barrier before writing its last

@@ -46,7 +46,7 @@ LEVEL_SPACE = {
     "engine": [1],
     "blocks_per_sm": [0, 2],
     "load_factor_pct": [25, 50],
-    "probe_scheme": [1, 2, 3],  # split, one call, CAS first
+    "probe_scheme": [1, 2, 3, 4],  # split, one call, CAS first, CAS first with clearing
     "stage_chunk": [64, 128, 192],
 }
 CONFIG_SPACE = {

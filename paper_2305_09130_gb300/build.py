@@ -17,8 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libmcgpu.so")
-SOURCES = ["mc_api.cu", "mc_kernels.cu", "mc_cfg.cu", "mc_cfg_jobs.cu", "mc_batch.cu", "mc_noalloc.cu", "mc_roofline.cu", "mc_pe.cu"]
-HEADERS = [os.path.join(CSRC, "mc_internal.h"), os.path.join(CSRC, "mc_cfg_jobs.h"), os.path.join(CSRC, "mc_device.cuh"), os.path.join(CSRC, "mc_host.h"),
+SOURCES = ["mc_api.cu", "mc_kernels.cu", "mc_explore_cas.cu", "mc_cfg.cu", "mc_cfg_jobs.cu", "mc_batch.cu", "mc_noalloc.cu", "mc_roofline.cu", "mc_pe.cu"]
+HEADERS = [os.path.join(CSRC, "mc_internal.h"), os.path.join(CSRC, "mc_cfg_jobs.h"), os.path.join(CSRC, "mc_device.cuh"), os.path.join(CSRC, "mc_explore.cuh"), os.path.join(CSRC, "mc_host.h"),
            os.path.join(INCLUDE, "mc.h"), os.path.join(INCLUDE, "mc_pe.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

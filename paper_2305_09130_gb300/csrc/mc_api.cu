@@ -327,7 +327,7 @@ bool valid_options(const mc_options* o) {
                                o->threads_per_block % 32))
     return false;
   if (o->table_log2 && (o->table_log2 < 3 || o->table_log2 > 40)) return false;
-  if (o->probe_scheme > MC_PROBE_CAS_FIRST) return false;
+  if (o->probe_scheme > MC_PROBE_CAS_CLEAR) return false;
   if (o->no_log_tags > 1) return false;
   if (o->engine > MC_ENGINE_CONFIG) return false;
   if (o->stage_chunk && (o->stage_chunk < 64 || o->stage_chunk > mc::kStageCap || o->stage_chunk % 32)) return false;
@@ -372,8 +372,8 @@ uint32_t log_tag_bits(const mc_model* m) {
 
 // the probe scheme of the exploration kernel: AUTO follows the key width
 // (measured: with 64-bit keys the split insert is fastest on C2 at G=80,
-// whose table stays in L2; with 128-bit keys the CAS-first insert is 25%
-// faster than the others on C3 at G=36 and G=24, whose probes go to DRAM)
+// whose table stays in L2; with 128-bit keys the CAS-first insert without
+// clearing is fastest on C3 at G=36 and G=24, whose probes go to DRAM)
 int resolve_scheme(uint32_t scheme, uint32_t key_words) {
   if (scheme == MC_PROBE_AUTO) return key_words == 1 ? MC_PROBE_SPLIT : MC_PROBE_CAS_FIRST;
   return (int)scheme;

@@ -120,7 +120,9 @@ struct ExploreArgs {
 };
 
 // Launch helpers implemented in mc_kernels.cu.  `scheme` is the probe scheme,
-// resolved (MC_PROBE_SPLIT, MC_PROBE_ONE_CALL or MC_PROBE_CAS_FIRST).
+// resolved (MC_PROBE_SPLIT, MC_PROBE_ONE_CALL, MC_PROBE_CAS_FIRST or
+// MC_PROBE_CAS_CLEAR); the CAS-first kernels come from mc_explore_cas.cu.
+const void* pick_explore_cas(int key_words, int tile, int rule, int scheme);
 int explore_kernel_occupancy(int key_words, int tile, int rule, int scheme, int threads, int* blocks_per_sm);
 cudaError_t launch_explore(int key_words, int tile, int rule, int scheme, int grid, int threads,
                            const ExploreArgs& args, cudaStream_t stream);

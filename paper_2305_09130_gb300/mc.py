@@ -27,7 +27,7 @@ MC_ERR_CUDA = -6
 MC_ERR_OVERFLOW = -7
 MC_FREE, MC_GREEDY = 0, 1
 SEARCH = {"single": 0, "lower": 1, "bisect": 2}
-PROBE = {"auto": 0, "split": 1, "one_call": 2, "cas_first": 3}  # mc_probe_scheme
+PROBE = {"auto": 0, "split": 1, "one_call": 2, "cas_first": 3, "cas_clear": 4}  # mc_probe_scheme
 ENGINE = {"auto": 0, "level": 1, "config": 2}  # mc_engine
 NO_LIMIT = (1 << 64) - 1
 

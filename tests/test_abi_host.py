@@ -101,12 +101,12 @@ def test_invalid_descriptions(lib):
         mc.mc_model_create(ok, mc.mc_options_default(load_factor_pct=95), allocator=None)
     assert e.value.code == mc.MC_ERR_INVAL
     with pytest.raises(mc.MCError) as e:
-        mc.mc_model_create(ok, mc.mc_options_default(probe_scheme=4), allocator=None)
+        mc.mc_model_create(ok, mc.mc_options_default(probe_scheme=5), allocator=None)
     assert e.value.code == mc.MC_ERR_INVAL
 
 
 def test_probe_schemes_are_accepted_by_name_and_number(lib):
-    for name, code in (("auto", 0), ("split", 1), ("one_call", 2), ("cas_first", 3)):
+    for name, code in (("auto", 0), ("split", 1), ("one_call", 2), ("cas_first", 3), ("cas_clear", 4)):
         o = mc.mc_options_default(probe_scheme=name)
         assert o.probe_scheme == code == mc.PROBE[name]
         mc.mc_model_create(W.c1(), o, allocator=None)
@@ -116,7 +116,8 @@ def test_probe_schemes_are_accepted_by_name_and_number(lib):
     assert layout(W.c1(), probe_scheme="one_call")["probe_scheme"] == mc.PROBE["one_call"]
     assert layout(W.c1().with_key_bits(128), probe_scheme="split")["probe_scheme"] == mc.PROBE["split"]
     for spec in (W.c1(), W.c1().with_key_bits(128)):
-        assert layout(spec, probe_scheme="cas_first")["probe_scheme"] == mc.PROBE["cas_first"]
+        for name in ("cas_first", "cas_clear"):
+            assert layout(spec, probe_scheme=name)["probe_scheme"] == mc.PROBE[name]
 
 
 def test_frontier_log_tags_use_spare_key_bits(lib):

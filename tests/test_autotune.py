@@ -102,9 +102,9 @@ def test_tuning_covers_both_engines_and_their_knobs(mc, tmp_path):
     keys = [json.loads(k) for k in out["timings"]]
     assert {k["engine"] for k in keys} == {1, 2}
     assert {k.get("stage_chunk") for k in keys if k["engine"] == 1} == {64, 128, 192}
-    assert {k.get("probe_scheme") for k in keys if k["engine"] == 1} == {1, 2, 3}
+    assert {k.get("probe_scheme") for k in keys if k["engine"] == 1} == {1, 2, 3, 4}
     assert {k.get("lanes_per_state") for k in keys if k["engine"] == 2} == {0, 16}
-    assert len(keys) == 9 + 4  # probe scheme x chunk, threads x lanes
+    assert len(keys) == 12 + 4  # probe scheme x chunk, threads x lanes
     m = mc.mc_model_create(spec, AT.options_for(spec, "min_time", path=path))
     assert mc.mc_min_time(m, trace=False)["t_min"] == 80
     specs = W.c4_instances(12)

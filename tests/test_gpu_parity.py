@@ -332,7 +332,7 @@ def test_lowering_chained_over_several_groups(mc, oracle, P, b, rule, engine):
 # ---------------------------------------------------------------- probe schemes
 
 @pytest.mark.parametrize("load_factor", [25, 90])
-@pytest.mark.parametrize("scheme", ["split", "one_call", "cas_first"])
+@pytest.mark.parametrize("scheme", ["split", "one_call", "cas_first", "cas_clear"])
 def test_probe_schemes_match_oracle(mc, oracle, scheme, load_factor):
     """Every insert (mc_options.probe_scheme), forced on 64- and 128-bit keys,
     gives the oracle's counts, widths, checks and minima; at a 90% load
@@ -353,7 +353,7 @@ def test_probe_schemes_match_oracle(mc, oracle, scheme, load_factor):
         assert gpu_min(mc, model, "single", True) == oracle.min_time(spec, search="single", prune=True)
 
 
-@pytest.mark.parametrize("scheme", ["split", "one_call", "cas_first"])
+@pytest.mark.parametrize("scheme", ["split", "one_call", "cas_first", "cas_clear"])
 def test_probe_schemes_at_full_size(mc, scheme):
     """C2 at G=80 (64-bit keys) and C3 literal under GREEDY (128-bit keys) with
     each insert forced: the full counts, every level's width and the minimum."""
