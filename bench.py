@@ -452,25 +452,39 @@ def measure_single(args, name: str, steps: int, warmup: int, device, stream, loc
         table_bytes = layout["table_slots"] * 8 * layout["key_words"]
         hbm = mc.mc_measure_random_access(64 << 30, 200_000_000, 0)
         hbm_cas = mc.mc_measure_random_access(64 << 30, 200_000_000, 1)
+        hbm_cas_only = mc.mc_measure_random_access(64 << 30, 200_000_000, 2)
         l2 = mc.mc_measure_random_access(max(table_bytes, 1 << 20), 200_000_000, 0)
         explore_s = st["explore_ms"] / 1000.0
         probes = spec.P * st["states"] / explore_s
-        # P probe reads and about one CAS per unique state: the rate of a
-        # kernel that did nothing else, at the measured random-access rates
-        ceiling = 1.0 / (spec.P / hbm["sectors_per_s"] + 1.0 / hbm_cas["sectors_per_s"])
+        # the rate of a kernel that did nothing but its visited-set accesses,
+        # at the measured random-access rates: P bucket reads and about one
+        # CAS per unique state (split, one call), P CAS (CAS first), P + 1
+        # CAS (CAS first with clearing: the expanded state's own slot)
+        if scheme in ("cas_first", "cas_clear"):
+            per_state = spec.P + (1 if scheme == "cas_clear" else 0)
+            ceiling = hbm_cas_only["sectors_per_s"] / per_state
+            note = (f"{per_state} random CAS per unique state (one per generated successor"
+                    f"{', one clearing the expanded state' if scheme == 'cas_clear' else ''}); "
+                    f"ceiling = CAS rate / {per_state} over 64 GiB")
+        else:
+            ceiling = 1.0 / (spec.P / hbm["sectors_per_s"] + 1.0 / hbm_cas["sectors_per_s"])
+            note = ("P random 32-byte bucket reads per unique state (one per generated successor) and about "
+                    "one CAS; ceiling = 1 / (P / read rate + 1 / read+CAS rate) over 64 GiB")
         roofline["random_access"] = {
             "hbm_64GiB_sector_reads_per_s": hbm["sectors_per_s"],
             "hbm_64GiB_sector_read_cas_per_s": hbm_cas["sectors_per_s"],
+            "hbm_64GiB_cas_per_s": hbm_cas_only["sectors_per_s"],
             "table_sized_sector_reads_per_s": l2["sectors_per_s"],
             "table_bytes": table_bytes,
-            "kernel_probe_reads_per_s": probes,
-            "frac_of_hbm_64GiB": probes / hbm["sectors_per_s"],
+            "probe_scheme": scheme,
+            "kernel_probes_per_s": probes,
+            "frac_of_hbm_64GiB": probes / (hbm_cas_only if scheme in ("cas_first", "cas_clear")
+                                           else hbm)["sectors_per_s"],
             "frac_of_table_sized": probes / l2["sectors_per_s"],
             "states_per_s_ceiling_hbm": ceiling,
             "kernel_states_per_s": st["states"] / explore_s,
             "frac_of_states_ceiling_hbm": (st["states"] / explore_s) / ceiling,
-            "note": "P random 32-byte bucket reads per unique state (one per generated successor) and about "
-                    "one CAS; ceiling = 1 / (P / read rate + 1 / read+CAS rate) over 64 GiB"}
+            "note": note}
         if traffic:
             roofline["random_access"]["dram_bytes_per_state"] = traffic / states_per_launch
 

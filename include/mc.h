@@ -489,10 +489,12 @@ void mc_server_destroy(mc_server* s);
 
 /* Random-access roofline of the current device (a measurement utility, not a
  * step of the method): times `accesses` independent random 32-byte sector
- * reads (op 0) or reads followed by an atomicCAS on the sector (op 1) over a
- * freshly allocated buffer of `buffer_bytes` (use one far larger than L2), and
- * writes the sustained sectors per second.  The visited set of an exploration
- * larger than L2 is accessed this way, so this rate bounds its HBM regime.
+ * reads (op 0), reads followed by an atomicCAS on the sector (op 1), or an
+ * atomicCAS from 0 alone (op 2) over a freshly allocated buffer of
+ * `buffer_bytes` (use one far larger than L2), and writes the sustained
+ * sectors per second.  The visited set of an exploration larger than L2 is
+ * accessed this way (ops 0 and 1: the split and one-call inserts; op 2: the
+ * CAS-first inserts), so these rates bound its HBM regime.
  * Allocates and frees its buffer.  Errors: INVAL, NOMEM, CUDA. */
 int mc_measure_random_access(uint64_t buffer_bytes, uint64_t accesses, int op,
                              double* sectors_per_s, double* ms);

@@ -1,9 +1,10 @@
 // Random-access roofline of the device: the rate at which independent random
-// 32-byte sector reads (and read + atomicCAS) can be served from a buffer far
-// larger than L2.  The visited set of a large exploration is accessed this
-// way -- one random 32-byte bucket read per generated successor, one CAS per
-// new state -- so this, not the streaming copy bandwidth, is the ceiling of
-// the HBM-bound regime.  A measurement utility: it allocates its buffer with
+// 32-byte sector reads (read + atomicCAS, or atomicCAS alone) can be served
+// from a buffer far larger than L2.  The visited set of a large exploration
+// is accessed this way -- one random 32-byte bucket read per generated
+// successor and one CAS per new state (split and one-call inserts), or one
+// CAS per generated successor (CAS-first inserts) -- so this, not the
+// streaming copy bandwidth, is the ceiling of the HBM-bound regime.  A measurement utility: it allocates its buffer with
 // cudaMalloc and frees it before returning.
 #include <cstdint>
 
@@ -20,8 +21,9 @@ __device__ __forceinline__ uint64_t rr_mix(uint64_t z) {
 
 // Each thread performs `per_thread` accesses (four in flight at a time) to pseudo-random 32-byte sectors
 // (a splitmix64 sequence per thread); op 0 reads the sector, op 1 reads it and
-// CASes its first word.  The xor of what was read goes to `sink` so nothing
-// is optimised away.
+// CASes its first word, op 2 only CASes its first word from 0 (the first
+// probe of the CAS-first inserts).  The xor of what was read goes to `sink`
+// so nothing is optimised away.
 __global__ void random_sector_kernel(uint64_t* buf, uint64_t sectors, uint32_t per_thread, int op,
                                      unsigned long long* sink) {
   constexpr int kUnroll = 4;  // independent accesses in flight per thread
@@ -35,8 +37,15 @@ __global__ void random_sector_kernel(uint64_t* buf, uint64_t sectors, uint32_t p
       state += 0x9E3779B97F4A7C15ull;
       sec[u] = rr_mix(state) % sectors;
       const ulonglong2* p = reinterpret_cast<const ulonglong2*>(buf + sec[u] * 4);
-      a[u] = __ldcg(p);
-      b[u] = __ldcg(p + 1);
+      if (op == 2) {
+        a[u] = make_ulonglong2(
+            atomicCAS(reinterpret_cast<unsigned long long*>(buf + sec[u] * 4), 0ull, (unsigned long long)state | 1ull),
+            0ull);
+        b[u] = make_ulonglong2(0ull, 0ull);
+      } else {
+        a[u] = __ldcg(p);
+        b[u] = __ldcg(p + 1);
+      }
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
@@ -53,7 +62,7 @@ __global__ void random_sector_kernel(uint64_t* buf, uint64_t sectors, uint32_t p
 
 extern "C" int mc_measure_random_access(uint64_t buffer_bytes, uint64_t accesses, int op,
                                         double* sectors_per_s, double* ms_out) {
-  if (!sectors_per_s || buffer_bytes < (1u << 20) || accesses == 0 || op < 0 || op > 1)
+  if (!sectors_per_s || buffer_bytes < (1u << 20) || accesses == 0 || op < 0 || op > 2)
     return MC_ERR_INVAL;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||

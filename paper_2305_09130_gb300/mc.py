@@ -491,8 +491,8 @@ def mc_check_noalloc(spec, T: int, prune: bool = True, early_exit: bool = True, 
 
 
 def mc_measure_random_access(buffer_bytes: int, accesses: int, op: int = 0) -> dict:
-    """Random 32-byte sector reads (op 0) or read + CAS (op 1) per second over
-    a buffer of buffer_bytes on the current device."""
+    """Random 32-byte sector reads (op 0), read + CAS (op 1) or CAS alone
+    (op 2) per second over a buffer of buffer_bytes on the current device."""
     rate = C.c_double()
     ms = C.c_double()
     rc = load().mc_measure_random_access(int(buffer_bytes), int(accesses), int(op), C.byref(rate),

@@ -292,3 +292,12 @@ def test_pe_queries_fail_loudly_without_a_gpu(lib):
     with pytest.raises(mc.MCError) as e:
         mc.mc_pe_count_states(m)
     assert e.value.code == mc.MC_ERR_CUDA
+
+
+def test_random_access_measurement_checks_its_arguments(lib):
+    """The measurement utility refuses an unknown operation and a buffer
+    below 1 MiB before it touches the device."""
+    for buffer_bytes, op in ((64 << 20, 3), (64 << 20, -1), (1 << 19, 0)):
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_measure_random_access(buffer_bytes, 1000, op)
+        assert e.value.code == mc.MC_ERR_INVAL
