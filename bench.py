@@ -493,6 +493,9 @@ def measure_single(args, name: str, steps: int, warmup: int, device, stream, loc
     # staging), query, read results, destroy; the library's own allocator and
     # no kernel timing
     e2e_opts = mc.mc_options_default(search=args.mode, prune=args.prune, **chosen)
+    retention = int(args.pool_retention_gib * (1 << 30)) if args.pool_retention_gib else None
+    if retention is not None:
+        mc.mc_set_pool_retention(retention)
     e2e_s = []
     h2d = d2h = 0
     for k in range(steps):
@@ -512,6 +515,8 @@ def measure_single(args, name: str, steps: int, warmup: int, device, stream, loc
         assert r2["t_min"] == r["t_min"]
     e2e_total = reduce_scalar(sum(e2e_s), "max", device)
     e2e_value = states_all / e2e_total
+    if retention is not None:
+        mc.mc_set_pool_retention(1 << 30)
     mc.mc_release_cached()
 
     line = {
@@ -536,7 +541,8 @@ def measure_single(args, name: str, steps: int, warmup: int, device, stream, loc
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // steps,
                 "d2h_bytes_per_step": d2h // steps,
-                "ms_per_step": 1000.0 * e2e_total / steps},
+                "ms_per_step": 1000.0 * e2e_total / steps,
+                "pool_retention_bytes": retention if retention is not None else 1 << 30},
         "gpu_launches": gpu_launches,
         "clocks": clocks,
         "wall_s_timed_region": wall,
@@ -1057,6 +1063,10 @@ def main(argv=None):
     p.add_argument("--mode", choices=["single", "lower", "bisect"], default="lower")
     p.add_argument("--prune", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--pool-retention-gib", type=float, default=64.0,
+                   help="end-to-end arm: device memory the library's pool keeps between models "
+                        "(mc_set_pool_retention, as a server creating and destroying models sets it; "
+                        "0 = the library default, 1 GiB)")
     p.add_argument("--no-random-roofline", action="store_true")
     p.add_argument("--no-extras", action="store_true",
                    help="default run: skip the secondary, batched and served objects")

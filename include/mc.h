@@ -524,10 +524,20 @@ int mc_check_noalloc(const mc_model_desc* desc, uint64_t T, uint32_t prune, uint
                      void* stream, mc_check_result* out);
 
 /* Give the library's cached memory back: the freed device blocks kept in its
- * stream-ordered pools (up to 1 GiB per device) and the pinned host blocks
- * kept for reuse (up to 64 MiB).  Models in use keep theirs.  Safe at any
- * time, also without a device.  Returns MC_OK. */
+ * stream-ordered pools (up to the retention below, per device) and the
+ * pinned host blocks kept for reuse (up to 64 MiB).  Models in use keep
+ * theirs.  Safe at any time, also without a device.  Returns MC_OK. */
 int mc_release_cached(void);
+
+/* How many bytes of freed device memory each of the library's pools keeps
+ * for later models instead of giving them back to the driver at the next
+ * synchronisation (cudaMemPoolAttrReleaseThreshold): 1 GiB by default.  A
+ * caller that creates and destroys large models in a loop (a server) raises
+ * it so that a model's buffers are not unmapped and mapped again each time.
+ * Applies to the pools that exist and to those made later; memory above the
+ * new value is given back at the pool's next synchronisation.  Not a step of
+ * the method.  Errors: CUDA when a pool refuses the value. */
+int mc_set_pool_retention(uint64_t bytes);
 
 /* Static name of an error code. */
 const char* mc_strerror(int code);

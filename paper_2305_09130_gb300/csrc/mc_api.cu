@@ -62,11 +62,13 @@ void* pinned_alloc(size_t bytes) {
 }
 
 // The library's stream-ordered device pool of each device, made on first
-// use; freed blocks stay in it for reuse up to 1 GiB (the process's other
-// allocations and pools are left alone).
+// use; freed blocks stay in it for reuse up to the retention (1 GiB unless
+// mc_set_pool_retention changed it; the process's other allocations and
+// pools are left alone).
 namespace {
 std::mutex g_pool_mu;
 cudaMemPool_t g_pools[64] = {};
+uint64_t g_pool_keep = 1ull << 30;  // guarded by g_pool_mu
 }  // namespace
 
 cudaMemPool_t device_pool(int dev) {
@@ -83,11 +85,26 @@ cudaMemPool_t device_pool(int dev) {
       cudaGetLastError();
       return nullptr;
     }
-    uint64_t keep = 1ull << 30;
+    uint64_t keep = g_pool_keep;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     g_pools[dev] = pool;
   }
   return g_pools[dev];
+}
+
+int set_pool_retention(uint64_t bytes) {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  g_pool_keep = bytes;
+  int rc = MC_OK;
+  for (cudaMemPool_t pool : g_pools) {
+    if (!pool) continue;
+    uint64_t keep = bytes;
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+      cudaGetLastError();
+      rc = MC_ERR_CUDA;
+    }
+  }
+  return rc;
 }
 
 void release_cached() {
@@ -1380,6 +1397,8 @@ int mc_release_cached(void) {
   mc::release_cached();
   return MC_OK;
 }
+
+int mc_set_pool_retention(uint64_t bytes) { return mc::set_pool_retention(bytes); }
 
 const char* mc_strerror(int code) {
   switch (code) {

@@ -17,5 +17,6 @@ cudaMemPool_t device_pool(int device);
 
 // Trim every device pool and free the cached pinned blocks.
 void release_cached();
+int set_pool_retention(uint64_t bytes);
 
 }  // namespace mc

@@ -242,6 +242,7 @@ def load(build: bool = True):
             "mc_trace_free": (None, [P]),
             "mc_strerror": (C.c_char_p, [C.c_int]),
             "mc_release_cached": (C.c_int, []),
+            "mc_set_pool_retention": (C.c_int, [C.c_uint64]),
             "mc_last_error": (C.c_char_p, [P]),
         }
         for name, (res, args) in sig.items():
@@ -257,6 +258,14 @@ def mc_release_cached():
     rc = load(build=False).mc_release_cached()
     if rc != MC_OK:
         raise MCError(rc, "mc_release_cached")
+
+
+def mc_set_pool_retention(nbytes: int):
+    """Bytes of freed device memory the library's pools keep for later models
+    (1 GiB by default); see mc_set_pool_retention in mc.h."""
+    rc = load(build=False).mc_set_pool_retention(int(nbytes))
+    if rc != MC_OK:
+        raise MCError(rc, "mc_set_pool_retention")
 
 
 def mc_strerror(code: int) -> str:

@@ -204,6 +204,12 @@ def test_release_cached_is_safe_without_a_device(lib):
     mc.mc_release_cached()
 
 
+def test_pool_retention_is_set_without_a_device(lib):
+    # no pool exists yet: the value is kept for the pools made later
+    mc.mc_set_pool_retention(8 << 30)
+    mc.mc_set_pool_retention(1 << 30)
+
+
 def test_strerror(lib):
     assert mc.mc_strerror(mc.MC_ERR_TABLE_FULL).startswith("visited set full")
     assert mc.mc_strerror(-99) == "unknown error"
