@@ -271,15 +271,22 @@ def test_threshold_zero_keeps_only_selects(mc, engine):
     assert r == {"holds": True, "states": 1 + spec.a + spec.a * spec.b, "levels": 3}
 
 
-def test_table_full_is_reported(mc):
-    model = make(mc, W.c1(FREE), table_log2=3, max_probes=2, engine="level")
-    with pytest.raises(mc.MCError) as e:
-        mc.mc_count_states(model)
-    assert e.value.code == mc.MC_ERR_TABLE_FULL
+@pytest.mark.parametrize("key_bits", [0, 128])
+@pytest.mark.parametrize("scheme", ["split", "one_call", "cas_first", "cas_clear"])
+def test_table_full_is_reported(mc, scheme, key_bits):
+    """A visited set of 8 slots with a 2-bucket probe limit fills at once with
+    every insert; the next query on the same model reports it again."""
+    model = make(mc, W.c1(FREE).with_key_bits(key_bits) if key_bits else W.c1(FREE), table_log2=3,
+                 max_probes=2, engine="level", probe_scheme=scheme)
+    for _ in range(2):
+        with pytest.raises(mc.MCError) as e:
+            mc.mc_count_states(model)
+        assert e.value.code == mc.MC_ERR_TABLE_FULL
 
 
-def test_frontier_overflow_is_reported(mc):
-    model = make(mc, W.c1(FREE), log_capacity=100, engine="level")
+@pytest.mark.parametrize("scheme", ["split", "cas_first"])
+def test_frontier_overflow_is_reported(mc, scheme):
+    model = make(mc, W.c1(FREE), log_capacity=100, engine="level", probe_scheme=scheme)
     with pytest.raises(mc.MCError) as e:
         mc.mc_count_states(model)
     assert e.value.code == mc.MC_ERR_FRONTIER
