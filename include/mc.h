@@ -186,7 +186,9 @@ typedef struct {
   uint32_t unit_threads;        /* CONFIG engine: threads of the block that
                                    explores one configuration, 64..512, a
                                    multiple of 32; 0 = from the model's
-                                   widest configuration level                */
+                                   widest configuration level, and one warp
+                                   per configuration when that level's lanes
+                                   fit a warp (P <= 4 under GREEDY)          */
   uint32_t stage_chunk;         /* LEVEL engine: winners a warp stages in
                                    shared memory before it reserves frontier-
                                    log space and copies them out: 64 to 192,
@@ -250,7 +252,11 @@ typedef struct {
                             resolved); with CONFIG, table_slots is the
                             shared-memory table of one block and the log
                             holds one segment per configuration           */
-  uint32_t unit_threads; /* CONFIG: threads per block (0 with LEVEL)       */
+  uint32_t unit_threads; /* CONFIG: threads that explore one configuration:
+                            32 when one warp does (its widest level x lanes
+                            per state fits a warp and mc_options.
+                            unit_threads is 0), else the block's threads;
+                            0 with LEVEL                                  */
   uint64_t unit_width;   /* bound on one configuration's widest level      */
 } mc_layout;
 

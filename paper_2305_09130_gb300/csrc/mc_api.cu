@@ -207,6 +207,7 @@ struct mc_model {
   uint32_t cfg_wcap = 0, cfg_tsize = 0;
   int cfg_threads = 0, cfg_grid = 0, cfg_grid_max = 0;
   size_t cfg_smem = 0;
+  bool cfg_warp = false;  // one warp per configuration (widest level x lanes per state <= 32)
   // device state
   bool reserved = false;
   int device = -1;
@@ -410,8 +411,13 @@ int size_buffers(mc_model* m) {
     m->cfg_wcap = w;
     m->cfg_tsize = 2 * w;  // at most half full
     m->table_slots = m->cfg_tsize;
-    // enough threads for the widest level's lanes in one round, 64..512
-    if (m->opt.unit_threads) {
+    // a warp per configuration when its widest level's lanes fit one warp
+    // (unless the caller asks for blocks of unit_threads); else enough
+    // threads for the widest level's lanes in one round, 64..512
+    m->cfg_warp = !m->opt.unit_threads && m->unit_width * m->tile <= mc::kCfgWarpLanes;
+    if (m->cfg_warp) {
+      m->cfg_threads = (int)mc::kCfgWarpBlockThreads;
+    } else if (m->opt.unit_threads) {
       m->cfg_threads = (int)m->opt.unit_threads;
     } else {
       const uint64_t want = m->unit_width * m->tile;
@@ -517,7 +523,9 @@ int reserve(mc_model* m) {
     // a block per configuration (threads from size_buffers), shared memory
     // for two frontiers and two tables; as many blocks as fit, at most one
     // per configuration
-    m->cfg_smem = mc::cfg_smem_bytes((int)m->key_words, m->cfg_wcap, m->cfg_tsize);
+    // (warp units use no dynamic shared memory: a launch of warp units only
+    // is sized by its threads, a warp per configuration)
+    m->cfg_smem = m->cfg_warp ? 0 : mc::cfg_smem_bytes((int)m->key_words, m->cfg_wcap, m->cfg_tsize);
     if (mc::cfg_occupancy((int)m->key_words, m->cfg_threads, m->cfg_smem, &bps) || bps < 1) {
       m->last_err = "occupancy query failed (configuration engine)";
       cudaGetLastError();
@@ -525,7 +533,8 @@ int reserve(mc_model* m) {
     }
     if (m->opt.blocks_per_sm) bps = std::min<int>(bps, (int)m->opt.blocks_per_sm);
     m->cfg_grid_max = sms * bps;
-    m->cfg_grid = (int)std::min<uint64_t>(ab, (uint64_t)sms * bps);
+    const uint64_t per_block = m->cfg_warp ? (uint64_t)m->cfg_threads / 32 : 1;
+    m->cfg_grid = (int)std::min<uint64_t>((ab + per_block - 1) / per_block, (uint64_t)sms * bps);
   }
 
   const uint64_t key_bytes = 8ull * m->key_words;
@@ -701,10 +710,16 @@ int enqueue_cfg_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t del
   Q.trace = m->d_trace;
   Q.tmin_out = tmin_out;
   Q.order = m->d_order;
-  L.n_units = (uint64_t)m->a * m->b;
-  L.next = &Q.ctrl->units_next;
   L.wcap = m->cfg_wcap;
   L.tsize = m->cfg_tsize;
+  if (m->cfg_warp) {  // every block serves warp units
+    L.n_wunits = (uint64_t)m->a * m->b;
+    L.wnext = &Q.ctrl->units_next;
+    L.warp_blocks = (uint32_t)m->cfg_grid;
+  } else {
+    L.n_units = (uint64_t)m->a * m->b;
+    L.next = &Q.ctrl->units_next;
+  }
   MC_CUDA(m, cudaMemsetAsync(Q.levels, 0, 16ull * (m->max_level + 2), m->stream));
   if (m->opt.timing) {
     const int rc_ = make_events(m);
@@ -728,17 +743,28 @@ int enqueue_cfg_pair(mc_model* m, bool prune, bool early_exit, bool refine) {
   MC_CUDA(m, cudaMemsetAsync(cfg_levels_at(m, 1), 0, 2 * 16ull * (m->max_level + 2), m->stream));
   mc::CfgLaunch L{};
   L.passes = m->d_pair_pass + 2 * ((prune ? 2 : 0) + (early_exit ? 1 : 0));  // descriptors per option pair
-  L.units = refine ? m->d_pair_units : m->d_pair_units + 2 * ab;
-  L.n_units = refine ? 2 * ab : ab;
-  L.next = &ctrl_at(m, 2)->units_next;  // the launch's unit counter (the header starts at zero)
+  const uint64_t* units = refine ? m->d_pair_units : m->d_pair_units + 2 * ab;
+  const uint64_t n_units = refine ? 2 * ab : ab;
+  uint32_t* next = &ctrl_at(m, 2)->units_next;  // the launch's unit counter (the header starts at zero)
   L.wcap = m->cfg_wcap;
   L.tsize = m->cfg_tsize;
+  const uint64_t per_block = m->cfg_warp ? (uint64_t)m->cfg_threads / 32 : 1;
+  const int grid = (int)std::min<uint64_t>((uint64_t)m->cfg_grid_max, (n_units + per_block - 1) / per_block);
+  if (m->cfg_warp) {
+    L.wunits = units;
+    L.n_wunits = n_units;
+    L.wnext = next;
+    L.warp_blocks = (uint32_t)grid;
+  } else {
+    L.units = units;
+    L.n_units = n_units;
+    L.next = next;
+  }
   if (m->opt.timing) {
     const int rc_ = make_events(m);
     if (rc_) return rc_;
     MC_CUDA(m, cudaEventRecord(m->ev[2], m->stream));
   }
-  const int grid = (int)std::min<uint64_t>((uint64_t)m->cfg_grid_max, L.n_units);
   MC_CUDA(m, mc::launch_cfg((int)m->key_words, grid, m->cfg_threads, m->cfg_smem, L, m->stream));
   if (m->opt.timing) {
     MC_CUDA(m, cudaEventRecord(m->ev[3], m->stream));
@@ -1097,7 +1123,8 @@ int mc_model_layout(const mc_model* m, mc_layout* out) {
   out->engine = m->engine;
   out->log_tag_bits = m->engine == MC_ENGINE_CONFIG ? 0 : log_tag_bits(m);
   out->unit_width = m->unit_width;
-  out->unit_threads = m->engine == MC_ENGINE_CONFIG ? (uint32_t)m->cfg_threads : 0;
+  // threads that explore one configuration: 32 for warp units
+  out->unit_threads = m->engine != MC_ENGINE_CONFIG ? 0 : m->cfg_warp ? 32u : (uint32_t)m->cfg_threads;
   return MC_OK;
 }
 

@@ -861,6 +861,7 @@ int breserve_cfg(mc_batch* b) {
   b->cfg_wcap = 32;
   for (const mc::CfgModelPrep& M : b->cm) {
     units += M.ab;
+    if (mc::cfg_warp_model(M, b->opt)) continue;  // a warp per configuration: no block shape
     b->cfg_threads = std::max<int>(b->cfg_threads, (int)M.threads);
     b->cfg_wcap = std::max(b->cfg_wcap, M.wcap);
   }

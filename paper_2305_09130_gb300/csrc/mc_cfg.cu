@@ -294,6 +294,234 @@ __device__ void explore_unit(const CfgPass& Q, uint32_t cfg, uint64_t T, K* fron
   }
 }
 
+// ------------------------------------------------------------------ warp units
+// A configuration whose widest level fits one warp (width bound x lanes per
+// state <= 32) is explored by a single warp, its level in registers: state
+// s of the level is held by lanes [s*g, s*g + g), every proposal of the level
+// is in the warp, so duplicates are found exactly by matching the proposed
+// keys across the warp (the lowest lane of equal keys wins), and the winners,
+// ranked by a ballot, become the next level.  No table, no shared counter, no
+// block barrier; the same counts, records, log entries and early exit as
+// explore_unit.
+
+// Position of set bit number k (from 0) of m; k < popc(m).
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t k) {
+  uint32_t pos = 0, c;
+  c = __popc(m & 0xFFFFu);
+  if (k >= c) { k -= c; pos += 16; m >>= 16; }
+  c = __popc(m & 0xFFu);
+  if (k >= c) { k -= c; pos += 8; m >>= 8; }
+  c = __popc(m & 0xFu);
+  if (k >= c) { k -= c; pos += 4; m >>= 4; }
+  c = __popc(m & 0x3u);
+  if (k >= c) { k -= c; pos += 2; m >>= 2; }
+  c = m & 1u;
+  if (k >= c) pos += 1;
+  return pos;
+}
+
+template <class K>
+__device__ __forceinline__ K shfl_key(K k, uint32_t src) {
+  if (sizeof(K) == 8) return (K)__shfl_sync(0xffffffffu, (unsigned long long)k, src);
+  const uint64_t lo = __shfl_sync(0xffffffffu, (unsigned long long)KeyOps<K>::lo(k), src);
+  const uint64_t hi = __shfl_sync(0xffffffffu, (unsigned long long)KeyOps<K>::hi(k), src);
+  return (K)(((u128)hi << 64) | lo);
+}
+
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <class K, class C>
+__device__ uint32_t explore_unit_warp(const CfgPass& Q, uint32_t cfg, uint64_t T) {
+  const uint32_t P = Q.p.P, n_bits = Q.p.n_bits, b = Q.p.b;
+  const uint64_t n_mask = Q.p.n_mask;
+  const bool greedy = Q.p.rule == MC_GREEDY, prune = Q.prune != 0, early = Q.early_exit != 0;
+  const uint32_t* costp = Q.p.cost;
+  const uint32_t* speedp = Q.p.speed;
+  void* const log_keys = Q.log_keys;
+  uint32_t* const log_par = Q.log_par;
+  uint64_t* const levels = Q.levels;
+  Ctrl* const ctrl = Q.ctrl;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t g = Q.group;
+  const uint32_t spw = 32u / g;  // states the warp holds
+  const uint32_t c = lane & (g - 1);
+  const uint32_t my = lane / g;
+  const uint32_t i = cfg / b, j = cfg % b;
+  const uint32_t N = __ldg(Q.p.N + cfg);
+  const bool unit_ok = c < P;
+  const C t_c = unit_ok ? (C)((uint64_t)__ldg(costp + cfg) * __ldg(speedp + c)) : (C)0;
+  const C Tc = T < (uint64_t)(C)~(C)0 ? (C)T : (C)~(C)0;
+  constexpr C kNoneC = (C)~(C)0;
+  const uint32_t c_shift = (P - 1 - (unit_ok ? c : 0)) * n_bits;
+  const K one_c = (K)1 << c_shift;
+  const bool log_on = Q.want_witness != 0;
+  const uint64_t seg0 = log_on ? Q.seg[cfg] : 0, seg1 = log_on ? Q.seg[cfg + 1] : 0;
+  const K key2 = ((K)(i + 1) << Q.p.wg_shift) | ((K)(j + 1) << Q.p.ts_shift);
+  if (log_on && lane == 0) {
+    log_store<K>(log_keys, seg0, key2);
+    log_par[seg0] = kNoParent;
+  }
+  K key = key2;  // the state of this lane's group (valid for my < W)
+  uint64_t lvl_base = seg0;
+  uint32_t W = 1, L = 2, deepest = 2, err = 0;
+  uint32_t cut = kNoLevel;  // least level known to violate, read one level before it is used
+  uint64_t vmin = kNone;
+  while (L < 2 + N) {
+    if (early && cut <= L) break;  // deeper widths are not counted
+    const uint32_t sc = early ? ld_relaxed_u32(&ctrl->stop_c) : 0u;
+    const bool valid = my < W;
+    C clk = 0;
+    if (valid && unit_ok) clk = (C)field(key, c_shift, n_mask) * t_c;
+    C mx = clk, mn = (valid && unit_ok) ? clk : kNoneC;
+    bool ok = valid && unit_ok;
+    if (greedy) {
+      group_minmax<true>(mx, mn, g);
+      ok = ok && clk == mn;
+    } else {
+      group_minmax<false>(mx, mn, g);
+    }
+    const C nclk = clk + t_c;
+    const C st = nclk > mx ? nclk : mx;  // model time of the successor
+    if (prune && st > Tc) ok = false;
+    const K succ = key + one_c;
+    // every proposal of the level is in the warp: of equal keys the lowest
+    // lane wins, the others are its duplicates
+    const uint32_t am = __ballot_sync(0xffffffffu, ok);
+    bool won = false;
+    if (ok) {
+      uint32_t peers = __match_any_sync(am, (unsigned long long)KeyOps<K>::lo(succ));
+      if (sizeof(K) == 16) peers &= __match_any_sync(am, (unsigned long long)KeyOps<K>::hi(succ));
+      won = lane == (uint32_t)(__ffs(peers) - 1);
+    }
+    const uint32_t wm = __ballot_sync(0xffffffffu, won);
+    const uint32_t Wn = __popc(wm);
+    if (won && log_on) {
+      const uint64_t at = lvl_base + W + __popc(wm & ((1u << lane) - 1u));
+      if (at < seg1) {
+        log_store<K>(log_keys, at, succ);
+        log_par[at] = (uint32_t)(lvl_base + my);
+      } else {
+        err = (uint32_t)MC_ERR_FRONTIER;
+      }
+    }
+    // Step 2: a terminal winner with time <= T violates G(FIN -> time > T)
+    if (L + 1 == 2 + N) vmin = warp_min_u64((won && (uint64_t)st <= T) ? (uint64_t)st : kNone);
+    if (Wn > spw) {  // cannot happen when the width bound holds
+      err = (uint32_t)MC_ERR_FRONTIER;
+      break;
+    }
+    if (lane == 0 && Wn) atomicAdd(reinterpret_cast<unsigned long long*>(levels + 2 * (L + 1)), (unsigned long long)Wn);
+    // the next level: state r from winner number r
+    const uint32_t r = my < Wn ? my : 0u;
+    key = shfl_key<K>(succ, Wn ? nth_set_bit(wm, r) : 0u);
+    cut = sc ? ~sc : kNoLevel;
+    lvl_base += W;
+    W = Wn;
+    ++L;
+    if (W == 0) break;
+    deepest = L;
+  }
+  // (uniform: the break above and a lane's log overflow)
+  const uint32_t errs = __ballot_sync(0xffffffffu, err != 0);
+  if (errs) return __shfl_sync(0xffffffffu, err, __ffs(errs) - 1);
+  // this configuration's violating terminals (all at level 2 + N, held by
+  // the warp): the smallest key of the least time, and its log index
+  uint64_t whi = kNone, wlo = kNone;
+  uint32_t widx = 0;
+  if (vmin != kNone) {
+    if (lane == 0 && early) atomicMax(&ctrl->stop_c, ~(2u + N));
+    const bool mine = my < W && c == 0;
+    uint64_t t = kNone;
+    if (mine) {
+      const uint64_t c0 = __ldg(costp + cfg);
+      t = 0;
+      for (uint32_t u = 0; u < P; ++u) {
+        const uint64_t tu = (uint64_t)field(key, (P - 1 - u) * n_bits, n_mask) * c0 * __ldg(speedp + u);
+        t = tu > t ? tu : t;
+      }
+    }
+    const bool cand = mine && t == vmin;
+    whi = warp_min_u64(cand ? (uint64_t)KeyOps<K>::hi(key) : kNone);
+    const bool cand_hi = cand && (uint64_t)KeyOps<K>::hi(key) == whi;
+    wlo = warp_min_u64(cand_hi ? (uint64_t)KeyOps<K>::lo(key) : kNone);
+    const uint32_t wl = __ballot_sync(0xffffffffu, cand_hi && (uint64_t)KeyOps<K>::lo(key) == wlo);
+    widx = (uint32_t)(lvl_base + (uint32_t)(__ffs(wl) - 1) / g);
+  }
+  if (lane == 0) {
+    CfgRec rec;
+    rec.vpack = vmin != kNone ? pack_tij(vmin, i, j) : kNone;
+    rec.wkey_lo = vmin != kNone ? wlo : kNone;
+    rec.wkey_hi = vmin != kNone ? whi : kNone;
+    rec.widx = vmin != kNone ? widx : 0u;
+    rec.deepest = deepest;
+    Q.rec[cfg] = rec;
+  }
+  return 0;
+}
+
+// The pass header from the combined records (one thread): counts, first
+// violating level, minima, the witness's trace, the published minimum.
+template <class K>
+__device__ void epilogue_publish(const CfgPass& Q, uint64_t T, uint32_t stop, uint32_t last, uint64_t e_best,
+                                 uint64_t e_wpack, uint64_t e_sum) {
+  const Params& p = Q.p;
+  const uint32_t ab = p.a * p.b;
+  Ctrl* ctrl = Q.ctrl;
+  const uint64_t wpack = stop != kNoLevel ? e_wpack : kNone;
+  const uint64_t best = Q.early_exit ? wpack : e_best;
+  Q.levels[0] = 1;
+  Q.levels[2] = p.a;
+  Q.levels[4] = (uint64_t)ab;
+  ctrl->T = T;
+  ctrl->levels = last + 1;
+  ctrl->states = 1 + (uint64_t)p.a + ab + e_sum;
+  ctrl->stop_level = stop != kNoLevel ? stop : 0u;
+  ctrl->best_pack = best;
+  ctrl->wpack = wpack;
+  if (Q.tmin_out && best != kNone) *Q.tmin_out = pack_time(best);
+  if (!Q.want_witness || stop == kNoLevel) return;
+  // witness: the smallest key of the least (time, i, j) at the first
+  // violating level, found by its configuration's block; trace s0 -> it
+  const uint32_t wi = pack_i(wpack), wj = pack_j(wpack);
+  const uint32_t wcfg = wi * p.b + wj;
+  const uint64_t klo = __ldcg(&Q.rec[wcfg].wkey_lo), khi = __ldcg(&Q.rec[wcfg].wkey_hi);
+  uint64_t idx = __ldcg(&Q.rec[wcfg].widx);
+  ctrl->wkey_lo = klo;
+  ctrl->wkey_hi = sizeof(K) == 16 ? khi : 0;
+  ctrl->widx = idx;
+  for (uint32_t l = stop; l >= 2; --l) {
+    const K key = KeyOps<K>::load(Q.log_keys, idx);
+    Q.trace[2 * l] = KeyOps<K>::lo(key);
+    Q.trace[2 * l + 1] = KeyOps<K>::hi(key);
+    if (l == 2) break;
+    idx = __ldcg(Q.log_par + idx);
+    if (idx >= Q.seg[wcfg + 1] || idx < Q.seg[wcfg]) {  // cannot happen when the log is intact
+      set_error(ctrl, MC_ERR_FRONTIER);
+      return;
+    }
+  }
+  const K k1 = (K)(wi + 1) << p.wg_shift;  // level 1: (i+1, 0, 0...0); level 0: s0
+  Q.trace[2] = KeyOps<K>::lo(k1);
+  Q.trace[3] = KeyOps<K>::hi(k1);
+  Q.trace[0] = 0;
+  Q.trace[1] = 0;
+  ctrl->witness_level = stop;
+  ctrl->trace_len = stop + 1;
+}
+
 // The block that finished a pass's last configuration: combine the
 // configurations' records and the level widths into the pass header, write
 // the trace of the witness, publish the minimum for a chained pass.
@@ -335,46 +563,101 @@ __device__ void cfg_epilogue(const CfgPass& Q, uint64_t T, CfgShared& S) {
   atomicAdd(&S.e_sum, (unsigned long long)part);
   __syncthreads();
   if (tid != 0) return;
-  const uint64_t wpack = stop != kNoLevel ? (uint64_t)S.e_wpack : kNone;
-  const uint64_t best = Q.early_exit ? wpack : (uint64_t)S.e_best;
-  Q.levels[0] = 1;
-  Q.levels[2] = p.a;
-  Q.levels[4] = (uint64_t)ab;
-  ctrl->T = T;
-  ctrl->levels = last + 1;
-  ctrl->states = 1 + (uint64_t)p.a + ab + S.e_sum;
-  ctrl->stop_level = stop != kNoLevel ? stop : 0u;
-  ctrl->best_pack = best;
-  ctrl->wpack = wpack;
-  if (Q.tmin_out && best != kNone) *Q.tmin_out = pack_time(best);
-  if (!Q.want_witness || stop == kNoLevel) return;
-  // witness: the smallest key of the least (time, i, j) at the first
-  // violating level, found by its configuration's block; trace s0 -> it
-  const uint32_t wi = pack_i(wpack), wj = pack_j(wpack);
-  const uint32_t wcfg = wi * p.b + wj;
-  const uint64_t klo = __ldcg(&Q.rec[wcfg].wkey_lo), khi = __ldcg(&Q.rec[wcfg].wkey_hi);
-  uint64_t idx = __ldcg(&Q.rec[wcfg].widx);
-  ctrl->wkey_lo = klo;
-  ctrl->wkey_hi = sizeof(K) == 16 ? khi : 0;
-  ctrl->widx = idx;
-  for (uint32_t l = stop; l >= 2; --l) {
-    const K key = KeyOps<K>::load(Q.log_keys, idx);
-    Q.trace[2 * l] = KeyOps<K>::lo(key);
-    Q.trace[2 * l + 1] = KeyOps<K>::hi(key);
-    if (l == 2) break;
-    idx = __ldcg(Q.log_par + idx);
-    if (idx >= Q.seg[wcfg + 1] || idx < Q.seg[wcfg]) {  // cannot happen when the log is intact
-      set_error(ctrl, MC_ERR_FRONTIER);
-      return;
+  epilogue_publish<K>(Q, T, stop, last, (uint64_t)S.e_best, (uint64_t)S.e_wpack, (uint64_t)S.e_sum);
+}
+
+// The warp that finished a pass's last configuration, when it is a warp
+// unit: the same combination as cfg_epilogue, reduced across the warp.
+template <class K>
+__device__ void cfg_epilogue_warp(const CfgPass& Q, uint64_t T) {
+  const Params& p = Q.p;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t ab = p.a * p.b;
+  if (ld_relaxed_u32(&Q.ctrl->err)) return;
+  uint64_t best = kNone;
+  uint32_t stop = kNoLevel, deep = 2;
+  for (uint32_t cfg = lane; cfg < ab; cfg += 32) {
+    const uint64_t v = __ldcg(&Q.rec[cfg].vpack);
+    const uint32_t d = __ldcg(&Q.rec[cfg].deepest);
+    deep = d > deep ? d : deep;
+    if (v != kNone) {
+      const uint32_t s = 2u + __ldg(p.N + cfg);
+      stop = s < stop ? s : stop;
+      best = v < best ? v : best;
     }
   }
-  const K k1 = (K)(wi + 1) << p.wg_shift;  // level 1: (i+1, 0, 0...0); level 0: s0
-  Q.trace[2] = KeyOps<K>::lo(k1);
-  Q.trace[3] = KeyOps<K>::hi(k1);
-  Q.trace[0] = 0;
-  Q.trace[1] = 0;
-  ctrl->witness_level = stop;
-  ctrl->trace_len = stop + 1;
+  deep = __reduce_max_sync(0xffffffffu, deep);
+  stop = __reduce_min_sync(0xffffffffu, stop);
+  best = warp_min_u64(best);
+  uint64_t wpack = kNone;
+  if (stop != kNoLevel) {
+    for (uint32_t cfg = lane; cfg < ab; cfg += 32) {
+      const uint64_t v = __ldcg(&Q.rec[cfg].vpack);
+      if (v != kNone && 2u + __ldg(p.N + cfg) == stop) wpack = v < wpack ? v : wpack;
+    }
+    wpack = warp_min_u64(wpack);
+  }
+  const uint32_t last = (Q.early_exit && stop != kNoLevel) ? stop : deep;
+  uint64_t part = 0;
+  for (uint32_t l = 3 + lane; l <= last; l += 32) part += __ldcg(Q.levels + 2 * l);
+  const uint64_t sum = warp_sum_u64(part);
+  if (lane == 0) epilogue_publish<K>(Q, T, stop, last, best, wpack, sum);
+}
+
+// Blocks [0, warp_blocks) of a launch: every warp takes warp units until
+// none is left (no block barrier: the warps of a block run independently).
+// (Measured: inlined, the block units' code runs 0.8% slower than without
+// the warp path; kept out of line, 3.7%.)
+template <class K>
+__device__ void warp_role(const CfgLaunch& A) {
+  const uint32_t lane = threadIdx.x & 31u;
+  for (;;) {
+    uint32_t u = 0;
+    if (lane == 0) u = atomicAdd(A.wnext, 1u);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    const uint64_t n = A.n_wunits_dev ? (uint64_t)*A.n_wunits_dev : A.n_wunits;
+    if (u >= n) return;
+    const uint64_t code = A.wunits ? __ldg(A.wunits_rev ? A.wunits - u : A.wunits + u) : 0ull;
+    const CfgPass& Q = A.wunits ? A.passes[code >> 32] : A.one;
+    const uint32_t cfg = A.wunits ? (uint32_t)code : __ldg(Q.order + u);
+    // the threshold, as for a block unit
+    unsigned long long t = 0;
+    uint32_t skip = 0;
+    if (lane == 0) {
+      t = Q.T;
+      if (Q.T_src) t = ld_relaxed_u64(Q.T_src) + (uint64_t)Q.T_delta;
+      if (Q.prev) {
+        const Ctrl* q = Q.prev;
+        if (ld_relaxed_u32(&q->err) || ld_relaxed_u32(&q->skipped) || ld_relaxed_u32(&q->stop_level) == 0) skip = 1;
+        else t = pack_time(ld_relaxed_u64(&q->wpack)) - 1;
+      }
+    }
+    t = __shfl_sync(0xffffffffu, t, 0);
+    skip = __shfl_sync(0xffffffffu, skip, 0);
+    if (!skip) {
+      const uint32_t err = Q.p.clk32 ? explore_unit_warp<K, uint32_t>(Q, cfg, t)
+                                     : explore_unit_warp<K, uint64_t>(Q, cfg, t);
+      if (lane == 0 && err) set_error(Q.ctrl, (int)err);
+    }
+    // completion, as for a block unit: the warp that finishes the pass's
+    // last configuration combines the pass
+    uint32_t last = 0;
+    if (lane == 0) {
+      __threadfence();
+      const uint32_t done = atomicAdd(&Q.ctrl->units_done, 1u) + 1;
+      last = done == Q.p.a * Q.p.b;
+      if (last) __threadfence();
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
+      if (skip) {
+        if (lane == 0) Q.ctrl->skipped = 1;
+      } else {
+        cfg_epilogue_warp<K>(Q, t);
+      }
+    }
+    __syncwarp();
+  }
 }
 
 template <class K>
@@ -385,6 +668,10 @@ __global__ void __launch_bounds__(kCfgMaxThreads) cfg_kernel(const __grid_consta
   K* front1 = front0 + A.wcap;
   K* tab0 = front1 + A.wcap;
   K* tab1 = tab0 + A.tsize;
+  if (blockIdx.x < A.warp_blocks) {  // a block of warp units (no block barrier below)
+    warp_role<K>(A);
+    return;
+  }
   const uint32_t tid = threadIdx.x, nthr = blockDim.x;
   constexpr uint32_t kWords = sizeof(CfgPass) / 8;
   static_assert(sizeof(CfgPass) % 8 == 0, "CfgPass is copied in 8-byte words");

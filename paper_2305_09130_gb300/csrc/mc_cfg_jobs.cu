@@ -191,7 +191,7 @@ void CfgRun::prepare(const std::vector<CfgModelPrep*>& models, const mc_query* q
   refine = opt.refine != 0;
   std::memset(h_cnt, 0, 256);
   uint32_t n_sim = 0;
-  std::vector<std::pair<uint32_t, uint64_t>> ua, ub;  // (work-groups, unit) for sorting
+  std::vector<std::pair<uint32_t, uint64_t>> ua, ub, wa, wb;  // (work-groups, unit) for sorting
   wcap = 32;
   threads = 64;
   any_min = false;
@@ -199,9 +199,12 @@ void CfgRun::prepare(const std::vector<CfgModelPrep*>& models, const mc_query* q
     CfgModelPrep& M = *models[k];
     const mc_query& q = queries[k];
     const bool mt = q.kind == MC_QUERY_MIN_TIME;
+    const bool warp = cfg_warp_model(M, opt);
     any_min |= mt;
-    wcap = std::max(wcap, M.wcap);
-    threads = std::max(threads, M.threads);
+    if (!warp) {  // blocks are sized for the models they explore
+      wcap = std::max(wcap, M.wcap);
+      threads = std::max(threads, M.threads);
+    }
     uint64_t* scal = d_scal + 2ull * k;
     for (uint32_t s = 0; s < 3; ++s) {
       CfgPass& Q = h_pass[3 * k + s];
@@ -253,11 +256,13 @@ void CfgRun::prepare(const std::vector<CfgModelPrep*>& models, const mc_query* q
     C.n_ctrl = 3;
     C.scal = scal;
     const uint32_t* N = M.params.data();
+    auto& la = warp ? wa : ua;
+    auto& lb = warp ? wb : ub;
     for (uint32_t c : M.order) {
-      ua.push_back({N[c], ((uint64_t)(3 * k) << 32) | c});
+      la.push_back({N[c], ((uint64_t)(3 * k) << 32) | c});
       if (mt) {
-        if (refine) ub.push_back({N[c], ((uint64_t)(3 * k + 1) << 32) | c});
-        ub.push_back({N[c], ((uint64_t)(3 * k + 2) << 32) | c});
+        if (refine) lb.push_back({N[c], ((uint64_t)(3 * k + 1) << 32) | c});
+        lb.push_back({N[c], ((uint64_t)(3 * k + 2) << 32) | c});
       }
     }
   }
@@ -267,19 +272,40 @@ void CfgRun::prepare(const std::vector<CfgModelPrep*>& models, const mc_query* q
   };
   std::stable_sort(ua.begin(), ua.end(), deeper);
   std::stable_sort(ub.begin(), ub.end(), deeper);
+  std::stable_sort(wa.begin(), wa.end(), deeper);
+  std::stable_sort(wb.begin(), wb.end(), deeper);
   n_units_a = ua.size();
   n_units_b = ub.size();
+  n_wunits_a = wa.size();
+  n_wunits_b = wb.size();
+  // pass A's region [0, cap), pass B's [cap, 3 cap): block units from the
+  // start, warp units from the end backwards (a model's configurations are
+  // in one list or the other, so the two never meet)
   for (uint64_t x = 0; x < ua.size(); ++x) h_units[x] = ua[x].second;
   for (uint64_t x = 0; x < ub.size(); ++x) h_units[cap_units + x] = ub[x].second;
+  for (uint64_t x = 0; x < wa.size(); ++x) h_units[cap_units - 1 - x] = wa[x].second;
+  for (uint64_t x = 0; x < wb.size(); ++x) h_units[3 * cap_units - 1 - x] = wb[x].second;
   // counters: [0] next unit of pass A, [1] of pass B, [2] units of A,
-  // [3] units of B, [4] models to clear, [5] min-time models to simulate
+  // [3] units of B, [4] models to clear, [5] min-time models to simulate,
+  // [6] warp units of A, [7] of B, [8] next warp unit of A, [9] of B
   h_cnt[2] = (uint32_t)n_units_a;
   h_cnt[3] = (uint32_t)n_units_b;
   h_cnt[4] = n;
   h_cnt[5] = n_sim;
+  h_cnt[6] = (uint32_t)n_wunits_a;
+  h_cnt[7] = (uint32_t)n_wunits_b;
   walks_max = std::max<uint32_t>(opt.sim_walks, 1);
   tsize = 2 * wcap;
   if (opt.unit_threads) threads = opt.unit_threads;
+  // blocks of warp units: from pass A's count, which depends on the models
+  // only (a replayed graph keeps them while the queries change), and twice
+  // that for pass B (every warp model a min-time query with both checks)
+  const uint64_t wpb = threads / 32;
+  auto blocks = [wpb](uint64_t units) {
+    return (uint32_t)std::min<uint64_t>((units + wpb - 1) / wpb, kCfgMaxWarpBlocks);
+  };
+  wblocks_a = blocks(n_wunits_a);
+  wblocks_b = blocks(2 * n_wunits_a);
 }
 
 cudaError_t CfgRun::enqueue(cudaStream_t st, int grid_a, int grid_b, size_t smem, cudaEvent_t ev0,
@@ -298,11 +324,20 @@ cudaError_t CfgRun::enqueue(cudaStream_t st, int grid_a, int grid_b, size_t smem
   L.next = d_cnt + 0;
   L.wcap = wcap;
   L.tsize = tsize;
-  if ((e = launch_cfg(2, grid_a, threads, smem, L, st))) return e;
+  L.wunits = d_units + cap_units - 1;
+  L.wunits_rev = 1;
+  L.n_wunits_dev = d_cnt + 6;
+  L.wnext = d_cnt + 8;
+  L.warp_blocks = wblocks_a;
+  if ((e = launch_cfg(2, grid_a + (int)wblocks_a, threads, smem, L, st))) return e;
   L.units = d_units + cap_units;
   L.n_units_dev = d_cnt + 3;
   L.next = d_cnt + 1;
-  if ((e = launch_cfg(2, grid_b, threads, smem, L, st))) return e;
+  L.wunits = d_units + 3 * cap_units - 1;
+  L.n_wunits_dev = d_cnt + 7;
+  L.wnext = d_cnt + 9;
+  L.warp_blocks = wblocks_b;
+  if ((e = launch_cfg(2, grid_b + (int)wblocks_b, threads, smem, L, st))) return e;
   if (ev1 && (e = capturing ? cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal) : cudaEventRecord(ev1, st)))
     return e;
   return cudaMemcpyAsync(h_block + result_off, d_block + result_off, result_bytes, cudaMemcpyDeviceToHost, st);

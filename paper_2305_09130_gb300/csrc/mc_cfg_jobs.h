@@ -33,6 +33,11 @@ struct CfgModelPrep {
 // Validate the description and lay the model out (host only).  Errors: as
 // mc_model_create, INVAL when the configuration engine cannot take it.
 int cfg_prepare(const mc_model_desc& d, const mc_options& o, CfgModelPrep& M);
+// One warp per configuration: the widest level's lanes fit a warp and the
+// options leave the block's threads to the library.
+inline bool cfg_warp_model(const CfgModelPrep& M, const mc_options& o) {
+  return !o.unit_threads && M.unit_width * M.group <= kCfgWarpLanes;
+}
 // Point the model at its region (M.region bytes, 256-byte aligned); the
 // caller uploads M.params and M.seg to M.base and M.d_seg.
 void cfg_place(CfgModelPrep& M, uint8_t* base);
@@ -59,6 +64,10 @@ struct CfgRun {
   // set by prepare
   uint32_t n_models = 0, wcap = 32, tsize = 64, threads = 64, walks_max = 1;
   uint64_t n_units_a = 0, n_units_b = 0;
+  // warp units (models whose widest configuration level fits a warp): in
+  // the same unit regions, from their ends backwards; blocks serving them
+  uint64_t n_wunits_a = 0, n_wunits_b = 0;
+  uint32_t wblocks_a = 0, wblocks_b = 0;
   bool refine = true, any_min = false;
 
   uint64_t tables_cap = 0, tables_used = 0;     // model tables carried by the upload

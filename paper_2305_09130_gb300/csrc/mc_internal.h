@@ -180,7 +180,13 @@ struct CfgPass {
 
 // A launch: one pass (`one`), or many passes of many models (`passes`, with
 // `units` listing (pass index << 32 | configuration) in the order blocks
-// take them).  `next` counts the units handed out.
+// take them).  `next` counts the units handed out.  Warp units: the
+// configurations of models whose widest level fits one warp (width bound x
+// lanes per state <= kCfgWarpLanes) are explored by one warp each; blocks
+// [0, warp_blocks) serve them, every warp taking units from `wunits` (same
+// encoding, read backwards from `wunits` when `wunits_rev` is set; a single
+// pass's configurations in `one.order` when null) with `wnext`, and the
+// other blocks serve `units`.
 struct CfgLaunch {
   CfgPass one;
   const CfgPass* passes;
@@ -190,7 +196,16 @@ struct CfgLaunch {
   uint32_t* next;
   uint32_t wcap;          // frontier capacity per level (states), a power of two
   uint32_t tsize;         // shared visited-set slots per level, a power of two
+  const uint64_t* wunits;
+  uint64_t n_wunits;
+  const uint32_t* n_wunits_dev;
+  uint32_t* wnext;
+  uint32_t warp_blocks;
+  uint32_t wunits_rev;
 };
+constexpr uint32_t kCfgWarpLanes = 32;  // a warp unit's widest level x lanes per state
+constexpr uint32_t kCfgWarpBlockThreads = 128;  // blocks of a launch of warp units only
+constexpr uint32_t kCfgMaxWarpBlocks = 1024;     // blocks serving warp units in a run's launch
 
 size_t cfg_smem_bytes(int key_words, uint32_t wcap, uint32_t tsize);
 int cfg_occupancy(int key_words, int threads, size_t smem, int* blocks_per_sm);

@@ -236,6 +236,35 @@ def test_c3_star_full(mc):
     assert got["level"] == first + 2
 
 
+def warp_eligible_models():
+    out = [W.tiny(GREEDY), W.c1(GREEDY), W.c2(G=256, rule=GREEDY)]
+    out += [s for s in sweep_models() if s.rule == GREEDY and s.P <= 4]
+    return out
+
+
+@pytest.mark.parametrize("spec", warp_eligible_models(), ids=lambda s: f"{s.name}_P{s.P}_k{s.key_bits}")
+def test_warp_and_block_units_match_oracle(mc, oracle, spec):
+    """Models whose widest configuration level fits a warp run one warp per
+    configuration by default and one block per configuration when the
+    block's threads are given; both give the oracle's counts, widths,
+    checks (witness and trace included) and minima."""
+    exp_count, exp_widths = oracle.count(spec), CF.widths(spec)
+    t_min = oracle.min_time(spec)["t_min"]
+    for threads in (0, 64):
+        model = make(mc, spec, engine="config", unit_threads=threads)
+        mc.mc_reserve(model)
+        lay = mc.mc_model_layout(model)
+        assert lay["engine"] == mc.ENGINE["config"]
+        assert lay["unit_threads"] == (32 if threads == 0 else 64), spec.name
+        assert mc.mc_count_states(model) == exp_count
+        assert mc.mc_last_widths(model) == exp_widths
+        for T in (t_min - 1, t_min, 2 * t_min):
+            for prune, ee in ((True, True), (False, False), (True, False)):
+                assert gpu_check(mc, model, T, prune, ee) == oracle.check(spec, T, prune=prune, early_exit=ee)
+        for search in ("single", "lower"):
+            assert gpu_min(mc, model, search, True) == oracle.min_time(spec, search=search, prune=True)
+
+
 # ---------------------------------------------------------------- edge cases and errors
 
 @pytest.mark.parametrize("engine", ENGINES)
