@@ -38,7 +38,7 @@ DEFAULT_SPACE = {
     "threads_per_block": [128, 256],
     "blocks_per_sm": [0, 2, 3],
     "load_factor_pct": [25, 50],
-    "probe_scheme": [1, 2],  # mc_probe_scheme: split, one call
+    "probe_scheme": [1, 2, 3],  # mc_probe_scheme: split, one call, CAS first
 }
 KNOBS = tuple(DEFAULT_SPACE) + ("engine", "stage_chunk", "unit_threads", "lanes_per_state")
 # per engine (mc_engine: 1 level-synchronous, 2 one block per configuration)
