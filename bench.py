@@ -599,6 +599,7 @@ def run_ours(args):
         if first:
             out["batched"] = measure_c4(args, device, local, steps=min(args.steps, 10), warmup=args.warmup)
             out["served"] = measure_c5(args, local, rates=[100.0, 1000.0], queries=args.served_queries)
+            out["swarm"] = measure_swarm(args, local)
     if rank == 0:
         print(json.dumps(out), flush=True)
     return 0
@@ -612,25 +613,58 @@ def percentile(xs, q):
     return xs[k]
 
 
+def swarm_searches(spec, walks: int, searches: int):
+    """The exact T_min, then `searches` swarm searches with consecutive
+    seeds (after one warm-up search)."""
+    from paper_2305_09130_gb300 import mc
+
+    m = mc.mc_model_create(spec, mc.mc_options_default(timing=1))
+    t_min = mc.mc_min_time(m, trace=False)["t_min"]
+    mc.mc_swarm(m, 1, walks, max_rounds=2, trace=False)  # warm-up
+    runs = [mc.mc_swarm(m, 2305091300 + k, walks, max_rounds=64, trace=True) for k in range(searches)]
+    mc.mc_model_destroy(m)
+    return t_min, runs
+
+
+def swarm_summary(t_min, runs) -> dict:
+    return {
+        "runs_per_s": sum(r["walks"] for r in runs) / (sum(r["total_ms"] for r in runs) / 1000.0),
+        "t_min_exact": t_min,
+        "searches": [{"first_trail_ms": r["first_trail_ms"], "total_ms": r["total_ms"], "rounds": r["rounds"],
+                      "first_time": r["first_time"], "best_time": r["best_time"],
+                      "first_trail_optimality": t_min / r["first_time"],
+                      "final_optimality": t_min / r["best_time"], "wg": r["wg"], "ts": r["ts"]} for r in runs],
+    }
+
+
+def measure_swarm(args, local: int) -> dict:
+    """The default line's swarm object (Section 5, Table 1's last columns):
+    five searches each on C2 at G=80 and on C3 literal, with the first
+    trail's time and optimality against the exact T_min."""
+    out = {"walks_per_round": args.swarm_walks,
+           "stop": "after the first round without a run at or below best - 1 (at most 64 rounds)"}
+    sampler = ClockSampler(local)
+    sampler.start()
+    for name in ("c2_star", "c3"):
+        wl = WORKLOADS[name]
+        t_min, runs = swarm_searches(wl.make(), args.swarm_walks, 5)
+        out[name] = {"workload": wl.desc, **swarm_summary(t_min, runs)}
+    out["clocks"] = sampler.stop()
+    return out
+
+
 def run_swarm(args):
     """Swarm search (Section 5) on a workload: rounds of random runs on the
     GPU, the first trail's time and optimality against the exact T_min, as in
     the paper's Table 1 (first trail, optimality of the first trail)."""
     import torch
 
-    from paper_2305_09130_gb300 import mc
-
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     wl = WORKLOADS[args.workload or DEFAULT_WORKLOAD]
     spec = wl.make()
-    m = mc.mc_model_create(spec, mc.mc_options_default(timing=1))
-    t_min = mc.mc_min_time(m, trace=False)["t_min"]
+    t_min, runs = swarm_searches(spec, args.swarm_walks, args.steps)
     walks = args.swarm_walks
-    mc.mc_swarm(m, 1, walks, max_rounds=2, trace=False)  # warm-up
-    runs = []
-    for k in range(args.steps):
-        runs.append(mc.mc_swarm(m, 2305091300 + k, walks, max_rounds=64, trace=True))
     best = runs[-1]
     line = {
         "metric": "swarm search: random runs per second, first-trail time and optimality",
