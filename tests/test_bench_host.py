@@ -62,3 +62,15 @@ def test_default_line_is_the_large_model_with_its_closed_form_optimum():
     assert CF.count(s2) == 10_385_335
     t2, cfg2 = CF.tmin(s2)
     assert c2.expect == (t2, s2.wg_values[cfg2[0][0]], s2.ts_values[cfg2[0][1]])
+
+
+def test_swarm_summary_reports_optimality_against_the_exact_minimum():
+    runs = [{"walks": 2_000_000, "total_ms": 2.0, "first_trail_ms": 0.5, "rounds": 2, "first_time": 120,
+             "best_time": 100, "wg": 8, "ts": 4},
+            {"walks": 2_000_000, "total_ms": 2.0, "first_trail_ms": 0.4, "rounds": 3, "first_time": 100,
+             "best_time": 100, "wg": 8, "ts": 4}]
+    s = bench.swarm_summary(100, runs)
+    assert s["runs_per_s"] == 4_000_000 / 0.004
+    assert s["t_min_exact"] == 100
+    assert [x["first_trail_optimality"] for x in s["searches"]] == [100 / 120, 1.0]
+    assert [x["final_optimality"] for x in s["searches"]] == [1.0, 1.0]
