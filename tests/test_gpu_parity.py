@@ -239,7 +239,24 @@ def test_c3_star_full(mc):
 def warp_eligible_models():
     out = [W.tiny(GREEDY), W.c1(GREEDY), W.c2(G=256, rule=GREEDY)]
     out += [s for s in sweep_models() if s.rule == GREEDY and s.P <= 4]
+    # at the boundary: FREE models with P=2 whose widest configuration level
+    # holds exactly 16 states (16 x 2 lanes fill the warp), one unit, three
+    # units under GREEDY, four FREE units with 4 states
+    out += [W.random_small(9505, 2, 2, 3, 16), W.random_small(9506, 2, 2, 3, 16, key_bits=128),
+            W.random_small(9500, 1, 2, 3, 30), W.random_small(9500, 3, 2, 3, 5, rule=GREEDY),
+            W.random_small(9528, 4, 2, 3, 2)]
     return out
+
+
+def test_a_level_one_state_wider_than_a_warp_takes_a_block(mc, oracle):
+    """17 states of 2 lanes: block units; the same answers as the oracle."""
+    spec = W.random_small(9502, 2, 2, 3, 16)
+    model = make(mc, spec, engine="config")
+    mc.mc_reserve(model)
+    lay = mc.mc_model_layout(model)
+    assert lay["unit_width"] == 17 and lay["unit_threads"] == 64
+    assert mc.mc_count_states(model) == oracle.count(spec)
+    assert gpu_min(mc, model, "single", True) == oracle.min_time(spec, search="single", prune=True)
 
 
 @pytest.mark.parametrize("spec", warp_eligible_models(), ids=lambda s: f"{s.name}_P{s.P}_k{s.key_bits}")
