@@ -102,27 +102,62 @@ def test_batch_matches_oracle(mc, oracle, engine):
 def test_batch_equals_single_model_queries(mc, engine):
     specs = W.c4_instances(96)
     t_mins = [CF.tmin(s)[0] for s in specs]
-    queries = [("min_time", None) if s.meta["query"] else ("check", round(t * s.meta["t_frac_milli"] / 1000))
-               for s, t in zip(specs, t_mins)]
+    queries = c4_queries(specs, t_mins)
     b = mc.mc_batch_create(specs, mc.mc_options_default(engine=engine))
     res = mc.mc_batch_run(b, queries)
     engine_launches(mc, b, engine, 1)
     for spec, q, r, t_min in zip(specs, queries, res, t_mins):
-        assert r["status"] == 0
-        m = mc.mc_model_create(spec.with_key_bits(128))
-        if q[0] == "min_time":
-            s = mc.mc_min_time(m, trace=False)
-            assert (r["time"], r["t_ini"], r["i"], r["j"], r["states"], r["checks"], r["level"], r["key"]) == \
-                   (s["t_min"], s["t_ini"], s["i"], s["j"], s["states"], s["checks"], s["level"], s["witness_key"])
-            assert r["time"] == t_min
-        else:
-            s = mc.mc_check(m, q[1], trace=False)
-            assert r["holds"] == s["holds"] == (q[1] < t_min)
-            assert (r["states"], r["levels"]) == (s["states"], s["levels"])
-            if not s["holds"]:
-                assert (r["time"], r["i"], r["j"], r["level"], r["key"]) == \
-                       (s["cex_time"], s["cex_i"], s["cex_j"], s["cex_level"], s["cex_key"])
+        check_against_single_model(mc, spec, q, r, t_min)
+
+
+def c4_queries(specs, t_mins):
+    return [("min_time", None) if s.meta["query"] else ("check", round(t * s.meta["t_frac_milli"] / 1000))
+            for s, t in zip(specs, t_mins)]
+
+
+def check_against_single_model(mc, spec, q, r, t_min):
+    """One batch answer equals the single-model entry point's, and a minimum
+    or a check's outcome agrees with the closed-form minimal time."""
+    assert r["status"] == 0
+    m = mc.mc_model_create(spec.with_key_bits(128))
+    if q[0] == "min_time":
+        s = mc.mc_min_time(m, trace=False)
+        assert (r["time"], r["t_ini"], r["i"], r["j"], r["states"], r["checks"], r["level"], r["key"]) == \
+               (s["t_min"], s["t_ini"], s["i"], s["j"], s["states"], s["checks"], s["level"], s["witness_key"])
+        assert r["time"] == t_min
+    else:
+        s = mc.mc_check(m, q[1], trace=False)
+        assert r["holds"] == s["holds"] == (q[1] < t_min)
+        assert (r["states"], r["levels"]) == (s["states"], s["levels"])
+        if not s["holds"]:
+            assert (r["time"], r["i"], r["j"], r["level"], r["key"]) == \
+                   (s["cex_time"], s["cex_i"], s["cex_j"], s["cex_level"], s["cex_key"])
+    mc.mc_model_destroy(m)
+
+
+@pytest.mark.parametrize("kind", ["warp", "block"])
+def test_configuration_batch_of_one_unit_kind(mc, kind):
+    """A configuration-engine batch whose models all run a warp per
+    configuration (no block units in its launches), or all a block per
+    configuration (no warp blocks), answers as the single-model entry points,
+    over two replays of its graph with the queries swapped between them."""
+    specs = []
+    for s in W.c4_instances(96):
+        m = mc.mc_model_create(s.with_key_bits(128), mc.mc_options_default(engine="config"))
+        mc.mc_reserve(m)
+        if (mc.mc_model_layout(m)["unit_threads"] == 32) == (kind == "warp"):
+            specs.append(s)
         mc.mc_model_destroy(m)
+    assert len(specs) >= 16
+    t_mins = [CF.tmin(s)[0] for s in specs]
+    queries = c4_queries(specs, t_mins)
+    swapped = [("min_time", None) if k == "check" else ("check", t - 1) for (k, _T), t in zip(queries, t_mins)]
+    b = mc.mc_batch_create(specs, mc.mc_options_default(engine="config"))
+    for qs in (queries, swapped, queries):
+        for spec, q, r, t_min in zip(specs, qs, mc.mc_batch_run(b, qs), t_mins):
+            check_against_single_model(mc, spec, q, r, t_min)
+    assert mc.mc_batch_get_stats(b)["graph_launches"] == 3
+    engine_launches(mc, b, "config", 3)
 
 
 @pytest.mark.parametrize("engine", ENGINES)
