@@ -443,7 +443,9 @@ def measure_single(args, name: str, steps: int, warmup: int, device, stream, loc
                            f"cfg_kernel<u{64 * layout['key_words']}> ({layout['unit_threads']} threads per "
                            f"configuration)"),
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
-                               if peak_kind == "measured" else "fallback 6.8 TB/s"}
+                               if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "launch_timing": "CUDA events on the model's stream, one pair around each query's chained "
+                                 "exploration launches (gaps between them included), over the timed steps"}
     if wl.traffic:
         roofline["traffic_source"] = (f"profiles/{wl.traffic}: dram__bytes_read.sum + dram__bytes_write.sum "
                                       f"per exploration launch from ncu (null when the kernel source changed "

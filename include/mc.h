@@ -166,8 +166,10 @@ typedef struct {
                                    expect that many extra arrivals, so it
                                    times out and the query returns
                                    MC_ERR_TIMEOUT.  Keep 0.                 */
-  uint32_t timing;              /* 1: time every exploration kernel with CUDA
-                                   events on the model's stream (mc_get_stats) */
+  uint32_t timing;              /* 1: time the exploration kernels with CUDA
+                                   events on the model's stream (mc_get_stats):
+                                   one pair around each run of launches a
+                                   query enqueues back to back              */
   uint32_t lanes_per_state;     /* lanes of the warp tile that expands one
                                    state.  Cost-table model: a power of two
                                    from P (rounded up) to 16, one unit per
@@ -268,7 +270,9 @@ typedef struct {
   uint64_t h2d_bytes;        /* host -> device bytes copied                  */
   uint64_t d2h_bytes;        /* device -> host bytes copied                  */
   double explore_ms;         /* summed CUDA-event time of the exploration
-                                kernels (only with mc_options.timing = 1)    */
+                                kernels (only with mc_options.timing = 1):
+                                a query's chained checks are timed as one
+                                window, gaps between their launches included */
   uint64_t device_steps;     /* device-wide barrier steps: BFS levels of the
                                 passes, or lockstep steps of a batch launch  */
   uint64_t probes;           /* successors generated, each one visited-set

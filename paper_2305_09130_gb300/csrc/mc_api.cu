@@ -141,6 +141,7 @@ void pinned_free(void* p, size_t bytes) {
 namespace {
 
 constexpr int kSlots = 4;  // per-pass result slots (device header + pinned copy)
+constexpr int kTimingRing = 64;  // event pairs of timed launches (their times are read lazily)
 // Device control block, in this order:
 //   barrier lines  kSlots x kBarBytes (one device-wide barrier per slot)
 //   headers        kSlots x Ctrl      (one pass result per slot)
@@ -245,8 +246,11 @@ struct mc_model {
   uint64_t* h_trace = nullptr;  // [(max_level + 2) * 2]
   size_t mirror_bytes = 0;
   uint32_t* h_params = nullptr; // staging of N, cost, speed (then seg and order)
-  cudaEvent_t ev[2 * kSlots] = {};
-  bool ev_pending[kSlots] = {};
+  cudaEvent_t ev[2 * kTimingRing] = {};  // [2p] start, [2p + 1] end of timed launch pair p
+  uint64_t ev_pending = 0;               // bit p: pair p recorded, its time not yet in stats
+  uint32_t ev_next = 0;                  // the pair the next timed run takes
+  bool chain_open = false;               // a timed run of exploration launches is open
+  uint32_t chain_pair = 0;               // its pair
   mc_stats stats{};
   std::string last_err;
   uint32_t last_levels = 0;
@@ -273,6 +277,69 @@ int make_events(mc_model* m) {
   if (m->ev[0]) return MC_OK;
   for (cudaEvent_t& e : m->ev) MC_CUDA(m, cudaEventCreate(&e));
   return MC_OK;
+}
+
+// Timing: the exploration launches a query enqueues back to back (the
+// chained checks of a search) are bracketed by one pair of events taken from
+// a ring; the window includes the short gaps between the launches.  An event
+// between two dependent kernels delays the second (about 2 us on a GB300),
+// so a pair per launch would lengthen the query it measures.  A pair's
+// elapsed time is added to the statistics when they are read (mc_get_stats)
+// or when the pair comes round again.  Every query waits for its stream
+// before returning, so a pending pair has completed by then.
+int settle_pair(mc_model* m, uint32_t p) {
+  float ms = 0.f;
+  MC_CUDA(m, cudaEventSynchronize(m->ev[2 * p + 1]));
+  MC_CUDA(m, cudaEventElapsedTime(&ms, m->ev[2 * p], m->ev[2 * p + 1]));
+  m->stats.explore_ms += ms;
+  m->ev_pending &= ~(1ull << p);
+  return MC_OK;
+}
+
+int settle_timing(mc_model* m) {
+  while (m->ev_pending) {
+    const int rc_ = settle_pair(m, (uint32_t)__builtin_ctzll(m->ev_pending));
+    if (rc_) return rc_;
+  }
+  return MC_OK;
+}
+
+// Records the start of a timed launch on the model's stream; *pair is the
+// ring index to pass to time_end after the launch.
+int time_begin(mc_model* m, uint32_t* pair) {
+  int rc_ = make_events(m);
+  if (rc_) return rc_;
+  const uint32_t p = m->ev_next;
+  m->ev_next = (p + 1) % kTimingRing;
+  if ((m->ev_pending >> p) & 1u) {
+    rc_ = settle_pair(m, p);
+    if (rc_) return rc_;
+  }
+  MC_CUDA(m, cudaEventRecord(m->ev[2 * p], m->stream));
+  *pair = p;
+  return MC_OK;
+}
+
+int time_end(mc_model* m, uint32_t p) {
+  MC_CUDA(m, cudaEventRecord(m->ev[2 * p + 1], m->stream));
+  m->ev_pending |= 1ull << p;
+  return MC_OK;
+}
+
+// Before an exploration launch: opens the timed run unless one is open.
+int timed_launch(mc_model* m) {
+  if (!m->opt.timing || m->chain_open) return MC_OK;
+  const int rc_ = time_begin(m, &m->chain_pair);
+  if (rc_) return rc_;
+  m->chain_open = true;
+  return MC_OK;
+}
+
+// Closes the open timed run (fetch_ctrl and sync call it).
+int close_chain(mc_model* m) {
+  if (!m->chain_open) return MC_OK;
+  m->chain_open = false;
+  return time_end(m, m->chain_pair);
 }
 
 // Makes the model's device current for the duration of a call.
@@ -326,6 +393,9 @@ void release(mc_model* m) {
   }
   if (m->h_block) mc::pinned_free(m->h_block, m->h_block_bytes);
   m->h_block = nullptr;
+  m->chain_open = false;
+  if (m->ev_pending && settle_timing(m) != MC_OK) m->ev_pending = 0;  // keep the times of launches already run
+  m->ev_next = 0;
   for (cudaEvent_t& e : m->ev) {
     if (e) cudaEventDestroy(e);
     e = nullptr;
@@ -492,6 +562,7 @@ void fill_params(const mc_model* m, Params& p) {
 }
 
 int reserve(mc_model* m) {
+  m->chain_open = false;  // every query starts here; a run left open by a failed query is dropped
   if (m->reserved) return MC_OK;
   int rc = size_buffers(m);
   if (rc) return rc;
@@ -676,6 +747,10 @@ int clear_ctrl(mc_model* m, int n_headers) {
 
 // One copy: every header, the scalars and the trace buffer into the mirror.
 int fetch_ctrl(mc_model* m) {
+  {
+    const int rc_ = close_chain(m);
+    if (rc_) return rc_;
+  }
   MC_CUDA(m, cudaMemcpyAsync(m->h_ctrl, m->d_ctrl, m->mirror_bytes, cudaMemcpyDeviceToHost, m->stream));
   m->stats.d2h_bytes += m->mirror_bytes;
   return MC_OK;
@@ -721,16 +796,11 @@ int enqueue_cfg_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t del
     L.next = &Q.ctrl->units_next;
   }
   MC_CUDA(m, cudaMemsetAsync(Q.levels, 0, 16ull * (m->max_level + 2), m->stream));
-  if (m->opt.timing) {
-    const int rc_ = make_events(m);
+  {
+    const int rc_ = timed_launch(m);
     if (rc_) return rc_;
-    MC_CUDA(m, cudaEventRecord(m->ev[2 * slot], m->stream));
   }
   MC_CUDA(m, mc::launch_cfg((int)m->key_words, m->cfg_grid, m->cfg_threads, m->cfg_smem, L, m->stream));
-  if (m->opt.timing) {
-    MC_CUDA(m, cudaEventRecord(m->ev[2 * slot + 1], m->stream));
-    m->ev_pending[slot] = true;
-  }
   m->stats.explore_launches += 1;
   return MC_OK;
 }
@@ -760,16 +830,11 @@ int enqueue_cfg_pair(mc_model* m, bool prune, bool early_exit, bool refine) {
     L.n_units = n_units;
     L.next = next;
   }
-  if (m->opt.timing) {
-    const int rc_ = make_events(m);
+  {
+    const int rc_ = timed_launch(m);
     if (rc_) return rc_;
-    MC_CUDA(m, cudaEventRecord(m->ev[2], m->stream));
   }
   MC_CUDA(m, mc::launch_cfg((int)m->key_words, grid, m->cfg_threads, m->cfg_smem, L, m->stream));
-  if (m->opt.timing) {
-    MC_CUDA(m, cudaEventRecord(m->ev[3], m->stream));
-    m->ev_pending[1] = true;
-  }
   m->stats.explore_launches += 1;
   return MC_OK;
 }
@@ -813,29 +878,21 @@ int enqueue_pass(mc_model* m, uint64_t T, const uint64_t* T_src, int64_t delta, 
     A.tag_bits = m->tag_bits;
     A.tag = m->tag;
   }
-  if (m->opt.timing) {
-    const int rc_ = make_events(m);
+  {
+    const int rc_ = timed_launch(m);
     if (rc_) return rc_;
   }
-  if (m->opt.timing) MC_CUDA(m, cudaEventRecord(m->ev[2 * slot], m->stream));
   MC_CUDA(m, mc::launch_explore(m->key_words, m->tile, m->rule, m->scheme, m->grid, m->threads, A, m->stream));
-  if (m->opt.timing) {
-    MC_CUDA(m, cudaEventRecord(m->ev[2 * slot + 1], m->stream));
-    m->ev_pending[slot] = true;
-  }
   m->stats.explore_launches += 1;
   return MC_OK;
 }
 
 int sync(mc_model* m) {
-  MC_CUDA(m, cudaStreamSynchronize(m->stream));
-  for (int s = 0; s < kSlots; ++s) {
-    if (!m->ev_pending[s]) continue;
-    float ms = 0.f;
-    MC_CUDA(m, cudaEventElapsedTime(&ms, m->ev[2 * s], m->ev[2 * s + 1]));
-    m->stats.explore_ms += ms;
-    m->ev_pending[s] = false;
+  {
+    const int rc_ = close_chain(m);
+    if (rc_) return rc_;
   }
+  MC_CUDA(m, cudaStreamSynchronize(m->stream));
   return MC_OK;
 }
 
@@ -1400,12 +1457,20 @@ int mc_last_widths(mc_model* m, uint64_t* out, uint32_t cap, uint32_t* n) {
 
 int mc_get_stats(const mc_model* m, mc_stats* out) {
   if (!m || !out) return MC_ERR_INVAL;
+  // the times of timed launches are added here (a cache the call may fill)
+  mc_model* w = const_cast<mc_model*>(m);
+  if (w->ev_pending) {
+    DeviceGuard g(w->device);
+    const int rc = settle_timing(w);
+    if (rc) return rc;
+  }
   *out = m->stats;
   return MC_OK;
 }
 
 int mc_reset_stats(mc_model* m) {
   if (!m) return MC_ERR_INVAL;
+  m->ev_pending = 0;  // launches before the reset do not count
   m->stats = mc_stats{};
   return MC_OK;
 }
