@@ -461,27 +461,36 @@ def measure_single(args, name: str, steps: int, warmup: int, device, stream, loc
         hbm_cas = mc.mc_measure_random_access(64 << 30, 200_000_000, 1)
         hbm_cas_only = mc.mc_measure_random_access(64 << 30, 200_000_000, 2)
         l2 = mc.mc_measure_random_access(max(table_bytes, 1 << 20), 200_000_000, 0)
+        l2_cas = mc.mc_measure_random_access(max(table_bytes, 1 << 20), 200_000_000, 1)
+        l2_cas_only = mc.mc_measure_random_access(max(table_bytes, 1 << 20), 200_000_000, 2)
         explore_s = st["explore_ms"] / 1000.0
         probes = spec.P * st["states"] / explore_s
         # the rate of a kernel that did nothing but its visited-set accesses,
         # at the measured random-access rates: P bucket reads and about one
         # CAS per unique state (split, one call), P CAS (CAS first), P + 1
         # CAS (CAS first with clearing: the expanded state's own slot)
+        def states_ceiling(read, read_cas, cas_only):
+            if scheme in ("cas_first", "cas_clear"):
+                return cas_only["sectors_per_s"] / (spec.P + (1 if scheme == "cas_clear" else 0))
+            return 1.0 / (spec.P / read["sectors_per_s"] + 1.0 / read_cas["sectors_per_s"])
+        ceiling = states_ceiling(hbm, hbm_cas, hbm_cas_only)
+        ceiling_table = states_ceiling(l2, l2_cas, l2_cas_only)
         if scheme in ("cas_first", "cas_clear"):
             per_state = spec.P + (1 if scheme == "cas_clear" else 0)
-            ceiling = hbm_cas_only["sectors_per_s"] / per_state
             note = (f"{per_state} random CAS per unique state (one per generated successor"
                     f"{', one clearing the expanded state' if scheme == 'cas_clear' else ''}); "
-                    f"ceiling = CAS rate / {per_state} over 64 GiB")
+                    f"ceiling = CAS rate / {per_state}, over 64 GiB and over a buffer of the visited set's size")
         else:
-            ceiling = 1.0 / (spec.P / hbm["sectors_per_s"] + 1.0 / hbm_cas["sectors_per_s"])
             note = ("P random 32-byte bucket reads per unique state (one per generated successor) and about "
-                    "one CAS; ceiling = 1 / (P / read rate + 1 / read+CAS rate) over 64 GiB")
+                    "one CAS; ceiling = 1 / (P / read rate + 1 / read+CAS rate), over 64 GiB and over a "
+                    "buffer of the visited set's size (L2-resident when it fits)")
         roofline["random_access"] = {
             "hbm_64GiB_sector_reads_per_s": hbm["sectors_per_s"],
             "hbm_64GiB_sector_read_cas_per_s": hbm_cas["sectors_per_s"],
             "hbm_64GiB_cas_per_s": hbm_cas_only["sectors_per_s"],
             "table_sized_sector_reads_per_s": l2["sectors_per_s"],
+            "table_sized_sector_read_cas_per_s": l2_cas["sectors_per_s"],
+            "table_sized_cas_per_s": l2_cas_only["sectors_per_s"],
             "table_bytes": table_bytes,
             "probe_scheme": scheme,
             "kernel_probes_per_s": probes,
@@ -491,6 +500,8 @@ def measure_single(args, name: str, steps: int, warmup: int, device, stream, loc
             "states_per_s_ceiling_hbm": ceiling,
             "kernel_states_per_s": st["states"] / explore_s,
             "frac_of_states_ceiling_hbm": (st["states"] / explore_s) / ceiling,
+            "states_per_s_ceiling_table_sized": ceiling_table,
+            "frac_of_states_ceiling_table_sized": (st["states"] / explore_s) / ceiling_table,
             "note": note}
         if traffic:
             roofline["random_access"]["dram_bytes_per_state"] = traffic / states_per_launch
@@ -594,7 +605,7 @@ def run_ours(args):
         # the medium workload beside the headline; then the batched and
         # served forms against one query at a time
         sec = measure_single(args, "c2_star", min(args.steps, 20), args.warmup, device, stream, local,
-                             cpu_baseline=False, random_roofline=False)
+                             cpu_baseline=False, random_roofline=not args.no_random_roofline)
         out["secondary"] = {"c2_star": {k: sec[k] for k in ("value", "unit", "ms_per_step", "dtype", "config",
                                                             "result", "roofline", "e2e", "clocks")}}
         out["gpu_launches"] += sec["gpu_launches"]
