@@ -169,7 +169,8 @@ typedef struct {
   uint32_t timing;              /* 1: time the exploration kernels with CUDA
                                    events on the model's stream (mc_get_stats):
                                    one pair around each run of launches a
-                                   query enqueues back to back              */
+                                   query enqueues back to back (PE-level
+                                   model, mc_pe.h: one pair per launch)     */
   uint32_t lanes_per_state;     /* lanes of the warp tile that expands one
                                    state.  Cost-table model: a power of two
                                    from P (rounded up) to 16, one unit per
@@ -272,7 +273,8 @@ typedef struct {
   double explore_ms;         /* summed CUDA-event time of the exploration
                                 kernels (only with mc_options.timing = 1):
                                 a query's chained checks are timed as one
-                                window, gaps between their launches included */
+                                window, gaps between their launches included
+                                (PE-level model: each launch alone)          */
   uint64_t device_steps;     /* device-wide barrier steps: BFS levels of the
                                 passes, or lockstep steps of a batch launch  */
   uint64_t probes;           /* successors generated, each one visited-set
