@@ -69,7 +69,8 @@ WORKLOADS = {
         "(splitmix64 seed 2305091303), speed 1, 128-bit packed states; 1,072,924,481 reachable states "
         "(closed form), widest level 193,344,684",
         "u128", expect=(1, 512, 2), cpu_T=30, ref_T=16,
-        tune={"probe_scheme": ["split", "one_call", "cas_first", "cas_clear"], "stage_chunk": [128, 192]},
+        tune={"probe_scheme": ["split", "one_call", "cas_first", "cas_clear"], "stage_chunk": [128, 192],
+              "load_factor_pct": [15, 25]},
         traffic="explore_kernel_c3star_traffic.txt"),
     "c2_star": Workload(
         lambda: W.c2_star(),
