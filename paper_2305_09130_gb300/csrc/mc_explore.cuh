@@ -299,7 +299,8 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
     // it succeeds the key was nowhere in its probe sequence (a key placed
     // further along means the slots before it held keys of this level when
     // it was placed, and those stay for the whole level); if it returns the
-    // key, a duplicate; anything else takes the general insert, which
+    // key, a duplicate; a key of an earlier level, one more compare-and-swap
+    // from it (below); anything else takes the general insert, which
     // rereads the bucket.
     constexpr bool kPicked = SCHEME == MC_PROBE_SPLIT || kCas;
     uint32_t pick[D];
@@ -317,6 +318,19 @@ __device__ __forceinline__ void expand_level(const ExploreArgs& A, Stage<K>& st,
 #pragma unroll
     for (uint32_t d = 0; d < D; ++d)
       if (kPicked && pick[d] < (uint32_t)S) old[d] = slot_cas(table + bkt[d] * S + pick[d], cur[d], succ[d]);
+    // CAS-first, when the first slot returned a key of an earlier level: the
+    // slot is free, and the key is in no slot of this level (a slot taken
+    // this level keeps its key until the level ends, so an earlier insert of
+    // the key would have stopped at this one), so compare-and-swap once more
+    // from the value returned instead of rereading the bucket
+    if (kCas) {
+#pragma unroll
+      for (uint32_t d = 0; d < D; ++d)
+        if (pick[d] == 0 && old[d] != cur[d] && old[d] != succ[d] && level_of(old[d]) <= k_cur) {
+          cur[d] = old[d];
+          old[d] = slot_cas(table + bkt[d] * S, cur[d], succ[d]);
+        }
+    }
 #pragma unroll
     for (uint32_t d = 0; d < D; ++d) {
       const uint64_t s = base + d * kTilesPerWarp + my;
