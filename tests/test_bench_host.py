@@ -43,6 +43,23 @@ dram_bytes_per_launch_lf10_split: 100
     assert bench.ncu_traffic_per_launch(str(tmp_path / "missing.txt"), 10, "split", 1.0) is None
 
 
+def test_committed_traffic_summaries_match_the_kernel_sources():
+    """The ncu summaries behind roofline.traffic were taken on the exploration
+    kernel as it stands (a kernel change needs new captures), and hold a line
+    for every probe scheme the bench tunes over, at every load factor it may
+    pick."""
+    import os
+    for name, lfs in (("c3_star", (15, 25)), ("c2_star", (10, 15))):
+        wl = bench.WORKLOADS[name]
+        path = os.path.join(bench.PROFILES, wl.traffic)
+        fields = bench.read_traffic_file(path)
+        assert fields["kernel_source_sha256_16"] == bench.kernel_source_hash(), wl.traffic
+        schemes = wl.tune["probe_scheme"] if name == "c3_star" else ["split", "cas_clear"]
+        for lf in lfs:
+            for scheme in schemes:
+                assert bench.ncu_traffic_per_launch(path, lf, scheme, 1e6) is not None, (name, lf, scheme)
+
+
 def test_default_line_is_the_large_model_with_its_closed_form_optimum():
     """The headline is C3 at G=36 (FREE, P=8, 128-bit keys); its expected
     optimum is the closed form's (T_min = min over configurations of
