@@ -6,7 +6,9 @@ still holds keys of earlier levels (a slot holding one is free) and is never
 cleared between levels.  This file restates the protocol's atomic steps --
 the CAS-first insert (a compare-and-swap from empty on the key's first slot;
 from a key of an earlier level, a second compare-and-swap from that key; the
-general insert otherwise), the general insert (read a bucket slot by slot,
+general insert otherwise), the split insert (a compare-and-swap on the first
+free slot of the fetched bucket, the general insert when it fails or the
+bucket holds no free slot), the general insert (read a bucket slot by slot,
 then compare-and-swap the first free slot, up to three tries a slot), and
 the clearing scheme's compare-and-swap of an expanded state's own first slot
 back to empty -- as explicit state machines, and explores every order of
@@ -36,7 +38,7 @@ class Model:
 
     # thread state: (kind, key, home, pc, bucket, probe, s, cur, tries, v, result)
     def start(self, kind, key, home):
-        pc = {"cas_first": "first", "general": "gread", "clear": "clear"}[kind]
+        pc = {"cas_first": "first", "split": "sread", "general": "gread", "clear": "clear"}[kind]
         return (kind, key, home, pc, home, 0, 0, 0, 0, (), None)
 
     def _general_from(self, th, bucket, probe):
@@ -78,6 +80,23 @@ class Model:
             return table, self._general_from(th, home, 0)
         if pc == "retry":
             table, old = cas(table, home * S, cur, key)
+            if old == cur:
+                return table, (kind, key, home, "done", bucket, probe, s, cur, tries, v, 1)
+            if old == key:
+                return table, (kind, key, home, "done", bucket, probe, s, cur, tries, v, 0)
+            return table, self._general_from(th, home, 0)
+        if pc == "sread":  # split: the first bucket is fetched, a free slot picked from it
+            v = v + (table[home * S + s],)
+            if len(v) < S:
+                return table, (kind, key, home, "sread", bucket, probe, s + 1, cur, tries, v, None)
+            if key in v:
+                return table, (kind, key, home, "done", bucket, probe, s, cur, tries, v, 0)
+            free = [i for i, x in enumerate(v) if x == 0 or lvl(x) <= L]
+            if not free:  # the bucket holds this level's keys: the general insert, rereading it
+                return table, self._general_from(th, home, 0)
+            return table, (kind, key, home, "spick", bucket, probe, free[0], v[free[0]], tries, v, None)
+        if pc == "spick":
+            table, old = cas(table, home * S + s, cur, key)
             if old == cur:
                 return table, (kind, key, home, "done", bucket, probe, s, cur, tries, v, 1)
             if old == key:
@@ -153,6 +172,8 @@ SCENARIOS = [
 ]
 # the same checks with four slots a bucket (64-bit keys) and with three buckets and six threads
 BIG = [
+    ("split_four_slots", 2, 4, (X, Z, 0, W, Y, 0, X, 0),
+     [("split", K1, 0), ("split", K1, 0), ("split", K2, 0), ("cas_first", K2, 0), ("general", K1, 0)], set()),
     ("four_slots", 2, 4, (X, 0, Z, W, Y, 0, 0, X),
      [("cas_first", K1, 0), ("cas_first", K1, 0), ("general", K2, 0), ("clear", X, 0)], set()),
     ("three_buckets", 3, 2, (X, Z, W, 0, Y, X),
