@@ -45,9 +45,9 @@ def gpu_check(mc, model, T, prune=True, early_exit=True, trace=True):
     return out
 
 
-def gpu_min(mc, model, search, prune, seed=2305091300, walks=1, refine=True):
+def gpu_min(mc, model, search, prune, seed=2305091300, walks=1, refine=True, **opts):
     mc.mc_set_options(model, mc.mc_options_default(prune=prune, search=search, sim_seed=seed,
-                                                   sim_walks=walks, refine=refine))
+                                                   sim_walks=walks, refine=refine, **opts))
     r = mc.mc_min_time(model)
     lay = mc.mc_model_layout(model)
     i, j, n = RP.decode(lay, r["witness_key"])
@@ -217,16 +217,20 @@ def test_c2_star_full(mc, load_factor_pct):
         assert got["t_min"] == t_min and (got["i"], got["j"]) in argmins
 
 
-def test_c3_star_full(mc):
-    """1,072,924,481 states with 128-bit keys, in the bench's launch shape."""
+@pytest.mark.parametrize("opts", [{}, {"load_factor_pct": 15, "stage_chunk": 192, "probe_scheme": 3}],
+                         ids=["defaults", "bench_tuned"])
+def test_c3_star_full(mc, opts):
+    """1,072,924,481 states with 128-bit keys, with the library's defaults and
+    in the configuration the bench's tuner picks (CAS-first insert, chunk 192,
+    load factor 15%), then the bench's own query: lowering without pruning."""
     spec = W.c3_star()
-    model = make(mc, spec)
+    model = make(mc, spec, **opts)
     lay = mc.mc_model_layout(model)
     assert lay["key_words"] == 2 and lay["max_width"] == 193_344_684
     assert mc.mc_count_states(model) == 1_072_924_481 == CF.count(spec)
     assert mc.mc_last_widths(model) == CF.widths(spec)
     t_min, argmins = CF.tmin(spec)
-    got = gpu_min(mc, model, "single", True)
+    got = gpu_min(mc, model, "single", True, **opts)
     assert got["t_min"] == t_min
     # the witness comes from the first BFS level holding a T_min terminal:
     # the optimal configurations with the fewest work-groups
@@ -234,6 +238,11 @@ def test_c3_star_full(mc):
     first = min(n_of(ij) for ij in argmins)
     assert (got["i"], got["j"]) == min(ij for ij in argmins if n_of(ij) == first)
     assert got["level"] == first + 2
+    # the check at T_ini stops at its first violating level (551 states), the
+    # check at T_min - 1 = 0 holds and explores every state
+    low = gpu_min(mc, model, "lower", False, **opts)
+    assert (low["t_min"], low["i"], low["j"], low["level"]) == (t_min, got["i"], got["j"], got["level"])
+    assert low["checks"] == 2 and low["states"] == 1_072_925_032
 
 
 def warp_eligible_models():
