@@ -93,9 +93,10 @@ typedef enum {
   MC_PROBE_CAS_FIRST = 3, /* compare-and-swap from empty on the first slot
                             of the first bucket, no fetch: an empty slot is
                             a win and the key itself a duplicate in one
-                            round trip; anything else (another key, or a
-                            key of an earlier level) falls back to the
-                            general insert                                 */
+                            round trip; a key of an earlier level (a free
+                            slot) gets a second compare-and-swap from that
+                            key; another key of the level falls back to
+                            the general insert                             */
   MC_PROBE_CAS_CLEAR = 4 /* CAS_FIRST, and every expanded state empties its
                             own first slot (compare-and-swap from its key),
                             so the table holds about two levels' keys and
