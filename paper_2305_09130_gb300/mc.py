@@ -468,6 +468,10 @@ def mc_last_widths(model: Model, cap: int = 1 << 16) -> list:
 
 
 def mc_get_stats(model: Model) -> dict:
+    """Counters since the last mc_reset_stats (mc_stats in mc.h).  With
+    ``timing=1`` ``explore_ms`` is the CUDA-event time of the exploration
+    kernels, one window around each query's chained launches; the windows'
+    events are read here, not while a query runs."""
     st = McStats()
     model._check(load().mc_get_stats(model.handle, C.byref(st)), "mc_get_stats")
     return {k: getattr(st, k) for k, _t in McStats._fields_}
